@@ -1,0 +1,446 @@
+"""Seeded synthetic inputs for the exchange-correlation quadrature workloads.
+
+This module is the one place both sides draw their inputs from: the CPU oracle
+(``oracle/``) and the GPU library (``paper_2605_10363_gb300``).  It produces only
+what a caller of the method would hand to it -- atoms, a Cartesian Gaussian
+basis specification, a density matrix D and the grid/threshold settings -- and
+contains none of the method's arithmetic (no basis evaluation, no grid, no
+screening, no functional).  The one piece of integral arithmetic here, the
+analytic overlap matrix, exists only to orthonormalise the random occupied
+orbitals that D is built from (D = 2 C C^T with C^T S C = I, the density-matrix
+definition of the paper's Appendix A, "The density matrix", with the factor 2 of
+a closed-shell occupation); the oracle carries its own, separately written
+overlap for its electron-count check.
+
+Units: bohr and Hartree.  All randomness is drawn from ``numpy.random.Generator``
+(PCG64) seeded with the integers stated per workload.
+
+Workloads (sizes follow the paper's synthetic stand-ins; the paper's molecules,
+basis files and dataset are not available):
+
+  1  two water-like units, O-H 0.96 A, 104.5 deg, O-O 3 A, random orientation
+     (seed 1); s/p basis, 50 functions (seed 2); D from 10 orbitals (seed 3);
+     30 radial x 128 angular points, unpruned; LDA exchange; t_b = t_d = 1e-12.
+  2  33 waters at liquid density (0.0334 / A^3), O-O >= 2.6 A (seed 11);
+     s/p/d basis with def2-SVP-like shell counts (825 functions); D localised
+     per molecule (seed 12); 75 radial shells pruned by thirds to 50/128/288
+     angular points; PBE-form GGA; t_b = t_d = 1e-10.
+  3  1000 atoms (240 C, 80 N, 80 O, 600 H) in a sphere of 0.1 atoms/A^3,
+     min distance 1.0 A (seed 21); 9000 functions; D localised per atom
+     neighbourhood (seed 22); grid as workload 2.
+  4  256 frames of 20..130 waters (sizes seed 31), each jittered 0.05 A rms
+     (seed 32), own D (seed 33 + frame); grid as workload 2.
+  5  167 waters (501 atoms, seed 41), D seed 43; grid as workload 2.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ANGSTROM = 1.0 / 0.529177210903  # bohr per angstrom (CODATA 2018)
+
+# Cartesian component order inside a shell: l=0: s; l=1: x y z;
+# l=2: xx xy xz yy yz zz (the usual lexicographic order).
+CART = {
+    0: [(0, 0, 0)],
+    1: [(1, 0, 0), (0, 1, 0), (0, 0, 1)],
+    2: [(2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)],
+}
+
+ELEMENT_ELECTRONS = {1: 1, 6: 6, 7: 7, 8: 8}
+
+
+def ladder(k: int, amin: float = 0.1, amax: float = 50.0) -> float:
+    """Even-tempered exponent ladder a_k = amin (amax/amin)^(k/11), k = 0..11."""
+    return amin * (amax / amin) ** (k / 11.0)
+
+
+# Shell recipes: (l, ladder indices) per element.  Workload 1: O 4s3p, H 3s1p
+# (2*13 + 4*6 = 50 functions).  Workloads 2-5: heavy atoms 3s2p1d (15 Cartesian
+# functions), H 2s1p (5 functions).
+RECIPE_SP = {
+    8: [(0, (9, 10, 11)), (0, (6, 7, 8)), (0, (3, 4, 5)), (0, (1, 2)),
+        (1, (7, 8, 9)), (1, (4, 5, 6)), (1, (1, 2, 3))],
+    1: [(0, (6, 7, 8)), (0, (3, 4, 5)), (0, (0, 1, 2)), (1, (2, 3))],
+}
+RECIPE_SVP = {
+    6: [(0, (9, 10, 11)), (0, (5, 6, 7)), (0, (1, 2)), (1, (5, 6, 7)), (1, (1, 2, 3)), (2, (3, 4))],
+    7: [(0, (9, 10, 11)), (0, (5, 6, 7)), (0, (1, 2)), (1, (5, 6, 7)), (1, (1, 2, 3)), (2, (3, 4))],
+    8: [(0, (9, 10, 11)), (0, (5, 6, 7)), (0, (1, 2)), (1, (5, 6, 7)), (1, (1, 2, 3)), (2, (3, 4))],
+    1: [(0, (5, 6, 7)), (0, (1, 2)), (1, (3, 4))],
+}
+
+
+@dataclass
+class Basis:
+    """Contracted Cartesian Gaussian shells.
+
+    ``exps``/``coefs`` are the raw primitive exponents and contraction
+    coefficients, concatenated shell after shell; ``prim_ptr[s]:prim_ptr[s+1]``
+    indexes shell s.  Coefficients multiply *unnormalised* primitives
+    x^i y^j z^k exp(-a r^2); normalisation is the method's business.
+    """
+    atom: np.ndarray      # int32 [nshell]
+    l: np.ndarray         # int32 [nshell]
+    nprim: np.ndarray     # int32 [nshell]
+    exps: np.ndarray      # float64 [nprim_total]
+    coefs: np.ndarray     # float64 [nprim_total]
+
+    @property
+    def nshell(self) -> int:
+        return int(self.atom.size)
+
+    @property
+    def prim_ptr(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.nprim)]).astype(np.int64)
+
+    @property
+    def nbf(self) -> int:
+        return int(sum(len(CART[int(l)]) for l in self.l))
+
+
+@dataclass
+class GridSpec:
+    """Atom-centred grid settings: ``nrad`` radial shells; the radial shells are
+    split into ``len(ntheta)`` equal index ranges (inner to outer) and range r
+    uses an angular rule of ntheta[r] polar x 2*ntheta[r] azimuthal points."""
+    nrad: int
+    ntheta: tuple
+    block: int = 128
+
+
+@dataclass
+class System:
+    name: str
+    Z: np.ndarray          # int32 [natm]
+    xyz: np.ndarray        # float64 [natm, 3], bohr
+    basis: Basis
+    D: np.ndarray          # float64 [nbf, nbf], symmetric
+    grid: GridSpec
+    t_b: float
+    t_d: float
+    xc: str                # "lda_x" | "pbe"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nbf(self) -> int:
+        return self.basis.nbf
+
+
+# ----------------------------------------------------------------------------
+# geometry
+# ----------------------------------------------------------------------------
+
+def random_rotation(rng: np.random.Generator) -> np.ndarray:
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([
+        [a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+        [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+        [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d],
+    ])
+
+
+def water_frame() -> np.ndarray:
+    """O at the origin, H-O-H angle 104.5 deg, O-H 0.96 A (bohr)."""
+    r = 0.96 * ANGSTROM
+    half = math.radians(104.5) / 2
+    return np.array([[0.0, 0.0, 0.0],
+                     [r * math.sin(half), 0.0, r * math.cos(half)],
+                     [-r * math.sin(half), 0.0, r * math.cos(half)]])
+
+
+def _spatial_order(points: np.ndarray) -> np.ndarray:
+    """Order points along a coarse 3-D Z-curve (input atom order only)."""
+    lo = points.min(axis=0)
+    q = np.floor((points - lo) / (2.0 * ANGSTROM)).astype(np.int64)
+    key = np.zeros(len(points), dtype=np.int64)
+    for bit in range(10):
+        for d in range(3):
+            key |= ((q[:, d] >> bit) & 1) << (3 * bit + (2 - d))
+    return np.argsort(key, kind="stable")
+
+
+def water_cluster(nw: int, seed: int, density_per_A3: float = 0.0334,
+                  min_oo_A: float = 2.6) -> tuple[np.ndarray, np.ndarray]:
+    """nw water molecules, oxygens rejection-sampled in a sphere at the given
+    number density with O-O >= min_oo, random orientations.  Molecules are
+    listed along a coarse spatial curve (atom order O H H per molecule)."""
+    rng = np.random.default_rng(seed)
+    radius = (3.0 * nw / (4.0 * math.pi * density_per_A3)) ** (1.0 / 3.0) * ANGSTROM
+    dmin = min_oo_A * ANGSTROM
+    centers: list[np.ndarray] = []
+    while len(centers) < nw:
+        p = rng.uniform(-radius, radius, size=3)
+        if p @ p > radius * radius:
+            continue
+        if centers and np.min(np.linalg.norm(np.asarray(centers) - p, axis=1)) < dmin:
+            continue
+        centers.append(p)
+    centers_a = np.asarray(centers)
+    order = _spatial_order(centers_a)
+    frame = water_frame()
+    xyz = []
+    for i in order:
+        R = random_rotation(rng)
+        xyz.append(frame @ R.T + centers_a[i])
+    Z = np.tile(np.array([8, 1, 1], dtype=np.int32), nw)
+    return Z, np.concatenate(xyz, axis=0)
+
+
+def two_waters(seed: int) -> tuple[np.ndarray, np.ndarray]:
+    rng = np.random.default_rng(seed)
+    frame = water_frame()
+    a = frame @ random_rotation(rng).T
+    b = frame @ random_rotation(rng).T + np.array([3.0 * ANGSTROM, 0.0, 0.0])
+    R = random_rotation(rng)
+    xyz = np.concatenate([a, b]) @ R.T
+    return np.array([8, 1, 1, 8, 1, 1], dtype=np.int32), xyz
+
+
+def organic_cluster(seed: int, counts=((6, 240), (7, 80), (8, 80), (1, 600)),
+                    density_per_A3: float = 0.1, min_dist_A: float = 1.0):
+    rng = np.random.default_rng(seed)
+    natm = sum(c for _, c in counts)
+    radius = (3.0 * natm / (4.0 * math.pi * density_per_A3)) ** (1.0 / 3.0) * ANGSTROM
+    dmin = min_dist_A * ANGSTROM
+    pts: list[np.ndarray] = []
+    while len(pts) < natm:
+        p = rng.uniform(-radius, radius, size=3)
+        if p @ p > radius * radius:
+            continue
+        if pts and np.min(np.linalg.norm(np.asarray(pts) - p, axis=1)) < dmin:
+            continue
+        pts.append(p)
+    pts_a = np.asarray(pts)
+    Z = np.concatenate([np.full(c, z, dtype=np.int32) for z, c in counts])
+    Z = Z[rng.permutation(natm)]
+    order = _spatial_order(pts_a)
+    return Z[order], pts_a[order]
+
+
+# ----------------------------------------------------------------------------
+# basis
+# ----------------------------------------------------------------------------
+
+def make_basis(Z: np.ndarray, recipe: dict, seed: int, amin: float = 0.1) -> Basis:
+    """Shells per the element recipe; contraction coefficients uniform in
+    [0.3, 1], drawn once per element (seeded) so equal elements share a basis."""
+    coef_table = {}
+    for z in sorted(recipe):
+        rng = np.random.default_rng([seed, int(z)])
+        coef_table[z] = [rng.uniform(0.3, 1.0, size=len(ks)) for (_, ks) in recipe[z]]
+    atom, ls, nprim, exps, coefs = [], [], [], [], []
+    for a, z in enumerate(Z):
+        for (l, ks), cs in zip(recipe[int(z)], coef_table[int(z)]):
+            atom.append(a)
+            ls.append(l)
+            nprim.append(len(ks))
+            exps.extend(ladder(k, amin) for k in ks)
+            coefs.extend(cs.tolist())
+    return Basis(np.asarray(atom, np.int32), np.asarray(ls, np.int32),
+                 np.asarray(nprim, np.int32), np.asarray(exps, np.float64),
+                 np.asarray(coefs, np.float64))
+
+
+def basis_function_atoms(Z: np.ndarray, basis: Basis) -> np.ndarray:
+    out = []
+    for a, l in zip(basis.atom, basis.l):
+        out.extend([int(a)] * len(CART[int(l)]))
+    return np.asarray(out, np.int64)
+
+
+# ----------------------------------------------------------------------------
+# density matrix (input preparation only)
+# ----------------------------------------------------------------------------
+
+def _dfact(n: int) -> float:
+    r = 1.0
+    while n > 1:
+        r *= n
+        n -= 2
+    return r
+
+
+def _prim_norm(a: float, lx: int, ly: int, lz: int) -> float:
+    l = lx + ly + lz
+    return ((2 * a / math.pi) ** 0.75 * (4 * a) ** (l / 2.0)
+            / math.sqrt(_dfact(2 * lx - 1) * _dfact(2 * ly - 1) * _dfact(2 * lz - 1)))
+
+
+def _overlap_1d(la: int, lb: int, PA: np.ndarray, PB: np.ndarray, p: np.ndarray) -> np.ndarray:
+    """int (x-A)^la (x-B)^lb exp(-p (x-P)^2) dx by binomial expansion about P."""
+    out = np.zeros_like(p)
+    for i in range(la + 1):
+        for j in range(lb + 1):
+            k = i + j
+            if k % 2:
+                continue
+            m = _dfact(k - 1) / (2.0 * p) ** (k // 2) * np.sqrt(np.pi / p)
+            out += math.comb(la, i) * math.comb(lb, j) * PA ** (la - i) * PB ** (lb - j) * m
+    return out
+
+
+def overlap_matrix(xyz: np.ndarray, basis: Basis) -> np.ndarray:
+    """Analytic overlap S of the normalised contracted Cartesian functions."""
+    ptr = basis.prim_ptr
+    # flatten to primitive-level records per basis function
+    fn_center, fn_pow, fn_pr = [], [], []
+    for s in range(basis.nshell):
+        a = basis.exps[ptr[s]:ptr[s + 1]]
+        c = basis.coefs[ptr[s]:ptr[s + 1]]
+        l = int(basis.l[s])
+        for (lx, ly, lz) in CART[l]:
+            d = c * np.array([_prim_norm(ai, lx, ly, lz) for ai in a])
+            fn_center.append(xyz[basis.atom[s]])
+            fn_pow.append((lx, ly, lz))
+            fn_pr.append((a, d))
+    nbf = len(fn_pow)
+    # primitive table; the primitives of one function are contiguous
+    pf, pa, pd = [], [], []
+    for f, (a, d) in enumerate(fn_pr):
+        for ai, di in zip(a, d):
+            pf.append(f)
+            pa.append(ai)
+            pd.append(di)
+    pf = np.asarray(pf)
+    pa = np.asarray(pa)
+    pd = np.asarray(pd)
+    pc = np.asarray(fn_center)[pf]
+    pw = np.asarray(fn_pow)[pf]
+    fstart = np.searchsorted(pf, np.arange(nbf))
+    S = np.zeros((nbf, nbf))
+    npr = pf.size
+    fchunk = max(1, 1_500_000 // (npr * 3))
+    for f0 in range(0, nbf, fchunk):
+        f1 = min(nbf, f0 + fchunk)
+        i0 = fstart[f0]
+        i1 = fstart[f1] if f1 < nbf else npr
+        a = pa[i0:i1, None]
+        b = pa[None, :]
+        p = a + b
+        A = pc[i0:i1, None, :]
+        B = pc[None, :, :]
+        AB2 = np.sum((A - B) ** 2, axis=-1)
+        val = np.exp(-a * b / p * AB2) * pd[i0:i1, None] * pd[None, :]
+        for dim in range(3):
+            Pd = (a * A[..., dim] + b * B[..., dim]) / p
+            la = pw[i0:i1, dim]
+            lb = pw[:, dim]
+            comp = np.zeros_like(p)
+            for li in range(3):
+                for lj in range(3):
+                    m = (la[:, None] == li) & (lb[None, :] == lj)
+                    if not m.any():
+                        continue
+                    comp = np.where(m, _overlap_1d(li, lj, Pd - A[..., dim], Pd - B[..., dim], p), comp)
+            val = val * comp
+        cols = np.add.reduceat(val, fstart, axis=1)
+        S[f0:f1] = np.add.reduceat(cols, fstart[f0:f1] - i0, axis=0)
+    # renormalise contractions to unit self-overlap
+    n = 1.0 / np.sqrt(np.diag(S))
+    return S * n[:, None] * n[None, :]
+
+
+def lowdin(C: np.ndarray, S: np.ndarray) -> np.ndarray:
+    M = C.T @ S @ C
+    w, U = np.linalg.eigh(M)
+    return C @ (U * (1.0 / np.sqrt(w))) @ U.T
+
+
+def density_random(nbf: int, nocc: int, S: np.ndarray, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    C = lowdin(rng.normal(size=(nbf, nocc)), S)
+    return 2.0 * C @ C.T
+
+
+def density_localised(supports: list, nbf: int, S: np.ndarray, seed: int) -> np.ndarray:
+    """One orbital per support (list of basis indices), random normal
+    coefficients on its support, then Loewdin-orthonormalised; D = 2 C C^T."""
+    rng = np.random.default_rng(seed)
+    C = np.zeros((nbf, len(supports)))
+    for k, sup in enumerate(supports):
+        C[sup, k] = rng.normal(size=len(sup))
+    C = lowdin(C, S)
+    D = 2.0 * C @ C.T
+    return 0.5 * (D + D.T)
+
+
+def _water_supports(Z: np.ndarray, basis: Basis):
+    fa = basis_function_atoms(Z, basis)
+    sups = []
+    for m in range(len(Z) // 3):
+        idx = np.nonzero((fa >= 3 * m) & (fa < 3 * m + 3))[0]
+        sups.extend([idx] * 5)  # 10 electrons -> 5 occupied orbitals
+    return sups
+
+
+def _atom_supports(Z: np.ndarray, xyz: np.ndarray, basis: Basis, radius_A: float = 1.6):
+    fa = basis_function_atoms(Z, basis)
+    sups = []
+    electrons = 0
+    for a, z in enumerate(Z):
+        before = electrons
+        electrons += ELEMENT_ELECTRONS[int(z)]
+        norb = electrons // 2 - before // 2
+        if norb == 0:
+            continue
+        near = np.nonzero(np.linalg.norm(xyz - xyz[a], axis=1) <= radius_A * ANGSTROM)[0]
+        idx = np.nonzero(np.isin(fa, near))[0]
+        sups.extend([idx] * norb)
+    return sups
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+
+GRID_SMALL = GridSpec(nrad=30, ntheta=(8,))
+GRID_PRUNED = GridSpec(nrad=75, ntheta=(5, 8, 12))
+
+
+def make_system(config: int, frame: int = 0, nwaters: int | None = None) -> System:
+    """The seeded synthetic system for one of the five workloads.
+
+    ``nwaters`` overrides the cluster size (water workloads only) for small
+    test variants of the same recipe."""
+    if config == 1:
+        Z, xyz = two_waters(1)
+        basis = make_basis(Z, RECIPE_SP, 2)
+        S = overlap_matrix(xyz, basis)
+        D = density_random(basis.nbf, 10, S, 3)
+        return System("two_waters_lda", Z, xyz, basis, D, GRID_SMALL, 1e-12, 1e-12, "lda_x")
+    if config in (2, 5):
+        nw = nwaters if nwaters is not None else (33 if config == 2 else 167)
+        Z, xyz = water_cluster(nw, 11 if config == 2 else 41)
+        basis = make_basis(Z, RECIPE_SVP, 2)
+        S = overlap_matrix(xyz, basis)
+        D = density_localised(_water_supports(Z, basis), basis.nbf, S, 12 if config == 2 else 43)
+        name = f"water{nw}_pbe"
+        return System(name, Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe")
+    if config == 3:
+        Z, xyz = organic_cluster(21)
+        basis = make_basis(Z, RECIPE_SVP, 2)
+        S = overlap_matrix(xyz, basis)
+        D = density_localised(_atom_supports(Z, xyz, basis), basis.nbf, S, 22)
+        return System("cnoh1000_pbe", Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe")
+    if config == 4:
+        sizes = np.random.default_rng(31).integers(20, 131, size=256)
+        nw = int(sizes[frame]) if nwaters is None else nwaters
+        Z, xyz = water_cluster(nw, 31_000 + nw)
+        rng = np.random.default_rng([32, frame])
+        xyz = xyz + rng.normal(scale=0.05 * ANGSTROM / math.sqrt(3.0), size=xyz.shape)
+        basis = make_basis(Z, RECIPE_SVP, 2)
+        S = overlap_matrix(xyz, basis)
+        D = density_localised(_water_supports(Z, basis), basis.nbf, S, 33 + frame)
+        return System(f"frame{frame}_water{nw}_pbe", Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe",
+                      meta={"frame": frame})
+    raise ValueError(f"unknown workload {config}")
+
+
+def frame_sizes(nframes: int = 256) -> np.ndarray:
+    """Water counts of the batched-frames workload (seed 31)."""
+    return np.random.default_rng(31).integers(20, 131, size=256)[:nframes]

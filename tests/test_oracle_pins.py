@@ -1,0 +1,278 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle: closed forms,
+exact invariants, textbook special cases, brute force and an independently
+written second implementation (the input generator's overlap)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis as ob
+from oracle import exc as oe
+from oracle import grid as og
+from oracle import screen as osc
+from oracle import xc as ox
+
+
+def single_gaussian_system(a, kind="lda_x", nrad=100):
+    Z = np.array([1])
+    xyz = np.zeros((1, 3))
+    bas = synth.Basis(np.array([0]), np.array([0]), np.array([1]), np.array([a]), np.array([1.0]))
+    return synth.System("s", Z, xyz, bas, np.array([[2.0]]), synth.GridSpec(nrad, (8,)), 0.0, 0.0, kind)
+
+
+# ---------------------------------------------------------------- closed form
+@pytest.mark.parametrize("a,expected", [(0.5, -0.6819858182557268), (1.0, -0.9644735935233612),
+                                        (2.0, -1.3639716365114531)])
+def test_slater_exchange_single_s_gaussian(a, expected):
+    """Restricted Slater exchange of a doubly occupied normalised s-Gaussian:
+    E_x = -(3/4)(3/pi)^(1/3) 2^(4/3) (2a/pi)^2 (3 pi / 8a)^(3/2)."""
+    s = single_gaussian_system(a)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    r = oe.evaluate(s, g, screened=False)
+    assert abs(r.E - expected) < 1e-12
+    assert abs(np.sum(g.weights * r.rho) - 2.0) < 1e-12
+
+
+# ---------------------------------------------------------------- grid
+def test_radial_rule_gaussian_moments():
+    r, w = og.treutler_radial(100)
+    for n in (0, 2, 4):
+        exact = math.gamma((n + 3) / 2) / 2.0  # int_0^inf r^(n+2) exp(-r^2) dr
+        assert abs(np.sum(w * r ** n * np.exp(-r * r)) - exact) < 1e-12 * max(1, exact)
+
+
+@pytest.mark.parametrize("nt", [5, 8, 12])
+def test_angular_rule_polynomials(nt):
+    dirs, w = og.angular_product(nt)
+    assert abs(w.sum() - 4 * math.pi) < 1e-13
+    deg = nt - 1  # exact for all monomials up to this total degree (and beyond in theta)
+    dfac = ob.double_factorial
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            for c in range(deg + 1 - a - b):
+                val = np.sum(w * dirs[:, 0] ** a * dirs[:, 1] ** b * dirs[:, 2] ** c)
+                if a % 2 or b % 2 or c % 2:
+                    exact = 0.0
+                else:
+                    exact = 4 * math.pi * dfac(a - 1) * dfac(b - 1) * dfac(c - 1) / dfac(a + b + c + 1)
+                assert abs(val - exact) < 1e-12, (a, b, c)
+
+
+def test_becke_partition_of_unity():
+    rng = np.random.default_rng(5)
+    xyz = rng.normal(scale=2.0, size=(5, 3))
+    pts = rng.normal(scale=3.0, size=(50, 3))
+    tot = np.zeros(50)
+    for a in range(5):
+        tot += og.becke_weights(pts, np.full(50, a), xyz)
+    assert np.allclose(tot, 1.0, atol=1e-14)
+
+
+def test_morton_bits_brute_force():
+    rng = np.random.default_rng(7)
+    q = rng.integers(0, 1 << 20, size=(200, 3))
+    m = og.morton_code(q)
+    for i in range(200):
+        for bit in range(60):
+            k, which = divmod(bit, 3)
+            coord = {0: 2, 1: 1, 2: 0}[which]   # bit 3k: z, 3k+1: y, 3k+2: x
+            assert ((int(m[i]) >> bit) & 1) == ((int(q[i, coord]) >> k) & 1)
+
+
+def test_grid_layout():
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    assert g.npoints % 128 == 0 and g.nreal == 6 * 30 * 128
+    assert np.all(np.diff(g.atom_of[:g.nreal]) >= 0)
+    for a in range(6):
+        idx = np.nonzero(g.atom_of[:g.nreal] == a)[0]
+        codes = og.morton_code(og.lattice(g.points[idx]))
+        assert np.all(np.diff(codes) >= 0)
+    # sum of Becke weights over all atoms' points reproduces a molecular integral:
+    # the electron count check below covers it; here only positivity.
+    assert np.all(g.weights[:g.nreal] >= 0)
+
+
+# ---------------------------------------------------------------- basis
+def test_basis_unit_norm_and_gradient():
+    s = synth.make_system(1)
+    shells = ob.build_shells(s.xyz, s.basis)
+    one = [sh for sh in shells if np.allclose(sh.center, s.xyz[0])]
+    pts, w = og.atom_points(s.xyz[0], 120, (16,))
+    phi, dphi = ob.eval_basis(pts, one, deriv=True)
+    norms = np.einsum("i,im->m", w, phi * phi)
+    assert np.allclose(norms, 1.0, atol=1e-9)
+    h = 1e-5
+    for ax in range(3):
+        e = np.zeros(3)
+        e[ax] = h
+        fd = (ob.eval_basis(pts[:200] + e, one)[0] - ob.eval_basis(pts[:200] - e, one)[0]) / (2 * h)
+        assert np.allclose(fd, dphi[ax, :200], atol=2e-6, rtol=1e-6)
+
+
+def test_overlap_two_independent_implementations_and_quadrature():
+    s = synth.make_system(1)
+    shells = ob.build_shells(s.xyz, s.basis)
+    S = ob.overlap_matrix(shells)
+    S2 = synth.overlap_matrix(s.xyz, s.basis)
+    assert np.abs(S - S2).max() < 1e-13
+    g = og.build_grid(s.Z, s.xyz, synth.GridSpec(60, (14,)))
+    phi, _ = ob.eval_basis(g.points, shells)
+    Sq = phi.T @ (g.weights[:, None] * phi)
+    assert np.abs(Sq - S).max() < 5e-5
+
+
+# ---------------------------------------------------------------- functional
+def test_xc_limits():
+    rho = np.array([1e-3, 0.1, 1.0, 30.0])
+    assert np.allclose(ox.f_pbe_x(rho, 0.0 * rho), ox.f_lda_x(rho), rtol=1e-15)
+    s2 = np.array([1e-8, 1e8])
+    F = ox.pbe_exchange_factor(s2)
+    assert abs((F[0] - 1) / s2[0] - ox.MU) < 1e-6
+    assert abs(F[1] - (1 + ox.KAPPA)) < 1e-7
+    # PW92 high-density limit: d eps / d ln rs -> A
+    r1, r2 = 1e-10, 1e-11
+    slope = (ox.eps_pw92(r1) - ox.eps_pw92(r2)) / math.log(r1 / r2)
+    assert abs(slope - ox.PW_A) < 1e-4
+    eps = ox.eps_pw92(np.array([2.0]))
+    assert abs(ox.pbe_h(eps, np.array([1e-9]))[0] / 1e-9 - ox.BETA) < 1e-6
+    assert abs(eps[0] + ox.pbe_h(eps, np.array([1e12]))[0]) < 1e-6
+
+
+def test_xc_derivatives_central_difference():
+    rng = np.random.default_rng(3)
+    rho = 10 ** rng.uniform(-5, 2, size=40)
+    sigma = rho ** (8 / 3) * 10 ** rng.uniform(-3, 2, size=40)
+    for kind in ("lda_x", "pbe"):
+        f, vr, vs = ox.evaluate(kind, rho, sigma)
+        fn = ox.f_lda_x if kind == "lda_x" else None
+        h = 1e-6 * rho
+        if kind == "lda_x":
+            fd = (fn(rho + h) - fn(rho - h)) / (2 * h)
+        else:
+            fd = (ox.f_pbe(rho + h, sigma) - ox.f_pbe(rho - h, sigma)) / (2 * h)
+            # v_sigma: exchange and correlation parts nearly cancel, so each part
+            # is differenced on its own and the tolerance scales with the parts
+            hs = 1e-4 * sigma
+            fdx = (ox.f_pbe_x(rho, sigma + hs) - ox.f_pbe_x(rho, sigma - hs)) / (2 * hs)
+            fdc = (ox.f_pbe_c(rho, sigma + hs) - ox.f_pbe_c(rho, sigma - hs)) / (2 * hs)
+            assert np.all(np.abs(vs - (fdx + fdc)) <= 1e-6 * (np.abs(fdx) + np.abs(fdc)))
+        assert np.allclose(vr, fd, rtol=1e-7)
+    _, vr, _ = ox.evaluate("lda_x", rho, None)
+    assert np.allclose(vr, -(3 / math.pi) ** (1 / 3) * rho ** (1 / 3), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- quadrature invariants
+@pytest.fixture(scope="module")
+def w1():
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    return s, g, sh
+
+
+def test_electron_count_and_symmetry(w1):
+    s, g, sh = w1
+    r = oe.evaluate(s, g, sh, screened=False)
+    S = ob.overlap_matrix(sh)
+    assert abs(np.sum(g.weights * r.rho) - np.trace(s.D @ S)) < 1e-3
+    assert abs(np.trace(s.D @ S) - 20.0) < 1e-10
+    assert np.array_equal(r.V, r.V.T)
+
+
+def test_lda_trace_and_scaling(w1):
+    s, g, sh = w1
+    r = oe.evaluate(s, g, sh, screened=False)
+    assert abs(np.sum(s.D * r.V) - 4.0 / 3.0 * r.E) < 1e-11 * abs(r.E)
+    s2 = synth.System(s.name, s.Z, s.xyz, s.basis, 1.7 * s.D, s.grid, s.t_b, s.t_d, s.xc)
+    r2 = oe.evaluate(s2, g, sh, screened=False, want_v=False)
+    assert abs(r2.E - 1.7 ** (4 / 3) * r.E) < 1e-12 * abs(r.E)
+
+
+def test_gga_trace_identity_and_derivative(w1):
+    s, g, sh = w1
+    r = oe.evaluate(s, g, sh, screened=False, xc_kind="pbe")
+    sigma = np.sum(r.grad ** 2, axis=1)
+    _, vr, vs = ox.evaluate("pbe", r.rho, sigma)
+    rhs = np.sum(g.weights * (r.rho * vr + 2 * sigma * vs))
+    assert abs(np.sum(s.D * r.V) - rhs) < 1e-11 * abs(rhs)
+    # dE/dD_{mu nu} (symmetric perturbation) = V_{mu nu} + V_{nu mu}
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        m, n = rng.integers(0, s.nbf, size=2)
+        h = 1e-5
+        dD = np.zeros_like(s.D)
+        dD[m, n] += h
+        dD[n, m] += h
+        Ep = oe.evaluate(synth.System("", s.Z, s.xyz, s.basis, s.D + dD, s.grid, 0, 0, "pbe"), g, sh,
+                         screened=False, want_v=False).E
+        Em = oe.evaluate(synth.System("", s.Z, s.xyz, s.basis, s.D - dD, s.grid, 0, 0, "pbe"), g, sh,
+                         screened=False, want_v=False).E
+        fd = (Ep - Em) / (2 * h)
+        an = r.V[m, n] + r.V[n, m] if m != n else r.V[m, m]
+        assert abs(fd - an) < 1e-7 * max(1.0, abs(an)), (m, n, fd, an)
+
+
+def test_dense_against_einsum_definition(w1):
+    s, g, sh = w1
+    pts = g.points[:128]
+    w = g.weights[:128]
+    phi, dphi = ob.eval_basis(pts, sh, deriv=True)
+    rho = np.einsum("mn,im,in->i", s.D, phi, phi)
+    grad = np.einsum("mn,cim,in->ic", s.D, dphi, phi) + np.einsum("mn,im,cin->ic", s.D, phi, dphi)
+    sigma = np.sum(grad ** 2, axis=1)
+    f, vr, vs = ox.evaluate("pbe", rho, sigma)
+    V = (np.einsum("i,im,in->mn", w * vr, phi, phi)
+         + 2 * np.einsum("i,ic,cim,in->mn", w * vs, grad, dphi, phi)
+         + 2 * np.einsum("i,ic,im,cin->mn", w * vs, grad, phi, dphi))
+    r = oe.evaluate(s, g, sh, screened=False, blocks=[0], xc_kind="pbe")
+    assert np.allclose(r.rho[:128], rho, rtol=1e-13, atol=1e-16)
+    assert np.allclose(r.grad[:128], grad, rtol=1e-12, atol=1e-15)
+    assert abs(r.E - np.sum(w * f)) < 1e-14
+    assert np.abs(r.V - V).max() < 1e-13
+
+
+def test_screened_limits(w1):
+    s, g, sh = w1
+    blocks = [0, 40, 97, 179]
+    dense = oe.evaluate(s, g, sh, screened=False, blocks=blocks, xc_kind="pbe")
+    zero = oe.evaluate(s, g, sh, screened=True, blocks=blocks, xc_kind="pbe", t_b=0.0, t_d=0.0)
+    assert np.array_equal(dense.rho, zero.rho) and np.array_equal(dense.V, zero.V)
+    loose = oe.evaluate(s, g, sh, screened=True, blocks=blocks, xc_kind="pbe", t_b=1e-6, t_d=1e-6)
+    # dropped pairs are bounded by t_d per element pair; the gap stays far below the bound
+    assert abs(loose.E - dense.E) < 1e-4
+    assert abs(loose.E - dense.E) > 0.0
+
+
+# ---------------------------------------------------------------- screening
+def test_parallel_addressing_against_nonzero():
+    rng = np.random.default_rng(11)
+    for n in (1, 7, 32, 128, 1000):
+        m = rng.random(n) < 0.3
+        S, I = osc.parallel_addressing(m)
+        assert S == m.sum() and np.array_equal(I, np.nonzero(m)[0])
+    S, I = osc.parallel_addressing(np.zeros(64, bool))
+    assert S == 0 and I.size == 0
+
+
+def test_executed_pairs_brute_force():
+    rng = np.random.default_rng(2)
+    nbf = 100
+    D = rng.normal(size=(nbf, nbf)) * 10 ** rng.uniform(-14, 0, size=(nbf, nbf))
+    D = D + D.T
+    phi = rng.normal(size=(128, nbf)) * 10 ** rng.uniform(-14, 0, size=(1, nbf))
+    t_b, t_d = 1e-9, 1e-8
+    b = osc.block_max_cols(phi)
+    S = osc.retained(b, t_b)
+    dmax = osc.d_block_max(D)
+    E1 = osc.executed_rho(S, b, dmax, t_b, t_d)
+    nb = osc.nbasis_blocks(nbf)
+    for p in range(nb):
+        bp = max(abs(phi[i, mu]) for i in range(128) for mu in range(32 * p, min(nbf, 32 * p + 32)))
+        assert (bp >= t_b) == (p in S)
+    for i, p in enumerate(S):
+        for j, q in enumerate(S):
+            dm = max(abs(D[m, n]) for m in range(32 * p, min(nbf, 32 * p + 32))
+                     for n in range(32 * q, min(nbf, 32 * q + 32)))
+            assert E1[i, j] == (dm >= t_b and b[p] * dm * b[q] >= t_d)
