@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the block-filtered exchange-correlation build on GB300.
+
+Metric: grid points per second of the rho + V_xc build (one kldi_exc call:
+D -> rho, grad rho -> PBE-form functional -> E_xc and V), on the 33-water
+cluster (99 atoms, 825 Cartesian functions, 1,153,350 grid points in 9,011
+blocks of 128, t_b = t_d = 1e-10), synthetic seeded inputs.  The headline
+mode is BF16x6 (three exact fixed-point BF16 slices per operand), the mode
+whose E_xc stays within 1e-6 Ha of the FP64 oracle; BF16x3 and the FP64 block
+form (the speedup denominator) are timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank evaluates its own replica of the workload
+(weak scaling, no data-path collective); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-points/s for rho+Vxc build; speedup vs plain FP64 form at dExc<1e-6 Ha"
+UNIT = "grid-points/s"
+WORKLOAD = ("water33_pbe: 33 waters at 0.0334/A^3 (99 atoms), 825 Cartesian s/p/d functions, "
+            "75 radial x (50/128/288) angular points pruned by thirds = 1,153,350 points (9,011 blocks of 128), "
+            "PBE-form GGA, t_b = t_d = 1e-10")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16x6")
+    ap.add_argument("--no-side-modes", action="store_true", help="skip the FP64 / BF16x3 side measurements")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n > 0 else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x, dev):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if "Active" in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- work counts
+def work_counts(plan, system, splits):
+    """Tensor-pipe FLOPs of one evaluation per product (algorithmic: executed
+    block pairs x 2 x 128 x d_p d_q x slice products), from the retained lists
+    and the D block maxima."""
+    ptr, idx, b = plan.lists()
+    D = system.D
+    n = D.shape[0]
+    nbb = (n + 31) // 32
+    dsz = np.array([min(32, n - 32 * p) for p in range(nbb)], float)
+    pad = np.zeros((nbb * 32, nbb * 32))
+    pad[:n, :n] = np.abs(D)
+    dmax = pad.reshape(nbb, 32, nbb, 32).max(axis=(1, 3))
+    f_rho = 0.0
+    f_v = 0.0
+    for g in range(len(ptr) - 1):
+        S = idx[ptr[g]:ptr[g + 1]]
+        if S.size == 0:
+            continue
+        bg = b[ptr[g]:ptr[g + 1]]
+        dm = dmax[np.ix_(S, S)]
+        e1 = (dm >= system.t_b) & (bg[:, None] * dm * bg[None, :] >= system.t_d)
+        dd = np.outer(dsz[S], dsz[S])
+        f_rho += 2.0 * 128 * float((dd * e1).sum())
+        f_v += 2.0 * 128 * float(dd.sum())
+    return splits * f_rho, splits * f_v
+
+
+# ---------------------------------------------------------------------------- oracle timing
+_ORACLE_GRID = {}
+
+
+def oracle_sample(system, nblocks_sample, seed=5):
+    """Time the CPU oracle's rho + V build on a seeded sample of grid blocks
+    of the workload (the grid and its Becke weights are preprocessing and are
+    not timed, as on the GPU side)."""
+    from oracle import basis as ob
+    from oracle import exc as oe
+    from oracle import grid as og
+    if "g" not in _ORACLE_GRID:
+        _ORACLE_GRID["g"] = og.build_grid(system.Z, system.xyz, system.grid, weight_blocks=[])
+        _ORACLE_GRID["sh"] = ob.build_shells(system.xyz, system.basis)
+    g, sh = _ORACLE_GRID["g"], _ORACLE_GRID["sh"]
+    rng = np.random.default_rng(seed)
+    blocks = sorted(rng.choice(g.nblocks, size=nblocks_sample, replace=False).tolist())
+    g.fill_weights(system.xyz, blocks)
+    t = time.perf_counter()
+    oe.evaluate(system, g, sh, screened=True, blocks=blocks)
+    dt = time.perf_counter() - t
+    return nblocks_sample * 128 / dt, dt, blocks
+
+
+def run_reference(args, world, rank):
+    import synth
+    if rank != 0:
+        return
+    s = synth.make_system(2)
+    cores = os.cpu_count()
+    nb = 12
+    for _ in range(args.warmup):
+        oracle_sample(s, 2, seed=99)
+    vals = []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        v, dt, _ = oracle_sample(s, nb, seed=1000 + k)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.median(vals))
+    sample = f"{nb} seeded grid blocks ({nb * 128} points) of the workload per step, screened FP64 oracle (numpy)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "arm": "CPU oracle (the reference arm of this repository)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+
+    import synth
+    from paper_2605_10363_gb300 import kldi
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    s = synth.make_system(2)
+    t_plan = time.perf_counter()
+    plan = kldi.plan_for_system(s, prec=args.prec, xc="pbe", stream=stream.cuda_stream)
+    t_plan = time.perf_counter() - t_plan
+    npts_real = plan.grid.nreal
+    nbf = s.nbf
+    D = torch.from_numpy(s.D).to(dev)
+    V = torch.zeros((nbf, nbf), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(max(3, args.warmup)):
+        kldi.exc(plan, "pbe", D, V, E)
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    plan.profile(True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        kldi.exc(plan, "pbe", D, V, E)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    stage_ms, stage_n = plan.stage_times()
+    plan.profile(False)
+    clk = clocks.stop()
+    ms_total = allmax(world, ms_total, dev)
+    ms_step = ms_total / args.steps
+    value = npts_real * args.steps * world / (ms_total * 1e-3)
+    E_ours = float(E.item())
+
+    # end to end through the public API with pinned host buffers
+    Dh = torch.from_numpy(s.D).pin_memory()
+    Vh = torch.zeros((nbf, nbf), dtype=torch.float64).pin_memory()
+    Eh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    kldi.exc(plan, "pbe", Dh, Vh, Eh)
+    ke = max(3, args.steps // 2)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        kldi.exc(plan, "pbe", Dh, Vh, Eh)
+    e2e_s = allmax(world, time.perf_counter() - t0, dev)
+    e2e = {"value": npts_real * ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbf * nbf * 8,
+           "d2h_bytes_per_step": nbf * nbf * 8 + 8}
+
+    out_extra = {}
+    # accuracy against the stored oracle values of this workload
+    gold_path = os.path.join(ROOT, "tests", "golden", "water33_pbe.json")
+    if os.path.exists(gold_path):
+        gold = json.load(open(gold_path))
+        out_extra["dExc_vs_oracle"] = E_ours - gold["E_screened"]
+        Vn = V.cpu().numpy()
+        vs = np.array(gold["V_samples"])
+        out_extra["max_dV_sampled_vs_oracle"] = float(np.abs(Vn[vs[:, 0].astype(int), vs[:, 1].astype(int)]
+                                                             - vs[:, 2]).max())
+
+    splits = {"bf16x3": 3, "bf16x6": 6, "fp64": 1}[args.prec]
+    f_rho, f_v = work_counts(plan, s, splits)
+    names = kldi.STAGES
+    per_stage = {names[k]: round(stage_ms[k] / args.steps, 4) for k in range(len(names))}
+    dom = "rho" if stage_ms[2] >= stage_ms[5] else "v"
+    dom_ms = (stage_ms[2] if dom == "rho" else stage_ms[5]) / max(1, stage_n[2] if dom == "rho" else stage_n[5])
+    dom_flops = f_rho if dom == "rho" else f_v
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        pk = json.load(open(peaks_path))
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        peak_src = "measured (bf16 sustained)"
+    else:
+        peak, peak_src = 1700.0, "fallback (bf16 sustained)"
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_rho_tc" if dom == "rho" else "k_w_tc", "peak_source": peak_src,
+            "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
+            "other_kernel": {"kernel": "k_w_tc" if dom == "rho" else "k_rho_tc",
+                             "achieved": (f_v if dom == "rho" else f_rho) /
+                             ((stage_ms[5] if dom == "rho" else stage_ms[2]) / max(1, stage_n[5] if dom == "rho"
+                                                                                   else stage_n[2]) * 1e-3) / 1e12}}
+
+    # side modes: the FP64 block form (speedup denominator) and BF16x3
+    modes = {}
+    if not args.no_side_modes and rank == 0:
+        for pm, steps in (("fp64", 2), ("bf16x3", max(3, args.steps // 2))):
+            p2 = kldi.plan_for_system(s, prec=pm, xc="pbe", stream=stream.cuda_stream)
+            kldi.exc(p2, "pbe", D, V, E)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            bb = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                kldi.exc(p2, "pbe", D, V, E)
+            bb.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(bb) / steps
+            m = {"ms_per_step": ms, "value": npts_real / (ms * 1e-3)}
+            if "dExc_vs_oracle" in out_extra:
+                m["dExc_vs_oracle"] = float(E.item()) - gold["E_screened"]
+            modes[pm] = m
+            del p2
+        out_extra["speedup_vs_fp64"] = modes["fp64"]["ms_per_step"] / ms_step
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, dt, blocks = oracle_sample(s, 160)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"160 seeded grid blocks ({160 * 128} points) of the workload, screened FP64 oracle "
+                         f"(numpy + BLAS), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.prec,
+                       "l2": "inputs larger than L2 (split tile buffers of several GB per step)",
+                       "parallelism": f"replicas x{world}", "plan_seconds": round(t_plan, 2)},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(stage_n.sum()), "clocks": clk, "stage_ms_per_step": per_stage,
+            "E_xc": E_ours, "modes": modes, **out_extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

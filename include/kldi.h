@@ -1,0 +1,228 @@
+/*
+ * kldi.h -- C ABI of the block-filtered exchange-correlation (EXC) quadrature
+ * library for NVIDIA GB300 (sm_103a).
+ *
+ * What it computes (arxiv 2605.10363, Sec. II-A): for Gaussian basis functions
+ * chi_mu, grid points r_i with weights w_i and a symmetric density matrix D,
+ *   Phi_{mu i}  = chi_mu(r_i)                                  (Eq. phi_def)
+ *   rho_i       = sum_{mu nu} D_{mu nu} chi_mu(r_i) chi_nu(r_i) (App. A), R = D Phi (Eq. r_equals_dphi)
+ *   E_xc        = sum_i w_i f(rho_i, sigma_i),  sigma = |grad rho|^2
+ *   V_{mu nu}   = sum_i w_i v_i chi_mu chi_nu  (Eq. exc_quadrature / fxc_matrix_form, b = 1),
+ *                 generalised for the GGA to (Phi^T X + X^T Phi)_{mu nu} with
+ *                 X_{i nu} = w_i (v_rho chi_nu / 2 + 2 v_sigma grad rho . grad chi_nu).
+ * Both products run only over the retained, executable 32 x 32 block pairs
+ * of the block-filtered representation (Sec. III-B-3 Eqs. block_summary_A..
+ * retained_blocks_B, Sec. III-C-1 Eqs. block_pair_filter..executed_block_pairs).
+ *
+ * Conventions for every entry point
+ *   - Units: bohr and Hartree.  Arrays are row-major.  Spin-restricted (b = 1).
+ *   - Return value: a kldi_status; nothing aborts.  On failure the message is
+ *     available from kldi_last_error() (thread-local, valid until the next call
+ *     on the same thread).
+ *   - Pointers passed to compute calls may be device or host memory; the
+ *     library asks the CUDA runtime which one it is.  Host arrays are copied
+ *     on the plan's stream; if any output is host memory the call synchronises
+ *     the stream before returning, otherwise it returns after enqueueing.
+ *   - Caller-owned: every array passed in.  Library-owned: the opaque handles,
+ *     released with kldi_grid_free / kldi_plan_free.  Work buffers are
+ *     allocated once when the plan is built; compute calls allocate nothing.
+ *   - A plan is used by one host thread at a time.  All work goes on the
+ *     stream given in kldi_options (0 = the legacy default stream).
+ */
+#ifndef KLDI_H
+#define KLDI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kldi_grid kldi_grid;
+typedef struct kldi_plan kldi_plan;
+
+typedef enum {
+  KLDI_OK = 0,
+  KLDI_EINVAL = -1,       /* bad argument (null pointer, size, enum value)   */
+  KLDI_ENOMEM = -2,       /* host or device allocation failed                */
+  KLDI_ECUDA = -3,        /* a CUDA runtime/driver call failed               */
+  KLDI_ETIMEOUT = -4,     /* a bounded device wait gave up                   */
+  KLDI_EUNSUPPORTED = -5  /* valid request this build or device cannot serve */
+} kldi_status;
+
+/* Functionals (Sec. III-F scope: local and semilocal).  KLDI_XC_LDA_X: Slater
+ * exchange.  KLDI_XC_PBE: PBE exchange + PW92/PBE correlation.  KLDI_XC_MLP:
+ * the learned 2-64-64-2 surrogate of the PBE form (see kldi_mlp_*). */
+typedef enum { KLDI_XC_LDA_X = 1, KLDI_XC_PBE = 2, KLDI_XC_MLP = 3 } kldi_xc;
+
+/* Arithmetic of the two block products.
+ * KLDI_FP64: FP64 CUDA-core block products (the plain block form).
+ * KLDI_BF16X3 / KLDI_BF16X6: tcgen05 tensor cores.  Every operand row (or
+ * column) is scaled by a power of two to |a| <= 1 and cut into 2 (x3) or 3
+ * (x6) BF16 slices on fixed-point grids of 2^-7, 2^-15, 2^-23; the products
+ * of slices whose levels sum below the slice count (3 resp. 6 products) are
+ * accumulated per level in FP32 tensor memory, where every partial sum of at
+ * most 256 terms is exactly representable, so the accumulator never rounds.
+ * Levels are combined and summed across K-segments in FP32/FP64 with
+ * round-to-nearest.  Truncation error: 2^-16 (x3) or 2^-24 (x6) of the row /
+ * column scale per element.
+ * KLDI_TF32X3: not provided (KLDI_EUNSUPPORTED): 11-bit slices cannot keep
+ * 256-term partial sums exact, so the accumulator's rounding would bias the
+ * result.
+ * The functional, the E_xc reduction and the scatter into V are FP64 in
+ * every mode. */
+typedef enum { KLDI_FP64 = 0, KLDI_BF16X3 = 1, KLDI_TF32X3 = 2, KLDI_BF16X6 = 3 } kldi_prec;
+
+/* Atoms: natm nuclei, atomic numbers Z[natm], positions xyz[natm*3] in bohr. */
+typedef struct {
+  int natm;
+  const int32_t* Z;
+  const double* xyz;
+} kldi_molecule;
+
+/* Contracted Cartesian Gaussian shells (App. A, "Gaussian basis functions").
+ * Shell s sits on atom atom[s], has angular momentum l[s] in {0,1,2} and
+ * nprim[s] primitives; its exponents and raw contraction coefficients are
+ * exps/coefs[off_s .. off_s + nprim[s]) with off_s = sum_{t<s} nprim[t].
+ * Coefficients multiply unnormalised primitives x^i y^j z^k exp(-a r^2); the
+ * library normalises each primitive and rescales the contraction to unit
+ * self-overlap.  Function order: shell by shell; inside a shell
+ * s | x y z | xx xy xz yy yz zz. */
+typedef struct {
+  int nshell;
+  const int32_t* atom;
+  const int32_t* l;
+  const int32_t* nprim;
+  const double* exps;
+  const double* coefs;
+} kldi_basis;
+
+/* Atom-centred grid (App. A, "Numerical integration grids"): nrad radial
+ * Treutler-Ahlrichs M4 points on Chebyshev nodes of the second kind; the
+ * radial shells are split into nregions equal index ranges (inner to outer)
+ * and range r uses the product angular rule ntheta[r] (Gauss-Legendre in
+ * cos theta) x 2*ntheta[r] (uniform azimuth).  Becke partition (three
+ * iterations).  Points are grouped by atom and stably sorted by the 60-bit
+ * Morton key of App. B Eq. morton_code within each atom, then cut into
+ * blocks of `block` points (only 128 is supported); the last block is padded
+ * with copies of the last point at weight 0. */
+typedef struct {
+  int nrad;
+  int nregions;
+  const int32_t* ntheta;
+  int block;
+} kldi_grid_spec;
+
+/* Thresholds and modes.  t_b: block-retention threshold (Eq. block_filter_A);
+ * t_d: block-pair execution threshold (Eq. block_pair_filter); rho_min: points
+ * with rho < rho_min contribute nothing; prec: kldi_prec; xc: the kldi_xc the
+ * plan will serve (KLDI_XC_PBE/MLP need basis gradients, LDA does not);
+ * stream: a cudaStream_t, or NULL for the legacy default stream. */
+typedef struct {
+  double t_b;
+  double t_d;
+  double rho_min;
+  int prec;
+  int xc;
+  void* stream;
+} kldi_options;
+
+/* Plan statistics (kldi_plan_info). */
+typedef struct {
+  int64_t nbf;            /* basis functions                                  */
+  int64_t nbasis_blocks;  /* ceil(nbf / 32)                                   */
+  int64_t npoints;        /* grid points incl. padding (multiple of 128)     */
+  int64_t nblocks;        /* grid blocks                                       */
+  int64_t retained;       /* sum over grid blocks of |S_g| (retained tiles)    */
+  int64_t pair_slots;     /* sum over grid blocks of |S_g|^2                   */
+  int64_t vtile_work;     /* (V tile, grid block) work items of the V product */
+  int64_t workspace_bytes;/* device bytes held by the plan                    */
+} kldi_plan_stats;
+
+/* Build the molecular grid on the host (preprocessing, run once per
+ * geometry; Sec. III-D).  *out is library-owned. */
+kldi_status kldi_make_grid(const kldi_molecule* mol, const kldi_grid_spec* spec, kldi_grid** out);
+
+/* Grid sizes: total points (multiple of the block size), real points, blocks. */
+kldi_status kldi_grid_info(const kldi_grid* grid, int64_t* npoints, int64_t* nreal, int64_t* nblocks);
+
+/* Copy the grid into caller host buffers: xyz[npoints*3], w[npoints],
+ * atom_of[npoints]; any of the three may be NULL. */
+kldi_status kldi_grid_export(const kldi_grid* grid, double* xyz, double* w, int32_t* atom_of);
+
+/* Geometry-fixed preprocessing (Sec. III-B-3, III-D): upload grid and basis,
+ * evaluate the block summaries b_gp = max |phi| (and |grad phi| for the GGA)
+ * over every grid block x 32-function basis block in FP64 on the GPU, keep
+ * S_g = {p : b_gp >= t_b} as a block-CSR list per grid block (the BCS(R)
+ * analogue of App. C) and the per-V-tile lists of grid blocks (the BCS(C)
+ * analogue), and allocate all work buffers.  The grid must stay alive while
+ * the plan is used.  *out is library-owned. */
+kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* mol, const kldi_basis* basis,
+                        const kldi_options* opt, kldi_plan** out);
+
+kldi_status kldi_plan_info(const kldi_plan* plan, kldi_plan_stats* stats);
+
+/* Export the retained lists for inspection: blk_ptr[nblocks+1] and
+ * blk_idx[retained] (ascending basis-block indices per grid block) and the
+ * summaries bmax[retained] (FP64).  Host buffers; any may be NULL. */
+kldi_status kldi_plan_export_lists(const kldi_plan* plan, int32_t* blk_ptr, int32_t* blk_idx, double* bmax);
+
+/* Density (Eq. r_equals_dphi then the row-dot of App. A): rho[npoints] and,
+ * for a GGA plan, grad[npoints*3] (may be NULL for LDA).  D is nbf x nbf,
+ * symmetric (only its values are used as given; no symmetrisation). */
+kldi_status kldi_density(kldi_plan* plan, const double* D, double* rho, double* grad);
+
+/* Potential from a given density: E_xc (one double) and V[nbf*nbf]
+ * (overwritten, symmetric) for functional xc; grad may be NULL for LDA. */
+kldi_status kldi_vxc(kldi_plan* plan, int xc, const double* rho, const double* grad, double* V,
+                     double* Exc);
+
+/* The fused hot path: D -> rho (grad rho) -> functional -> E_xc and V. */
+kldi_status kldi_exc(kldi_plan* plan, int xc, const double* D, double* V, double* Exc);
+
+/* Many molecules / frames of uneven size in one call: plans[k], D[k], V[k]
+ * and Exc[k] for k < nframes.  Every plan must have been built with the same
+ * options.  Device pointers only (KLDI_EINVAL otherwise). */
+kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
+                             double* const* V, double* Exc);
+
+/* Stages of one evaluation, for kldi_plan_stage_times. */
+typedef enum {
+  KLDI_STAGE_DPREP = 0,   /* D block maxima (and slicing for tensor modes)        */
+  KLDI_STAGE_PHI = 1,     /* basis values Phi of the retained tiles                */
+  KLDI_STAGE_RHO = 2,     /* density product R = Phi D and the row-dot            */
+  KLDI_STAGE_XC = 3,      /* functional, E_xc partial sums                         */
+  KLDI_STAGE_X = 4,       /* X tiles (and the V-product operands)                  */
+  KLDI_STAGE_V = 5,       /* potential product                                     */
+  KLDI_STAGE_FINISH = 6,  /* E_xc reduction, V symmetrisation                      */
+  KLDI_NSTAGES = 7
+} kldi_stage;
+
+/* Per-stage device timing with CUDA events on the plan's stream.  enable = 1
+ * starts recording (and clears earlier records), 0 stops.  Recording adds two
+ * event records per stage and batch; it allocates its events here, not in the
+ * compute calls (at most 4096 stage records are kept per reset). */
+kldi_status kldi_plan_profile(kldi_plan* plan, int enable);
+
+/* Synchronise the plan's stream and return, per kldi_stage, the summed device
+ * time in milliseconds (ms[KLDI_NSTAGES]) and the number of kernel launches
+ * (launches[KLDI_NSTAGES]) recorded since kldi_plan_profile(plan, 1); either
+ * pointer may be NULL.  Host buffers. */
+kldi_status kldi_plan_stage_times(kldi_plan* plan, double* ms, int64_t* launches);
+
+/* Switch the product arithmetic of an existing plan (kldi_prec). */
+kldi_status kldi_plan_set_precision(kldi_plan* plan, int prec);
+
+void kldi_plan_free(kldi_plan* plan);
+void kldi_grid_free(kldi_grid* grid);
+const char* kldi_last_error(void);
+
+/* Version string of the library build. */
+const char* kldi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KLDI_H */

@@ -117,12 +117,13 @@ class Grid:
     """points [N, 3], weights [N], atom_of [N], block size and counts; N is a
     multiple of the block size (padding points carry weight 0)."""
 
-    def __init__(self, points, weights, atom_of, nreal, block):
+    def __init__(self, points, weights, atom_of, nreal, block, raw_w=None):
         self.points = points
         self.weights = weights
         self.atom_of = atom_of
         self.nreal = nreal
         self.block = block
+        self.raw_w = raw_w
 
     @property
     def npoints(self) -> int:
@@ -131,6 +132,17 @@ class Grid:
     @property
     def nblocks(self) -> int:
         return self.npoints // self.block
+
+    def fill_weights(self, xyz, blocks):
+        """Becke-partitioned weights of the given blocks (the others stay as they are)."""
+        B = self.block
+        idx = np.concatenate([np.arange(b * B, (b + 1) * B) for b in blocks]) if len(blocks) else np.zeros(0, int)
+        idx = idx[idx < self.nreal]
+        chunk = 20000
+        for i0 in range(0, idx.size, chunk):
+            sel = idx[i0:i0 + chunk]
+            self.weights[sel] = self.raw_w[sel] * becke_weights(self.points[sel], self.atom_of[sel], xyz)
+        return self
 
 
 def build_grid(Z, xyz, spec, weight_blocks=None) -> Grid:
@@ -154,14 +166,7 @@ def build_grid(Z, xyz, spec, weight_blocks=None) -> Grid:
         raw_w = np.concatenate([raw_w, np.zeros(npad)])
         owner = np.concatenate([owner, np.repeat(owner[-1:], npad)])
     w = np.full(pts.shape[0], np.nan)
-    if weight_blocks is None:
-        idx = np.arange(nreal)
-    else:
-        idx = np.concatenate([np.arange(b * B, (b + 1) * B) for b in weight_blocks])
-        idx = idx[idx < nreal]
-    chunk = 20000
-    for i0 in range(0, idx.size, chunk):
-        sel = idx[i0:i0 + chunk]
-        w[sel] = raw_w[sel] * becke_weights(pts[sel], owner[sel], xyz)
     w[nreal:] = 0.0
-    return Grid(pts, w, owner, nreal, B)
+    g = Grid(pts, w, owner, nreal, B, raw_w)
+    blocks = range(g.nblocks) if weight_blocks is None else weight_blocks
+    return g.fill_weights(xyz, list(blocks))

@@ -1,0 +1,238 @@
+// Compute entry points: kldi_density, kldi_vxc, kldi_exc, kldi_exc_batched.
+// Every step runs in this library's CUDA kernels on the plan's stream.
+#include <cstring>
+
+#include "internal.h"
+
+using namespace kldi;
+
+namespace kldi {
+kldi_status ensure_tile_buffers(kldi_plan* P, int prec);
+}
+
+namespace {
+
+// Stage timing: record an event pair around `fn` when profiling is on.
+template <typename F>
+kldi_status staged(kldi_plan* P, int stage, int launches, F&& fn) {
+  P->launch_count += launches;
+  if (!P->prof || P->prof_stage.size() * 2 + 2 > P->prof_ev.size()) return fn();
+  const size_t k = P->prof_stage.size() * 2;
+  KLDI_TRY_CUDA(cudaEventRecord(P->prof_ev[k], P->stream));
+  KLDI_TRY(fn());
+  KLDI_TRY_CUDA(cudaEventRecord(P->prof_ev[k + 1], P->stream));
+  P->prof_stage.push_back(stage);
+  P->prof_launches.push_back(launches);
+  return KLDI_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// D -> per-evaluation operands (block maxima; split tiles for tensor modes).
+kldi_status prepare_D(kldi_plan* P, const double* D) {
+  return staged(P, KLDI_STAGE_DPREP, P->prec == KLDI_FP64 ? 1 : 3, [&]() -> kldi_status {
+    KLDI_TRY(launch_dmax(P, D, P->stream));
+    if (P->prec != KLDI_FP64) KLDI_TRY(launch_dsplit(P, D, P->stream));
+    return KLDI_OK;
+  });
+}
+
+kldi_status density_batch(kldi_plan* P, const Batch& b, const double* D, double* rho, double* grad) {
+  if (P->prec == KLDI_FP64) {
+    KLDI_TRY(staged(P, KLDI_STAGE_PHI, 1, [&] { return launch_phi64(P, b, P->stream); }));
+    KLDI_TRY(staged(P, KLDI_STAGE_RHO, 1, [&] { return launch_rho64(P, b, D, rho, grad, P->stream); }));
+  } else {
+    KLDI_TRY(staged(P, KLDI_STAGE_PHI, 1, [&] { return launch_phi_split(P, b, P->stream); }));
+    KLDI_TRY(staged(P, KLDI_STAGE_RHO, 1, [&] { return launch_rho_tc(P, b, rho, grad, P->stream); }));
+  }
+  return KLDI_OK;
+}
+
+kldi_status potential_batch(kldi_plan* P, const Batch& b, int xc, const double* rho, const double* grad,
+                            double* V, bool phi_ready) {
+  KLDI_TRY(staged(P, KLDI_STAGE_XC, 1, [&] { return launch_xc(P, b, xc, rho, grad, P->stream); }));
+  if (P->prec == KLDI_FP64) {
+    if (!phi_ready) KLDI_TRY(staged(P, KLDI_STAGE_PHI, 1, [&] { return launch_phi64(P, b, P->stream); }));
+    KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x64(P, b, P->stream); }));
+    KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_v64(P, b, V, P->stream); }));
+  } else {
+    // the V product's operands come from the X kernel; the per-point Phi slices are not needed
+    KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x_split(P, b, P->stream); }));
+    KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_v_tc(P, b, V, P->stream); }));
+  }
+  return KLDI_OK;
+}
+
+// After a synchronising call: report a bounded device wait that gave up.
+kldi_status check_device_error(kldi_plan* P) {
+  int e = 0;
+  KLDI_TRY_CUDA(cudaMemcpy(&e, P->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    cudaMemset(P->d_err, 0, sizeof(int));
+    set_error("a device-side bounded wait gave up (code %d)", e);
+    return e == 101 ? KLDI_EUNSUPPORTED : KLDI_ETIMEOUT;
+  }
+  return KLDI_OK;
+}
+
+kldi_status check_xc(const kldi_plan* P, int xc) {
+  if (xc < KLDI_XC_LDA_X || xc > KLDI_XC_PBE) {
+    set_error("functional %d is not available in this call", xc);
+    return xc == KLDI_XC_MLP ? KLDI_EUNSUPPORTED : KLDI_EINVAL;
+  }
+  if (xc != KLDI_XC_LDA_X && !P->gga) {
+    set_error("a GGA functional needs a plan screened with a GGA functional (basis gradients)");
+    return KLDI_EINVAL;
+  }
+  return KLDI_OK;
+}
+
+kldi_status exc_device(kldi_plan* P, int xc, const double* D, double* V, double* exc) {
+  KLDI_TRY(prepare_D(P, D));
+  KLDI_TRY_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
+  for (const Batch& b : P->batches) {
+    KLDI_TRY(density_batch(P, b, D, P->d_rho, P->d_grad));
+    KLDI_TRY(potential_batch(P, b, xc, P->d_rho, P->d_grad, V, true));
+  }
+  KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 2, [&] { return launch_finish(P, V, exc, P->stream); }));
+  return KLDI_OK;
+}
+
+}  // namespace
+
+extern "C" kldi_status kldi_density(kldi_plan* P, const double* D, double* rho, double* grad) {
+  if (!P || !D || !rho) { set_error("kldi_density: null argument"); return KLDI_EINVAL; }
+  if (P->gga && !grad) { set_error("kldi_density: a GGA plan needs grad"); return KLDI_EINVAL; }
+  const size_t nbf2 = (size_t)P->nbf * P->nbf;
+  const double* dD = D;
+  if (!is_device_ptr(D)) {
+    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
+    dD = P->d_D;
+  }
+  const bool host_out = !is_device_ptr(rho);
+  double* drho = host_out ? P->d_rho : rho;
+  double* dgrad = P->gga ? (host_out ? P->d_grad : grad) : P->d_grad;
+  KLDI_TRY(prepare_D(P, dD));
+  for (const Batch& b : P->batches) KLDI_TRY(density_batch(P, b, dD, drho, dgrad));
+  if (host_out) {
+    KLDI_TRY_CUDA(cudaMemcpyAsync(rho, drho, P->npoints * 8, cudaMemcpyDeviceToHost, P->stream));
+    if (P->gga) KLDI_TRY_CUDA(cudaMemcpyAsync(grad, dgrad, P->npoints * 24, cudaMemcpyDeviceToHost, P->stream));
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    KLDI_TRY(check_device_error(P));
+  } else if (P->gga && !is_device_ptr(grad)) {
+    set_error("kldi_density: rho and grad must both be device or both host memory");
+    return KLDI_EINVAL;
+  }
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_vxc(kldi_plan* P, int xc, const double* rho, const double* grad, double* V,
+                                double* Exc) {
+  if (!P || !rho || !V || !Exc) { set_error("kldi_vxc: null argument"); return KLDI_EINVAL; }
+  KLDI_TRY(check_xc(P, xc));
+  if (xc != KLDI_XC_LDA_X && !grad) { set_error("kldi_vxc: the GGA needs grad"); return KLDI_EINVAL; }
+  const double* drho = rho;
+  const double* dgrad = grad;
+  if (!is_device_ptr(rho)) {
+    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_rho, rho, P->npoints * 8, cudaMemcpyHostToDevice, P->stream));
+    drho = P->d_rho;
+  }
+  if (grad && !is_device_ptr(grad)) {
+    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_grad, grad, P->npoints * 24, cudaMemcpyHostToDevice, P->stream));
+    dgrad = P->d_grad;
+  }
+  if (!dgrad) dgrad = P->d_grad;
+  const bool hostV = !is_device_ptr(V), hostE = !is_device_ptr(Exc);
+  double* dV = hostV ? P->d_V : V;
+  double* dE = hostE ? P->d_exc : Exc;
+  KLDI_TRY_CUDA(cudaMemsetAsync(dV, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
+  for (const Batch& b : P->batches) KLDI_TRY(potential_batch(P, b, xc, drho, dgrad, dV, false));
+  KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 2, [&] { return launch_finish(P, dV, dE, P->stream); }));
+  if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, sizeof(double) * P->nbf * P->nbf, cudaMemcpyDeviceToHost, P->stream));
+  if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
+  if (hostV || hostE) {
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    KLDI_TRY(check_device_error(P));
+  }
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_exc(kldi_plan* P, int xc, const double* D, double* V, double* Exc) {
+  if (!P || !D || !V || !Exc) { set_error("kldi_exc: null argument"); return KLDI_EINVAL; }
+  KLDI_TRY(check_xc(P, xc));
+  const size_t nbf2 = (size_t)P->nbf * P->nbf;
+  const double* dD = D;
+  if (!is_device_ptr(D)) {
+    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
+    dD = P->d_D;
+  }
+  const bool hostV = !is_device_ptr(V), hostE = !is_device_ptr(Exc);
+  double* dV = hostV ? P->d_V : V;
+  double* dE = hostE ? P->d_exc : Exc;
+  KLDI_TRY(exc_device(P, xc, dD, dV, dE));
+  if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, nbf2 * 8, cudaMemcpyDeviceToHost, P->stream));
+  if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
+  if (hostV || hostE) {
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    KLDI_TRY(check_device_error(P));
+  }
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
+                                        double* const* V, double* Exc) {
+  if (!plans || nframes <= 0 || !D || !V || !Exc) { set_error("kldi_exc_batched: bad argument"); return KLDI_EINVAL; }
+  for (int k = 0; k < nframes; ++k) {
+    if (!plans[k] || !D[k] || !V[k]) { set_error("kldi_exc_batched: null entry %d", k); return KLDI_EINVAL; }
+    if (!is_device_ptr(D[k]) || !is_device_ptr(V[k])) {
+      set_error("kldi_exc_batched: device pointers only (entry %d)", k);
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY(check_xc(plans[k], xc));
+  }
+  if (!is_device_ptr(Exc)) { set_error("kldi_exc_batched: Exc must be device memory"); return KLDI_EINVAL; }
+  for (int k = 0; k < nframes; ++k) KLDI_TRY(exc_device(plans[k], xc, D[k], V[k], Exc + k));
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_plan_profile(kldi_plan* P, int enable) {
+  if (!P) { set_error("kldi_plan_profile: null plan"); return KLDI_EINVAL; }
+  if (enable && P->prof_ev.empty()) {
+    P->prof_ev.resize(8192);
+    for (auto& e : P->prof_ev) KLDI_TRY_CUDA(cudaEventCreate(&e));
+  }
+  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+  P->prof_stage.clear();
+  P->prof_launches.clear();
+  P->prof = enable != 0;
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_plan_stage_times(kldi_plan* P, double* ms, int64_t* launches) {
+  if (!P) { set_error("kldi_plan_stage_times: null plan"); return KLDI_EINVAL; }
+  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+  double t[KLDI_NSTAGES] = {0};
+  int64_t n[KLDI_NSTAGES] = {0};
+  for (size_t k = 0; k < P->prof_stage.size(); ++k) {
+    float e = 0.f;
+    KLDI_TRY_CUDA(cudaEventElapsedTime(&e, P->prof_ev[2 * k], P->prof_ev[2 * k + 1]));
+    t[P->prof_stage[k]] += e;
+    n[P->prof_stage[k]] += P->prof_launches[k];
+  }
+  for (int s = 0; s < KLDI_NSTAGES; ++s) {
+    if (ms) ms[s] = t[s];
+    if (launches) launches[s] = n[s];
+  }
+  return KLDI_OK;
+}

@@ -1,0 +1,218 @@
+// Internal declarations of libkldi: handle structures, device views and the
+// launchers shared between translation units.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kldi.h"
+
+namespace kldi {
+
+constexpr int kBlockPts = 128;   // grid block (points); one tcgen05 M = 128 tile
+constexpr int kBasisBlk = 32;    // basis block d (Sec. IV numerical settings: d = 32)
+constexpr int kVTile = 128;      // W output tile edge of the tensor-core V product (4 basis blocks)
+
+void set_error(const char* fmt, ...);
+
+#define KLDI_TRY_CUDA(expr)                                                                    \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      kldi::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return KLDI_ECUDA;                                                                       \
+    }                                                                                          \
+  } while (0)
+
+#define KLDI_TRY(expr)            \
+  do {                            \
+    kldi_status s_ = (expr);      \
+    if (s_ != KLDI_OK) return s_; \
+  } while (0)
+
+// One shell as the kernels see it.  coef[k] already carries the primitive norm
+// (2a/pi)^(3/4) (4a)^(l/2) and the contraction rescale; the per-component factor
+// 1/sqrt((2i-1)!!(2j-1)!!(2k-1)!!) is applied in the kernels.
+struct DevShell {
+  double cx, cy, cz;
+  int32_t l;
+  int32_t nprim;
+  int32_t prim_off;
+  int32_t fn_off;
+  int32_t atom;
+  int32_t pad;
+};
+
+// Read-only device view of basis, grid and retained lists.
+struct BasisView {
+  const DevShell* shells;
+  const double* alpha;        // [nprim_total]
+  const double* coef;         // [nprim_total]
+  const float* alpha_f;       // FP32 hi/lo pairs (value = hi + lo to ~2^-48) of the
+  const float* alpha_lo;      // exponents, coefficients and their products a*c,
+  const float* coef_f;        // for the FP32 basis kernels
+  const float* coef_lo;
+  const float* ac_f;
+  const float* ac_lo;
+  const int32_t* bb_shell_begin;  // [nbb] first shell with a function in basis block p
+  const int32_t* bb_shell_end;    // [nbb] one past the last such shell
+  // FP32 evaluation in coordinates relative to an anchor atom: relatom[(a * natm + b) * 8 + 0..5]
+  // = A_b - A_a as hi (0..2) and lo (3..5) FP32 parts
+  const float* relatom;
+  int32_t natm;
+  int32_t nbf;
+  int32_t nbb;
+};
+
+struct GridView {
+  const double* xyz;   // [npoints*3]
+  const double* w;     // [npoints]
+  const float4* prel;  // [npoints] FP32 point coordinates relative to the block's anchor atom
+  const int32_t* anchor;  // [nblocks] anchor atom of each grid block (atom of its first point)
+  int64_t npoints;
+  int64_t nblocks;
+};
+
+struct ListView {
+  const int32_t* blk_ptr;  // [nblocks+1] CSR over grid blocks
+  const int32_t* blk_idx;  // [ntiles] retained basis block p of tile t
+  const double* bmax;      // [ntiles] b_gp
+  const int32_t* tile_of;  // [nblocks*nbb] tile index of (g, p), -1 if not retained
+  int32_t nbb;
+};
+
+// Work item of the FP64 V product: one 32 x 32 block pair (p <= q) over the
+// grid blocks list_g[beg, end).
+struct VWork64 {
+  int32_t p, q;
+  int32_t beg, end;
+};
+
+// Work item of the tensor-core V product: one 128 x 128 tile pair (P, Q) of
+// the full square W = Phi^T X (units of 4 basis blocks) over grid blocks
+// list_g[beg, end).
+struct VWorkTC {
+  int32_t P, Q;
+  int32_t beg, end;
+};
+
+struct Batch {
+  int64_t g0 = 0, g1 = 0;     // grid blocks [g0, g1)
+  int64_t t0 = 0, t1 = 0;     // tiles [t0, t1)
+  // FP64 V product
+  int32_t* d_v64_g = nullptr;  VWork64* d_v64_work = nullptr;  int64_t n_v64_work = 0;
+  // tensor V product
+  int32_t* d_vtc_g = nullptr;  VWorkTC* d_vtc_work = nullptr;  int64_t n_vtc_work = 0;
+};
+
+}  // namespace kldi
+
+struct kldi_grid {
+  std::vector<double> xyz;      // [npoints*3]
+  std::vector<double> w;        // [npoints]
+  std::vector<int32_t> atom;    // [npoints]
+  int64_t npoints = 0, nreal = 0, nblocks = 0;
+  int block = kldi::kBlockPts;
+};
+
+struct kldi_plan {
+  kldi_options opt{};
+  int gga = 0;
+  int prec = KLDI_FP64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t nbf = 0, nbb = 0, nbf_pad = 0, npoints = 0, nblocks = 0, ntiles = 0, nshell = 0, nprim_total = 0;
+  int64_t nvt = 0;  // W tiles per edge (ceil(nbb / 4))
+  int* d_err = nullptr;         // device error word (bounded-wait timeouts)
+
+  // host copies of the retained lists
+  std::vector<int32_t> blk_ptr, blk_idx;
+  std::vector<double> bmax;
+
+  // device: grid, basis, lists
+  double* d_xyz = nullptr;
+  double* d_w = nullptr;
+  float4* d_prel = nullptr;
+  int32_t* d_anchor = nullptr;
+  float* d_relatom = nullptr;
+  int32_t natm = 0;
+  kldi::DevShell* d_shells = nullptr;
+  double* d_alpha = nullptr;
+  double* d_coef = nullptr;
+  float* d_alpha_f = nullptr;   // [4][nprim]: alpha hi, alpha lo, coef hi, coef lo
+  float* d_coef_f = nullptr;    // [2][nprim]: (alpha coef) hi, lo
+  int32_t* d_bb_begin = nullptr;
+  int32_t* d_bb_end = nullptr;
+  int32_t* d_blk_ptr = nullptr;
+  int32_t* d_blk_idx = nullptr;
+  double* d_bmax = nullptr;
+  int32_t* d_tile_of = nullptr;
+
+  // device: per-evaluation buffers
+  double* d_D = nullptr;        // staging copy of a host D
+  double* d_V = nullptr;        // staging V when the caller passes host memory
+  double* d_dmax = nullptr;     // [nbb*nbb]
+  double* d_rho = nullptr;      // [npoints]
+  double* d_grad = nullptr;     // [npoints*3]
+  double* d_xcoef = nullptr;    // [npoints*4]: w v_rho / 2, 2 w v_sigma grad rho
+  double* d_xmax = nullptr;     // [ntiles]
+  double* d_eblk = nullptr;     // [nblocks]
+  double* d_exc = nullptr;      // [1]
+  // tiles of the current batch
+  double* d_phi64 = nullptr;    // FP64: [tiles][32][128]
+  double* d_x64 = nullptr;      // FP64: [tiles][32][128]
+  uint16_t* d_phi_s = nullptr;  // Phi sliced per point: [tiles][NS planes][128][32] BF16
+  uint16_t* d_phic_s = nullptr; // Phi sliced per function: [tiles][NS planes][128][32] BF16
+  uint16_t* d_x_s = nullptr;    // X sliced per function: [tiles][NS planes][128][32] BF16
+  float* d_phic_scale = nullptr;// [tiles][32] function scales of d_phic_s
+  float* d_x_scale = nullptr;   // [tiles][32] function scales of d_x_s
+  float* d_rowscale = nullptr;  // [npoints] point scales of d_phi_s
+  float* d_pscale = nullptr;    // [npoints] per-point balance c_i: Phi c and X / c in the V product
+  float* d_dscale = nullptr;    // [nbf_pad] column scales of d_dsplit
+  uint16_t* d_dsplit = nullptr; // sliced D block pairs [nbb*nbb][NS planes][32][32]
+  uint16_t* d_zero = nullptr;   // zero block (bulk-copy source for masked / absent blocks)
+  int64_t tile_cap = 0;         // tiles per batch the buffers hold
+
+  std::vector<kldi::Batch> batches;
+
+  // stage timing (kldi_plan_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;       // pool, pairs (start, end)
+  std::vector<int> prof_stage;            // stage of each recorded pair
+  std::vector<int> prof_launches;         // kernel launches of each recorded pair
+  int64_t launch_count = 0;               // kernels launched by this plan
+  int64_t vtile_work = 0;
+  int64_t workspace_bytes = 0;
+
+  kldi::BasisView basis_view() const;
+  kldi::GridView grid_view() const;
+  kldi::ListView list_view() const;
+};
+
+namespace kldi {
+
+// launchers (kernels.cu)
+kldi_status launch_block_max(const kldi_plan* P, const int32_t* d_cand_g, const int32_t* d_cand_p,
+                             int64_t ncand, double* d_out, cudaStream_t s);
+kldi_status launch_dmax(const kldi_plan* P, const double* D, cudaStream_t s);
+kldi_status launch_phi64(const kldi_plan* P, const Batch& b, cudaStream_t s);
+kldi_status launch_rho64(const kldi_plan* P, const Batch& b, const double* D, double* rho, double* grad,
+                         cudaStream_t s);
+kldi_status launch_xc(const kldi_plan* P, const Batch& b, int xc, const double* rho, const double* grad,
+                      cudaStream_t s);
+kldi_status launch_x64(const kldi_plan* P, const Batch& b, cudaStream_t s);
+kldi_status launch_v64(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
+kldi_status launch_finish(const kldi_plan* P, double* V, double* exc, cudaStream_t s);
+
+// tensor-core path (tc.cu)
+kldi_status launch_dsplit(const kldi_plan* P, const double* D, cudaStream_t s);
+kldi_status launch_phi_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
+kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho, double* grad, cudaStream_t s);
+kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
+kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
+kldi_status launch_symm(const kldi_plan* P, double* V, cudaStream_t s);
+
+}  // namespace kldi

@@ -1,0 +1,507 @@
+// kldi_screen and plan management: basis normalisation, geometric candidate
+// search, FP64 block summaries on the GPU (Eq. block_summary_A applied to Phi),
+// retained lists S_g (Eq. retained_blocks_A; a block-CSR list per grid block,
+// the BCS(R) analogue of App. C), batching of grid blocks, the per-pair grid
+// block lists of the V product (the BCS(C) analogue), and all work buffers.
+#include <omp.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "internal.h"
+
+using namespace kldi;
+
+BasisView kldi_plan::basis_view() const {
+  BasisView v;
+  v.shells = d_shells;
+  v.alpha = d_alpha;
+  v.coef = d_coef;
+  v.alpha_f = d_alpha_f;
+  v.alpha_lo = d_alpha_f ? d_alpha_f + nprim_total : nullptr;
+  v.coef_f = d_alpha_f ? d_alpha_f + 2 * nprim_total : nullptr;
+  v.coef_lo = d_alpha_f ? d_alpha_f + 3 * nprim_total : nullptr;
+  v.ac_f = d_coef_f;
+  v.ac_lo = d_coef_f ? d_coef_f + nprim_total : nullptr;
+  v.bb_shell_begin = d_bb_begin;
+  v.bb_shell_end = d_bb_end;
+  v.relatom = d_relatom;
+  v.natm = natm;
+  v.nbf = (int32_t)nbf;
+  v.nbb = (int32_t)nbb;
+  return v;
+}
+
+GridView kldi_plan::grid_view() const {
+  GridView v;
+  v.xyz = d_xyz;
+  v.w = d_w;
+  v.prel = d_prel;
+  v.anchor = d_anchor;
+  v.npoints = npoints;
+  v.nblocks = nblocks;
+  return v;
+}
+
+ListView kldi_plan::list_view() const {
+  ListView v;
+  v.blk_ptr = d_blk_ptr;
+  v.blk_idx = d_blk_idx;
+  v.bmax = d_bmax;
+  v.tile_of = d_tile_of;
+  v.nbb = (int32_t)nbb;
+  return v;
+}
+
+namespace {
+
+template <typename T>
+kldi_status dalloc(kldi_plan* P, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return KLDI_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    *p = nullptr;
+    return KLDI_ENOMEM;
+  }
+  P->workspace_bytes += (int64_t)(count * sizeof(T));
+  return KLDI_OK;
+}
+
+template <typename T>
+kldi_status upload(kldi_plan* P, T** p, const T* h, size_t count) {
+  KLDI_TRY(dalloc(P, p, count));
+  if (count) KLDI_TRY_CUDA(cudaMemcpy(*p, h, count * sizeof(T), cudaMemcpyHostToDevice));
+  return KLDI_OK;
+}
+
+void free_plan_buffers(kldi_plan* P) {
+  void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f,
+                  P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of,
+                  P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
+                  P->d_exc, P->d_err, P->d_phi64, P->d_x64, P->d_phi_s, P->d_phic_s, P->d_x_s,
+                  P->d_phic_scale, P->d_x_scale, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& b : P->batches) {
+    if (b.d_v64_g) cudaFree(b.d_v64_g);
+    if (b.d_v64_work) cudaFree(b.d_v64_work);
+    if (b.d_vtc_g) cudaFree(b.d_vtc_g);
+    if (b.d_vtc_work) cudaFree(b.d_vtc_work);
+  }
+}
+
+}  // namespace
+
+namespace kldi {
+
+// Bytes of the per-tile buffers each precision mode needs.
+int64_t tile_bytes_for(int prec) {
+  if (prec == KLDI_FP64) return 2LL * kBasisBlk * kBlockPts * 8;        // Phi and X tiles, FP64
+  return 3LL * 3 * kBasisBlk * kBlockPts * 2 + 2LL * kBasisBlk * 4;      // Phi (two slicings) and X, 3 planes
+}
+
+kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
+  if (prec == KLDI_TF32X3) {
+    set_error("KLDI_TF32X3 is not provided: 11-bit slices cannot keep the tensor-core sums exact");
+    return KLDI_EUNSUPPORTED;
+  }
+  if (prec == KLDI_FP64) {
+    if (!P->d_phi64) KLDI_TRY(dalloc(P, &P->d_phi64, (size_t)P->tile_cap * kBasisBlk * kBlockPts));
+    if (!P->d_x64) KLDI_TRY(dalloc(P, &P->d_x64, (size_t)P->tile_cap * kBasisBlk * kBlockPts));
+    return KLDI_OK;
+  }
+  const size_t per_tile = (size_t)3 * kBasisBlk * kBlockPts;  // 16-bit words, up to 3 planes
+  if (!P->d_phi_s) KLDI_TRY(dalloc(P, &P->d_phi_s, (size_t)P->tile_cap * per_tile));
+  if (!P->d_phic_s) KLDI_TRY(dalloc(P, &P->d_phic_s, (size_t)P->tile_cap * per_tile));
+  if (!P->d_x_s) KLDI_TRY(dalloc(P, &P->d_x_s, (size_t)P->tile_cap * per_tile));
+  if (!P->d_phic_scale) KLDI_TRY(dalloc(P, &P->d_phic_scale, (size_t)P->tile_cap * kBasisBlk));
+  if (!P->d_x_scale) KLDI_TRY(dalloc(P, &P->d_x_scale, (size_t)P->tile_cap * kBasisBlk));
+  if (!P->d_rowscale) KLDI_TRY(dalloc(P, &P->d_rowscale, (size_t)P->npoints));
+  if (!P->d_pscale) KLDI_TRY(dalloc(P, &P->d_pscale, (size_t)P->npoints));
+  if (!P->d_dscale) KLDI_TRY(dalloc(P, &P->d_dscale, (size_t)P->nbf_pad));
+  if (!P->d_dsplit) KLDI_TRY(dalloc(P, &P->d_dsplit, (size_t)P->nbb * P->nbb * 3 * kBasisBlk * kBasisBlk));
+  if (!P->d_zero) {
+    KLDI_TRY(dalloc(P, &P->d_zero, (size_t)kBasisBlk * kBlockPts));
+    KLDI_TRY_CUDA(cudaMemset(P->d_zero, 0, (size_t)kBasisBlk * kBlockPts * sizeof(uint16_t)));
+  }
+  return KLDI_OK;
+}
+
+}  // namespace kldi
+
+extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* mol, const kldi_basis* basis,
+                                   const kldi_options* opt, kldi_plan** out) {
+  if (!grid || !mol || !basis || !opt || !out) {
+    set_error("kldi_screen: null argument");
+    return KLDI_EINVAL;
+  }
+  if (basis->nshell <= 0 || !basis->atom || !basis->l || !basis->nprim || !basis->exps || !basis->coefs) {
+    set_error("kldi_screen: empty or incomplete basis");
+    return KLDI_EINVAL;
+  }
+  if (opt->prec < KLDI_FP64 || opt->prec > KLDI_BF16X6 || opt->xc < KLDI_XC_LDA_X || opt->xc > KLDI_XC_MLP) {
+    set_error("kldi_screen: bad precision or functional");
+    return KLDI_EINVAL;
+  }
+  if (!(opt->t_b >= 0.0) || !(opt->t_d >= 0.0) || !(opt->rho_min >= 0.0)) {
+    set_error("kldi_screen: thresholds must be >= 0");
+    return KLDI_EINVAL;
+  }
+  kldi_plan* P = new (std::nothrow) kldi_plan;
+  if (!P) { set_error("kldi_screen: out of host memory"); return KLDI_ENOMEM; }
+  P->opt = *opt;
+  P->gga = opt->xc != KLDI_XC_LDA_X;
+  P->prec = opt->prec;
+  P->stream = (cudaStream_t)opt->stream;
+  cudaGetDevice(&P->device);
+  auto fail = [&](kldi_status s) {
+    free_plan_buffers(P);
+    delete P;
+    return s;
+  };
+
+  // ---- basis: normalised coefficients, function offsets, block -> shell ranges
+  const int ns = basis->nshell;
+  std::vector<DevShell> shells(ns);
+  std::vector<double> alpha, coef;
+  int fn = 0, off = 0;
+  for (int s = 0; s < ns; ++s) {
+    const int l = basis->l[s], np = basis->nprim[s], a = basis->atom[s];
+    if (l < 0 || l > 2 || np <= 0 || a < 0 || a >= mol->natm) {
+      set_error("kldi_screen: shell %d has l=%d nprim=%d atom=%d (supported: l <= 2)", s, l, np, a);
+      return fail(l > 2 ? KLDI_EUNSUPPORTED : KLDI_EINVAL);
+    }
+    const double* ex = basis->exps + off;
+    const double* cc = basis->coefs + off;
+    double so = 0.0;
+    for (int i = 0; i < np; ++i)
+      for (int j = 0; j < np; ++j)
+        so += cc[i] * cc[j] * std::pow(2.0 * std::sqrt(ex[i] * ex[j]) / (ex[i] + ex[j]), l + 1.5);
+    if (!(so > 0.0)) {
+      set_error("kldi_screen: shell %d has zero norm", s);
+      return fail(KLDI_EINVAL);
+    }
+    const double rescale = 1.0 / std::sqrt(so);
+    for (int i = 0; i < np; ++i) {
+      if (!(ex[i] > 0.0)) { set_error("kldi_screen: non-positive exponent"); return fail(KLDI_EINVAL); }
+      alpha.push_back(ex[i]);
+      coef.push_back(cc[i] * std::pow(2.0 * ex[i] / M_PI, 0.75) * std::pow(4.0 * ex[i], 0.5 * l) * rescale);
+    }
+    shells[s] = DevShell{mol->xyz[3 * a], mol->xyz[3 * a + 1], mol->xyz[3 * a + 2], l, np, off, fn, a, 0};
+    fn += (l + 1) * (l + 2) / 2;
+    off += np;
+  }
+  P->nbf = fn;
+  P->nshell = ns;
+  P->nbb = (fn + kBasisBlk - 1) / kBasisBlk;
+  P->nbf_pad = P->nbb * kBasisBlk;
+  P->nvt = (P->nbb + 3) / 4;
+  P->npoints = grid->npoints;
+  P->nblocks = grid->nblocks;
+  const int64_t nbb = P->nbb, nblk = P->nblocks;
+  std::vector<int32_t> bb_begin(nbb, ns), bb_end(nbb, 0);
+  for (int s = 0; s < ns; ++s) {
+    const int f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
+    for (int p = f0 / kBasisBlk; p <= (f1 - 1) / kBasisBlk; ++p) {
+      bb_begin[p] = std::min(bb_begin[p], s);
+      bb_end[p] = std::max(bb_end[p], s + 1);
+    }
+  }
+  // FP32 hi/lo pairs: hi = fp32(v), lo = fp32(v - hi)
+  const size_t npr = alpha.size();
+  P->nprim_total = (int64_t)npr;
+  std::vector<float> alpha_f(4 * npr), coef_f(2 * npr);
+  for (size_t k = 0; k < npr; ++k) {
+    const double ac = alpha[k] * coef[k];
+    alpha_f[k] = (float)alpha[k];
+    alpha_f[npr + k] = (float)(alpha[k] - (double)alpha_f[k]);
+    alpha_f[2 * npr + k] = (float)coef[k];
+    alpha_f[3 * npr + k] = (float)(coef[k] - (double)alpha_f[2 * npr + k]);
+    coef_f[k] = (float)ac;
+    coef_f[npr + k] = (float)(ac - (double)coef_f[k]);
+  }
+  kldi_status st;
+  if ((st = upload(P, &P->d_xyz, grid->xyz.data(), grid->xyz.size())) != KLDI_OK) return fail(st);
+  {
+    // anchors and relative FP32 coordinates for the FP32 basis kernels
+    const int natm = mol->natm;
+    P->natm = natm;
+    std::vector<int32_t> anchor(grid->nblocks);
+    std::vector<float4> prel(grid->npoints);
+    for (int64_t g = 0; g < grid->nblocks; ++g) {
+      const int a = grid->atom[g * kBlockPts];
+      anchor[g] = a;
+      for (int i = 0; i < kBlockPts; ++i) {
+        const int64_t k = g * kBlockPts + i;
+        prel[k] = make_float4((float)(grid->xyz[k * 3] - mol->xyz[3 * a]), (float)(grid->xyz[k * 3 + 1] - mol->xyz[3 * a + 1]),
+                              (float)(grid->xyz[k * 3 + 2] - mol->xyz[3 * a + 2]), 0.f);
+      }
+    }
+    std::vector<float> rel((size_t)natm * natm * 8, 0.f);
+    for (int a = 0; a < natm; ++a)
+      for (int b = 0; b < natm; ++b) {
+        float* r = &rel[((size_t)a * natm + b) * 8];
+        for (int c = 0; c < 3; ++c) {
+          const double d = mol->xyz[3 * b + c] - mol->xyz[3 * a + c];
+          r[c] = (float)d;
+          r[3 + c] = (float)(d - (double)r[c]);
+        }
+      }
+    if ((st = upload(P, &P->d_anchor, anchor.data(), anchor.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_prel, prel.data(), prel.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_relatom, rel.data(), rel.size())) != KLDI_OK) return fail(st);
+  }
+  if ((st = upload(P, &P->d_w, grid->w.data(), grid->w.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_shells, shells.data(), shells.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_alpha, alpha.data(), alpha.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_coef, coef.data(), coef.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_alpha_f, alpha_f.data(), alpha_f.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_coef_f, coef_f.data(), coef_f.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_bb_begin, bb_begin.data(), bb_begin.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_bb_end, bb_end.data(), bb_end.size())) != KLDI_OK) return fail(st);
+
+  // ---- geometric candidates: shell extent R_s beyond which the value (and
+  // gradient) bound r^l sum|c| e^{-a r^2} (+ l r^(l-1) .. + 2 a r^(l+1) ..) < t_b/2.
+  const double tb = opt->t_b;
+  std::vector<double> ext(ns, 0.0);
+  for (int s = 0; s < ns; ++s) {
+    const int l = shells[s].l, np = shells[s].nprim, o = shells[s].prim_off;
+    double Rs = 0.0;
+    for (double r = 60.0; r >= 0.0; r -= 0.01) {
+      double v = 0.0, gd = 0.0;
+      for (int k = 0; k < np; ++k) {
+        const double e = std::fabs(coef[o + k]) * std::exp(-alpha[o + k] * r * r);
+        v += e;
+        gd += 2.0 * alpha[o + k] * e;
+      }
+      double b = std::pow(r, l) * v;
+      if (P->gga) b = std::max(b, (l > 0 ? l * std::pow(r, l - 1) * v : 0.0) + std::pow(r, l + 1) * gd);
+      if (b >= 0.5 * tb) { Rs = r + 0.05; break; }
+    }
+    ext[s] = tb > 0.0 ? Rs : 1e300;
+  }
+  std::vector<double> gc(nblk * 4);
+  for (int64_t g = 0; g < nblk; ++g) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < kBlockPts; ++i)
+      for (int c = 0; c < 3; ++c) {
+        const double v = grid->xyz[(g * kBlockPts + i) * 3 + c];
+        lo[c] = std::min(lo[c], v);
+        hi[c] = std::max(hi[c], v);
+      }
+    double rad = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      gc[g * 4 + c] = 0.5 * (lo[c] + hi[c]);
+      rad += 0.25 * (hi[c] - lo[c]) * (hi[c] - lo[c]);
+    }
+    gc[g * 4 + 3] = std::sqrt(rad);
+  }
+  std::vector<std::vector<int32_t>> cand(nblk);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t g = 0; g < nblk; ++g) {
+    std::vector<char> mark(nbb, 0);
+    for (int s = 0; s < ns; ++s) {
+      const double dx = shells[s].cx - gc[g * 4], dy = shells[s].cy - gc[g * 4 + 1], dz = shells[s].cz - gc[g * 4 + 2];
+      const double d = std::sqrt(dx * dx + dy * dy + dz * dz) - gc[g * 4 + 3];
+      if (d <= ext[s]) {
+        const int f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
+        for (int p = f0 / kBasisBlk; p <= (f1 - 1) / kBasisBlk; ++p) mark[p] = 1;
+      }
+    }
+    for (int p = 0; p < nbb; ++p)
+      if (mark[p]) cand[g].push_back(p);
+  }
+  std::vector<int64_t> cptr(nblk + 1, 0);
+  for (int64_t g = 0; g < nblk; ++g) cptr[g + 1] = cptr[g] + (int64_t)cand[g].size();
+  const int64_t ncand = cptr[nblk];
+  std::vector<int32_t> cg(ncand), cp(ncand);
+  for (int64_t g = 0; g < nblk; ++g)
+    for (size_t k = 0; k < cand[g].size(); ++k) {
+      cg[cptr[g] + k] = (int32_t)g;
+      cp[cptr[g] + k] = cand[g][k];
+    }
+  int32_t *d_cg = nullptr, *d_cp = nullptr;
+  double* d_cb = nullptr;
+  std::vector<double> cb(ncand);
+  if (ncand) {
+    if (cudaMalloc(&d_cg, ncand * 4) != cudaSuccess || cudaMalloc(&d_cp, ncand * 4) != cudaSuccess ||
+        cudaMalloc(&d_cb, ncand * 8) != cudaSuccess) {
+      cudaFree(d_cg); cudaFree(d_cp); cudaFree(d_cb);
+      set_error("kldi_screen: cudaMalloc of the candidate list failed");
+      return fail(KLDI_ENOMEM);
+    }
+    cudaMemcpy(d_cg, cg.data(), ncand * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_cp, cp.data(), ncand * 4, cudaMemcpyHostToDevice);
+    st = launch_block_max(P, d_cg, d_cp, ncand, d_cb, 0);
+    cudaError_t e = cudaMemcpy(cb.data(), d_cb, ncand * 8, cudaMemcpyDeviceToHost);
+    cudaFree(d_cg); cudaFree(d_cp); cudaFree(d_cb);
+    if (st != KLDI_OK) return fail(st);
+    if (e != cudaSuccess) {
+      set_error("kldi_screen: block summary kernel failed: %s", cudaGetErrorString(e));
+      return fail(KLDI_ECUDA);
+    }
+  }
+  // ---- retained lists S_g = {p : b_gp >= t_b}
+  P->blk_ptr.assign(nblk + 1, 0);
+  for (int64_t g = 0; g < nblk; ++g) {
+    for (int64_t k = cptr[g]; k < cptr[g + 1]; ++k)
+      if (cb[k] >= tb) {
+        P->blk_idx.push_back(cp[k]);
+        P->bmax.push_back(cb[k]);
+      }
+    if ((int64_t)P->blk_idx.size() > INT32_MAX) {
+      set_error("kldi_screen: more than 2^31 retained tiles");
+      return fail(KLDI_EUNSUPPORTED);
+    }
+    P->blk_ptr[g + 1] = (int32_t)P->blk_idx.size();
+  }
+  P->ntiles = (int64_t)P->blk_idx.size();
+  std::vector<int32_t> tile_of(nblk * nbb, -1);
+  for (int64_t g = 0; g < nblk; ++g)
+    for (int32_t t = P->blk_ptr[g]; t < P->blk_ptr[g + 1]; ++t) tile_of[g * nbb + P->blk_idx[t]] = t;
+  if ((st = upload(P, &P->d_blk_ptr, P->blk_ptr.data(), P->blk_ptr.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_blk_idx, P->blk_idx.data(), P->blk_idx.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_bmax, P->bmax.data(), P->bmax.size())) != KLDI_OK) return fail(st);
+  if ((st = upload(P, &P->d_tile_of, tile_of.data(), tile_of.size())) != KLDI_OK) return fail(st);
+
+  // ---- batches: grid blocks whose tiles fit the per-batch tile capacity
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const int64_t per_tile = std::max(tile_bytes_for(KLDI_FP64), tile_bytes_for(KLDI_TF32X3));
+  int64_t cap = (int64_t)(0.35 * (double)free_b) / per_tile;
+  if (const char* env = getenv("KLDI_TILE_CAP")) cap = std::max<int64_t>(1, atoll(env));
+  int64_t maxblk = 0;
+  for (int64_t g = 0; g < nblk; ++g) maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
+  cap = std::max(cap, maxblk);
+  cap = std::min<int64_t>(cap, std::max<int64_t>(P->ntiles, 1));
+  P->tile_cap = cap;
+  {
+    int64_t g0 = 0;
+    while (g0 < nblk) {
+      int64_t g1 = g0;
+      while (g1 < nblk && P->blk_ptr[g1 + 1] - P->blk_ptr[g0] <= cap) ++g1;
+      Batch b;
+      b.g0 = g0;
+      b.g1 = g1;
+      b.t0 = P->blk_ptr[g0];
+      b.t1 = P->blk_ptr[g1];
+      P->batches.push_back(b);
+      g0 = g1;
+    }
+  }
+  // ---- V work lists per batch
+  const int kSeg = 64;
+  for (auto& b : P->batches) {
+    // FP64: per basis-block pair (p <= q)
+    std::map<int64_t, std::vector<int32_t>> pl;
+    for (int64_t g = b.g0; g < b.g1; ++g)
+      for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i)
+        for (int32_t j = i; j < P->blk_ptr[g + 1]; ++j)
+          pl[(int64_t)P->blk_idx[i] * nbb + P->blk_idx[j]].push_back((int32_t)g);
+    std::vector<int32_t> gl;
+    std::vector<VWork64> wk;
+    for (auto& kv : pl) {
+      const int32_t p = (int32_t)(kv.first / nbb), q = (int32_t)(kv.first % nbb);
+      const int32_t base = (int32_t)gl.size();
+      gl.insert(gl.end(), kv.second.begin(), kv.second.end());
+      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += kSeg)
+        wk.push_back(VWork64{p, q, base + s0, base + std::min<int32_t>(s0 + kSeg, (int32_t)kv.second.size())});
+    }
+    if ((st = upload(P, &b.d_v64_g, gl.data(), gl.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &b.d_v64_work, wk.data(), wk.size())) != KLDI_OK) return fail(st);
+    b.n_v64_work = (int64_t)wk.size();
+    // tensor cores: per W tile pair (P, Q) of the full square, 128-function tiles
+    std::map<int64_t, std::vector<int32_t>> tl;
+    const int64_t nvt = P->nvt;
+    for (int64_t g = b.g0; g < b.g1; ++g) {
+      std::vector<int32_t> vt;
+      for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i) {
+        const int32_t T = P->blk_idx[i] / 4;
+        if (vt.empty() || vt.back() != T) vt.push_back(T);
+      }
+      for (size_t i = 0; i < vt.size(); ++i)
+        for (size_t j = 0; j < vt.size(); ++j) tl[(int64_t)vt[i] * nvt + vt[j]].push_back((int32_t)g);
+    }
+    std::vector<int32_t> tg;
+    std::vector<VWorkTC> tw;
+    // segment length: about 4 work items per SM over the whole batch, at least 16 grid blocks
+    int64_t total = 0;
+    for (auto& kv : tl) total += (int64_t)kv.second.size();
+    const int32_t kSegTC = (int32_t)std::max<int64_t>(16, total / (4 * 148) + 1);
+    for (auto& kv : tl) {
+      const int32_t Pt = (int32_t)(kv.first / nvt), Qt = (int32_t)(kv.first % nvt);
+      const int32_t base = (int32_t)tg.size();
+      tg.insert(tg.end(), kv.second.begin(), kv.second.end());
+      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += kSegTC)
+        tw.push_back(VWorkTC{Pt, Qt, base + s0, base + std::min<int32_t>(s0 + kSegTC, (int32_t)kv.second.size())});
+      P->vtile_work += (int64_t)kv.second.size();
+    }
+    if ((st = upload(P, &b.d_vtc_g, tg.data(), tg.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &b.d_vtc_work, tw.data(), tw.size())) != KLDI_OK) return fail(st);
+    b.n_vtc_work = (int64_t)tw.size();
+  }
+
+  // ---- per-evaluation buffers
+  const size_t nbf2 = (size_t)P->nbf * P->nbf;
+  if ((st = dalloc(P, &P->d_D, nbf2)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_V, nbf2)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_dmax, (size_t)nbb * nbb)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_rho, (size_t)P->npoints)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_grad, (size_t)P->npoints * 3)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_xcoef, (size_t)P->npoints * 4)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_xmax, (size_t)std::max<int64_t>(P->ntiles, 1))) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_eblk, (size_t)nblk)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_exc, 1)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_err, 1)) != KLDI_OK) return fail(st);
+  if (cudaMemset(P->d_err, 0, sizeof(int)) != cudaSuccess) { set_error("kldi_screen: memset failed"); return fail(KLDI_ECUDA); }
+  if ((st = ensure_tile_buffers(P, P->prec)) != KLDI_OK) return fail(st);
+  *out = P;
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_plan_set_precision(kldi_plan* P, int prec) {
+  if (!P || prec < KLDI_FP64 || prec > KLDI_BF16X6) {
+    set_error("kldi_plan_set_precision: bad argument");
+    return KLDI_EINVAL;
+  }
+  KLDI_TRY(ensure_tile_buffers(P, prec));
+  P->prec = prec;
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_plan_info(const kldi_plan* P, kldi_plan_stats* s) {
+  if (!P || !s) { set_error("kldi_plan_info: null argument"); return KLDI_EINVAL; }
+  s->nbf = P->nbf;
+  s->nbasis_blocks = P->nbb;
+  s->npoints = P->npoints;
+  s->nblocks = P->nblocks;
+  s->retained = P->ntiles;
+  int64_t ps = 0;
+  for (int64_t g = 0; g < P->nblocks; ++g) {
+    const int64_t n = P->blk_ptr[g + 1] - P->blk_ptr[g];
+    ps += n * n;
+  }
+  s->pair_slots = ps;
+  s->vtile_work = P->vtile_work;
+  s->workspace_bytes = P->workspace_bytes;
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_plan_export_lists(const kldi_plan* P, int32_t* blk_ptr, int32_t* blk_idx, double* bmax) {
+  if (!P) { set_error("kldi_plan_export_lists: null plan"); return KLDI_EINVAL; }
+  if (blk_ptr) std::memcpy(blk_ptr, P->blk_ptr.data(), P->blk_ptr.size() * 4);
+  if (blk_idx) std::memcpy(blk_idx, P->blk_idx.data(), P->blk_idx.size() * 4);
+  if (bmax) std::memcpy(bmax, P->bmax.data(), P->bmax.size() * 8);
+  return KLDI_OK;
+}
+
+extern "C" void kldi_plan_free(kldi_plan* P) {
+  if (!P) return;
+  for (auto& e : P->prof_ev) cudaEventDestroy(e);
+  free_plan_buffers(P);
+  delete P;
+}

@@ -1,0 +1,881 @@
+// Split-precision tensor-core path (tcgen05, sm_103a) with exact accumulation.
+//
+// Slicing.  A row (or column) of an operand is scaled by a power of two s so
+// that |a / s| <= 1, and a / s is cut into NS BF16 slices on fixed-point grids
+//   a0 = rint(a/s * 2^7) 2^-7,  a1 = rint((a/s - a0) 2^15) 2^-15,
+//   a2 = rint((a/s - a0 - a1) 2^23) 2^-23,
+// every slice an integer of at most 8 bits times its grid step, hence exact in
+// BF16.  The product sum over k of slice products is kept per "level"
+// l = i + j (only levels l < NS are formed: 3 products for NS = 2, 6 for
+// NS = 3).  All products of one level are multiples of 2^-(14 + 8 l) and at
+// most (l + 1) 2^-8l in size, so a level's partial sum over at most 256 terms
+// needs at most 24 significant bits: the FP32 tensor-memory accumulator
+// represents every partial sum exactly and its own rounding never acts.
+// Levels are combined, and K-segments summed, on CUDA cores with
+// round-to-nearest.  The tensor cores therefore add no bias; the only error is
+// the dropped tail of each slice expansion (2^-8 NS of the scale, unbiased).
+//
+// Kernels
+//  k_dscale     power-of-two column scales f_nu >= max_mu |D_mu nu|.
+//  k_dsplit     per 32 x 32 block pair (p, q): the density product's B operand
+//               [32 n][32 k] = D[32p + k][32q + n] / f_n in NS BF16 planes,
+//               64-byte swizzle.
+//  k_phi_split  per grid block: point scales e_i >= max_mu |phi_mu(r_i)| from the
+//               shell bound r^l sum_k |c_k| exp(-a_k r^2); then per retained
+//               tile (g, p) two slicings of Phi (Eq. phi_def): by point (the
+//               A operand of the density product) and by function with the
+//               tile's column maxima (the A operand of the V product).
+//  k_rho_tc     density product R = Phi_g D over the executed pairs of grid
+//               block g (Eq. executed_block_output), warp-ballot pair screen
+//               (Eq. block_pair_filter), bulk-copy pipeline, tcgen05.mma
+//               M = 128 N = 128 per level, drains every <= 8 executed chunks
+//               (256 K), fused row-dot rho = sum Phi . R, grad rho.
+//  k_x_split    X tile = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi),
+//               sliced by function with its column maxima; x_gq = max |X|.
+//  k_w_tc       W = Phi^T X, one 128 x 128 tile pair (P, Q) of the full square
+//               over a segment of its grid-block list; one grid block
+//               (K = 128) per exact accumulation, drained into compensated FP32
+//               sums, FP64 scatter-add at the end.  V = W + W^T (k_symm).
+#include <cuda_bf16.h>
+
+#include "basis.cuh"
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace kldi {
+
+using namespace tc;
+
+constexpr int kPlaneBytes = 8192;   // [128][32] BF16 plane of a tile
+constexpr int kDPlane = 2048;       // [32][32] BF16 plane of a D block pair
+constexpr int kMaxRet = 256;        // retained basis blocks per grid block the density kernel handles
+
+__host__ __device__ constexpr int tile_bytes(int ns) { return ns * kPlaneBytes; }
+
+// ---------------------------------------------------------------------------
+// slicing helpers
+__device__ __forceinline__ float pow2_ceil(float m) {
+  // smallest power of two >= m (m > 0), 1 for m <= 0
+  if (!(m > 0.f)) return 1.f;
+  int e;
+  const float f = frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+  return ldexpf(1.f, f == 0.5f ? e - 1 : e);
+}
+
+template <int NS>
+__device__ __forceinline__ void slice(float a, float* s) {  // |a| <= 1
+  const float s0 = rintf(a * 128.f) * (1.f / 128.f);
+  float r = a - s0;
+  s[0] = s0;
+  if (NS >= 2) {
+    const float s1 = rintf(r * 32768.f) * (1.f / 32768.f);
+    r = r - s1;
+    s[1] = s1;
+  }
+  if (NS >= 3) s[2] = rintf(r * 8388608.f) * (1.f / 8388608.f);
+}
+
+template <int NS>
+__device__ __forceinline__ void slice_d(double a, float* s) {  // |a| <= 1, FP64 input
+  const double s0 = rint(a * 128.0) / 128.0;
+  double r = a - s0;
+  s[0] = (float)s0;
+  if (NS >= 2) {
+    const double s1 = rint(r * 32768.0) / 32768.0;
+    r = r - s1;
+    s[1] = (float)s1;
+  }
+  if (NS >= 3) s[2] = (float)(rint(r * 8388608.0) / 8388608.0);
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+// Row `row` of NS swizzled [rows][32] planes (plane stride `pstride` bytes)
+// from 32 scaled values v[] (|v| <= 1).
+template <int NS>
+__device__ __forceinline__ void store_sliced_row(uint8_t* base, int pstride, int row, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint32_t w[NS][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s0[NS], s1[NS];
+      slice<NS>(v[c * 8 + 2 * k], s0);
+      slice<NS>(v[c * 8 + 2 * k + 1], s1);
+#pragma unroll
+      for (int l = 0; l < NS; ++l) w[l][k] = pack2(s0[l], s1[l]);
+    }
+    const uint32_t off = swz64_off(row, c * 8);
+#pragma unroll
+    for (int l = 0; l < NS; ++l)
+      *reinterpret_cast<uint4*>(base + l * pstride + off) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
+  }
+}
+
+__device__ __forceinline__ int64_t tile_block(const ListView& L, int64_t g0, int64_t nblocks, int64_t t) {
+  int64_t lo = g0, hi = nblocks;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (L.blk_ptr[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// D column scales (D symmetric: the row maximum is the column maximum).
+__global__ void k_dscale(const double* __restrict__ D, int nbf, int nbf_pad, float* dscale) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= nbf_pad) return;
+  double m = 0.0;
+  if (row < nbf)
+    for (int c = lane; c < nbf; c += 32) m = fmax(m, fabs(D[(int64_t)row * nbf + c]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) dscale[row] = pow2_ceil((float)(m * (1.0 + 1e-6)));
+}
+
+template <int NS>
+__global__ void k_dsplit(const double* __restrict__ D, const float* __restrict__ dscale, int nbf, int nbb,
+                         uint8_t* out) {
+  __shared__ double Ds[kBasisBlk][kBasisBlk + 1];
+  const int p = blockIdx.y, q = blockIdx.x;
+  for (int e = threadIdx.x; e < kBasisBlk * kBasisBlk; e += blockDim.x) {
+    const int k = e / kBasisBlk, n = e % kBasisBlk;
+    const int r = p * kBasisBlk + k, c = q * kBasisBlk + n;
+    Ds[k][n] = (r < nbf && c < nbf) ? D[(int64_t)r * nbf + c] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < kBasisBlk) {
+    const int n = threadIdx.x;
+    const double inv = 1.0 / (double)dscale[q * kBasisBlk + n];
+    uint8_t* base = out + ((int64_t)p * nbb + q) * (NS * kDPlane);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint32_t w[NS][4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float s0[NS], s1[NS];
+        slice_d<NS>(Ds[c * 8 + 2 * k][n] * inv, s0);
+        slice_d<NS>(Ds[c * 8 + 2 * k + 1][n] * inv, s1);
+#pragma unroll
+        for (int l = 0; l < NS; ++l) w[l][k] = pack2(s0[l], s1[l]);
+      }
+      const uint32_t off = swz64_off(n, c * 8);
+#pragma unroll
+      for (int l = 0; l < NS; ++l)
+        *reinterpret_cast<uint4*>(base + l * kDPlane + off) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
+    }
+  }
+}
+
+template <int NS>
+static kldi_status dsplit_ns(const kldi_plan* P, const double* D, cudaStream_t s) {
+  k_dscale<<<(unsigned)((P->nbf_pad + 7) / 8), 256, 0, s>>>(D, (int)P->nbf, (int)P->nbf_pad, P->d_dscale);
+  dim3 grid((unsigned)P->nbb, (unsigned)P->nbb);
+  k_dsplit<NS><<<grid, 128, 0, s>>>(D, P->d_dscale, (int)P->nbf, (int)P->nbb,
+                                    reinterpret_cast<uint8_t*>(P->d_dsplit));
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+kldi_status launch_dsplit(const kldi_plan* P, const double* D, cudaStream_t s) {
+  return P->prec == KLDI_BF16X6 ? dsplit_ns<3>(P, D, s) : dsplit_ns<2>(P, D, s);
+}
+
+// ---------------------------------------------------------------------------
+// Phi tiles: one CTA (128 threads = points) per grid block.
+template <int NS>
+__global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
+                                                   uint8_t* out_row, float* rowscale) {
+  __shared__ float st[kBasisBlk][kBlockPts + 1];
+  const int64_t g = g0 + blockIdx.x;
+  const int i = threadIdx.x;
+  const int64_t pt = g * kBlockPts + i;
+  const float4 pr = G.prel[pt];
+  const float px = pr.x, py = pr.y, pz = pr.z;
+  const int anc = G.anchor[g];
+  const int tb = L.blk_ptr[g], te = L.blk_ptr[g + 1];
+  // pass 1: point scale from the shell bound r^l sum_k |c_k| exp(-a_k r^2) >= |phi_mu(r_i)|
+  float M = 0.f;
+  for (int j = tb; j < te; ++j) {
+    const int p = L.blk_idx[j];
+    for (int s = B.bb_shell_begin[p]; s < B.bb_shell_end[p]; ++s) {
+      const DevShell sh = B.shells[s];
+      const float* ra = B.relatom + ((size_t)anc * B.natm + sh.atom) * 8;
+      const float dx = (px - ra[0]) - ra[3], dy = (py - ra[1]) - ra[4], dz = (pz - ra[2]) - ra[5];
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      float sum = 0.f;
+      for (int k = 0; k < sh.nprim; ++k)
+        sum += fabsf(B.coef_f[sh.prim_off + k]) * exp_rn(-B.alpha_f[sh.prim_off + k] * r2);
+      const float poly = sh.l == 0 ? 1.f : (sh.l == 1 ? sqrtf(r2) : r2);
+      M = fmaxf(M, poly * sum);
+    }
+  }
+  const float rs = pow2_ceil(M * 1.001f);
+  rowscale[pt] = rs;
+  const float rinv = 1.f / rs;
+  // pass 2: per-point slicing of every retained tile
+  for (int j = tb; j < te; ++j) {
+    const int p = L.blk_idx[j];
+    float v[kBasisBlk];
+#pragma unroll
+    for (int nu = 0; nu < kBasisBlk; ++nu) st[nu][i] = 0.f;
+    for_block_functions<float, false>(
+        B, p, px, py, pz, [&](int nu, float x, float, float, float) { st[nu][i] = x; }, anc);
+#pragma unroll
+    for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = st[nu][i] * rinv;
+    store_sliced_row<NS>(out_row + (int64_t)(j - t0) * tile_bytes(NS), kPlaneBytes, i, v);
+  }
+}
+
+template <int NS>
+static kldi_status phi_ns(const kldi_plan* P, const Batch& b, cudaStream_t s) {
+  const int64_t n = b.g1 - b.g0;
+  if (n == 0) return KLDI_OK;
+  k_phi_split<NS><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.t0,
+                                                    reinterpret_cast<uint8_t*>(P->d_phi_s), P->d_rowscale);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+kldi_status launch_phi_split(const kldi_plan* P, const Batch& b, cudaStream_t s) {
+  return P->prec == KLDI_BF16X6 ? phi_ns<3>(P, b, s) : phi_ns<2>(P, b, s);
+}
+
+// ---------------------------------------------------------------------------
+// Column maxima of a [32][128 + 1] staging array -> power-of-two scales.
+__device__ __forceinline__ void column_scales(float (*st)[kBlockPts + 1], float* out, float* raw) {
+  const int i = threadIdx.x;
+  const int col = i >> 2, part = i & 3;
+  float m = 0.f;
+  for (int r = part * 32; r < part * 32 + 32; ++r) m = fmaxf(m, fabsf(st[col][r]));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+  if (part == 0) {
+    out[col] = pow2_ceil(m * 1.000001f);
+    if (raw) raw[col] = m;
+  }
+}
+
+// V-product operands of tile (g, p): Phi~ = c_i Phi and X~ = X / c_i with
+// X = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi), each sliced per
+// function with its own column scale.
+template <int NS, bool GRAD>
+__global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
+                                                 const double* __restrict__ xcoef, const float* __restrict__ pscale,
+                                                 uint8_t* out_phi, float* phi_scale, uint8_t* out_x, float* x_scale,
+                                                 double* xmax) {
+  __shared__ float sp[kBasisBlk][kBlockPts + 1];
+  __shared__ float sx[kBasisBlk][kBlockPts + 1];
+  __shared__ float cp[kBasisBlk], cx[kBasisBlk], rawx[kBasisBlk];
+  const int64_t t = t0 + blockIdx.x;
+  const int64_t g = tile_block(L, g0, G.nblocks, t);
+  const int p = L.blk_idx[t];
+  const int i = threadIdx.x;
+  const int64_t pt = g * kBlockPts + i;
+  const float c = pscale[pt], cinv = 1.f / c;
+  const float a = (float)xcoef[pt * 4], bx = (float)xcoef[pt * 4 + 1], by = (float)xcoef[pt * 4 + 2],
+              bz = (float)xcoef[pt * 4 + 3];
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) sp[nu][i] = sx[nu][i] = 0.f;
+  const float4 pr = G.prel[pt];
+  for_block_functions<float, GRAD>(
+      B, p, pr.x, pr.y, pr.z,
+      [&](int nu, float v, float dx, float dy, float dz) {
+        float x = a * v;
+        if (GRAD) x = fmaf(bx, dx, fmaf(by, dy, fmaf(bz, dz, x)));
+        sp[nu][i] = v * c;
+        sx[nu][i] = x * cinv;
+      },
+      G.anchor[g]);
+  __syncthreads();
+  column_scales(sp, cp, nullptr);
+  column_scales(sx, cx, rawx);
+  __syncthreads();
+  float v[kBasisBlk];
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sp[nu][i] / cp[nu];
+  store_sliced_row<NS>(out_phi + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sx[nu][i] / cx[nu];
+  store_sliced_row<NS>(out_x + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
+  if (i < kBasisBlk) {
+    phi_scale[(t - t0) * kBasisBlk + i] = cp[i];
+    x_scale[(t - t0) * kBasisBlk + i] = cx[i];
+  }
+  // x_gq = max |X| over the tile, with X = X~ c_i
+  float mx = 0.f;
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) mx = fmaxf(mx, fabsf(sx[nu][i]) * c);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((i & 31) == 0) rawx[i >> 5] = mx;
+  __syncthreads();
+  if (i == 0) xmax[t] = (double)fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
+}
+
+template <int NS>
+static kldi_status x_ns(const kldi_plan* P, const Batch& b, cudaStream_t s) {
+  const int64_t n = b.t1 - b.t0;
+  if (n == 0) return KLDI_OK;
+  uint8_t* op = reinterpret_cast<uint8_t*>(P->d_phic_s);
+  uint8_t* ox = reinterpret_cast<uint8_t*>(P->d_x_s);
+  if (P->gga)
+    k_x_split<NS, true><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                          b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
+                                                          P->d_x_scale, P->d_xmax);
+  else
+    k_x_split<NS, false><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                           b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
+                                                           P->d_x_scale, P->d_xmax);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s) {
+  return P->prec == KLDI_BF16X6 ? x_ns<3>(P, b, s) : x_ns<2>(P, b, s);
+}
+
+// ---------------------------------------------------------------------------
+// MMA issue of one K = 16 step for all slice products of levels < NS.
+template <int NS>
+__device__ __forceinline__ void issue_levels(uint32_t d0, uint32_t lstride, const uint64_t* a, const uint64_t* b,
+                                             uint32_t idesc, uint32_t* started) {
+#pragma unroll
+  for (int l = 0; l < NS; ++l) {
+#pragma unroll
+    for (int i = 0; i <= l; ++i) {
+      mma_f16(d0 + l * lstride, a[i], b[l - i], idesc, started[l]);
+      started[l] = 1;
+    }
+  }
+}
+
+// Density product.  192 threads: warp 0 = bulk-copy producer, warp 1 = TMEM
+// owner and MMA issuer, warps 2..5 = epilogue (TMEM lane quarter = warp % 4).
+template <int NS>
+struct RhoCfg {
+  static constexpr int kNQ = 4;                                   // q blocks per N tile (N = 128)
+  static constexpr int kBufCols = NS * 128;                       // NS level accumulators
+  static constexpr int kBufs = 512 / (NS == 2 ? 256 : 512);       // 2 buffers (NS = 2) or 1 (NS = 3)
+  static constexpr int kStageBytes = NS * kPlaneBytes + NS * kNQ * kDPlane;
+  static constexpr int kStages = NS == 2 ? 5 : 4;
+  static constexpr int kOffR = kStages * kStageBytes;
+  static constexpr int kOffMask = kOffR + kBasisBlk * kBlockPts * 4;
+  static constexpr int kOffList = kOffMask + kMaxRet * (kMaxRet / 32) * 4;
+  static constexpr int kOffBar = kOffList + kMaxRet * 4;
+  static constexpr int kSmem = kOffBar + 256 + 1024;
+  static constexpr int kSegChunks = 8;                            // 8 x 32 = 256 K per exact accumulation
+};
+
+template <int NS, bool GRAD>
+__global__ void __launch_bounds__(192, 1)
+    k_rho_tc(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0, const uint8_t* __restrict__ phi,
+             const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero, const double* __restrict__ dmax,
+             const float* __restrict__ dscale, const float* __restrict__ rowscale, double t_b, double t_d,
+             double* rho, double* grad, int* err) {
+  using C = RhoCfg<NS>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* Rs = reinterpret_cast<float*>(sm + C::kOffR);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(sm + C::kOffMask);
+  int32_t* plist = reinterpret_cast<int32_t*>(sm + C::kOffList);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kOffBar);
+  uint64_t* empty = full + C::kStages;
+  uint64_t* tfull = empty + C::kStages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = g0 + blockIdx.x;
+  const int tb = L.blk_ptr[g];
+  const int n = L.blk_ptr[g + 1] - tb;
+  if (n > kMaxRet) {
+    if (threadIdx.x == 0) atomicCAS(err, 0, 101);
+    return;
+  }
+  const int nwords = (n + 31) >> 5;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) plist[k] = L.blk_idx[tb + k];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  // executed pairs E1_g: one ballot per 32 (jp, jq) predicates
+  for (int wi = warp; wi < n * nwords; wi += 6) {
+    const int jp = wi / nwords, w = wi % nwords;
+    const int jq = w * 32 + lane;
+    bool pred = false;
+    if (jq < n) {
+      const double dm = dmax[plist[jp] * L.nbb + plist[jq]];
+      pred = dm >= t_b && L.bmax[tb + jp] * dm * L.bmax[tb + jq] >= t_d;
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, pred);
+    if (lane == 0) mask[jp * nwords + w] = word;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tmem_slot;
+  const int ntile = (n + C::kNQ - 1) / C::kNQ;
+  auto tile_bits = [&](int jp, int q0, int nq) -> uint32_t {
+    return (mask[jp * nwords + (q0 >> 5)] >> (q0 & 31)) & ((1u << nq) - 1u);
+  };
+  // number of exact-accumulation segments of N tile nt (>= 1; an empty tile has one empty segment)
+  auto nsegs = [&](int q0, int nq) -> int {
+    int c = 0;
+    for (int jp = 0; jp < n; ++jp) c += tile_bits(jp, q0, nq) != 0;
+    return c == 0 ? 1 : (c + C::kSegChunks - 1) / C::kSegChunks;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int nt = 0; nt < ntile && !*abort_flag; ++nt) {
+        const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+        for (int jp = 0; jp < n; ++jp) {
+          const uint32_t bits = tile_bits(jp, q0, nq);
+          if (!bits) continue;
+          const int s = it % C::kStages;
+          const uint32_t ph = (it / C::kStages) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, 111)) break;
+          uint8_t* st = sm + s * C::kStageBytes;
+          mbar_arrive_expect_tx(&full[s], NS * kPlaneBytes + NS * nq * kDPlane);
+          const uint8_t* src = phi + (int64_t)(tb + jp - t0) * tile_bytes(NS);
+#pragma unroll
+          for (int l = 0; l < NS; ++l) bulk_g2s(st + l * kPlaneBytes, src + l * kPlaneBytes, kPlaneBytes, &full[s]);
+          uint8_t* bb = st + NS * kPlaneBytes;
+          for (int k = 0; k < nq; ++k) {
+            const bool on = (bits >> k) & 1u;
+            const uint8_t* d = dsplit + ((int64_t)plist[jp] * L.nbb + plist[q0 + k]) * (NS * kDPlane);
+#pragma unroll
+            for (int l = 0; l < NS; ++l)
+              bulk_g2s(bb + l * (C::kNQ * kDPlane) + k * kDPlane, on ? d + l * kDPlane : zero, kDPlane, &full[s]);
+          }
+          ++it;
+        }
+      }
+      for (uint32_t k = (it > (uint32_t)C::kStages ? it - C::kStages : 0); k < it; ++k) {
+        volatile int no_abort = 0;
+        mbar_wait(&full[k % C::kStages], (k / C::kStages) & 1, &no_abort, nullptr, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t it = 0, job = 0;
+      bool ok = true;
+      for (int nt = 0; nt < ntile && ok && !*abort_flag; ++nt) {
+        const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+        const uint32_t idesc = instr_desc(128, 32 * nq, 1, 0, 0);
+        int jp = 0;
+        const int ns = nsegs(q0, nq);
+        for (int sg = 0; sg < ns && ok; ++sg, ++job) {
+          const int buf = job % C::kBufs;
+          const uint32_t use = job / C::kBufs;
+          if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, err, 112)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d0 = tbase + buf * C::kBufCols;
+          uint32_t started[NS];
+#pragma unroll
+          for (int l = 0; l < NS; ++l) started[l] = 0;
+          int taken = 0;
+          for (; jp < n && taken < C::kSegChunks; ++jp) {
+            if (!tile_bits(jp, q0, nq)) continue;
+            const int s = it % C::kStages;
+            const uint32_t ph = (it / C::kStages) & 1;
+            if (!mbar_wait(&full[s], ph, abort_flag, err, 113)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a = smem_u32(sm + s * C::kStageBytes);
+            const uint32_t bsm = a + NS * kPlaneBytes;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              uint64_t ad[NS], bd[NS];
+#pragma unroll
+              for (int l = 0; l < NS; ++l) {
+                ad[l] = smem_desc(a + l * kPlaneBytes + k * 32, 16, 512, kSwz64);
+                bd[l] = smem_desc(bsm + l * (C::kNQ * kDPlane) + k * 32, 16, 512, kSwz64);
+              }
+              issue_levels<NS>(d0, 128, ad, bd, idesc, started);
+            }
+            mma_commit(&empty[s]);
+            ++it;
+            ++taken;
+          }
+          if (!ok) break;
+          mma_commit(&tfull[buf]);
+        }
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else {
+    // epilogue: point i = TMEM lane
+    const int quarter = warp & 3;
+    const int i = quarter * 32 + lane;
+    const int64_t pt = g * kBlockPts + i;
+    const float4 prl = G.prel[pt];
+    const float px = prl.x, py = prl.y, pz = prl.z;
+    const int anc = G.anchor[g];
+    const double rsc = (double)rowscale[pt];
+    double r_i = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    uint32_t job = 0;
+    bool ok = true;
+    for (int nt = 0; nt < ntile && ok; ++nt) {
+      const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+      const int ns = nsegs(q0, nq);
+      bool work = false;
+      for (int jp = 0; jp < n && !work; ++jp) work = tile_bits(jp, q0, nq) != 0;
+      float R[C::kNQ][32];
+#pragma unroll
+      for (int k = 0; k < C::kNQ; ++k)
+#pragma unroll
+        for (int c = 0; c < 32; ++c) R[k][c] = 0.f;
+      for (int sg = 0; sg < ns; ++sg, ++job) {
+        const int buf = job % C::kBufs;
+        const uint32_t use = job / C::kBufs;
+        if (!mbar_wait_warp(&tfull[buf], use & 1, abort_flag, err, 114)) { ok = false; break; }
+        tc_fence_after();
+        if (work) {
+#pragma unroll
+          for (int k = 0; k < C::kNQ; ++k) {
+            if (k < nq) {
+              float acc[32];
+#pragma unroll
+              for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+#pragma unroll
+              for (int l = NS - 1; l >= 0; --l) {  // smallest level first
+                float lv[32];
+                tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + l * 128 + k * 32, lv);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) acc[c] += lv[c];
+              }
+#pragma unroll
+              for (int c = 0; c < 32; ++c) R[k][c] += acc[c];
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+      }
+      if (!ok) break;
+      // row-dot with this tile's functions: R_i,nu = e_i f_nu R[k][c]
+#pragma unroll
+      for (int k = 0; k < C::kNQ; ++k) {
+        if (k >= nq) continue;
+        const int q = plist[q0 + k];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[k][c] * dscale[q * kBasisBlk + c];
+        float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
+        for_block_functions<float, GRAD>(
+            B, q, px, py, pz,
+            [&](int nu, float v, float dx, float dy, float dz) {
+              const float rr = Rs[nu * kBlockPts + i];
+              pr = fmaf(v, rr, pr);
+              if (GRAD) {
+                px_ = fmaf(dx, rr, px_);
+                py_ = fmaf(dy, rr, py_);
+                pz_ = fmaf(dz, rr, pz_);
+              }
+            },
+            anc);
+        r_i += rsc * (double)pr;
+        if (GRAD) {
+          gx += 2.0 * rsc * (double)px_;
+          gy += 2.0 * rsc * (double)py_;
+          gz += 2.0 * rsc * (double)pz_;
+        }
+      }
+    }
+    rho[pt] = r_i;
+    if (GRAD) {
+      grad[pt * 3] = gx;
+      grad[pt * 3 + 1] = gy;
+      grad[pt * 3 + 2] = gz;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+template <int NS>
+static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, double* grad_out, cudaStream_t s) {
+  using C = RhoCfg<NS>;
+  const int64_t n = b.g1 - b.g0;
+  if (n == 0) return KLDI_OK;
+  static bool attr = false;
+  if (!attr) {
+    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+    attr = true;
+  }
+  const uint8_t* phi = reinterpret_cast<const uint8_t*>(P->d_phi_s);
+  const uint8_t* ds = reinterpret_cast<const uint8_t*>(P->d_dsplit);
+  const uint8_t* z = reinterpret_cast<const uint8_t*>(P->d_zero);
+  if (P->gga)
+    k_rho_tc<NS, true><<<(unsigned)n, 192, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                          b.t0, phi, ds, z, P->d_dmax, P->d_dscale, P->d_rowscale,
+                                                          P->opt.t_b, P->opt.t_d, rho_out, grad_out, P->d_err);
+  else
+    k_rho_tc<NS, false><<<(unsigned)n, 192, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                           b.t0, phi, ds, z, P->d_dmax, P->d_dscale, P->d_rowscale,
+                                                           P->opt.t_b, P->opt.t_d, rho_out, grad_out, P->d_err);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho_out, double* grad_out, cudaStream_t s) {
+  return P->prec == KLDI_BF16X6 ? rho_ns<3>(P, b, rho_out, grad_out, s) : rho_ns<2>(P, b, rho_out, grad_out, s);
+}
+
+// ---------------------------------------------------------------------------
+// W = Phi^T X over one 128 x 128 tile pair (P, Q) of the full square.
+// 320 threads: warp 0 producer, warp 1 TMEM owner + MMA, warps 2..9 epilogue
+// (lane quarter = warp % 4, column half = (warp - 2) / 4).
+template <int NS>
+struct WCfg {
+  static constexpr int kChunk = 2048;                   // 32 points x 64 B of one plane of one tile
+  static constexpr int kOp = 4 * kChunk;                // 4 tiles (128 functions) of one plane
+  static constexpr int kStageBytes = 2 * NS * kOp;      // A planes then B planes
+  static constexpr int kStages = 4;
+  static constexpr int kOffBar = kStages * kStageBytes;
+  static constexpr int kSmem = kOffBar + 256 + 1024;
+  static constexpr int kThreads = 320;
+};
+
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  const float e = (s - (t - bp)) + (x - bp);
+  s = t;
+  c += e;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(320, 1)
+    k_w_tc(ListView L, const VWorkTC* __restrict__ work, const int32_t* __restrict__ glist, int64_t t0,
+           const uint8_t* __restrict__ phic, const float* __restrict__ phic_scale, const uint8_t* __restrict__ xs,
+           const float* __restrict__ x_scale, const double* __restrict__ xmax, const uint8_t* __restrict__ zero,
+           int nbf, double t_b, double* W, int* err) {
+  using C = WCfg<NS>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kOffBar);
+  uint64_t* empty = full + C::kStages;
+  uint64_t* tfull = empty + C::kStages;
+  uint64_t* tempty = tfull + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const VWorkTC wk = work[blockIdx.x];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 8);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tmem_slot;
+  const int nblk = wk.end - wk.beg;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int c = 0; c < nblk * 4 && !*abort_flag; ++c) {
+        const int64_t gb = glist[wk.beg + c / 4];
+        const int kc = c & 3;
+        const int s = it % C::kStages;
+        const uint32_t ph = (it / C::kStages) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, 121)) break;
+        uint8_t* st = sm + s * C::kStageBytes;
+        mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+        for (int side = 0; side < 2; ++side) {
+          const int T = side == 0 ? wk.P : wk.Q;
+          for (int j = 0; j < 4; ++j) {
+            const int p = T * 4 + j;
+            const uint8_t* src = nullptr;
+            if (p < L.nbb) {
+              const int t = L.tile_of[gb * L.nbb + p];
+              if (t >= 0 && (side == 0 || xmax[t] >= t_b))
+                src = (side == 0 ? phic : xs) + (int64_t)(t - t0) * tile_bytes(NS) + kc * C::kChunk;
+            }
+#pragma unroll
+            for (int l = 0; l < NS; ++l)
+              bulk_g2s(st + (side * NS + l) * C::kOp + j * C::kChunk, src ? src + l * kPlaneBytes : zero, C::kChunk,
+                       &full[s]);
+          }
+        }
+        ++it;
+      }
+      for (uint32_t k = (it > (uint32_t)C::kStages ? it - C::kStages : 0); k < it; ++k) {
+        volatile int no_abort = 0;
+        mbar_wait(&full[k % C::kStages], (k / C::kStages) & 1, &no_abort, nullptr, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(128, 128, 1, 1, 1);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int e = 0; e < nblk && ok; ++e) {
+        if (!mbar_wait(tempty, (e & 1) ^ 1, abort_flag, err, 124)) { ok = false; break; }
+        tc_fence_after();
+        uint32_t started[NS];
+#pragma unroll
+        for (int l = 0; l < NS; ++l) started[l] = 0;
+        for (int kc = 0; kc < 4; ++kc) {
+          const int s = it % C::kStages;
+          const uint32_t ph = (it / C::kStages) & 1;
+          if (!mbar_wait(&full[s], ph, abort_flag, err, 122)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a = smem_u32(sm + s * C::kStageBytes);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            uint64_t ad[NS], bd[NS];
+#pragma unroll
+            for (int l = 0; l < NS; ++l) {
+              ad[l] = smem_desc(a + l * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
+              bd[l] = smem_desc(a + (NS + l) * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
+            }
+            issue_levels<NS>(tbase, 128, ad, bd, idesc, started);
+          }
+          mma_commit(&empty[s]);
+          ++it;
+        }
+        if (!ok) break;
+        mma_commit(tfull);
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else {
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int m = quarter * 32 + lane;       // row inside the tile (function of P)
+    float S[64], Cc[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) S[c] = Cc[c] = 0.f;
+    for (int e = 0; e < nblk; ++e) {
+      const int64_t gb = glist[wk.beg + e];
+      // scales: row (Phi tile of P, function m), columns (X tiles of Q)
+      const int pr = wk.P * 4 + (m >> 5);
+      float rsc = 0.f;
+      if (pr < L.nbb) {
+        const int t = L.tile_of[gb * L.nbb + pr];
+        if (t >= 0) rsc = phic_scale[(int64_t)(t - t0) * kBasisBlk + (m & 31)];
+      }
+      if (!mbar_wait_warp(tfull, e & 1, abort_flag, err, 123)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const int qb = wk.Q * 4 + half * 2 + cc;
+        float csc = 0.f;
+        if (qb < L.nbb) {
+          const int t = L.tile_of[gb * L.nbb + qb];
+          if (t >= 0) csc = x_scale[(int64_t)(t - t0) * kBasisBlk + lane];
+        }
+        float acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+#pragma unroll
+        for (int l = NS - 1; l >= 0; --l) {
+          float lv[32];
+          tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + l * 128 + half * 64 + cc * 32, lv);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[c] += lv[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float sc = rsc * __shfl_sync(0xffffffffu, csc, c);
+          two_sum_acc(S[cc * 32 + c], Cc[cc * 32 + c], acc[c] * sc);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+    }
+    const int r = wk.P * 128 + m;
+    if (r < nbf) {
+#pragma unroll
+      for (int c = 0; c < 64; ++c) {
+        const int col = wk.Q * 128 + half * 64 + c;
+        if (col < nbf) atomicAdd(&W[(int64_t)r * nbf + col], (double)S[c] + (double)Cc[c]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+template <int NS>
+static kldi_status w_ns(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
+  using C = WCfg<NS>;
+  if (b.n_vtc_work == 0) return KLDI_OK;
+  static bool attr = false;
+  if (!attr) {
+    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_w_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+    attr = true;
+  }
+  k_w_tc<NS><<<(unsigned)b.n_vtc_work, C::kThreads, C::kSmem, s>>>(
+      P->list_view(), b.d_vtc_work, b.d_vtc_g, b.t0, reinterpret_cast<const uint8_t*>(P->d_phic_s), P->d_phic_scale,
+      reinterpret_cast<const uint8_t*>(P->d_x_s), P->d_x_scale, P->d_xmax, reinterpret_cast<const uint8_t*>(P->d_zero),
+      (int)P->nbf, P->opt.t_b, V, P->d_err);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
+  return P->prec == KLDI_BF16X6 ? w_ns<3>(P, b, V, s) : w_ns<2>(P, b, V, s);
+}
+
+// V = W + W^T (the tensor-core path accumulates the full square of W = Phi^T X).
+__global__ void k_symm(double* V, int nbf) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nbf * nbf) return;
+  const int r = (int)(idx / nbf), c = (int)(idx % nbf);
+  if (r > c) return;
+  const double v = V[idx] + V[(int64_t)c * nbf + r];
+  V[idx] = v;
+  V[(int64_t)c * nbf + r] = v;
+}
+
+kldi_status launch_symm(const kldi_plan* P, double* V, cudaStream_t s) {
+  const int64_t n = P->nbf * P->nbf;
+  k_symm<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, (int)P->nbf);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+}  // namespace kldi

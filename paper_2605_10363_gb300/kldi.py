@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libkldi (include/kldi.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  The functions carry the C names without the
+``kldi_`` prefix.  Arrays may be numpy arrays (host) or torch tensors (host or
+CUDA); the library detects device pointers itself.  Importing this module
+raises if the library has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkldi.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+XC = {"lda_x": 1, "pbe": 2, "mlp": 3}
+PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "bf16x6": 3}
+STAGES = ("dprep", "phi", "rho", "xc", "x", "v", "finish")
+NSTAGES = len(STAGES)
+
+
+class KldiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"kldi status {status}: {msg}")
+        self.status = status
+
+
+class Molecule(C.Structure):
+    _fields_ = [("natm", C.c_int), ("Z", C.POINTER(C.c_int32)), ("xyz", C.POINTER(C.c_double))]
+
+
+class Basis(C.Structure):
+    _fields_ = [("nshell", C.c_int), ("atom", C.POINTER(C.c_int32)), ("l", C.POINTER(C.c_int32)),
+                ("nprim", C.POINTER(C.c_int32)), ("exps", C.POINTER(C.c_double)),
+                ("coefs", C.POINTER(C.c_double))]
+
+
+class GridSpec(C.Structure):
+    _fields_ = [("nrad", C.c_int), ("nregions", C.c_int), ("ntheta", C.POINTER(C.c_int32)), ("block", C.c_int)]
+
+
+class Options(C.Structure):
+    _fields_ = [("t_b", C.c_double), ("t_d", C.c_double), ("rho_min", C.c_double), ("prec", C.c_int),
+                ("xc", C.c_int), ("stream", C.c_void_p)]
+
+
+class PlanStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("nbf", "nbasis_blocks", "npoints", "nblocks", "retained",
+                                          "pair_slots", "vtile_work", "workspace_bytes")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libkldi.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
+    sig = {
+        "kldi_make_grid": (C.c_int, [C.POINTER(Molecule), C.POINTER(GridSpec), C.POINTER(vp)]),
+        "kldi_grid_info": (C.c_int, [vp, i64p, i64p, i64p]),
+        "kldi_grid_export": (C.c_int, [vp, vp, vp, vp]),
+        "kldi_screen": (C.c_int, [vp, C.POINTER(Molecule), C.POINTER(Basis), C.POINTER(Options), C.POINTER(vp)]),
+        "kldi_plan_info": (C.c_int, [vp, C.POINTER(PlanStats)]),
+        "kldi_plan_export_lists": (C.c_int, [vp, vp, vp, vp]),
+        "kldi_density": (C.c_int, [vp, vp, vp, vp]),
+        "kldi_vxc": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
+        "kldi_exc": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+        "kldi_exc_batched": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), vp]),
+        "kldi_plan_set_precision": (C.c_int, [vp, C.c_int]),
+        "kldi_plan_profile": (C.c_int, [vp, C.c_int]),
+        "kldi_plan_stage_times": (C.c_int, [vp, vp, vp]),
+        "kldi_plan_free": (None, [vp]),
+        "kldi_grid_free": (None, [vp]),
+        "kldi_last_error": (C.c_char_p, []),
+        "kldi_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def _check(status):
+    if status != OK:
+        raise KldiError(status, LIB.kldi_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+class Grid:
+    """Owning handle of a kldi_grid."""
+
+    def __init__(self, handle):
+        self.h = C.c_void_p(handle)
+        n, r, b = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(LIB.kldi_grid_info(self.h, C.byref(n), C.byref(r), C.byref(b)))
+        self.npoints, self.nreal, self.nblocks = n.value, r.value, b.value
+
+    def export(self):
+        xyz = np.empty((self.npoints, 3))
+        w = np.empty(self.npoints)
+        atom = np.empty(self.npoints, np.int32)
+        _check(LIB.kldi_grid_export(self.h, _ptr(xyz), _ptr(w), _ptr(atom)))
+        return xyz, w, atom
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            LIB.kldi_grid_free(self.h)
+            self.h = None
+
+
+def _molecule(Z, xyz):
+    Z = np.ascontiguousarray(Z, np.int32)
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    m = Molecule(len(Z), Z.ctypes.data_as(C.POINTER(C.c_int32)), xyz.ctypes.data_as(C.POINTER(C.c_double)))
+    return m, (Z, xyz)
+
+
+def make_grid(Z, xyz, nrad, ntheta, block=128) -> Grid:
+    m, keep = _molecule(Z, xyz)
+    nt = np.ascontiguousarray(ntheta, np.int32)
+    spec = GridSpec(int(nrad), len(nt), nt.ctypes.data_as(C.POINTER(C.c_int32)), int(block))
+    h = C.c_void_p()
+    _check(LIB.kldi_make_grid(C.byref(m), C.byref(spec), C.byref(h)))
+    return Grid(h.value)
+
+
+class Plan:
+    """Owning handle of a kldi_plan (the grid is kept alive with it)."""
+
+    def __init__(self, handle, grid, keep):
+        self.h = C.c_void_p(handle)
+        self.grid = grid
+        self._keep = keep
+        s = PlanStats()
+        _check(LIB.kldi_plan_info(self.h, C.byref(s)))
+        self.stats = {n: getattr(s, n) for n, _ in PlanStats._fields_}
+        self.nbf = self.stats["nbf"]
+        self.npoints = self.stats["npoints"]
+
+    def lists(self):
+        nblk = self.stats["nblocks"]
+        nt = self.stats["retained"]
+        ptr = np.empty(nblk + 1, np.int32)
+        idx = np.empty(nt, np.int32)
+        b = np.empty(nt)
+        _check(LIB.kldi_plan_export_lists(self.h, _ptr(ptr), _ptr(idx), _ptr(b)))
+        return ptr, idx, b
+
+    def profile(self, enable=True):
+        _check(LIB.kldi_plan_profile(self.h, int(enable)))
+
+    def stage_times(self):
+        """(ms[7], launches[7]) per stage since profile(True)."""
+        ms = np.zeros(NSTAGES)
+        n = np.zeros(NSTAGES, np.int64)
+        _check(LIB.kldi_plan_stage_times(self.h, _ptr(ms), _ptr(n)))
+        return ms, n
+
+    def set_precision(self, prec):
+        _check(LIB.kldi_plan_set_precision(self.h, PREC[prec] if isinstance(prec, str) else int(prec)))
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            LIB.kldi_plan_free(self.h)
+            self.h = None
+
+
+def screen(grid: Grid, Z, xyz, shells_atom, shells_l, shells_nprim, exps, coefs, t_b, t_d,
+           rho_min=1e-14, prec="bf16x3", xc="pbe", stream=0) -> Plan:
+    m, keepm = _molecule(Z, xyz)
+    arrs = [np.ascontiguousarray(a, np.int32) for a in (shells_atom, shells_l, shells_nprim)]
+    ex = np.ascontiguousarray(exps, np.float64)
+    co = np.ascontiguousarray(coefs, np.float64)
+    b = Basis(len(arrs[0]), *[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs],
+              ex.ctypes.data_as(C.POINTER(C.c_double)), co.ctypes.data_as(C.POINTER(C.c_double)))
+    opt = Options(float(t_b), float(t_d), float(rho_min), PREC[prec] if isinstance(prec, str) else int(prec),
+                  XC[xc] if isinstance(xc, str) else int(xc), C.c_void_p(int(stream)))
+    h = C.c_void_p()
+    _check(LIB.kldi_screen(grid.h, C.byref(m), C.byref(b), C.byref(opt), C.byref(h)))
+    return Plan(h.value, grid, (keepm, arrs, ex, co))
+
+
+def density(plan: Plan, D, rho, grad=None):
+    _check(LIB.kldi_density(plan.h, _ptr(D), _ptr(rho), _ptr(grad)))
+
+
+def vxc(plan: Plan, xc, rho, grad, V, Exc):
+    _check(LIB.kldi_vxc(plan.h, XC[xc] if isinstance(xc, str) else int(xc), _ptr(rho), _ptr(grad), _ptr(V),
+                        _ptr(Exc)))
+
+
+def exc(plan: Plan, xc, D, V, Exc):
+    _check(LIB.kldi_exc(plan.h, XC[xc] if isinstance(xc, str) else int(xc), _ptr(D), _ptr(V), _ptr(Exc)))
+
+
+def exc_batched(plans, xc, Ds, Vs, Exc):
+    n = len(plans)
+    ph = (C.c_void_p * n)(*[p.h.value for p in plans])
+    dh = (C.c_void_p * n)(*[_ptr(d) for d in Ds])
+    vh = (C.c_void_p * n)(*[_ptr(v) for v in Vs])
+    _check(LIB.kldi_exc_batched(ph, n, XC[xc] if isinstance(xc, str) else int(xc), dh, vh, _ptr(Exc)))
+
+
+def version() -> str:
+    return LIB.kldi_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# convenience: build grid + plan for a ``synth.System``
+def plan_for_system(system, prec="bf16x3", xc=None, stream=0, rho_min=1e-14):
+    g = make_grid(system.Z, system.xyz, system.grid.nrad, system.grid.ntheta, system.grid.block)
+    b = system.basis
+    return screen(g, system.Z, system.xyz, b.atom, b.l, b.nprim, b.exps, b.coefs, system.t_b, system.t_d,
+                  rho_min=rho_min, prec=prec, xc=xc or system.xc, stream=stream)
