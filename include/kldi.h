@@ -211,6 +211,24 @@ kldi_status kldi_plan_profile(kldi_plan* plan, int enable);
  * pointer may be NULL.  Host buffers. */
 kldi_status kldi_plan_stage_times(kldi_plan* plan, double* ms, int64_t* launches);
 
+/* E_xc = sum_i w_i f(rho_i, sigma_i) of a density already on the device, for
+ * callers that must not allocate device memory.  The paper has no
+ * counterpart: this is an interface addition.  Callers that cannot allocate
+ * include code running while a stream is captured into a CUDA graph (an
+ * allocation cannot be captured), hosts that reserve all device memory up
+ * front, and allocator callbacks that must not re-enter the allocator.
+ *   xc: KLDI_XC_LDA_X or KLDI_XC_PBE; npoints points; rho[npoints],
+ *   grad[npoints*3] (PBE only, may be NULL for LDA), w[npoints]: device
+ *   arrays, FP64; points with rho < rho_min contribute nothing; Exc: one
+ *   device double, written; stream: a cudaStream_t or NULL.
+ * The per-block partial sums live in a fixed device array of 65536 slots, so
+ * npoints may be at most 8,388,608 (KLDI_EINVAL beyond, and for host
+ * pointers).  Allocates nothing and returns after enqueueing.  The first call
+ * on a device resolves the array's address; make it outside stream capture.
+ * Calls whose work overlaps on one GPU share the array and race. */
+kldi_status kldi_exc_energy_noalloc(int xc, int64_t npoints, const double* rho, const double* grad,
+                                    const double* w, double rho_min, double* Exc, void* stream);
+
 /* Switch the product arithmetic of an existing plan (kldi_prec). */
 kldi_status kldi_plan_set_precision(kldi_plan* plan, int prec);
 

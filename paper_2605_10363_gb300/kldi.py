@@ -72,6 +72,7 @@ def _load():
         "kldi_plan_set_precision": (C.c_int, [vp, C.c_int]),
         "kldi_plan_profile": (C.c_int, [vp, C.c_int]),
         "kldi_plan_stage_times": (C.c_int, [vp, vp, vp]),
+        "kldi_exc_energy_noalloc": (C.c_int, [C.c_int, C.c_int64, vp, vp, vp, C.c_double, vp, vp]),
         "kldi_plan_free": (None, [vp]),
         "kldi_grid_free": (None, [vp]),
         "kldi_last_error": (C.c_char_p, []),
@@ -218,6 +219,12 @@ def exc_batched(plans, xc, Ds, Vs, Exc):
     dh = (C.c_void_p * n)(*[_ptr(d) for d in Ds])
     vh = (C.c_void_p * n)(*[_ptr(v) for v in Vs])
     _check(LIB.kldi_exc_batched(ph, n, XC[xc] if isinstance(xc, str) else int(xc), dh, vh, _ptr(Exc)))
+
+
+def exc_energy_noalloc(xc, npoints, rho, grad, w, Exc, rho_min=1e-14, stream=0):
+    """E_xc of a device-resident density with no allocation (kldi_exc_energy_noalloc)."""
+    _check(LIB.kldi_exc_energy_noalloc(XC[xc] if isinstance(xc, str) else int(xc), int(npoints), _ptr(rho),
+                                       _ptr(grad), _ptr(w), float(rho_min), _ptr(Exc), C.c_void_p(int(stream))))
 
 
 def version() -> str:
