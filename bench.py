@@ -282,9 +282,9 @@ def main():
         peak, peak_src = 1700.0, "fallback (bf16 sustained)"
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_rho_tc" if dom == "rho" else "k_w_tc", "peak_source": peak_src,
+            "traffic": None, "kernel": "k_rho_tc" if dom == "rho" else "k_v_tc", "peak_source": peak_src,
             "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
-            "other_kernel": {"kernel": "k_w_tc" if dom == "rho" else "k_rho_tc",
+            "other_kernel": {"kernel": "k_v_tc" if dom == "rho" else "k_rho_tc",
                              "achieved": (f_v if dom == "rho" else f_rho) /
                              ((stage_ms[5] if dom == "rho" else stage_ms[2]) / max(1, stage_n[5] if dom == "rho"
                                                                                    else stage_n[2]) * 1e-3) / 1e12}}

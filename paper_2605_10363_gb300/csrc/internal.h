@@ -91,9 +91,8 @@ struct VWork64 {
   int32_t beg, end;
 };
 
-// Work item of the tensor-core V product: one 128 x 128 tile pair (P, Q) of
-// the full square W = Phi^T X (units of 4 basis blocks) over grid blocks
-// list_g[beg, end).
+// Work item of the tensor-core V product: one 128 x 128 tile pair P <= Q
+// (units of 4 basis blocks) over grid blocks list_g[beg, end).
 struct VWorkTC {
   int32_t P, Q;
   int32_t beg, end;
@@ -124,6 +123,7 @@ struct kldi_plan {
   int prec = KLDI_FP64;
   cudaStream_t stream = nullptr;
   int device = 0;
+  int num_sms = 148;
   int64_t nbf = 0, nbb = 0, nbf_pad = 0, npoints = 0, nblocks = 0, ntiles = 0, nshell = 0, nprim_total = 0;
   int64_t nvt = 0;  // W tiles per edge (ceil(nbb / 4))
   int* d_err = nullptr;         // device error word (bounded-wait timeouts)
@@ -213,6 +213,5 @@ kldi_status launch_phi_split(const kldi_plan* P, const Batch& b, cudaStream_t s)
 kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho, double* grad, cudaStream_t s);
 kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
-kldi_status launch_symm(const kldi_plan* P, double* V, cudaStream_t s);
 
 }  // namespace kldi

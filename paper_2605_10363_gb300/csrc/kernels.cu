@@ -251,9 +251,11 @@ __global__ void k_xc(GridView G, int64_t g0, int xc, double rho_min, const doubl
   xcoef[pt * 4 + 3] = bz;
   if (pscale) {
     // balance c_i = 2^round(log2(|a| + |b|) / 2): the V product uses Phi c and X / c,
-    // whose magnitudes are then alike at every point (X ~ (|a| + |b|) Phi)
+    // whose magnitudes are then alike at every point (X ~ (|a| + |b|) Phi).  A point
+    // with X = 0 (zero weight, rho below rho_min) adds nothing to Phi^T X: c_i = 0
+    // drops its Phi row too, so it cannot inflate a function's column maximum.
     const double m = fabs(a) + sqrt(bx * bx + by * by + bz * bz);
-    float c = 1.f;
+    float c = 0.f;
     if (m > 0.0) c = ldexpf(1.f, (int)lrint(0.5 * log2(m)));
     pscale[pt] = c;
   }
@@ -415,7 +417,6 @@ kldi_status launch_finish(const kldi_plan* P, double* V, double* exc, cudaStream
   k_esum<<<1, 1024, 0, s>>>(P->d_eblk, P->nblocks, exc);
   KLDI_TRY_CUDA(cudaGetLastError());
   if (V) {
-    if (P->prec != KLDI_FP64) return launch_symm(P, V, s);
     const int64_t n = P->nbf * P->nbf;
     k_mirror<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, (int)P->nbf);
     KLDI_TRY_CUDA(cudaGetLastError());

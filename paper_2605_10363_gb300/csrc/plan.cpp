@@ -158,6 +158,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   P->prec = opt->prec;
   P->stream = (cudaStream_t)opt->stream;
   cudaGetDevice(&P->device);
+  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
   auto fail = [&](kldi_status s) {
     free_plan_buffers(P);
     delete P;
@@ -414,7 +415,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     if ((st = upload(P, &b.d_v64_g, gl.data(), gl.size())) != KLDI_OK) return fail(st);
     if ((st = upload(P, &b.d_v64_work, wk.data(), wk.size())) != KLDI_OK) return fail(st);
     b.n_v64_work = (int64_t)wk.size();
-    // tensor cores: per W tile pair (P, Q) of the full square, 128-function tiles
+    // tensor cores: per V tile pair (P <= Q), 128-function tiles
     std::map<int64_t, std::vector<int32_t>> tl;
     const int64_t nvt = P->nvt;
     for (int64_t g = b.g0; g < b.g1; ++g) {
@@ -424,7 +425,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
         if (vt.empty() || vt.back() != T) vt.push_back(T);
       }
       for (size_t i = 0; i < vt.size(); ++i)
-        for (size_t j = 0; j < vt.size(); ++j) tl[(int64_t)vt[i] * nvt + vt[j]].push_back((int32_t)g);
+        for (size_t j = i; j < vt.size(); ++j) tl[(int64_t)vt[i] * nvt + vt[j]].push_back((int32_t)g);
     }
     std::vector<int32_t> tg;
     std::vector<VWorkTC> tw;

@@ -30,13 +30,17 @@
 //               (Eq. block_pair_filter), bulk-copy pipeline, tcgen05.mma
 //               M = 128 N = 128 per level, drains every <= 8 executed chunks
 //               (256 K), fused row-dot rho = sum Phi . R, grad rho.
-//  k_x_split    X tile = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi),
-//               sliced by function with its column maxima; x_gq = max |X|.
-//  k_w_tc       W = Phi^T X, one 128 x 128 tile pair (P, Q) of the full square
-//               over a segment of its grid-block list; one grid block
-//               (K = 128) per exact accumulation, drained into compensated FP32
-//               sums, FP64 scatter-add at the end.  V = W + W^T (k_symm).
+//  k_x_split    X tile = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi);
+//               Phi~ = c phi and X~ = X / c (per-point balance c), sliced per
+//               function with one shared column scale; x_gq = max |X|.
+//  k_v_tc       V = Phi^T X + X^T Phi, one 128 x 128 tile pair P <= Q over a
+//               segment of its grid-block list; one grid block per exact
+//               accumulation (K = 256: [Phi~ | X~] against [X~ ; Phi~]),
+//               drained into compensated FP32 sums, FP64 scatter-add; the
+//               lower block triangle is mirrored afterwards.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "basis.cuh"
 #include "internal.h"
@@ -261,8 +265,8 @@ __device__ __forceinline__ void column_scales(float (*st)[kBlockPts + 1], float*
 }
 
 // V-product operands of tile (g, p): Phi~ = c_i Phi and X~ = X / c_i with
-// X = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi), each sliced per
-// function with its own column scale.
+// X = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi), both sliced per
+// function with the larger of their two column maxima.
 template <int NS, bool GRAD>
 __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
                                                  const double* __restrict__ xcoef, const float* __restrict__ pscale,
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
   const int p = L.blk_idx[t];
   const int i = threadIdx.x;
   const int64_t pt = g * kBlockPts + i;
-  const float c = pscale[pt], cinv = 1.f / c;
+  const float c = pscale[pt], cinv = c > 0.f ? 1.f / c : 0.f;   // c = 0: X = 0 at this point
   const float a = (float)xcoef[pt * 4], bx = (float)xcoef[pt * 4 + 1], by = (float)xcoef[pt * 4 + 2],
               bz = (float)xcoef[pt * 4 + 3];
 #pragma unroll
@@ -295,16 +299,20 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
   column_scales(sp, cp, nullptr);
   column_scales(sx, cx, rawx);
   __syncthreads();
+  // one scale per function for Phi~ and X~: they meet in one exact chain
+  // (A = [Phi~ | X~], B = [X~ ; Phi~]); balancing keeps the two maxima alike
+  if (i < kBasisBlk) cp[i] = fmaxf(cp[i], cx[i]);
+  __syncthreads();
   float v[kBasisBlk];
 #pragma unroll
   for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sp[nu][i] / cp[nu];
   store_sliced_row<NS>(out_phi + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
 #pragma unroll
-  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sx[nu][i] / cx[nu];
+  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sx[nu][i] / cp[nu];
   store_sliced_row<NS>(out_x + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
   if (i < kBasisBlk) {
     phi_scale[(t - t0) * kBasisBlk + i] = cp[i];
-    x_scale[(t - t0) * kBasisBlk + i] = cx[i];
+    x_scale[(t - t0) * kBasisBlk + i] = cp[i];
   }
   // x_gq = max |X| over the tile, with X = X~ c_i
   float mx = 0.f;
@@ -354,52 +362,49 @@ __device__ __forceinline__ void issue_levels(uint32_t d0, uint32_t lstride, cons
   }
 }
 
-// Density product.  192 threads: warp 0 = bulk-copy producer, warp 1 = TMEM
-// owner and MMA issuer, warps 2..5 = epilogue (TMEM lane quarter = warp % 4).
+// Density product, persistent: one CTA per SM walks grid blocks g0 + c,
+// g0 + c + G, ...  320 threads: warp 0 = producer (all lanes build the next
+// block's retained list and executed-pair bit matrix with warp ballots into a
+// double-buffered shared-memory record; lane 0 issues the bulk copies),
+// warp 1 = TMEM owner and MMA issuer, warps 2..9 = epilogue (lane quarter =
+// warp % 4; the two warps of a quarter split each N tile's four basis blocks).
 template <int NS>
 struct RhoCfg {
   static constexpr int kNQ = 4;                                   // q blocks per N tile (N = 128)
   static constexpr int kBufCols = NS * 128;                       // NS level accumulators
-  static constexpr int kBufs = 512 / (NS == 2 ? 256 : 512);       // 2 buffers (NS = 2) or 1 (NS = 3)
+  static constexpr int kBufs = NS == 2 ? 2 : 1;
   static constexpr int kStageBytes = NS * kPlaneBytes + NS * kNQ * kDPlane;
-  static constexpr int kStages = NS == 2 ? 5 : 4;
-  static constexpr int kOffR = kStages * kStageBytes;
-  static constexpr int kOffMask = kOffR + kBasisBlk * kBlockPts * 4;
-  static constexpr int kOffList = kOffMask + kMaxRet * (kMaxRet / 32) * 4;
-  static constexpr int kOffBar = kOffList + kMaxRet * 4;
+  static constexpr int kStages = NS == 2 ? 4 : 3;
+  static constexpr int kOffR = kStages * kStageBytes;             // [2 halves][32][128] float
+  static constexpr int kMetaWords = 4 + kMaxRet + kMaxRet * (kMaxRet / 32);
+  static constexpr int kOffMeta = kOffR + 2 * kBasisBlk * kBlockPts * 4;
+  static constexpr int kOffBar = kOffMeta + 2 * kMetaWords * 4;
   static constexpr int kSmem = kOffBar + 256 + 1024;
   static constexpr int kSegChunks = 8;                            // 8 x 32 = 256 K per exact accumulation
+  static constexpr int kThreads = 320;
 };
 
 template <int NS, bool GRAD>
-__global__ void __launch_bounds__(192, 1)
-    k_rho_tc(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0, const uint8_t* __restrict__ phi,
-             const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero, const double* __restrict__ dmax,
-             const float* __restrict__ dscale, const float* __restrict__ rowscale, double t_b, double t_d,
-             double* rho, double* grad, int* err) {
+__global__ void __launch_bounds__(320, 1)
+    k_rho_tc(BasisView B, GridView G, ListView L, int64_t g0, int64_t g1, int64_t t0,
+             const uint8_t* __restrict__ phi, const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero,
+             const double* __restrict__ dmax, const float* __restrict__ dscale, const float* __restrict__ rowscale,
+             double t_b, double t_d, double* rho, double* grad, int* err) {
   using C = RhoCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float* Rs = reinterpret_cast<float*>(sm + C::kOffR);
-  uint32_t* mask = reinterpret_cast<uint32_t*>(sm + C::kOffMask);
-  int32_t* plist = reinterpret_cast<int32_t*>(sm + C::kOffList);
+  int32_t* meta_base = reinterpret_cast<int32_t*>(sm + C::kOffMeta);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kOffBar);
   uint64_t* empty = full + C::kStages;
   uint64_t* tfull = empty + C::kStages;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* mfull = tempty + 2;
+  uint64_t* mempty = mfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t g = g0 + blockIdx.x;
-  const int tb = L.blk_ptr[g];
-  const int n = L.blk_ptr[g + 1] - tb;
-  if (n > kMaxRet) {
-    if (threadIdx.x == 0) atomicCAS(err, 0, 101);
-    return;
-  }
-  const int nwords = (n + 31) >> 5;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) plist[k] = L.blk_idx[tb + k];
+  const int64_t G_ = gridDim.x;
+
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(&full[s], 1);
@@ -407,7 +412,9 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], 8);
+      mbar_init(&mfull[b], 1);
+      mbar_init(&mempty[b], 9);   // the MMA thread and the 8 epilogue warps
     }
     *abort_flag = 0;
     fence_barrier_init();
@@ -416,197 +423,252 @@ __global__ void __launch_bounds__(192, 1)
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
-  __syncthreads();
-  // executed pairs E1_g: one ballot per 32 (jp, jq) predicates
-  for (int wi = warp; wi < n * nwords; wi += 6) {
-    const int jp = wi / nwords, w = wi % nwords;
-    const int jq = w * 32 + lane;
-    bool pred = false;
-    if (jq < n) {
-      const double dm = dmax[plist[jp] * L.nbb + plist[jq]];
-      pred = dm >= t_b && L.bmax[tb + jp] * dm * L.bmax[tb + jq] >= t_d;
-    }
-    const uint32_t word = __ballot_sync(0xffffffffu, pred);
-    if (lane == 0) mask[jp * nwords + w] = word;
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const int ntile = (n + C::kNQ - 1) / C::kNQ;
-  auto tile_bits = [&](int jp, int q0, int nq) -> uint32_t {
-    return (mask[jp * nwords + (q0 >> 5)] >> (q0 & 31)) & ((1u << nq) - 1u);
+  // per-block record: [0] n, [1] tb, [4 .. 4+kMaxRet) plist, then the bit matrix
+  auto meta = [&](int b) { return meta_base + b * C::kMetaWords; };
+  auto tile_bits = [](const int32_t* m, int jp, int q0, int nq) -> uint32_t {
+    const int nw = (m[0] + 31) >> 5;
+    const uint32_t* mask = reinterpret_cast<const uint32_t*>(m + 4 + kMaxRet);
+    return (mask[jp * nw + (q0 >> 5)] >> (q0 & 31)) & ((1u << nq) - 1u);
   };
-  // number of exact-accumulation segments of N tile nt (>= 1; an empty tile has one empty segment)
-  auto nsegs = [&](int q0, int nq) -> int {
+  auto nsegs = [&](const int32_t* m, int q0, int nq) -> int {
     int c = 0;
-    for (int jp = 0; jp < n; ++jp) c += tile_bits(jp, q0, nq) != 0;
+    for (int jp = 0; jp < m[0]; ++jp) c += tile_bits(m, jp, q0, nq) != 0;
     return c == 0 ? 1 : (c + C::kSegChunks - 1) / C::kSegChunks;
   };
 
   if (warp == 0) {
-    if (lane == 0) {
-      uint32_t it = 0;
-      for (int nt = 0; nt < ntile && !*abort_flag; ++nt) {
-        const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
-        for (int jp = 0; jp < n; ++jp) {
-          const uint32_t bits = tile_bits(jp, q0, nq);
-          if (!bits) continue;
-          const int s = it % C::kStages;
-          const uint32_t ph = (it / C::kStages) & 1;
-          if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, 111)) break;
-          uint8_t* st = sm + s * C::kStageBytes;
-          mbar_arrive_expect_tx(&full[s], NS * kPlaneBytes + NS * nq * kDPlane);
-          const uint8_t* src = phi + (int64_t)(tb + jp - t0) * tile_bytes(NS);
+    uint32_t it = 0;
+    for (int64_t k = 0;; ++k) {
+      const int64_t g = g0 + blockIdx.x + k * G_;
+      if (g >= g1 || *abort_flag) break;
+      const int b = (int)(k & 1);
+      if (!mbar_wait_warp(&mempty[b], (uint32_t)(((k >> 1) & 1) ^ 1), abort_flag, err, 110)) break;
+      int32_t* m = meta(b);
+      const int tb = L.blk_ptr[g];
+      int n = L.blk_ptr[g + 1] - tb;
+      if (n > kMaxRet) {
+        if (lane == 0) atomicCAS(err, 0, 101);
+        n = 0;
+      }
+      const int nw = (n + 31) >> 5;
+      int32_t* plist = m + 4;
+      uint32_t* mask = reinterpret_cast<uint32_t*>(m + 4 + kMaxRet);
+      for (int j = lane; j < n; j += 32) plist[j] = L.blk_idx[tb + j];
+      __syncwarp();
+      // executed pairs E1_g: one ballot per 32 (jp, jq) predicates
+      for (int wi = 0; wi < n * nw; ++wi) {
+        const int jp = wi / nw, w = wi % nw;
+        const int jq = w * 32 + lane;
+        bool pred = false;
+        if (jq < n) {
+          const double dm = dmax[plist[jp] * L.nbb + plist[jq]];
+          pred = dm >= t_b && L.bmax[tb + jp] * dm * L.bmax[tb + jq] >= t_d;
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, pred);
+        if (lane == 0) mask[wi] = word;
+      }
+      if (lane == 0) {
+        m[0] = n;
+        m[1] = tb;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&mfull[b]);
+        const int ntile = (n + C::kNQ - 1) / C::kNQ;
+        bool ok = true;
+        for (int nt = 0; nt < ntile && ok; ++nt) {
+          const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+          for (int jp = 0; jp < n; ++jp) {
+            const uint32_t bits = tile_bits(m, jp, q0, nq);
+            if (!bits) continue;
+            const int s = it % C::kStages;
+            const uint32_t ph = (it / C::kStages) & 1;
+            if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, 111)) { ok = false; break; }
+            uint8_t* st = sm + s * C::kStageBytes;
+            mbar_arrive_expect_tx(&full[s], NS * kPlaneBytes + NS * nq * kDPlane);
+            const uint8_t* src = phi + (int64_t)(tb + jp - t0) * tile_bytes(NS);
 #pragma unroll
-          for (int l = 0; l < NS; ++l) bulk_g2s(st + l * kPlaneBytes, src + l * kPlaneBytes, kPlaneBytes, &full[s]);
-          uint8_t* bb = st + NS * kPlaneBytes;
-          for (int k = 0; k < nq; ++k) {
-            const bool on = (bits >> k) & 1u;
-            const uint8_t* d = dsplit + ((int64_t)plist[jp] * L.nbb + plist[q0 + k]) * (NS * kDPlane);
+            for (int l = 0; l < NS; ++l) bulk_g2s(st + l * kPlaneBytes, src + l * kPlaneBytes, kPlaneBytes, &full[s]);
+            uint8_t* bb = st + NS * kPlaneBytes;
+            for (int kq = 0; kq < nq; ++kq) {
+              const bool on = (bits >> kq) & 1u;
+              const uint8_t* d = dsplit + ((int64_t)plist[jp] * L.nbb + plist[q0 + kq]) * (NS * kDPlane);
 #pragma unroll
-            for (int l = 0; l < NS; ++l)
-              bulk_g2s(bb + l * (C::kNQ * kDPlane) + k * kDPlane, on ? d + l * kDPlane : zero, kDPlane, &full[s]);
+              for (int l = 0; l < NS; ++l)
+                bulk_g2s(bb + l * (C::kNQ * kDPlane) + kq * kDPlane, on ? d + l * kDPlane : zero, kDPlane, &full[s]);
+            }
+            ++it;
           }
-          ++it;
         }
       }
+      __syncwarp();
+    }
+    if (lane == 0)
       for (uint32_t k = (it > (uint32_t)C::kStages ? it - C::kStages : 0); k < it; ++k) {
         volatile int no_abort = 0;
         mbar_wait(&full[k % C::kStages], (k / C::kStages) & 1, &no_abort, nullptr, 0);
       }
-    }
   } else if (warp == 1) {
     if (lane == 0) {
       uint32_t it = 0, job = 0;
       bool ok = true;
-      for (int nt = 0; nt < ntile && ok && !*abort_flag; ++nt) {
-        const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
-        const uint32_t idesc = instr_desc(128, 32 * nq, 1, 0, 0);
-        int jp = 0;
-        const int ns = nsegs(q0, nq);
-        for (int sg = 0; sg < ns && ok; ++sg, ++job) {
-          const int buf = job % C::kBufs;
-          const uint32_t use = job / C::kBufs;
-          if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, err, 112)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t d0 = tbase + buf * C::kBufCols;
-          uint32_t started[NS];
-#pragma unroll
-          for (int l = 0; l < NS; ++l) started[l] = 0;
-          int taken = 0;
-          for (; jp < n && taken < C::kSegChunks; ++jp) {
-            if (!tile_bits(jp, q0, nq)) continue;
-            const int s = it % C::kStages;
-            const uint32_t ph = (it / C::kStages) & 1;
-            if (!mbar_wait(&full[s], ph, abort_flag, err, 113)) { ok = false; break; }
+      for (int64_t k = 0; ok; ++k) {
+        const int64_t g = g0 + blockIdx.x + k * G_;
+        if (g >= g1 || *abort_flag) break;
+        const int b = (int)(k & 1);
+        if (!mbar_wait(&mfull[b], (uint32_t)((k >> 1) & 1), abort_flag, err, 115)) break;
+        const int32_t* m = meta(b);
+        const int n = m[0];
+        const int ntile = (n + C::kNQ - 1) / C::kNQ;
+        for (int nt = 0; nt < ntile && ok; ++nt) {
+          const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+          const uint32_t idesc = instr_desc(128, 32 * nq, 1, 0, 0);
+          int jp = 0;
+          const int ns = nsegs(m, q0, nq);
+          for (int sg = 0; sg < ns && ok; ++sg, ++job) {
+            const int buf = job % C::kBufs;
+            const uint32_t use = job / C::kBufs;
+            if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, err, 112)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t a = smem_u32(sm + s * C::kStageBytes);
-            const uint32_t bsm = a + NS * kPlaneBytes;
+            const uint32_t d0 = tbase + buf * C::kBufCols;
+            uint32_t started[NS];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              uint64_t ad[NS], bd[NS];
+            for (int l = 0; l < NS; ++l) started[l] = 0;
+            int taken = 0;
+            for (; jp < n && taken < C::kSegChunks; ++jp) {
+              if (!tile_bits(m, jp, q0, nq)) continue;
+              const int s = it % C::kStages;
+              const uint32_t ph = (it / C::kStages) & 1;
+              if (!mbar_wait(&full[s], ph, abort_flag, err, 113)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t a = smem_u32(sm + s * C::kStageBytes);
+              const uint32_t bsm = a + NS * kPlaneBytes;
 #pragma unroll
-              for (int l = 0; l < NS; ++l) {
-                ad[l] = smem_desc(a + l * kPlaneBytes + k * 32, 16, 512, kSwz64);
-                bd[l] = smem_desc(bsm + l * (C::kNQ * kDPlane) + k * 32, 16, 512, kSwz64);
+              for (int kk = 0; kk < 2; ++kk) {
+                uint64_t ad[NS], bd[NS];
+#pragma unroll
+                for (int l = 0; l < NS; ++l) {
+                  ad[l] = smem_desc(a + l * kPlaneBytes + kk * 32, 16, 512, kSwz64);
+                  bd[l] = smem_desc(bsm + l * (C::kNQ * kDPlane) + kk * 32, 16, 512, kSwz64);
+                }
+                issue_levels<NS>(d0, 128, ad, bd, idesc, started);
               }
-              issue_levels<NS>(d0, 128, ad, bd, idesc, started);
+              mma_commit(&empty[s]);
+              ++it;
+              ++taken;
             }
-            mma_commit(&empty[s]);
-            ++it;
-            ++taken;
+            if (!ok) break;
+            mma_commit(&tfull[buf]);
           }
-          if (!ok) break;
-          mma_commit(&tfull[buf]);
         }
+        mbar_arrive(&mempty[b]);
       }
       if (!ok) *abort_flag = 1;
     }
   } else {
-    // epilogue: point i = TMEM lane
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int i = quarter * 32 + lane;
-    const int64_t pt = g * kBlockPts + i;
-    const float4 prl = G.prel[pt];
-    const float px = prl.x, py = prl.y, pz = prl.z;
-    const int anc = G.anchor[g];
-    const double rsc = (double)rowscale[pt];
-    double r_i = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    float* Rs = reinterpret_cast<float*>(sm + C::kOffR) + half * (kBasisBlk * kBlockPts);
     uint32_t job = 0;
     bool ok = true;
-    for (int nt = 0; nt < ntile && ok; ++nt) {
-      const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
-      const int ns = nsegs(q0, nq);
-      bool work = false;
-      for (int jp = 0; jp < n && !work; ++jp) work = tile_bits(jp, q0, nq) != 0;
-      float R[C::kNQ][32];
+    for (int64_t k = 0; ok; ++k) {
+      const int64_t g = g0 + blockIdx.x + k * G_;
+      if (g >= g1 || *abort_flag) break;
+      const int b = (int)(k & 1);
+      if (!mbar_wait_warp(&mfull[b], (uint32_t)((k >> 1) & 1), abort_flag, err, 116)) break;
+      const int32_t* m = meta(b);
+      const int n = m[0];
+      const int32_t* plist = m + 4;
+      const int64_t pt = g * kBlockPts + i;
+      const float4 prl = G.prel[pt];
+      const int anc = G.anchor[g];
+      const double rsc = (double)rowscale[pt];
+      double r_i = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+      const int ntile = (n + C::kNQ - 1) / C::kNQ;
+      for (int nt = 0; nt < ntile && ok; ++nt) {
+        const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+        const int ns = nsegs(m, q0, nq);
+        bool work = false;
+        for (int jp = 0; jp < n && !work; ++jp) work = tile_bits(m, jp, q0, nq) != 0;
+        float R[2][32];
 #pragma unroll
-      for (int k = 0; k < C::kNQ; ++k)
+        for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
-        for (int c = 0; c < 32; ++c) R[k][c] = 0.f;
-      for (int sg = 0; sg < ns; ++sg, ++job) {
-        const int buf = job % C::kBufs;
-        const uint32_t use = job / C::kBufs;
-        if (!mbar_wait_warp(&tfull[buf], use & 1, abort_flag, err, 114)) { ok = false; break; }
-        tc_fence_after();
-        if (work) {
+          for (int c = 0; c < 32; ++c) R[kk][c] = 0.f;
+        for (int sg = 0; sg < ns; ++sg, ++job) {
+          const int buf = job % C::kBufs;
+          const uint32_t use = job / C::kBufs;
+          if (!mbar_wait_warp(&tfull[buf], use & 1, abort_flag, err, 114)) { ok = false; break; }
+          tc_fence_after();
+          if (work) {
 #pragma unroll
-          for (int k = 0; k < C::kNQ; ++k) {
-            if (k < nq) {
-              float acc[32];
+            for (int kk = 0; kk < 2; ++kk) {
+              const int k4 = half * 2 + kk;
+              if (k4 < nq) {
+                float acc[32];
 #pragma unroll
-              for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+                for (int c = 0; c < 32; ++c) acc[c] = 0.f;
 #pragma unroll
-              for (int l = NS - 1; l >= 0; --l) {  // smallest level first
-                float lv[32];
-                tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + l * 128 + k * 32, lv);
+                for (int l = NS - 1; l >= 0; --l) {  // smallest level first
+                  float lv[32];
+                  tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + l * 128 + k4 * 32, lv);
 #pragma unroll
-                for (int c = 0; c < 32; ++c) acc[c] += lv[c];
+                  for (int c = 0; c < 32; ++c) acc[c] += lv[c];
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) R[kk][c] += acc[c];
               }
-#pragma unroll
-              for (int c = 0; c < 32; ++c) R[k][c] += acc[c];
             }
           }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
-      }
-      if (!ok) break;
-      // row-dot with this tile's functions: R_i,nu = e_i f_nu R[k][c]
+        if (!ok) break;
+        // row-dot with this warp's basis blocks: R_i,nu = e_i f_nu R[kk][c]
 #pragma unroll
-      for (int k = 0; k < C::kNQ; ++k) {
-        if (k >= nq) continue;
-        const int q = plist[q0 + k];
+        for (int kk = 0; kk < 2; ++kk) {
+          const int k4 = half * 2 + kk;
+          if (k4 >= nq) continue;
+          const int q = plist[q0 + k4];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[k][c] * dscale[q * kBasisBlk + c];
-        float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
-        for_block_functions<float, GRAD>(
-            B, q, px, py, pz,
-            [&](int nu, float v, float dx, float dy, float dz) {
-              const float rr = Rs[nu * kBlockPts + i];
-              pr = fmaf(v, rr, pr);
-              if (GRAD) {
-                px_ = fmaf(dx, rr, px_);
-                py_ = fmaf(dy, rr, py_);
-                pz_ = fmaf(dz, rr, pz_);
-              }
-            },
-            anc);
-        r_i += rsc * (double)pr;
-        if (GRAD) {
-          gx += 2.0 * rsc * (double)px_;
-          gy += 2.0 * rsc * (double)py_;
-          gz += 2.0 * rsc * (double)pz_;
+          for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[kk][c] * dscale[q * kBasisBlk + c];
+          float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
+          for_block_functions<float, GRAD>(
+              B, q, prl.x, prl.y, prl.z,
+              [&](int nu, float v, float dx, float dy, float dz) {
+                const float rr = Rs[nu * kBlockPts + i];
+                pr = fmaf(v, rr, pr);
+                if (GRAD) {
+                  px_ = fmaf(dx, rr, px_);
+                  py_ = fmaf(dy, rr, py_);
+                  pz_ = fmaf(dz, rr, pz_);
+                }
+              },
+              anc);
+          r_i += rsc * (double)pr;
+          if (GRAD) {
+            gx += 2.0 * rsc * (double)px_;
+            gy += 2.0 * rsc * (double)py_;
+            gz += 2.0 * rsc * (double)pz_;
+          }
         }
       }
-    }
-    rho[pt] = r_i;
-    if (GRAD) {
-      grad[pt * 3] = gx;
-      grad[pt * 3 + 1] = gy;
-      grad[pt * 3 + 2] = gz;
+      // the two halves of each point add into zeroed outputs: 0 + a + b is the
+      // same in either order, so the result is deterministic
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&mempty[b]);
+      atomicAdd(&rho[pt], r_i);
+      if (GRAD) {
+        atomicAdd(&grad[pt * 3], gx);
+        atomicAdd(&grad[pt * 3 + 1], gy);
+        atomicAdd(&grad[pt * 3 + 2], gz);
+      }
     }
   }
   tc_fence_before();
@@ -628,17 +690,22 @@ static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, d
     KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
     attr = true;
   }
+  const unsigned grid = (unsigned)std::min<int64_t>(n, P->num_sms);
+  KLDI_TRY_CUDA(cudaMemsetAsync(rho_out + b.g0 * kBlockPts, 0, sizeof(double) * n * kBlockPts, s));
+  if (P->gga) KLDI_TRY_CUDA(cudaMemsetAsync(grad_out + b.g0 * kBlockPts * 3, 0, sizeof(double) * n * kBlockPts * 3, s));
   const uint8_t* phi = reinterpret_cast<const uint8_t*>(P->d_phi_s);
   const uint8_t* ds = reinterpret_cast<const uint8_t*>(P->d_dsplit);
   const uint8_t* z = reinterpret_cast<const uint8_t*>(P->d_zero);
   if (P->gga)
-    k_rho_tc<NS, true><<<(unsigned)n, 192, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
-                                                          b.t0, phi, ds, z, P->d_dmax, P->d_dscale, P->d_rowscale,
-                                                          P->opt.t_b, P->opt.t_d, rho_out, grad_out, P->d_err);
+    k_rho_tc<NS, true><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                           b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
+                                                           P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
+                                                           P->d_err);
   else
-    k_rho_tc<NS, false><<<(unsigned)n, 192, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
-                                                           b.t0, phi, ds, z, P->d_dmax, P->d_dscale, P->d_rowscale,
-                                                           P->opt.t_b, P->opt.t_d, rho_out, grad_out, P->d_err);
+    k_rho_tc<NS, false><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                            b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
+                                                            P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
+                                                            P->d_err);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
@@ -648,18 +715,32 @@ kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho_out, d
 }
 
 // ---------------------------------------------------------------------------
-// W = Phi^T X over one 128 x 128 tile pair (P, Q) of the full square.
-// 320 threads: warp 0 producer, warp 1 TMEM owner + MMA, warps 2..9 epilogue
-// (lane quarter = warp % 4, column half = (warp - 2) / 4).
+// V product, persistent over work items (tile pair P <= Q of 128 functions,
+// segment of its grid-block list).  Per grid block one exact chain of K = 256:
+// A = [Phi~_P | X~_P]^T, B = [X~_Q ; Phi~_Q] (MN-major operands), so the chain
+// yields Phi^T X + X^T Phi of the tile pair at once.  384 threads in three
+// warpgroups: warpgroup 0 = warp 0 producer (one lane per bulk copy), warp 1
+// TMEM owner + MMA issue, warps 2-3 idle; warpgroups 1-2 = epilogue (lane
+// quarter = warp % 4, column half = warpgroup - 1) with compensated FP32 sums
+// per element (sums in registers, compensation terms in the TMEM columns after
+// the level accumulators) and an FP64 scatter-add at the end of each work
+// item.  Registers move from warpgroup 0 (kRegsLow) to the epilogue (kRegsHigh).
 template <int NS>
-struct WCfg {
+struct VCfg {
   static constexpr int kChunk = 2048;                   // 32 points x 64 B of one plane of one tile
   static constexpr int kOp = 4 * kChunk;                // 4 tiles (128 functions) of one plane
   static constexpr int kStageBytes = 2 * NS * kOp;      // A planes then B planes
   static constexpr int kStages = 4;
+  static constexpr int kBufCols = NS * 128;
+  static constexpr int kCcCol = NS * 128;               // TMEM columns of the compensation terms
+  static_assert(kCcCol + 128 <= 512, "levels and compensation terms exceed TMEM");
   static constexpr int kOffBar = kStages * kStageBytes;
   static constexpr int kSmem = kOffBar + 256 + 1024;
-  static constexpr int kThreads = 320;
+  static constexpr int kThreads = 384;
+  static constexpr int kLaunchRegs = 168;               // per thread at launch (checked on the host)
+  static constexpr uint32_t kRegsLow = 64, kRegsHigh = 200;
+  static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * kLaunchRegs, "register budgets exceed the pool");
+  static_assert(8 * NS <= 32, "one producer lane per copy of a stage");
 };
 
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
@@ -671,29 +752,30 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
 }
 
 template <int NS>
-__global__ void __launch_bounds__(320, 1)
-    k_w_tc(ListView L, const VWorkTC* __restrict__ work, const int32_t* __restrict__ glist, int64_t t0,
-           const uint8_t* __restrict__ phic, const float* __restrict__ phic_scale, const uint8_t* __restrict__ xs,
-           const float* __restrict__ x_scale, const double* __restrict__ xmax, const uint8_t* __restrict__ zero,
-           int nbf, double t_b, double* W, int* err) {
-  using C = WCfg<NS>;
+__global__ void __launch_bounds__(384, 1)
+    k_v_tc(ListView L, const VWorkTC* __restrict__ work, int64_t nwork, const int32_t* __restrict__ glist,
+           int64_t t0, const uint8_t* __restrict__ phic, const uint8_t* __restrict__ xs,
+           const float* __restrict__ scale, const double* __restrict__ xmax, const uint8_t* __restrict__ zero,
+           int nbf, double t_b, double* V, int* err) {
+  using C = VCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kOffBar);
   uint64_t* empty = full + C::kStages;
   uint64_t* tfull = empty + C::kStages;
-  uint64_t* tempty = tfull + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 1);
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const VWorkTC wk = work[blockIdx.x];
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(tfull, 1);
-    mbar_init(tempty, 8);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);
+    }
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -705,129 +787,173 @@ __global__ void __launch_bounds__(320, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const int nblk = wk.end - wk.beg;
 
-  if (warp == 0) {
-    if (lane == 0) {
-      uint32_t it = 0;
-      for (int c = 0; c < nblk * 4 && !*abort_flag; ++c) {
-        const int64_t gb = glist[wk.beg + c / 4];
-        const int kc = c & 3;
-        const int s = it % C::kStages;
-        const uint32_t ph = (it / C::kStages) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, 121)) break;
-        uint8_t* st = sm + s * C::kStageBytes;
-        mbar_arrive_expect_tx(&full[s], C::kStageBytes);
-        for (int side = 0; side < 2; ++side) {
-          const int T = side == 0 ? wk.P : wk.Q;
-          for (int j = 0; j < 4; ++j) {
-            const int p = T * 4 + j;
-            const uint8_t* src = nullptr;
-            if (p < L.nbb) {
-              const int t = L.tile_of[gb * L.nbb + p];
-              if (t >= 0 && (side == 0 || xmax[t] >= t_b))
-                src = (side == 0 ? phic : xs) + (int64_t)(t - t0) * tile_bytes(NS) + kc * C::kChunk;
-            }
-#pragma unroll
-            for (int l = 0; l < NS; ++l)
-              bulk_g2s(st + (side * NS + l) * C::kOp + j * C::kChunk, src ? src + l * kPlaneBytes : zero, C::kChunk,
-                       &full[s]);
-          }
-        }
-        ++it;
-      }
-      for (uint32_t k = (it > (uint32_t)C::kStages ? it - C::kStages : 0); k < it; ++k) {
-        volatile int no_abort = 0;
-        mbar_wait(&full[k % C::kStages], (k / C::kStages) & 1, &no_abort, nullptr, 0);
-      }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = instr_desc(128, 128, 1, 1, 1);
+  if (warp < 4) {
+    regs_dec<C::kRegsLow>();
+    if (warp == 0) {
+      // lane -> copy (plane l, side, tile j): lanes 0..8 NS-1, one bulk copy each per stage
+      const int q = lane & 7, side = q >> 2, j = q & 3, l = lane >> 3;
+      const bool copier = lane < 8 * NS;
       uint32_t it = 0;
       bool ok = true;
-      for (int e = 0; e < nblk && ok; ++e) {
-        if (!mbar_wait(tempty, (e & 1) ^ 1, abort_flag, err, 124)) { ok = false; break; }
-        tc_fence_after();
-        uint32_t started[NS];
-#pragma unroll
-        for (int l = 0; l < NS; ++l) started[l] = 0;
-        for (int kc = 0; kc < 4; ++kc) {
-          const int s = it % C::kStages;
-          const uint32_t ph = (it / C::kStages) & 1;
-          if (!mbar_wait(&full[s], ph, abort_flag, err, 122)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t a = smem_u32(sm + s * C::kStageBytes);
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            uint64_t ad[NS], bd[NS];
-#pragma unroll
-            for (int l = 0; l < NS; ++l) {
-              ad[l] = smem_desc(a + l * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
-              bd[l] = smem_desc(a + (NS + l) * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
+      for (int64_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+        const VWorkTC wk = work[wi];
+        for (int e = 0; e < wk.end - wk.beg && ok; ++e) {
+          const int64_t gb = glist[wk.beg + e];
+          const int p = (side == 0 ? wk.P : wk.Q) * 4 + j;
+          const uint8_t* sp = zero;   // Phi~ plane l of tile (gb, p), or zeros
+          const uint8_t* sx = zero;   // X~ plane l, or zeros (tile absent or x_gq < t_b)
+          if (p < L.nbb) {
+            const int t = L.tile_of[gb * L.nbb + p];
+            if (t >= 0) {
+              const int64_t off = (int64_t)(t - t0) * tile_bytes(NS) + (int64_t)l * kPlaneBytes;
+              sp = phic + off;
+              if (xmax[t] >= t_b) sx = xs + off;
             }
-            issue_levels<NS>(tbase, 128, ad, bd, idesc, started);
           }
-          mma_commit(&empty[s]);
-          ++it;
+          for (int c = 0; c < 8; ++c) {
+            const int h = c >> 2, kc = c & 3;
+            const int s = it % C::kStages;
+            const uint32_t ph = (it / C::kStages) & 1;
+            if (!mbar_wait_warp(&empty[s], ph ^ 1, abort_flag, err, 121)) { ok = false; break; }
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], C::kStageBytes);
+            __syncwarp();
+            if (copier) {
+              // A = Phi~ then X~ along K; B = X~ then Phi~
+              const bool use_x = (side == 0) == (h == 1);
+              const uint8_t* src = use_x ? sx : sp;
+              if (src != zero) src += kc * C::kChunk;
+              bulk_g2s(sm + s * C::kStageBytes + (side * NS + l) * C::kOp + j * C::kChunk, src, C::kChunk,
+                       &full[s]);
+            }
+            ++it;
+          }
         }
-        if (!ok) break;
-        mma_commit(tfull);
       }
-      if (!ok) *abort_flag = 1;
+      if (lane == 0)
+        for (uint32_t k = (it > (uint32_t)C::kStages ? it - C::kStages : 0); k < it; ++k) {
+          volatile int no_abort = 0;
+          mbar_wait(&full[k % C::kStages], (k / C::kStages) & 1, &no_abort, nullptr, 0);
+        }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        const uint32_t idesc = instr_desc(128, 128, 1, 1, 1);
+        uint32_t it = 0, job = 0;
+        bool ok = true;
+        for (int64_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+          const VWorkTC wk = work[wi];
+          for (int e = 0; e < wk.end - wk.beg && ok; ++e, ++job) {
+            if (!mbar_wait(&tempty[0], (job & 1) ^ 1, abort_flag, err, 124)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d0 = tbase;
+            uint32_t started[NS];
+#pragma unroll
+            for (int l = 0; l < NS; ++l) started[l] = 0;
+            for (int c = 0; c < 8; ++c) {
+              const int s = it % C::kStages;
+              const uint32_t ph = (it / C::kStages) & 1;
+              if (!mbar_wait(&full[s], ph, abort_flag, err, 122)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t a = smem_u32(sm + s * C::kStageBytes);
+#pragma unroll
+              for (int k = 0; k < 2; ++k) {
+                uint64_t ad[NS], bd[NS];
+#pragma unroll
+                for (int l = 0; l < NS; ++l) {
+                  ad[l] = smem_desc(a + l * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
+                  bd[l] = smem_desc(a + (NS + l) * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
+                }
+                issue_levels<NS>(d0, 128, ad, bd, idesc, started);
+              }
+              mma_commit(&empty[s]);
+              ++it;
+            }
+            if (!ok) break;
+            mma_commit(&tfull[0]);
+          }
+        }
+        if (!ok) *abort_flag = 1;
+      }
     }
   } else {
+    regs_inc<C::kRegsHigh>();
     const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int half = (warp >> 2) - 1;
     const int m = quarter * 32 + lane;       // row inside the tile (function of P)
-    float S[64], Cc[64];
+    const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16) + half * 64;
+    uint32_t job = 0;
+    bool ok = true;
+    for (int64_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+      const VWorkTC wk = work[wi];
+      float S[64];
 #pragma unroll
-    for (int c = 0; c < 64; ++c) S[c] = Cc[c] = 0.f;
-    for (int e = 0; e < nblk; ++e) {
-      const int64_t gb = glist[wk.beg + e];
-      // scales: row (Phi tile of P, function m), columns (X tiles of Q)
-      const int pr = wk.P * 4 + (m >> 5);
-      float rsc = 0.f;
-      if (pr < L.nbb) {
-        const int t = L.tile_of[gb * L.nbb + pr];
-        if (t >= 0) rsc = phic_scale[(int64_t)(t - t0) * kBasisBlk + (m & 31)];
+      for (int c = 0; c < 64; ++c) S[c] = 0.f;
+      {
+        float z[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) z[c] = 0.f;
+#pragma unroll
+        for (int cq = 0; cq < 4; ++cq) tmem_st16(trow + C::kCcCol + cq * 16, z);
+        tmem_st_wait();
       }
-      if (!mbar_wait_warp(tfull, e & 1, abort_flag, err, 123)) break;
-      tc_fence_after();
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int qb = wk.Q * 4 + half * 2 + cc;
-        float csc = 0.f;
-        if (qb < L.nbb) {
-          const int t = L.tile_of[gb * L.nbb + qb];
-          if (t >= 0) csc = x_scale[(int64_t)(t - t0) * kBasisBlk + lane];
+      for (int e = 0; e < wk.end - wk.beg; ++e, ++job) {
+        const int64_t gb = glist[wk.beg + e];
+        const int pr = wk.P * 4 + (m >> 5);
+        float rsc = 0.f;
+        if (pr < L.nbb) {
+          const int t = L.tile_of[gb * L.nbb + pr];
+          if (t >= 0) rsc = scale[(int64_t)(t - t0) * kBasisBlk + (m & 31)];
         }
-        float acc[32];
+        float csc[2];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-#pragma unroll
-        for (int l = NS - 1; l >= 0; --l) {
-          float lv[32];
-          tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + l * 128 + half * 64 + cc * 32, lv);
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[c] += lv[c];
+        for (int cc = 0; cc < 2; ++cc) {
+          const int qb = wk.Q * 4 + half * 2 + cc;
+          csc[cc] = 0.f;
+          if (qb < L.nbb) {
+            const int t = L.tile_of[gb * L.nbb + qb];
+            if (t >= 0) csc[cc] = scale[(int64_t)(t - t0) * kBasisBlk + lane];
+          }
         }
+        if (!mbar_wait_warp(&tfull[0], job & 1, abort_flag, err, 123)) { ok = false; break; }
+        tc_fence_after();
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const float sc = rsc * __shfl_sync(0xffffffffu, csc, c);
-          two_sum_acc(S[cc * 32 + c], Cc[cc * 32 + c], acc[c] * sc);
+        for (int cq = 0; cq < 4; ++cq) {            // 16 columns at a time
+          const int cc = cq >> 1;
+          float acc[16], cmp[16];
+          tmem_ld16(trow + (NS - 1) * 128 + cq * 16, acc);
+#pragma unroll
+          for (int l = NS - 2; l >= 0; --l) {
+            float lv[16];
+            tmem_ld16(trow + l * 128 + cq * 16, lv);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] += lv[c];
+          }
+          tmem_ld16(trow + C::kCcCol + cq * 16, cmp);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const float sc = rsc * __shfl_sync(0xffffffffu, csc[cc], (cq & 1) * 16 + c);
+            two_sum_acc(S[cq * 16 + c], cmp[c], acc[c] * sc);
+          }
+          tmem_st16(trow + C::kCcCol + cq * 16, cmp);
         }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[0]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty);
-    }
-    const int r = wk.P * 128 + m;
-    if (r < nbf) {
+      if (!ok) break;
+      const int r = wk.P * 128 + m;
 #pragma unroll
-      for (int c = 0; c < 64; ++c) {
-        const int col = wk.Q * 128 + half * 64 + c;
-        if (col < nbf) atomicAdd(&W[(int64_t)r * nbf + col], (double)S[c] + (double)Cc[c]);
+      for (int cq = 0; cq < 4; ++cq) {
+        float cmp[16];
+        tmem_ld16(trow + C::kCcCol + cq * 16, cmp);
+        if (r < nbf) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int col = wk.Q * 128 + half * 64 + cq * 16 + c;
+            if (col < nbf) atomicAdd(&V[(int64_t)r * nbf + col], (double)S[cq * 16 + c] + (double)cmp[c]);
+          }
+        }
       }
     }
   }
@@ -840,42 +966,33 @@ __global__ void __launch_bounds__(320, 1)
 }
 
 template <int NS>
-static kldi_status w_ns(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
-  using C = WCfg<NS>;
+static kldi_status v_ns(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
+  using C = VCfg<NS>;
   if (b.n_vtc_work == 0) return KLDI_OK;
   static bool attr = false;
   if (!attr) {
-    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_w_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+    // the register budgets of the warpgroups assume the launch allocation
+    cudaFuncAttributes fa;
+    KLDI_TRY_CUDA(cudaFuncGetAttributes(&fa, k_v_tc<NS>));
+    if (fa.numRegs != C::kLaunchRegs) {
+      set_error("k_v_tc: built with %d registers per thread, register budgets assume %d", fa.numRegs,
+                C::kLaunchRegs);
+      return KLDI_EUNSUPPORTED;
+    }
+    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_v_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
     attr = true;
   }
-  k_w_tc<NS><<<(unsigned)b.n_vtc_work, C::kThreads, C::kSmem, s>>>(
-      P->list_view(), b.d_vtc_work, b.d_vtc_g, b.t0, reinterpret_cast<const uint8_t*>(P->d_phic_s), P->d_phic_scale,
-      reinterpret_cast<const uint8_t*>(P->d_x_s), P->d_x_scale, P->d_xmax, reinterpret_cast<const uint8_t*>(P->d_zero),
-      (int)P->nbf, P->opt.t_b, V, P->d_err);
+  const unsigned grid = (unsigned)std::min<int64_t>(b.n_vtc_work, P->num_sms);
+  k_v_tc<NS><<<grid, C::kThreads, C::kSmem, s>>>(
+      P->list_view(), b.d_vtc_work, b.n_vtc_work, b.d_vtc_g, b.t0, reinterpret_cast<const uint8_t*>(P->d_phic_s),
+      reinterpret_cast<const uint8_t*>(P->d_x_s), P->d_phic_scale, P->d_xmax,
+      reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, P->opt.t_b, V, P->d_err);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
 
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
-  return P->prec == KLDI_BF16X6 ? w_ns<3>(P, b, V, s) : w_ns<2>(P, b, V, s);
-}
-
-// V = W + W^T (the tensor-core path accumulates the full square of W = Phi^T X).
-__global__ void k_symm(double* V, int nbf) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nbf * nbf) return;
-  const int r = (int)(idx / nbf), c = (int)(idx % nbf);
-  if (r > c) return;
-  const double v = V[idx] + V[(int64_t)c * nbf + r];
-  V[idx] = v;
-  V[(int64_t)c * nbf + r] = v;
-}
-
-kldi_status launch_symm(const kldi_plan* P, double* V, cudaStream_t s) {
-  const int64_t n = P->nbf * P->nbf;
-  k_symm<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, (int)P->nbf);
-  KLDI_TRY_CUDA(cudaGetLastError());
-  return KLDI_OK;
+  return P->prec == KLDI_BF16X6 ? v_ns<3>(P, b, V, s) : v_ns<2>(P, b, V, s);
 }
 
 }  // namespace kldi
