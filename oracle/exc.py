@@ -30,6 +30,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import basis as obasis
+from . import mlp as omlp
 from . import screen as oscreen
 from . import xc as oxc
 
@@ -50,14 +51,16 @@ def _block_phi(shells, points, gga):
 
 
 def evaluate(system, grid, shells=None, screened=True, blocks=None, want_v=True,
-             keep_lists=False, xc_kind=None, t_b=None, t_d=None, rho_min=oxc.RHO_MIN):
+             keep_lists=False, xc_kind=None, t_b=None, t_d=None, rho_min=oxc.RHO_MIN, mlp=None):
     """rho, grad rho, E_xc and V over the grid blocks ``blocks`` (default all).
 
-    With a subset of blocks, E and V are the partial sums over those blocks."""
+    With a subset of blocks, E and V are the partial sums over those blocks.
+    ``xc_kind="mlp"`` uses the learned functional ``mlp = (fp16 weights, Box)``
+    of oracle.mlp (a GGA: it needs grad rho)."""
     if shells is None:
         shells = obasis.build_shells(system.xyz, system.basis)
     kind = xc_kind or system.xc
-    gga = kind == "pbe"
+    gga = kind in ("pbe", "mlp")
     t_b = system.t_b if t_b is None else t_b
     t_d = system.t_d if t_d is None else t_d
     D = system.D
@@ -109,7 +112,10 @@ def evaluate(system, grid, shells=None, screened=True, blocks=None, want_v=True,
         else:
             dph = None
             sigma = None
-        f, vr, vs = oxc.evaluate(kind, rho, sigma, rho_min)
+        if kind == "mlp":
+            f, vr, vs, _ = omlp.functional(mlp[0], mlp[1], rho, sigma, rho_min)
+        else:
+            f, vr, vs = oxc.evaluate(kind, rho, sigma, rho_min)
         eg = float(np.sum(w * f))
         res.exc_blocks[k] = eg
         res.E += eg

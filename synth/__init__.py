@@ -444,3 +444,46 @@ def make_system(config: int, frame: int = 0, nwaters: int | None = None) -> Syst
 def frame_sizes(nframes: int = 256) -> np.ndarray:
     """Water counts of the batched-frames workload (seed 31)."""
     return np.random.default_rng(31).integers(20, 131, size=256)[:nframes]
+
+
+# ---------------------------------------------------------------------------- learned functional inputs
+MLP_HIDDEN = 64
+MLP_NPARAMS = MLP_HIDDEN * 2 + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + 2 * MLP_HIDDEN + 2
+
+
+def mlp_init(seed: int = 42) -> np.ndarray:
+    """Seeded FP32 initial parameters of the 2 -> 64 -> 64 -> 2 surrogate
+    (order W1, b1, W2, b2, W3, b3): Glorot-uniform weights, zero hidden biases,
+    output biases (1, 1) (the network starts at Slater exchange)."""
+    rng = np.random.default_rng(seed)
+    h = MLP_HIDDEN
+
+    def glorot(nout, nin):
+        lim = math.sqrt(6.0 / (nin + nout))
+        return rng.uniform(-lim, lim, size=(nout, nin))
+
+    p = np.concatenate([glorot(h, 2).ravel(), np.zeros(h), glorot(h, h).ravel(), np.zeros(h),
+                        glorot(2, h).ravel(), np.ones(2)])
+    assert p.size == MLP_NPARAMS
+    return p.astype(np.float32)
+
+
+def mlp_box(rho: np.ndarray, sigma: np.ndarray, rho_lo: float = 1e-10, sigma_floor: float = 1e-30):
+    """Training box (lo, hi of ln rho; lo, hi of ln sigma) of the points with
+    rho >= rho_lo, as four doubles."""
+    rho = np.asarray(rho, dtype=np.float64)
+    keep = rho >= rho_lo
+    u1 = np.log(rho[keep])
+    u2 = np.log(np.maximum(np.asarray(sigma, dtype=np.float64)[keep], sigma_floor))
+    return np.array([u1.min(), u1.max(), u2.min(), u2.max()], dtype=np.float64)
+
+
+def mlp_points(nsample: int, seed: int = 42) -> tuple[np.ndarray, np.ndarray]:
+    """Seeded (rho, sigma) pairs spread over the ranges met on molecular grids
+    (ln rho uniform in [ln 1e-10, ln 1e3], reduced gradient s in [0, 3]), for
+    tests of the network that need no grid."""
+    rng = np.random.default_rng(seed)
+    rho = np.exp(rng.uniform(math.log(1e-10), math.log(1e3), size=nsample))
+    s = rng.uniform(0.0, 3.0, size=nsample)
+    sigma = (s * 2.0 * (3.0 * math.pi ** 2) ** (1.0 / 3.0) * rho ** (4.0 / 3.0)) ** 2
+    return rho, sigma
