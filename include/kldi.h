@@ -229,6 +229,75 @@ kldi_status kldi_plan_stage_times(kldi_plan* plan, double* ms, int64_t* launches
 kldi_status kldi_exc_energy_noalloc(int xc, int64_t npoints, const double* rho, const double* grad,
                                     const double* w, double rho_min, double* Exc, void* stream);
 
+/* ---- Learned functional ------------------------------------------------
+ * A 2 -> 64 -> 64 -> 2 MLP surrogate of the per-point GGA functional, the
+ * evaluation that sits between the density product and the V product (Sec.
+ * III-F; Eq. exc_quadrature gives the potential v_i it must supply).  The
+ * paper has no learned part; the network is this project's addition:
+ *   inputs  z = ((ln rho, ln max(sigma, 1e-30)) - centre) / half-width of the
+ *           training box box[4] = {lo, hi of ln rho, lo, hi of ln sigma};
+ *   layers  h1 = tanh(W1 z + b1), h2 = tanh(W2 h1 + b2), o = W3 h2 + b3;
+ *   outputs f = e0(rho) o1, v_rho = v0(rho) o2 (e0, v0: Slater exchange and its
+ *           derivative), v_sigma = e0 (d o1 / d z2) / (half-width_2 sigma);
+ *   points outside the box use the analytic PBE-form functional; points with
+ *   rho < rho_min contribute nothing.
+ * Parameters (KLDI_MLP_NPARAMS floats, FP32 master copy): W1 [64][2], b1[64],
+ * W2 [64][64] (row = output unit), b2[64], W3 [2][64], b3[2].  The forward
+ * pass uses their FP16 values with FP32 arithmetic. */
+#define KLDI_MLP_NPARAMS 4482
+typedef struct kldi_mlp kldi_mlp;
+
+typedef struct {
+  int epochs;          /* passes over the training points                     */
+  int batch;           /* points per Adam step (1 .. 65536)                   */
+  double lr0, lr1;     /* learning rate: cosine schedule from lr0 to lr1      */
+  double beta1, beta2, eps;   /* Adam                                         */
+  double rho_min;      /* points with rho < rho_min or outside the box are not
+                          trained on                                          */
+  void* stream;        /* cudaStream_t or NULL                                */
+} kldi_train_options;
+
+/* New network with parameters params[KLDI_MLP_NPARAMS] (host or device, FP32)
+ * and training box box[4] (host).  Owns its device memory. */
+kldi_status kldi_mlp_create(const float* params, const double* box, kldi_mlp** out);
+
+/* Copy the FP32 master parameters to params[KLDI_MLP_NPARAMS] (host). */
+kldi_status kldi_mlp_get_params(const kldi_mlp* mlp, float* params);
+
+/* Mean loss over the valid points of (rho[n], sigma[n]) (host or device,
+ * FP64) of (o1 - F*)^2 + (o2 - G*)^2 with F* = f / e0, G* = v_rho / v0 of the
+ * analytic PBE-form functional, and its gradient grad[KLDI_MLP_NPARAMS]
+ * (host, FP32); *loss (host).  Synchronises. */
+kldi_status kldi_mlp_loss_grad(kldi_mlp* mlp, const double* rho, const double* sigma, int64_t n,
+                               double rho_min, float* grad, float* loss);
+
+/* One Adam step with gradient grad[KLDI_MLP_NPARAMS] (host or device, FP32),
+ * learning rate lr; the step counter is kept by the network. */
+kldi_status kldi_mlp_adam_step(kldi_mlp* mlp, const float* grad, double lr, double beta1, double beta2,
+                               double eps);
+
+/* Train on the GPU: per epoch one pass over all n points in a fixed
+ * pseudo-random order (an affine permutation of the indices, new offset per
+ * epoch), one Adam step per batch.  rho, sigma: host or device, FP64.
+ * loss_per_epoch[epochs] (host, may be NULL): mean batch loss of each epoch.
+ * Synchronises. */
+kldi_status kldi_mlp_train(kldi_mlp* mlp, const double* rho, const double* sigma, int64_t n,
+                           const kldi_train_options* opt, float* loss_per_epoch);
+
+/* Evaluate the surrogate (with its fallback) at n points: f, vrho, vsigma
+ * (FP64) and used[n] (1 where the network was used, int32), all host or all
+ * device (used may be NULL).  Synchronises for host outputs. */
+kldi_status kldi_mlp_eval(const kldi_mlp* mlp, const double* rho, const double* sigma, int64_t n,
+                          double rho_min, double* f, double* vrho, double* vsigma, int32_t* used);
+
+/* Attach a network to a GGA plan: kldi_vxc / kldi_exc with KLDI_XC_MLP then
+ * evaluate it between the two products (fused into the functional kernel).
+ * The plan keeps a reference: free the network after the plan or detach it
+ * with mlp = NULL. */
+kldi_status kldi_plan_set_mlp(kldi_plan* plan, const kldi_mlp* mlp);
+
+void kldi_mlp_free(kldi_mlp* mlp);
+
 /* Switch the product arithmetic of an existing plan (kldi_prec). */
 kldi_status kldi_plan_set_precision(kldi_plan* plan, int prec);
 

@@ -8,7 +8,19 @@ using namespace kldi;
 
 namespace kldi {
 kldi_status ensure_tile_buffers(kldi_plan* P, int prec);
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+}  // namespace kldi
+
+using kldi::is_device_ptr;
 
 namespace {
 
@@ -26,15 +38,6 @@ kldi_status staged(kldi_plan* P, int stage, int launches, F&& fn) {
   return KLDI_OK;
 }
 
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 // D -> per-evaluation operands (block maxima; split tiles for tensor modes).
 kldi_status prepare_D(kldi_plan* P, const double* D) {
@@ -84,12 +87,16 @@ kldi_status check_device_error(kldi_plan* P) {
 }
 
 kldi_status check_xc(const kldi_plan* P, int xc) {
-  if (xc < KLDI_XC_LDA_X || xc > KLDI_XC_PBE) {
+  if (xc < KLDI_XC_LDA_X || xc > KLDI_XC_MLP) {
     set_error("functional %d is not available in this call", xc);
-    return xc == KLDI_XC_MLP ? KLDI_EUNSUPPORTED : KLDI_EINVAL;
+    return KLDI_EINVAL;
   }
   if (xc != KLDI_XC_LDA_X && !P->gga) {
     set_error("a GGA functional needs a plan screened with a GGA functional (basis gradients)");
+    return KLDI_EINVAL;
+  }
+  if (xc == KLDI_XC_MLP && !P->mlp) {
+    set_error("KLDI_XC_MLP needs a network attached with kldi_plan_set_mlp");
     return KLDI_EINVAL;
   }
   return KLDI_OK;

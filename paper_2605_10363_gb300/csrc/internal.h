@@ -2,6 +2,7 @@
 // launchers shared between translation units.  Not part of the C ABI.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -117,9 +118,26 @@ struct kldi_grid {
   int block = kldi::kBlockPts;
 };
 
+// Learned functional: FP32 master parameters, their FP16 copy used by the
+// forward pass, Adam moments and the training box.
+struct kldi_mlp {
+  int device = 0;
+  float* d_param = nullptr;          // [KLDI_MLP_NPARAMS] FP32 master
+  __half* d_half = nullptr;          // [KLDI_MLP_NPARAMS] FP16 copy
+  float* d_m = nullptr;              // Adam first moment
+  float* d_v = nullptr;              // Adam second moment
+  float* d_grad = nullptr;           // [KLDI_MLP_NPARAMS] scratch gradient
+  float* d_part = nullptr;           // per-CTA partial gradients [cap][KLDI_MLP_NPARAMS + 2]
+  int64_t part_cap = 0;              // CTAs the partial buffer holds
+  float* d_loss = nullptr;           // [1 + loss history]
+  int64_t step = 0;                  // Adam steps taken
+  double box[4] = {0, 0, 0, 0};      // lo, hi of ln rho; lo, hi of ln sigma
+};
+
 struct kldi_plan {
   kldi_options opt{};
   int gga = 0;
+  const kldi_mlp* mlp = nullptr;   // learned functional for KLDI_XC_MLP (not owned)
   int prec = KLDI_FP64;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -213,5 +231,8 @@ kldi_status launch_phi_split(const kldi_plan* P, const Batch& b, cudaStream_t s)
 kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho, double* grad, cudaStream_t s);
 kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
+kldi_status launch_xc_mlp(const kldi_plan* P, const Batch& b, const double* rho, const double* grad,
+                          cudaStream_t s);
+bool is_device_ptr(const void* p);
 
 }  // namespace kldi

@@ -14,6 +14,7 @@
 #include "basis.cuh"
 #include "internal.h"
 #include "xc.cuh"
+#include "xc_point.cuh"
 
 namespace kldi {
 
@@ -33,15 +34,6 @@ static __device__ double block_max128(double v, double* red) {
   if ((threadIdx.x & 31) == 0) red[w] = v;
   __syncthreads();
   double r = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
-  __syncthreads();
-  return r;
-}
-static __device__ double block_sum128(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = v;
-  __syncthreads();
-  double r = (red[0] + red[1]) + (red[2] + red[3]);
   __syncthreads();
   return r;
 }
@@ -245,26 +237,12 @@ __global__ void k_xc(GridView G, int64_t g0, int xc, double rho_min, const doubl
       bz = c * g0z;
     }
   }
-  xcoef[pt * 4 + 0] = a;
-  xcoef[pt * 4 + 1] = bx;
-  xcoef[pt * 4 + 2] = by;
-  xcoef[pt * 4 + 3] = bz;
-  if (pscale) {
-    // balance c_i = 2^round(log2(|a| + |b|) / 2): the V product uses Phi c and X / c,
-    // whose magnitudes are then alike at every point (X ~ (|a| + |b|) Phi).  A point
-    // with X = 0 (zero weight, rho below rho_min) adds nothing to Phi^T X: c_i = 0
-    // drops its Phi row too, so it cannot inflate a function's column maximum.
-    const double m = fabs(a) + sqrt(bx * bx + by * by + bz * bz);
-    float c = 0.f;
-    if (m > 0.0) c = ldexpf(1.f, (int)lrint(0.5 * log2(m)));
-    pscale[pt] = c;
-  }
-  const double es = block_sum128(e, red);
-  if (threadIdx.x == 0) eblk[g] = es;
+  xc_point_tail(g, pt, e, a, bx, by, bz, xcoef, eblk, pscale, red);
 }
 
 kldi_status launch_xc(const kldi_plan* P, const Batch& b, int xc, const double* rho, const double* grad,
                       cudaStream_t s) {
+  if (xc == KLDI_XC_MLP) return launch_xc_mlp(P, b, rho, grad, s);
   const int64_t n = b.g1 - b.g0;
   if (n == 0) return KLDI_OK;
   k_xc<<<(unsigned)n, kBlockPts, 0, s>>>(P->grid_view(), b.g0, xc, P->opt.rho_min, rho, grad, P->d_xcoef,

@@ -48,6 +48,15 @@ class Options(C.Structure):
                 ("xc", C.c_int), ("stream", C.c_void_p)]
 
 
+class TrainOptions(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr0", C.c_double), ("lr1", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double), ("rho_min", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+MLP_NPARAMS = 4482
+
+
 class PlanStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("nbf", "nbasis_blocks", "npoints", "nblocks", "retained",
                                           "pair_slots", "vtile_work", "workspace_bytes")]
@@ -73,6 +82,14 @@ def _load():
         "kldi_plan_profile": (C.c_int, [vp, C.c_int]),
         "kldi_plan_stage_times": (C.c_int, [vp, vp, vp]),
         "kldi_exc_energy_noalloc": (C.c_int, [C.c_int, C.c_int64, vp, vp, vp, C.c_double, vp, vp]),
+        "kldi_mlp_create": (C.c_int, [vp, vp, C.POINTER(vp)]),
+        "kldi_mlp_get_params": (C.c_int, [vp, vp]),
+        "kldi_mlp_loss_grad": (C.c_int, [vp, vp, vp, C.c_int64, C.c_double, vp, vp]),
+        "kldi_mlp_adam_step": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+        "kldi_mlp_train": (C.c_int, [vp, vp, vp, C.c_int64, C.POINTER(TrainOptions), vp]),
+        "kldi_mlp_eval": (C.c_int, [vp, vp, vp, C.c_int64, C.c_double, vp, vp, vp, vp]),
+        "kldi_plan_set_mlp": (C.c_int, [vp, vp]),
+        "kldi_mlp_free": (None, [vp]),
         "kldi_plan_free": (None, [vp]),
         "kldi_grid_free": (None, [vp]),
         "kldi_last_error": (C.c_char_p, []),
@@ -225,6 +242,68 @@ def exc_energy_noalloc(xc, npoints, rho, grad, w, Exc, rho_min=1e-14, stream=0):
     """E_xc of a device-resident density with no allocation (kldi_exc_energy_noalloc)."""
     _check(LIB.kldi_exc_energy_noalloc(XC[xc] if isinstance(xc, str) else int(xc), int(npoints), _ptr(rho),
                                        _ptr(grad), _ptr(w), float(rho_min), _ptr(Exc), C.c_void_p(int(stream))))
+
+
+class Mlp:
+    """Owning handle of a kldi_mlp (the learned functional)."""
+
+    def __init__(self, params, box):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == MLP_NPARAMS
+        self.box = np.ascontiguousarray(box, np.float64)
+        h = C.c_void_p()
+        _check(LIB.kldi_mlp_create(_ptr(p), _ptr(self.box), C.byref(h)))
+        self.h = h
+
+    def params(self):
+        out = np.empty(MLP_NPARAMS, np.float32)
+        _check(LIB.kldi_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def loss_grad(self, rho, sigma, rho_min=1e-14):
+        rho = np.ascontiguousarray(rho, np.float64) if isinstance(rho, np.ndarray) else rho
+        sigma = np.ascontiguousarray(sigma, np.float64) if isinstance(sigma, np.ndarray) else sigma
+        g = np.empty(MLP_NPARAMS, np.float32)
+        loss = np.empty(1, np.float32)
+        _check(LIB.kldi_mlp_loss_grad(self.h, _ptr(rho), _ptr(sigma), int(len(rho)), float(rho_min), _ptr(g),
+                                      _ptr(loss)))
+        return float(loss[0]), g
+
+    def adam_step(self, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        g = np.ascontiguousarray(grad, np.float32) if isinstance(grad, np.ndarray) else grad
+        _check(LIB.kldi_mlp_adam_step(self.h, _ptr(g), float(lr), float(beta1), float(beta2), float(eps)))
+
+    def train(self, rho, sigma, epochs, batch=8192, lr0=3e-3, lr1=3e-5, beta1=0.9, beta2=0.999, eps=1e-8,
+              rho_min=1e-14, stream=0):
+        """GPU training; returns the mean batch loss of each epoch."""
+        rho = np.ascontiguousarray(rho, np.float64) if isinstance(rho, np.ndarray) else rho
+        sigma = np.ascontiguousarray(sigma, np.float64) if isinstance(sigma, np.ndarray) else sigma
+        opt = TrainOptions(int(epochs), int(batch), float(lr0), float(lr1), float(beta1), float(beta2), float(eps),
+                           float(rho_min), C.c_void_p(int(stream)))
+        hist = np.zeros(int(epochs), np.float32)
+        _check(LIB.kldi_mlp_train(self.h, _ptr(rho), _ptr(sigma), int(len(rho)), C.byref(opt), _ptr(hist)))
+        return hist
+
+    def eval(self, rho, sigma, rho_min=1e-14):
+        """(f, v_rho, v_sigma, used) at the points (host arrays)."""
+        rho = np.ascontiguousarray(rho, np.float64)
+        sigma = np.ascontiguousarray(sigma, np.float64)
+        n = rho.size
+        f, vr, vs = np.empty(n), np.empty(n), np.empty(n)
+        used = np.empty(n, np.int32)
+        _check(LIB.kldi_mlp_eval(self.h, _ptr(rho), _ptr(sigma), n, float(rho_min), _ptr(f), _ptr(vr), _ptr(vs),
+                                 _ptr(used)))
+        return f, vr, vs, used.astype(bool)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            LIB.kldi_mlp_free(self.h)
+            self.h = None
+
+
+def plan_set_mlp(plan: Plan, mlp):
+    _check(LIB.kldi_plan_set_mlp(plan.h, mlp.h if mlp is not None else None))
+    plan._mlp = mlp            # keep the network alive as long as the plan uses it
 
 
 def version() -> str:

@@ -470,12 +470,15 @@ def mlp_init(seed: int = 42) -> np.ndarray:
 
 def mlp_box(rho: np.ndarray, sigma: np.ndarray, rho_lo: float = 1e-10, sigma_floor: float = 1e-30):
     """Training box (lo, hi of ln rho; lo, hi of ln sigma) of the points with
-    rho >= rho_lo, as four doubles."""
+    rho >= rho_lo, as four doubles, widened by 1e-6 of each range so that the
+    extreme points lie strictly inside."""
     rho = np.asarray(rho, dtype=np.float64)
     keep = rho >= rho_lo
     u1 = np.log(rho[keep])
     u2 = np.log(np.maximum(np.asarray(sigma, dtype=np.float64)[keep], sigma_floor))
-    return np.array([u1.min(), u1.max(), u2.min(), u2.max()], dtype=np.float64)
+    m1 = 1e-6 * (u1.max() - u1.min())
+    m2 = 1e-6 * (u2.max() - u2.min())
+    return np.array([u1.min() - m1, u1.max() + m1, u2.min() - m2, u2.max() + m2], dtype=np.float64)
 
 
 def mlp_points(nsample: int, seed: int = 42) -> tuple[np.ndarray, np.ndarray]:
