@@ -182,8 +182,9 @@ kldi_status kldi_vxc(kldi_plan* plan, int xc, const double* rho, const double* g
 kldi_status kldi_exc(kldi_plan* plan, int xc, const double* D, double* V, double* Exc);
 
 /* Many molecules / frames of uneven size in one call: plans[k], D[k], V[k]
- * and Exc[k] for k < nframes.  Every plan must have been built with the same
- * options.  Device pointers only (KLDI_EINVAL otherwise). */
+ * and Exc[k] for k < nframes, captured into one CUDA graph (kldi_batch_*)
+ * and run as one launch on the first plan's stream; synchronises.  Device
+ * pointers only (KLDI_EINVAL otherwise). */
 kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
                              double* const* V, double* Exc);
 
@@ -228,6 +229,62 @@ kldi_status kldi_plan_stage_times(kldi_plan* plan, double* ms, int64_t* launches
  * Calls whose work overlaps on one GPU share the array and race. */
 kldi_status kldi_exc_energy_noalloc(int xc, int64_t npoints, const double* rho, const double* grad,
                                     const double* w, double rho_min, double* Exc, void* stream);
+
+/* ---- Many frames: shared workspace, tuning, one graph launch ------------
+ * The paper runs many molecules and trajectory frames through the same
+ * integration (Sec. IV; its multi-GPU pull scheduler, Sec. III-E, balances
+ * their uneven sizes).  Here the frames share one device workspace for the
+ * per-tile buffers, a tuner picks the V work decomposition, and all frames'
+ * launches are captured into one CUDA graph that runs as one launch. */
+typedef struct kldi_workspace kldi_workspace;
+
+/* Device arena of `bytes` bytes for the per-tile buffers of any number of
+ * plans on the current device.  Plans sharing it must not run concurrently
+ * (use one stream, or one batch). */
+kldi_status kldi_workspace_create(int64_t bytes, kldi_workspace** out);
+void kldi_workspace_free(kldi_workspace* ws);
+
+/* Use `ws` for the plan's per-tile buffers (NULL: the plan's own, sized from
+ * free memory, allocated at the next compute call).  The grid blocks are
+ * regrouped into batches that fit the workspace; KLDI_EINVAL if one grid
+ * block's tiles do not fit.  Free the workspace after the plans. */
+kldi_status kldi_plan_set_workspace(kldi_plan* plan, const kldi_workspace* ws);
+
+/* Tunable decomposition of the tensor-core V product: a work item is one
+ * 128 x 128 tile pair over v_seg consecutive grid blocks of its list
+ * (K = 256 v_seg); v_seg = 0 chooses about four items per SM. */
+typedef struct {
+  int v_seg;
+} kldi_tuning;
+
+kldi_status kldi_plan_set_tuning(kldi_plan* plan, const kldi_tuning* tuning);
+kldi_status kldi_plan_get_tuning(const kldi_plan* plan, kldi_tuning* tuning);
+
+/* Time kldi_exc(plan, xc, D) (D on the device) with CUDA events over the
+ * candidate tunings, `reps` timed calls each after one warm-up, and keep the
+ * fastest on the plan.  best (host, may be NULL) receives it, best_ms (host,
+ * may be NULL) its mean time per call in milliseconds.  Overwrites the
+ * plan's scratch outputs; synchronises. */
+kldi_status kldi_plan_autotune(kldi_plan* plan, int xc, const double* D, int reps, kldi_tuning* best,
+                               double* best_ms);
+
+typedef struct kldi_batch kldi_batch;
+
+/* Capture kldi_exc for every frame k (plans[k], D[k] -> V[k], Exc[k]; all
+ * device pointers, all plans on this device) into one CUDA graph, frames in
+ * order, on `stream` (a cudaStream_t; NULL: a stream the batch creates).
+ * Tile buffers are prepared before capture; the captured work allocates
+ * nothing.  The pointers are baked into the graph: keep them valid. */
+kldi_status kldi_batch_create(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
+                              double* const* V, double* Exc, void* stream, kldi_batch** out);
+
+/* One graph launch of the whole batch on its stream (asynchronous). */
+kldi_status kldi_batch_launch(kldi_batch* batch);
+
+/* Synchronise the batch's stream and report a device-side error of its last
+ * launch. */
+kldi_status kldi_batch_sync(kldi_batch* batch);
+void kldi_batch_free(kldi_batch* batch);
 
 /* ---- Learned functional ------------------------------------------------
  * A 2 -> 64 -> 64 -> 2 MLP surrogate of the per-point GGA functional, the

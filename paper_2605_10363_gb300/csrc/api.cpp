@@ -1,6 +1,7 @@
 // Compute entry points: kldi_density, kldi_vxc, kldi_exc, kldi_exc_batched.
 // Every step runs in this library's CUDA kernels on the plan's stream.
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -103,6 +104,7 @@ kldi_status check_xc(const kldi_plan* P, int xc) {
 }
 
 kldi_status exc_device(kldi_plan* P, int xc, const double* D, double* V, double* exc) {
+  KLDI_TRY(ensure_tile_buffers(P, P->prec));
   KLDI_TRY(prepare_D(P, D));
   KLDI_TRY_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
   for (const Batch& b : P->batches) {
@@ -127,6 +129,7 @@ extern "C" kldi_status kldi_density(kldi_plan* P, const double* D, double* rho, 
   const bool host_out = !is_device_ptr(rho);
   double* drho = host_out ? P->d_rho : rho;
   double* dgrad = P->gga ? (host_out ? P->d_grad : grad) : P->d_grad;
+  KLDI_TRY(ensure_tile_buffers(P, P->prec));
   KLDI_TRY(prepare_D(P, dD));
   for (const Batch& b : P->batches) KLDI_TRY(density_batch(P, b, dD, drho, dgrad));
   if (host_out) {
@@ -147,6 +150,7 @@ extern "C" kldi_status kldi_vxc(kldi_plan* P, int xc, const double* rho, const d
   if (!P || !rho || !V || !Exc) { set_error("kldi_vxc: null argument"); return KLDI_EINVAL; }
   KLDI_TRY(check_xc(P, xc));
   if (xc != KLDI_XC_LDA_X && !grad) { set_error("kldi_vxc: the GGA needs grad"); return KLDI_EINVAL; }
+  KLDI_TRY(ensure_tile_buffers(P, P->prec));
   const double* drho = rho;
   const double* dgrad = grad;
   if (!is_device_ptr(rho)) {
@@ -209,8 +213,14 @@ extern "C" kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, in
     KLDI_TRY(check_xc(plans[k], xc));
   }
   if (!is_device_ptr(Exc)) { set_error("kldi_exc_batched: Exc must be device memory"); return KLDI_EINVAL; }
-  for (int k = 0; k < nframes; ++k) KLDI_TRY(exc_device(plans[k], xc, D[k], V[k], Exc + k));
-  return KLDI_OK;
+  // one graph of all frames, launched once on the first plan's stream
+  kldi_batch* B = nullptr;
+  KLDI_TRY(kldi_batch_create(plans, nframes, xc, D, V, Exc, plans[0]->stream, &B));
+  const kldi_status st = kldi_batch_launch(B);
+  const kldi_status st2 = kldi_batch_sync(B);
+  kldi_batch_free(B);
+  KLDI_TRY(st);
+  return st2;
 }
 
 extern "C" kldi_status kldi_plan_profile(kldi_plan* P, int enable) {
@@ -242,4 +252,152 @@ extern "C" kldi_status kldi_plan_stage_times(kldi_plan* P, double* ms, int64_t* 
     if (launches) launches[s] = n[s];
   }
   return KLDI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuning and batched frames.
+struct kldi_batch {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<kldi_plan*> plans;
+};
+
+extern "C" kldi_status kldi_plan_autotune(kldi_plan* P, int xc, const double* D, int reps, kldi_tuning* best,
+                                          double* best_ms) {
+  if (!P || !D || reps < 1 || !is_device_ptr(D)) {
+    set_error("kldi_plan_autotune: bad argument (D must be device memory, reps >= 1)");
+    return KLDI_EINVAL;
+  }
+  KLDI_TRY(check_xc(P, xc));
+  const int cand[] = {0, 4, 8, 16, 32, 64, 128};
+  const kldi_tuning start = P->tune;
+  cudaEvent_t e0, e1;
+  KLDI_TRY_CUDA(cudaEventCreate(&e0));
+  KLDI_TRY_CUDA(cudaEventCreate(&e1));
+  double bms = 1e300;
+  kldi_tuning bt = start;
+  kldi_status st = KLDI_OK;
+  const int prof = P->prof;
+  P->prof = 0;
+  for (int c : cand) {
+    kldi_tuning t{c};
+    if ((st = kldi_plan_set_tuning(P, &t)) != KLDI_OK) break;
+    if ((st = exc_device(P, xc, D, P->d_V, P->d_exc)) != KLDI_OK) break;
+    cudaEventRecord(e0, P->stream);
+    for (int r = 0; r < reps && st == KLDI_OK; ++r) st = exc_device(P, xc, D, P->d_V, P->d_exc);
+    cudaEventRecord(e1, P->stream);
+    if (st != KLDI_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      set_error("kldi_plan_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+      st = KLDI_ECUDA;
+      break;
+    }
+    if ((st = check_device_error(P)) != KLDI_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / reps < bms) {
+      bms = ms / reps;
+      bt = t;
+    }
+  }
+  P->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  KLDI_TRY(st);
+  KLDI_TRY(kldi_plan_set_tuning(P, &bt));
+  if (best) *best = bt;
+  if (best_ms) *best_ms = bms;
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_batch_create(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
+                                         double* const* V, double* Exc, void* stream, kldi_batch** out) {
+  if (!plans || nframes <= 0 || !D || !V || !Exc || !out) {
+    set_error("kldi_batch_create: bad argument");
+    return KLDI_EINVAL;
+  }
+  *out = nullptr;
+  if (!is_device_ptr(Exc)) { set_error("kldi_batch_create: Exc must be device memory"); return KLDI_EINVAL; }
+  for (int k = 0; k < nframes; ++k) {
+    if (!plans[k] || !D[k] || !V[k]) { set_error("kldi_batch_create: null entry %d", k); return KLDI_EINVAL; }
+    if (!is_device_ptr(D[k]) || !is_device_ptr(V[k])) {
+      set_error("kldi_batch_create: device pointers only (entry %d)", k);
+      return KLDI_EINVAL;
+    }
+    if (plans[k]->device != plans[0]->device) {
+      set_error("kldi_batch_create: plans on different devices");
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY(check_xc(plans[k], xc));
+    KLDI_TRY(ensure_tile_buffers(plans[k], plans[k]->prec));
+  }
+  KLDI_TRY(prepare_tc_kernels());
+  kldi_batch* B = new kldi_batch;
+  B->plans.assign(plans, plans + nframes);
+  B->stream = static_cast<cudaStream_t>(stream);
+  if (!B->stream) {
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete B;
+      set_error("kldi_batch_create: stream creation failed");
+      return KLDI_ECUDA;
+    }
+    B->own_stream = true;
+  }
+  for (kldi_plan* P : B->plans) cudaStreamSynchronize(P->stream);
+  if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    set_error("kldi_batch_create: %s", cudaGetErrorString(cudaGetLastError()));
+    kldi_batch_free(B);
+    return KLDI_ECUDA;
+  }
+  kldi_status st = KLDI_OK;
+  for (int k = 0; k < nframes && st == KLDI_OK; ++k) {
+    kldi_plan* P = plans[k];
+    const cudaStream_t keep = P->stream;
+    const int prof = P->prof;
+    P->stream = B->stream;
+    P->prof = 0;
+    st = exc_device(P, xc, D[k], V[k], Exc + k);
+    P->stream = keep;
+    P->prof = prof;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(B->stream, &graph);
+  if (st == KLDI_OK && (ec != cudaSuccess || !graph)) {
+    set_error("kldi_batch_create: capture failed: %s", cudaGetErrorString(ec));
+    st = KLDI_ECUDA;
+  }
+  if (st == KLDI_OK && cudaGraphInstantiate(&B->exec, graph, 0) != cudaSuccess) {
+    set_error("kldi_batch_create: graph instantiation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    st = KLDI_ECUDA;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  if (st != KLDI_OK) {
+    kldi_batch_free(B);
+    return st;
+  }
+  *out = B;
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_batch_launch(kldi_batch* B) {
+  if (!B || !B->exec) { set_error("kldi_batch_launch: null batch"); return KLDI_EINVAL; }
+  KLDI_TRY_CUDA(cudaGraphLaunch(B->exec, B->stream));
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_batch_sync(kldi_batch* B) {
+  if (!B) { set_error("kldi_batch_sync: null batch"); return KLDI_EINVAL; }
+  KLDI_TRY_CUDA(cudaStreamSynchronize(B->stream));
+  for (kldi_plan* P : B->plans) KLDI_TRY(check_device_error(P));
+  return KLDI_OK;
+}
+
+extern "C" void kldi_batch_free(kldi_batch* B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+  delete B;
 }

@@ -134,8 +134,17 @@ struct kldi_mlp {
   double box[4] = {0, 0, 0, 0};      // lo, hi of ln rho; lo, hi of ln sigma
 };
 
+// Shared device arena for the per-tile buffers of several plans.
+struct kldi_workspace {
+  int device = 0;
+  void* base = nullptr;
+  int64_t bytes = 0;
+};
+
 struct kldi_plan {
   kldi_options opt{};
+  const kldi_workspace* ws = nullptr;   // shared per-tile buffers (not owned), or NULL
+  kldi_tuning tune{0};
   int gga = 0;
   const kldi_mlp* mlp = nullptr;   // learned functional for KLDI_XC_MLP (not owned)
   int prec = KLDI_FP64;
@@ -231,6 +240,11 @@ kldi_status launch_phi_split(const kldi_plan* P, const Batch& b, cudaStream_t s)
 kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho, double* grad, cudaStream_t s);
 kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
+kldi_status prepare_tc_kernels();
+kldi_status ensure_tile_buffers(kldi_plan* P, int prec);
+kldi_status build_work(kldi_plan* P, int64_t cap);
+int64_t tile_bytes_max();
+void free_own_tile_buffers(kldi_plan* P);
 kldi_status launch_xc_mlp(const kldi_plan* P, const Batch& b, const double* rho, const double* grad,
                           cudaStream_t s);
 bool is_device_ptr(const void* p);

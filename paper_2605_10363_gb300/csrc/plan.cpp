@@ -79,11 +79,11 @@ kldi_status upload(kldi_plan* P, T** p, const T* h, size_t count) {
 }
 
 void free_plan_buffers(kldi_plan* P) {
+  free_own_tile_buffers(P);
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of,
                   P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
-                  P->d_exc, P->d_err, P->d_phi64, P->d_x64, P->d_phi_s, P->d_phic_s, P->d_x_s,
-                  P->d_phic_scale, P->d_x_scale, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
+                  P->d_exc, P->d_err, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& b : P->batches) {
@@ -92,11 +92,23 @@ void free_plan_buffers(kldi_plan* P) {
     if (b.d_vtc_g) cudaFree(b.d_vtc_g);
     if (b.d_vtc_work) cudaFree(b.d_vtc_work);
   }
+  P->batches.clear();
 }
 
 }  // namespace
 
 namespace kldi {
+
+void free_own_tile_buffers(kldi_plan* P) {
+  if (!P->ws) {
+    void* own[] = {P->d_phi64, P->d_x64, P->d_phi_s, P->d_phic_s, P->d_x_s, P->d_phic_scale, P->d_x_scale};
+    for (void* p : own)
+      if (p) cudaFree(p);
+  }
+  P->d_phi64 = P->d_x64 = nullptr;
+  P->d_phi_s = P->d_phic_s = P->d_x_s = nullptr;
+  P->d_phic_scale = P->d_x_scale = nullptr;
+}
 
 // Bytes of the per-tile buffers each precision mode needs.
 int64_t tile_bytes_for(int prec) {
@@ -104,10 +116,116 @@ int64_t tile_bytes_for(int prec) {
   return 3LL * 3 * kBasisBlk * kBlockPts * 2 + 2LL * kBasisBlk * 4;      // Phi (two slicings) and X, 3 planes
 }
 
+// Largest per-tile footprint of the precision modes (the shared workspace
+// holds either layout).
+int64_t tile_bytes_max() { return std::max(tile_bytes_for(KLDI_FP64), tile_bytes_for(KLDI_BF16X6)); }
+
+void free_work_lists(kldi_plan* P) {
+  for (auto& b : P->batches) {
+    if (b.d_v64_g) cudaFree(b.d_v64_g);
+    if (b.d_v64_work) cudaFree(b.d_v64_work);
+    if (b.d_vtc_g) cudaFree(b.d_vtc_g);
+    if (b.d_vtc_work) cudaFree(b.d_vtc_work);
+  }
+  P->batches.clear();
+}
+
+// Batches of grid blocks whose tiles fit `cap` tiles, and per batch the V
+// work lists: FP64 per basis-block pair (p <= q), tensor cores per 128-tile
+// pair (P <= Q), each cut into segments of grid blocks.
+kldi_status build_work(kldi_plan* P, int64_t cap) {
+  free_work_lists(P);
+  P->vtile_work = 0;
+  const int64_t nblk = P->nblocks, nbb = P->nbb;
+  int64_t maxblk = 0;
+  for (int64_t g = 0; g < nblk; ++g) maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
+  cap = std::max(cap, maxblk);
+  cap = std::min<int64_t>(cap, std::max<int64_t>(P->ntiles, 1));
+  P->tile_cap = cap;
+  {
+    int64_t g0 = 0;
+    while (g0 < nblk) {
+      int64_t g1 = g0;
+      while (g1 < nblk && P->blk_ptr[g1 + 1] - P->blk_ptr[g0] <= cap) ++g1;
+      Batch b;
+      b.g0 = g0;
+      b.g1 = g1;
+      b.t0 = P->blk_ptr[g0];
+      b.t1 = P->blk_ptr[g1];
+      P->batches.push_back(b);
+      g0 = g1;
+    }
+  }
+  const int kSeg = 64;
+  for (auto& b : P->batches) {
+    std::map<int64_t, std::vector<int32_t>> pl;
+    for (int64_t g = b.g0; g < b.g1; ++g)
+      for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i)
+        for (int32_t j = i; j < P->blk_ptr[g + 1]; ++j)
+          pl[(int64_t)P->blk_idx[i] * nbb + P->blk_idx[j]].push_back((int32_t)g);
+    std::vector<int32_t> gl;
+    std::vector<VWork64> wk;
+    for (auto& kv : pl) {
+      const int32_t p = (int32_t)(kv.first / nbb), q = (int32_t)(kv.first % nbb);
+      const int32_t base = (int32_t)gl.size();
+      gl.insert(gl.end(), kv.second.begin(), kv.second.end());
+      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += kSeg)
+        wk.push_back(VWork64{p, q, base + s0, base + std::min<int32_t>(s0 + kSeg, (int32_t)kv.second.size())});
+    }
+    KLDI_TRY(upload(P, &b.d_v64_g, gl.data(), gl.size()));
+    KLDI_TRY(upload(P, &b.d_v64_work, wk.data(), wk.size()));
+    b.n_v64_work = (int64_t)wk.size();
+    std::map<int64_t, std::vector<int32_t>> tl;
+    const int64_t nvt = P->nvt;
+    for (int64_t g = b.g0; g < b.g1; ++g) {
+      std::vector<int32_t> vt;
+      for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i) {
+        const int32_t T = P->blk_idx[i] / 4;
+        if (vt.empty() || vt.back() != T) vt.push_back(T);
+      }
+      for (size_t i = 0; i < vt.size(); ++i)
+        for (size_t j = i; j < vt.size(); ++j) tl[(int64_t)vt[i] * nvt + vt[j]].push_back((int32_t)g);
+    }
+    std::vector<int32_t> tg;
+    std::vector<VWorkTC> tw;
+    // segment length (grid blocks per work item): the tuned value, else about
+    // 4 work items per SM over the batch and at least 16 grid blocks
+    int64_t total = 0;
+    for (auto& kv : tl) total += (int64_t)kv.second.size();
+    const int32_t seg = P->tune.v_seg > 0 ? P->tune.v_seg
+                                         : (int32_t)std::max<int64_t>(16, total / (4 * std::max(P->num_sms, 1)) + 1);
+    for (auto& kv : tl) {
+      const int32_t Pt = (int32_t)(kv.first / nvt), Qt = (int32_t)(kv.first % nvt);
+      const int32_t base = (int32_t)tg.size();
+      tg.insert(tg.end(), kv.second.begin(), kv.second.end());
+      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += seg)
+        tw.push_back(VWorkTC{Pt, Qt, base + s0, base + std::min<int32_t>(s0 + seg, (int32_t)kv.second.size())});
+      P->vtile_work += (int64_t)kv.second.size();
+    }
+    KLDI_TRY(upload(P, &b.d_vtc_g, tg.data(), tg.size()));
+    KLDI_TRY(upload(P, &b.d_vtc_work, tw.data(), tw.size()));
+    b.n_vtc_work = (int64_t)tw.size();
+  }
+  return KLDI_OK;
+}
+
 kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
   if (prec == KLDI_TF32X3) {
     set_error("KLDI_TF32X3 is not provided: 11-bit slices cannot keep the tensor-core sums exact");
     return KLDI_EUNSUPPORTED;
+  }
+  if (P->ws) {
+    // per-tile buffers are views into the shared workspace (either layout)
+    uint8_t* base = static_cast<uint8_t*>(P->ws->base);
+    const int64_t cap = P->tile_cap;
+    P->d_phi64 = reinterpret_cast<double*>(base);
+    P->d_x64 = P->d_phi64 + cap * kBasisBlk * kBlockPts;
+    const size_t plane3 = (size_t)cap * 3 * kBasisBlk * kBlockPts;
+    P->d_phi_s = reinterpret_cast<uint16_t*>(base);
+    P->d_phic_s = P->d_phi_s + plane3;
+    P->d_x_s = P->d_phic_s + plane3;
+    P->d_phic_scale = reinterpret_cast<float*>(P->d_x_s + plane3);
+    P->d_x_scale = P->d_phic_scale + cap * kBasisBlk;
   }
   if (prec == KLDI_FP64) {
     if (!P->d_phi64) KLDI_TRY(dalloc(P, &P->d_phi64, (size_t)P->tile_cap * kBasisBlk * kBlockPts));
@@ -369,81 +487,13 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   if ((st = upload(P, &P->d_bmax, P->bmax.data(), P->bmax.size())) != KLDI_OK) return fail(st);
   if ((st = upload(P, &P->d_tile_of, tile_of.data(), tile_of.size())) != KLDI_OK) return fail(st);
 
-  // ---- batches: grid blocks whose tiles fit the per-batch tile capacity
-  size_t free_b = 0, total_b = 0;
-  cudaMemGetInfo(&free_b, &total_b);
-  const int64_t per_tile = std::max(tile_bytes_for(KLDI_FP64), tile_bytes_for(KLDI_TF32X3));
-  int64_t cap = (int64_t)(0.35 * (double)free_b) / per_tile;
-  if (const char* env = getenv("KLDI_TILE_CAP")) cap = std::max<int64_t>(1, atoll(env));
-  int64_t maxblk = 0;
-  for (int64_t g = 0; g < nblk; ++g) maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
-  cap = std::max(cap, maxblk);
-  cap = std::min<int64_t>(cap, std::max<int64_t>(P->ntiles, 1));
-  P->tile_cap = cap;
+  // ---- batches and V work lists (tile buffers are allocated at first use)
   {
-    int64_t g0 = 0;
-    while (g0 < nblk) {
-      int64_t g1 = g0;
-      while (g1 < nblk && P->blk_ptr[g1 + 1] - P->blk_ptr[g0] <= cap) ++g1;
-      Batch b;
-      b.g0 = g0;
-      b.g1 = g1;
-      b.t0 = P->blk_ptr[g0];
-      b.t1 = P->blk_ptr[g1];
-      P->batches.push_back(b);
-      g0 = g1;
-    }
-  }
-  // ---- V work lists per batch
-  const int kSeg = 64;
-  for (auto& b : P->batches) {
-    // FP64: per basis-block pair (p <= q)
-    std::map<int64_t, std::vector<int32_t>> pl;
-    for (int64_t g = b.g0; g < b.g1; ++g)
-      for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i)
-        for (int32_t j = i; j < P->blk_ptr[g + 1]; ++j)
-          pl[(int64_t)P->blk_idx[i] * nbb + P->blk_idx[j]].push_back((int32_t)g);
-    std::vector<int32_t> gl;
-    std::vector<VWork64> wk;
-    for (auto& kv : pl) {
-      const int32_t p = (int32_t)(kv.first / nbb), q = (int32_t)(kv.first % nbb);
-      const int32_t base = (int32_t)gl.size();
-      gl.insert(gl.end(), kv.second.begin(), kv.second.end());
-      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += kSeg)
-        wk.push_back(VWork64{p, q, base + s0, base + std::min<int32_t>(s0 + kSeg, (int32_t)kv.second.size())});
-    }
-    if ((st = upload(P, &b.d_v64_g, gl.data(), gl.size())) != KLDI_OK) return fail(st);
-    if ((st = upload(P, &b.d_v64_work, wk.data(), wk.size())) != KLDI_OK) return fail(st);
-    b.n_v64_work = (int64_t)wk.size();
-    // tensor cores: per V tile pair (P <= Q), 128-function tiles
-    std::map<int64_t, std::vector<int32_t>> tl;
-    const int64_t nvt = P->nvt;
-    for (int64_t g = b.g0; g < b.g1; ++g) {
-      std::vector<int32_t> vt;
-      for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i) {
-        const int32_t T = P->blk_idx[i] / 4;
-        if (vt.empty() || vt.back() != T) vt.push_back(T);
-      }
-      for (size_t i = 0; i < vt.size(); ++i)
-        for (size_t j = i; j < vt.size(); ++j) tl[(int64_t)vt[i] * nvt + vt[j]].push_back((int32_t)g);
-    }
-    std::vector<int32_t> tg;
-    std::vector<VWorkTC> tw;
-    // segment length: about 4 work items per SM over the whole batch, at least 16 grid blocks
-    int64_t total = 0;
-    for (auto& kv : tl) total += (int64_t)kv.second.size();
-    const int32_t kSegTC = (int32_t)std::max<int64_t>(16, total / (4 * 148) + 1);
-    for (auto& kv : tl) {
-      const int32_t Pt = (int32_t)(kv.first / nvt), Qt = (int32_t)(kv.first % nvt);
-      const int32_t base = (int32_t)tg.size();
-      tg.insert(tg.end(), kv.second.begin(), kv.second.end());
-      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += kSegTC)
-        tw.push_back(VWorkTC{Pt, Qt, base + s0, base + std::min<int32_t>(s0 + kSegTC, (int32_t)kv.second.size())});
-      P->vtile_work += (int64_t)kv.second.size();
-    }
-    if ((st = upload(P, &b.d_vtc_g, tg.data(), tg.size())) != KLDI_OK) return fail(st);
-    if ((st = upload(P, &b.d_vtc_work, tw.data(), tw.size())) != KLDI_OK) return fail(st);
-    b.n_vtc_work = (int64_t)tw.size();
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    int64_t cap = (int64_t)(0.35 * (double)free_b) / tile_bytes_max();
+    if (const char* env = getenv("KLDI_TILE_CAP")) cap = std::max<int64_t>(1, atoll(env));
+    if ((st = build_work(P, cap)) != KLDI_OK) return fail(st);
   }
 
   // ---- per-evaluation buffers
@@ -459,7 +509,6 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   if ((st = dalloc(P, &P->d_exc, 1)) != KLDI_OK) return fail(st);
   if ((st = dalloc(P, &P->d_err, 1)) != KLDI_OK) return fail(st);
   if (cudaMemset(P->d_err, 0, sizeof(int)) != cudaSuccess) { set_error("kldi_screen: memset failed"); return fail(KLDI_ECUDA); }
-  if ((st = ensure_tile_buffers(P, P->prec)) != KLDI_OK) return fail(st);
   *out = P;
   return KLDI_OK;
 }
@@ -471,6 +520,87 @@ extern "C" kldi_status kldi_plan_set_precision(kldi_plan* P, int prec) {
   }
   KLDI_TRY(ensure_tile_buffers(P, prec));
   P->prec = prec;
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_workspace_create(int64_t bytes, kldi_workspace** out) {
+  if (!out || bytes <= 0) {
+    set_error("kldi_workspace_create: bad argument");
+    return KLDI_EINVAL;
+  }
+  *out = nullptr;
+  kldi_workspace* ws = new (std::nothrow) kldi_workspace;
+  if (!ws) {
+    set_error("kldi_workspace_create: out of host memory");
+    return KLDI_ENOMEM;
+  }
+  cudaGetDevice(&ws->device);
+  if (cudaMalloc(&ws->base, (size_t)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete ws;
+    set_error("kldi_workspace_create: cudaMalloc of %lld bytes failed", (long long)bytes);
+    return KLDI_ENOMEM;
+  }
+  ws->bytes = bytes;
+  *out = ws;
+  return KLDI_OK;
+}
+
+extern "C" void kldi_workspace_free(kldi_workspace* ws) {
+  if (!ws) return;
+  if (ws->base) cudaFree(ws->base);
+  delete ws;
+}
+
+extern "C" kldi_status kldi_plan_set_workspace(kldi_plan* P, const kldi_workspace* ws) {
+  if (!P) {
+    set_error("kldi_plan_set_workspace: null plan");
+    return KLDI_EINVAL;
+  }
+  int64_t cap;
+  if (ws) {
+    if (ws->device != P->device) {
+      set_error("kldi_plan_set_workspace: workspace and plan live on different devices");
+      return KLDI_EINVAL;
+    }
+    cap = ws->bytes / tile_bytes_max();
+    int64_t maxblk = 0;
+    for (int64_t g = 0; g < P->nblocks; ++g) maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
+    if (cap < maxblk) {
+      set_error("kldi_plan_set_workspace: %lld bytes hold %lld tiles, a grid block needs %lld", (long long)ws->bytes,
+                (long long)cap, (long long)maxblk);
+      return KLDI_EINVAL;
+    }
+  } else {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    cap = (int64_t)(0.35 * (double)free_b) / tile_bytes_max();
+  }
+  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+  free_own_tile_buffers(P);
+  P->ws = ws;
+  KLDI_TRY(build_work(P, cap));
+  if (ws) KLDI_TRY(ensure_tile_buffers(P, P->prec));
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_plan_set_tuning(kldi_plan* P, const kldi_tuning* t) {
+  if (!P || !t || t->v_seg < 0) {
+    set_error("kldi_plan_set_tuning: bad argument");
+    return KLDI_EINVAL;
+  }
+  if (t->v_seg == P->tune.v_seg) return KLDI_OK;
+  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+  P->tune = *t;
+  return build_work(P, P->tile_cap);
+}
+
+extern "C" kldi_status kldi_plan_get_tuning(const kldi_plan* P, kldi_tuning* t) {
+  if (!P || !t) {
+    set_error("kldi_plan_get_tuning: null argument");
+    return KLDI_EINVAL;
+  }
+  *t = P->tune;
   return KLDI_OK;
 }
 

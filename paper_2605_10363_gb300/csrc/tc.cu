@@ -679,17 +679,14 @@ __global__ void __launch_bounds__(320, 1)
   }
 }
 
+kldi_status prepare_tc_kernels();   // defined after the kernels: shared-memory opt-in, register check
+
 template <int NS>
 static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, double* grad_out, cudaStream_t s) {
   using C = RhoCfg<NS>;
   const int64_t n = b.g1 - b.g0;
   if (n == 0) return KLDI_OK;
-  static bool attr = false;
-  if (!attr) {
-    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
-    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
-    attr = true;
-  }
+  KLDI_TRY(prepare_tc_kernels());
   const unsigned grid = (unsigned)std::min<int64_t>(n, P->num_sms);
   KLDI_TRY_CUDA(cudaMemsetAsync(rho_out + b.g0 * kBlockPts, 0, sizeof(double) * n * kBlockPts, s));
   if (P->gga) KLDI_TRY_CUDA(cudaMemsetAsync(grad_out + b.g0 * kBlockPts * 3, 0, sizeof(double) * n * kBlockPts * 3, s));
@@ -969,19 +966,7 @@ template <int NS>
 static kldi_status v_ns(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
   using C = VCfg<NS>;
   if (b.n_vtc_work == 0) return KLDI_OK;
-  static bool attr = false;
-  if (!attr) {
-    // the register budgets of the warpgroups assume the launch allocation
-    cudaFuncAttributes fa;
-    KLDI_TRY_CUDA(cudaFuncGetAttributes(&fa, k_v_tc<NS>));
-    if (fa.numRegs != C::kLaunchRegs) {
-      set_error("k_v_tc: built with %d registers per thread, register budgets assume %d", fa.numRegs,
-                C::kLaunchRegs);
-      return KLDI_EUNSUPPORTED;
-    }
-    KLDI_TRY_CUDA(cudaFuncSetAttribute(k_v_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
-    attr = true;
-  }
+  KLDI_TRY(prepare_tc_kernels());
   const unsigned grid = (unsigned)std::min<int64_t>(b.n_vtc_work, P->num_sms);
   k_v_tc<NS><<<grid, C::kThreads, C::kSmem, s>>>(
       P->list_view(), b.d_vtc_work, b.n_vtc_work, b.d_vtc_g, b.t0, reinterpret_cast<const uint8_t*>(P->d_phic_s),
@@ -989,6 +974,45 @@ static kldi_status v_ns(const kldi_plan* P, const Batch& b, double* V, cudaStrea
       reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, P->opt.t_b, V, P->d_err);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
+}
+
+template <int NS>
+static kldi_status prepare_v_kernel() {
+  using C = VCfg<NS>;
+  // the register budgets of the warpgroups assume the launch allocation
+  cudaFuncAttributes fa;
+  KLDI_TRY_CUDA(cudaFuncGetAttributes(&fa, k_v_tc<NS>));
+  if (fa.numRegs != C::kLaunchRegs) {
+    set_error("k_v_tc: built with %d registers per thread, register budgets assume %d", fa.numRegs, C::kLaunchRegs);
+    return KLDI_EUNSUPPORTED;
+  }
+  KLDI_TRY_CUDA(cudaFuncSetAttribute(k_v_tc<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+  return KLDI_OK;
+}
+
+template <int NS>
+static kldi_status prepare_rho_kernel() {
+  using C = RhoCfg<NS>;
+  KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+  KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+  return KLDI_OK;
+}
+
+// Kernel attributes set once per process (outside any stream capture).
+kldi_status prepare_tc_kernels() {
+  static kldi_status done = KLDI_EINVAL;
+  static bool tried = false;
+  if (tried) {
+    if (done != KLDI_OK) set_error("tensor-core kernels could not be prepared");
+    return done;
+  }
+  tried = true;
+  done = KLDI_OK;
+  if ((done = prepare_rho_kernel<2>()) != KLDI_OK) return done;
+  if ((done = prepare_rho_kernel<3>()) != KLDI_OK) return done;
+  if ((done = prepare_v_kernel<2>()) != KLDI_OK) return done;
+  done = prepare_v_kernel<3>();
+  return done;
 }
 
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {

@@ -90,6 +90,17 @@ def _load():
         "kldi_mlp_eval": (C.c_int, [vp, vp, vp, C.c_int64, C.c_double, vp, vp, vp, vp]),
         "kldi_plan_set_mlp": (C.c_int, [vp, vp]),
         "kldi_mlp_free": (None, [vp]),
+        "kldi_workspace_create": (C.c_int, [C.c_int64, C.POINTER(vp)]),
+        "kldi_workspace_free": (None, [vp]),
+        "kldi_plan_set_workspace": (C.c_int, [vp, vp]),
+        "kldi_plan_set_tuning": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "kldi_plan_get_tuning": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "kldi_plan_autotune": (C.c_int, [vp, C.c_int, vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "kldi_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), vp, vp,
+                                        C.POINTER(vp)]),
+        "kldi_batch_launch": (C.c_int, [vp]),
+        "kldi_batch_sync": (C.c_int, [vp]),
+        "kldi_batch_free": (None, [vp]),
         "kldi_plan_free": (None, [vp]),
         "kldi_grid_free": (None, [vp]),
         "kldi_last_error": (C.c_char_p, []),
@@ -193,6 +204,27 @@ class Plan:
         _check(LIB.kldi_plan_stage_times(self.h, _ptr(ms), _ptr(n)))
         return ms, n
 
+    def set_workspace(self, ws):
+        _check(LIB.kldi_plan_set_workspace(self.h, ws.h if ws is not None else None))
+        self._ws = ws               # the workspace must outlive its use by the plan
+
+    def set_tuning(self, v_seg):
+        t = C.c_int(int(v_seg))
+        _check(LIB.kldi_plan_set_tuning(self.h, C.byref(t)))
+
+    def tuning(self):
+        t = C.c_int()
+        _check(LIB.kldi_plan_get_tuning(self.h, C.byref(t)))
+        return {"v_seg": t.value}
+
+    def autotune(self, xc, D, reps=3):
+        """Tune on a device density matrix; returns (tuning, ms per call)."""
+        t = C.c_int()
+        ms = C.c_double()
+        _check(LIB.kldi_plan_autotune(self.h, XC[xc] if isinstance(xc, str) else int(xc), _ptr(D), int(reps),
+                                      C.byref(t), C.byref(ms)))
+        return {"v_seg": t.value}, ms.value
+
     def set_precision(self, prec):
         _check(LIB.kldi_plan_set_precision(self.h, PREC[prec] if isinstance(prec, str) else int(prec)))
 
@@ -242,6 +274,47 @@ def exc_energy_noalloc(xc, npoints, rho, grad, w, Exc, rho_min=1e-14, stream=0):
     """E_xc of a device-resident density with no allocation (kldi_exc_energy_noalloc)."""
     _check(LIB.kldi_exc_energy_noalloc(XC[xc] if isinstance(xc, str) else int(xc), int(npoints), _ptr(rho),
                                        _ptr(grad), _ptr(w), float(rho_min), _ptr(Exc), C.c_void_p(int(stream))))
+
+
+class Workspace:
+    """Shared device arena for the per-tile buffers of several plans."""
+
+    def __init__(self, nbytes):
+        h = C.c_void_p()
+        _check(LIB.kldi_workspace_create(int(nbytes), C.byref(h)))
+        self.h = h
+        self.nbytes = int(nbytes)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            LIB.kldi_workspace_free(self.h)
+            self.h = None
+
+
+class Batch:
+    """All frames' evaluations captured into one CUDA graph (device arrays)."""
+
+    def __init__(self, plans, xc, Ds, Vs, Exc, stream=0):
+        n = len(plans)
+        self._keep = (list(plans), list(Ds), list(Vs), Exc)
+        ph = (C.c_void_p * n)(*[p.h.value for p in plans])
+        dh = (C.c_void_p * n)(*[_ptr(d) for d in Ds])
+        vh = (C.c_void_p * n)(*[_ptr(v) for v in Vs])
+        h = C.c_void_p()
+        _check(LIB.kldi_batch_create(ph, n, XC[xc] if isinstance(xc, str) else int(xc), dh, vh, _ptr(Exc),
+                                     C.c_void_p(int(stream)), C.byref(h)))
+        self.h = h
+
+    def launch(self):
+        _check(LIB.kldi_batch_launch(self.h))
+
+    def sync(self):
+        _check(LIB.kldi_batch_sync(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            LIB.kldi_batch_free(self.h)
+            self.h = None
 
 
 class Mlp:

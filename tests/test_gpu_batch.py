@@ -1,0 +1,124 @@
+"""Batched frames (uneven water clusters, each with its own D): a shared
+workspace, one CUDA-graph launch for all frames, and the V-product tuner.
+
+Batched and single-frame results must agree: E_xc bitwise (per-block sums in a
+fixed order, independent of how grid blocks are batched) and V to 1e-12
+relative (FP64 atomics of work-item partial sums, whose segmentation depends
+on the batches).  One frame is also held to the oracle at the BF16x6
+tolerance (|dE| <= 1e-6 Ha, max|dV| <= 3e-7)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis as ob
+from oracle import exc as oe
+from oracle import grid as og
+
+pytestmark = pytest.mark.gpu
+
+FRAMES = [(0, 3), (1, 5), (2, 4)]      # (frame index, waters): uneven sizes
+TILE_BYTES = 73984                     # per-tile footprint of the shared workspace
+
+
+def _kldi():
+    from paper_2605_10363_gb300 import kldi
+    return kldi
+
+
+@pytest.fixture(scope="module")
+def frames():
+    return [synth.make_system(4, frame=k, nwaters=n) for k, n in FRAMES]
+
+
+def _single(system, prec):
+    kldi = _kldi()
+    plan = kldi.plan_for_system(system, prec=prec, xc="pbe")
+    V = np.zeros((system.nbf, system.nbf))
+    E = np.zeros(1)
+    kldi.exc(plan, "pbe", system.D, V, E)
+    return E[0], V
+
+
+def _batched_setup(frames, prec, ws_tiles):
+    import torch
+    kldi = _kldi()
+    ws = kldi.Workspace(ws_tiles * TILE_BYTES)
+    plans = []
+    for s in frames:
+        p = kldi.plan_for_system(s, prec=prec, xc="pbe")
+        p.set_workspace(ws)
+        plans.append(p)
+    Ds = [torch.from_numpy(s.D).cuda() for s in frames]
+    Vs = [torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda") for s in frames]
+    E = torch.zeros(len(frames), dtype=torch.float64, device="cuda")
+    return ws, plans, Ds, Vs, E
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
+def test_batched_equals_single_frames(frames, prec):
+    kldi = _kldi()
+    ws, plans, Ds, Vs, E = _batched_setup(frames, prec, 4000)
+    assert any(len(p.stats) and p.stats["retained"] > 4000 for p in plans)   # several batches per frame
+    kldi.exc_batched(plans, "pbe", Ds, Vs, E)
+    Eb = E.cpu().numpy()
+    for k, s in enumerate(frames):
+        E1, V1 = _single(s, prec)
+        assert Eb[k] == E1, (k, Eb[k], E1)
+        Vb = Vs[k].cpu().numpy()
+        assert np.abs(Vb - V1).max() <= 1e-12 * np.abs(V1).max()
+        assert np.array_equal(Vb, Vb.T)
+
+
+def test_graph_relaunch_and_oracle(frames):
+    import torch
+    kldi = _kldi()
+    ws, plans, Ds, Vs, E = _batched_setup(frames, "bf16x6", 4000)
+    b = kldi.Batch(plans, "pbe", Ds, Vs, E)
+    b.launch()
+    b.sync()
+    E1 = E.cpu().numpy().copy()
+    V1 = [v.cpu().numpy().copy() for v in Vs]
+    for v in Vs:
+        v.fill_(7.0)                               # the graph overwrites V
+    E.fill_(0.0)
+    b.launch()
+    b.sync()
+    assert np.array_equal(E.cpu().numpy(), E1)
+    for v, v1 in zip(Vs, V1):
+        assert np.abs(v.cpu().numpy() - v1).max() <= 1e-12 * np.abs(v1).max()
+    # frame 0 against the oracle
+    s = frames[0]
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    ref = oe.evaluate(s, g, ob.build_shells(s.xyz, s.basis), screened=True)
+    assert abs(E1[0] - ref.E) <= 1e-6
+    assert np.abs(V1[0] - ref.V).max() <= 3e-7
+
+
+def test_autotune_keeps_results(frames):
+    import torch
+    kldi = _kldi()
+    s = frames[1]
+    plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe")
+    D = torch.from_numpy(s.D).cuda()
+    V0 = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda")
+    E0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    kldi.exc(plan, "pbe", D, V0, E0)
+    best, ms = plan.autotune("pbe", D, reps=2)
+    assert best["v_seg"] in (0, 4, 8, 16, 32, 64, 128) and ms > 0
+    assert plan.tuning() == best
+    V1 = torch.zeros_like(V0)
+    E1 = torch.zeros_like(E0)
+    kldi.exc(plan, "pbe", D, V1, E1)
+    assert E1.item() == E0.item()
+    assert (V1 - V0).abs().max().item() <= 1e-12 * V0.abs().max().item()
+    plan.set_tuning(8)
+    assert plan.tuning()["v_seg"] == 8
+
+
+def test_workspace_too_small(frames):
+    kldi = _kldi()
+    plan = kldi.plan_for_system(frames[0], prec="bf16x6", xc="pbe")
+    ws = kldi.Workspace(TILE_BYTES)            # one tile: less than a grid block retains
+    with pytest.raises(kldi.KldiError) as e:
+        plan.set_workspace(ws)
+    assert e.value.status == kldi.EINVAL
