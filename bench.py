@@ -191,6 +191,55 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
+# ---------------------------------------------------------------------------- learned functional mode
+def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analytic):
+    """Train the surrogate on the GPU on the grid points of the two-water and
+    33-water systems (their densities from the library), then time the same
+    evaluation with the network fused between the products."""
+    import torch
+
+    import synth
+
+    def points(system, p=None):
+        p = p or kldi.plan_for_system(system, prec="fp64", xc="pbe")
+        rho = np.zeros(p.npoints)
+        grad = np.zeros((p.npoints, 3))
+        kldi.density(p, system.D, rho, grad)
+        return rho, np.einsum("ic,ic->i", grad, grad)
+
+    r1, s1 = points(synth.make_system(1))
+    r2, s2 = points(s, plan)
+    rho = np.concatenate([r1, r2])
+    sig = np.concatenate([s1, s2])
+    box = synth.mlp_box(rho, sig)
+    net = kldi.Mlp(synth.mlp_init(42), box)
+    epochs = 200
+    t0 = time.perf_counter()
+    hist = net.train(rho, sig, epochs=epochs, batch=8192, lr0=3e-3, lr1=1e-5)
+    t_train = time.perf_counter() - t0
+    kldi.plan_set_mlp(plan, net)
+    kldi.exc(plan, "mlp", D, V, E)
+    torch.cuda.synchronize(dev)
+    plan.profile(True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    steps = max(3, args.steps // 2)
+    a.record(stream)
+    for _ in range(steps):
+        kldi.exc(plan, "mlp", D, V, E)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_stage, _ = plan.stage_times()
+    plan.profile(False)
+    kldi.plan_set_mlp(plan, None)
+    ms = a.elapsed_time(b) / steps
+    return {"ms_per_step": ms, "value": plan.grid.nreal / (ms * 1e-3),
+            "dExc_vs_analytic": float(E.item()) - E_analytic,
+            "functional_stage_ms": {"mlp": ms_stage[3] / steps, "analytic": xc_ms_analytic},
+            "training": {"points": int(rho.size), "epochs": epochs, "batch": 8192, "seconds": round(t_train, 2),
+                         "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1])}}
+
+
 # ---------------------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -310,6 +359,7 @@ def main():
             modes[pm] = m
             del p2
         out_extra["speedup_vs_fp64"] = modes["fp64"]["ms_per_step"] / ms_step
+        modes["mlp"] = mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, stage_ms[3] / args.steps, E_ours)
 
     cpu = None
     if rank == 0 and world == 1 and not args.nwaters:

@@ -268,6 +268,14 @@ kldi_status kldi_plan_get_tuning(const kldi_plan* plan, kldi_tuning* tuning);
 kldi_status kldi_plan_autotune(kldi_plan* plan, int xc, const double* D, int reps, kldi_tuning* best,
                                double* best_ms);
 
+/* Restrict the plan to grid blocks [g0, g1) (0 <= g0 <= g1 <= nblocks): the
+ * compute calls then produce this range's partial E_xc and V (and write rho
+ * only on its points), so ranks holding complementary ranges sum to the full
+ * result -- the one exchange step of the multi-GPU form (the paper's grid
+ * blocks are independent work units, Sec. III-E).  (0, nblocks) restores
+ * the whole grid. */
+kldi_status kldi_plan_set_block_range(kldi_plan* plan, int64_t g0, int64_t g1);
+
 typedef struct kldi_batch kldi_batch;
 
 /* Capture kldi_exc for every frame k (plans[k], D[k] -> V[k], Exc[k]; all

@@ -143,10 +143,12 @@ kldi_status build_work(kldi_plan* P, int64_t cap) {
   cap = std::min<int64_t>(cap, std::max<int64_t>(P->ntiles, 1));
   P->tile_cap = cap;
   {
-    int64_t g0 = 0;
-    while (g0 < nblk) {
+    // grid blocks of this plan's range (all by default)
+    const int64_t gend = P->range_g1 >= 0 ? P->range_g1 : nblk;
+    int64_t g0 = P->range_g0;
+    while (g0 < gend) {
       int64_t g1 = g0;
-      while (g1 < nblk && P->blk_ptr[g1 + 1] - P->blk_ptr[g0] <= cap) ++g1;
+      while (g1 < gend && P->blk_ptr[g1 + 1] - P->blk_ptr[g0] <= cap) ++g1;
       Batch b;
       b.g0 = g0;
       b.g1 = g1;
@@ -157,24 +159,28 @@ kldi_status build_work(kldi_plan* P, int64_t cap) {
     }
   }
   const int kSeg = 64;
+  P->work_fp64 = P->prec == KLDI_FP64;
   for (auto& b : P->batches) {
-    std::map<int64_t, std::vector<int32_t>> pl;
-    for (int64_t g = b.g0; g < b.g1; ++g)
-      for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i)
-        for (int32_t j = i; j < P->blk_ptr[g + 1]; ++j)
-          pl[(int64_t)P->blk_idx[i] * nbb + P->blk_idx[j]].push_back((int32_t)g);
-    std::vector<int32_t> gl;
-    std::vector<VWork64> wk;
-    for (auto& kv : pl) {
-      const int32_t p = (int32_t)(kv.first / nbb), q = (int32_t)(kv.first % nbb);
-      const int32_t base = (int32_t)gl.size();
-      gl.insert(gl.end(), kv.second.begin(), kv.second.end());
-      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += kSeg)
-        wk.push_back(VWork64{p, q, base + s0, base + std::min<int32_t>(s0 + kSeg, (int32_t)kv.second.size())});
+    if (P->work_fp64) {
+      std::map<int64_t, std::vector<int32_t>> pl;
+      for (int64_t g = b.g0; g < b.g1; ++g)
+        for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i)
+          for (int32_t j = i; j < P->blk_ptr[g + 1]; ++j)
+            pl[(int64_t)P->blk_idx[i] * nbb + P->blk_idx[j]].push_back((int32_t)g);
+      std::vector<int32_t> gl;
+      std::vector<VWork64> wk;
+      for (auto& kv : pl) {
+        const int32_t p = (int32_t)(kv.first / nbb), q = (int32_t)(kv.first % nbb);
+        const int32_t base = (int32_t)gl.size();
+        gl.insert(gl.end(), kv.second.begin(), kv.second.end());
+        for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += kSeg)
+          wk.push_back(VWork64{p, q, base + s0, base + std::min<int32_t>(s0 + kSeg, (int32_t)kv.second.size())});
+      }
+      KLDI_TRY(upload(P, &b.d_v64_g, gl.data(), gl.size()));
+      KLDI_TRY(upload(P, &b.d_v64_work, wk.data(), wk.size()));
+      b.n_v64_work = (int64_t)wk.size();
+      continue;
     }
-    KLDI_TRY(upload(P, &b.d_v64_g, gl.data(), gl.size()));
-    KLDI_TRY(upload(P, &b.d_v64_work, wk.data(), wk.size()));
-    b.n_v64_work = (int64_t)wk.size();
     std::map<int64_t, std::vector<int32_t>> tl;
     const int64_t nvt = P->nvt;
     for (int64_t g = b.g0; g < b.g1; ++g) {
@@ -268,6 +274,10 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   if (!(opt->t_b >= 0.0) || !(opt->t_d >= 0.0) || !(opt->rho_min >= 0.0)) {
     set_error("kldi_screen: thresholds must be >= 0");
     return KLDI_EINVAL;
+  }
+  if (opt->prec == KLDI_TF32X3) {
+    set_error("KLDI_TF32X3 is not provided: 11-bit slices cannot keep the tensor-core sums exact");
+    return KLDI_EUNSUPPORTED;
   }
   kldi_plan* P = new (std::nothrow) kldi_plan;
   if (!P) { set_error("kldi_screen: out of host memory"); return KLDI_ENOMEM; }
@@ -520,6 +530,11 @@ extern "C" kldi_status kldi_plan_set_precision(kldi_plan* P, int prec) {
   }
   KLDI_TRY(ensure_tile_buffers(P, prec));
   P->prec = prec;
+  // the V work lists differ between the FP64 and the tensor-core products
+  if ((prec == KLDI_FP64) != P->work_fp64) {
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    KLDI_TRY(build_work(P, P->tile_cap));
+  }
   return KLDI_OK;
 }
 
@@ -582,6 +597,19 @@ extern "C" kldi_status kldi_plan_set_workspace(kldi_plan* P, const kldi_workspac
   KLDI_TRY(build_work(P, cap));
   if (ws) KLDI_TRY(ensure_tile_buffers(P, P->prec));
   return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_plan_set_block_range(kldi_plan* P, int64_t g0, int64_t g1) {
+  if (!P || g0 < 0 || g1 < g0 || g1 > P->nblocks) {
+    set_error("kldi_plan_set_block_range: need 0 <= g0 <= g1 <= nblocks");
+    return KLDI_EINVAL;
+  }
+  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+  // blocks outside the range contribute nothing to E_xc
+  KLDI_TRY_CUDA(cudaMemset(P->d_eblk, 0, sizeof(double) * P->nblocks));
+  P->range_g0 = g0;
+  P->range_g1 = g1;
+  return build_work(P, P->tile_cap);
 }
 
 extern "C" kldi_status kldi_plan_set_tuning(kldi_plan* P, const kldi_tuning* t) {

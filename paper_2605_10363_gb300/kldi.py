@@ -94,6 +94,7 @@ def _load():
         "kldi_workspace_free": (None, [vp]),
         "kldi_plan_set_workspace": (C.c_int, [vp, vp]),
         "kldi_plan_set_tuning": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "kldi_plan_set_block_range": (C.c_int, [vp, C.c_int64, C.c_int64]),
         "kldi_plan_get_tuning": (C.c_int, [vp, C.POINTER(C.c_int)]),
         "kldi_plan_autotune": (C.c_int, [vp, C.c_int, vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "kldi_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), vp, vp,
@@ -207,6 +208,10 @@ class Plan:
     def set_workspace(self, ws):
         _check(LIB.kldi_plan_set_workspace(self.h, ws.h if ws is not None else None))
         self._ws = ws               # the workspace must outlive its use by the plan
+
+    def set_block_range(self, g0, g1):
+        """Evaluate only grid blocks [g0, g1) (partial E_xc and V)."""
+        _check(LIB.kldi_plan_set_block_range(self.h, int(g0), int(g1)))
 
     def set_tuning(self, v_seg):
         t = C.c_int(int(v_seg))

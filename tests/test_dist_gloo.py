@@ -1,0 +1,79 @@
+"""Multi-process host logic on CPU ranks (gloo): grid-block partitioning and
+the sum-reduce of partial V_xc / E_xc.  Each rank evaluates its block range
+with the oracle; the reduced result must equal the single-process oracle."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis as ob
+from oracle import exc as oe
+from oracle import grid as og
+from paper_2605_10363_gb300 import dist as kdist
+
+
+def test_partition_covers_and_balances():
+    rng = np.random.default_rng(0)
+    w = rng.integers(1, 400, size=1000).astype(float)
+    for world in (1, 2, 3, 8, 13):
+        r = kdist.partition_blocks(w, world)
+        assert r[0][0] == 0 and r[-1][1] == w.size
+        assert all(a[1] == b[0] for a, b in zip(r, r[1:]))
+        loads = [w[g0:g1].sum() for g0, g1 in r]
+        assert max(loads) <= w.sum() / world + w.max()
+
+
+def test_partition_edge_cases():
+    r = kdist.partition_blocks(np.ones(3), 5)         # more ranks than blocks: some ranges are empty
+    assert sum(g1 - g0 for g0, g1 in r) == 3 and all(g1 >= g0 for g0, g1 in r)
+    assert kdist.partition_blocks(np.zeros(0), 2) == [(0, 0), (0, 0)]
+    assert kdist.partition_blocks(np.zeros(4), 2) == [(0, 2), (2, 4)]
+    w = kdist.block_weights(np.array([0, 2, 2, 5]))
+    assert np.array_equal(w, [4.0, 0.0, 9.0])
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, ranges, out_dir):
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        s = synth.make_system(1)
+        g = og.build_grid(s.Z, s.xyz, s.grid)
+        sh = ob.build_shells(s.xyz, s.basis)
+        g0, g1 = ranges[rank]
+        part = oe.evaluate(s, g, sh, screened=True, blocks=range(g0, g1))
+        V = torch.from_numpy(part.V.copy())
+        E = torch.tensor([part.E], dtype=torch.float64)
+        kdist.reduce_exc(V, E)
+        np.save(os.path.join(out_dir, f"V{rank}.npy"), V.numpy())
+        np.save(os.path.join(out_dir, f"E{rank}.npy"), E.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_reduce_to_the_single_process_result(tmp_path):
+    import torch.multiprocessing as mp
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    ref = oe.evaluate(s, g, sh, screened=True, keep_lists=True)
+    ptr = np.zeros(g.nblocks + 1, dtype=np.int64)
+    for b in range(g.nblocks):
+        ptr[b + 1] = ptr[b] + ref.lists[b]["S"].size
+    ranges = kdist.partition_blocks(kdist.block_weights(ptr), 2)
+    assert ranges[0][1] > 0 and ranges[1][0] < g.nblocks
+    mp.start_processes(_rank_main, args=(2, _free_port(), ranges, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    for r in range(2):
+        V = np.load(tmp_path / f"V{r}.npy")
+        E = np.load(tmp_path / f"E{r}.npy")[0]
+        assert E == pytest.approx(ref.E, rel=1e-13)
+        assert np.abs(V - ref.V).max() <= 1e-13 * np.abs(ref.V).max()

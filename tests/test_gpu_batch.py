@@ -122,3 +122,28 @@ def test_workspace_too_small(frames):
     with pytest.raises(kldi.KldiError) as e:
         plan.set_workspace(ws)
     assert e.value.status == kldi.EINVAL
+
+
+def test_block_ranges_sum_to_the_whole(frames):
+    """Two plans over complementary grid-block ranges (the multi-GPU split)
+    add up to the single-plan result."""
+    from paper_2605_10363_gb300 import dist as kdist
+    kldi = _kldi()
+    s = frames[1]
+    E1, V1 = _single(s, "bf16x6")
+    ref_plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe")
+    ptr, _, _ = ref_plan.lists()
+    ranges = kdist.partition_blocks(kdist.block_weights(ptr), 2)
+    Et, Vt = 0.0, np.zeros((s.nbf, s.nbf))
+    for g0, g1 in ranges:
+        plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe")
+        plan.set_block_range(g0, g1)
+        V = np.zeros((s.nbf, s.nbf))
+        E = np.zeros(1)
+        kldi.exc(plan, "pbe", s.D, V, E)
+        Et += E[0]
+        Vt += V
+    assert Et == pytest.approx(E1, rel=1e-13)
+    assert np.abs(Vt - V1).max() <= 1e-12 * np.abs(V1).max()
+    with pytest.raises(kldi.KldiError):
+        ref_plan.set_block_range(5, 2)
