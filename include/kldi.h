@@ -250,9 +250,11 @@ void kldi_workspace_free(kldi_workspace* ws);
  * block's tiles do not fit.  Free the workspace after the plans. */
 kldi_status kldi_plan_set_workspace(kldi_plan* plan, const kldi_workspace* ws);
 
-/* Tunable decomposition of the tensor-core V product: a work item is one
- * 128 x 128 tile pair over v_seg consecutive grid blocks of its list
- * (K = 256 v_seg); v_seg = 0 chooses about four items per SM. */
+/* Tunable decomposition of the tensor-core V product: the grid blocks are cut
+ * into ranges of v_seg consecutive blocks, a work item is one 128 x 128 tile
+ * pair over the blocks of one range in its list, and items run range by
+ * range (so concurrent items share the range's tiles in L2); v_seg = 0
+ * chooses 16. */
 typedef struct {
   int v_seg;
 } kldi_tuning;

@@ -154,8 +154,9 @@ struct kldi_plan {
   int device = 0;
   int num_sms = 148;
   int64_t nbf = 0, nbb = 0, nbf_pad = 0, npoints = 0, nblocks = 0, ntiles = 0, nshell = 0, nprim_total = 0;
-  int64_t nvt = 0;  // W tiles per edge (ceil(nbb / 4))
+  int64_t nvt = 0;  // 128-function V tiles per edge (ceil(nbb / 4))
   int* d_err = nullptr;         // device error word (bounded-wait timeouts)
+  int* d_vnext = nullptr;       // work-item counter of the tensor-core V product
 
   // host copies of the retained lists
   std::vector<int32_t> blk_ptr, blk_idx;

@@ -83,7 +83,7 @@ void free_plan_buffers(kldi_plan* P) {
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of,
                   P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
-                  P->d_exc, P->d_err, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
+                  P->d_exc, P->d_err, P->d_vnext, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& b : P->batches) {
@@ -194,19 +194,31 @@ kldi_status build_work(kldi_plan* P, int64_t cap) {
     }
     std::vector<int32_t> tg;
     std::vector<VWorkTC> tw;
-    // segment length (grid blocks per work item): the tuned value, else about
-    // 4 work items per SM over the batch and at least 16 grid blocks
-    int64_t total = 0;
-    for (auto& kv : tl) total += (int64_t)kv.second.size();
-    const int32_t seg = P->tune.v_seg > 0 ? P->tune.v_seg
-                                         : (int32_t)std::max<int64_t>(16, total / (4 * std::max(P->num_sms, 1)) + 1);
+    // Work items are cut at grid-block ranges of `span` blocks and ordered
+    // range-major: CTAs running at the same time then work on the same few
+    // ranges, whose Phi~ / X~ tiles stay in L2 across the tile pairs that
+    // reuse them.  span: the tuned value, else 16 grid blocks.
+    const int64_t span = P->tune.v_seg > 0 ? P->tune.v_seg : 16;
+    struct PairList {
+      int32_t Pt, Qt, base, n;
+    };
+    std::vector<PairList> pls;
     for (auto& kv : tl) {
-      const int32_t Pt = (int32_t)(kv.first / nvt), Qt = (int32_t)(kv.first % nvt);
       const int32_t base = (int32_t)tg.size();
       tg.insert(tg.end(), kv.second.begin(), kv.second.end());
-      for (int32_t s0 = 0; s0 < (int32_t)kv.second.size(); s0 += seg)
-        tw.push_back(VWorkTC{Pt, Qt, base + s0, base + std::min<int32_t>(s0 + seg, (int32_t)kv.second.size())});
+      pls.push_back({(int32_t)(kv.first / nvt), (int32_t)(kv.first % nvt), base, (int32_t)kv.second.size()});
       P->vtile_work += (int64_t)kv.second.size();
+    }
+    std::vector<int32_t> pos(pls.size(), 0);   // next unassigned entry of each pair list
+    for (int64_t r0 = b.g0; r0 < b.g1; r0 += span) {
+      const int64_t r1 = std::min<int64_t>(r0 + span, b.g1);
+      for (size_t k = 0; k < pls.size(); ++k) {
+        const PairList& pl = pls[k];
+        int32_t e = pos[k];
+        while (e < pl.n && tg[pl.base + e] < r1) ++e;
+        if (e > pos[k]) tw.push_back(VWorkTC{pl.Pt, pl.Qt, pl.base + pos[k], pl.base + e});
+        pos[k] = e;
+      }
     }
     KLDI_TRY(upload(P, &b.d_vtc_g, tg.data(), tg.size()));
     KLDI_TRY(upload(P, &b.d_vtc_work, tw.data(), tw.size()));
@@ -518,6 +530,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   if ((st = dalloc(P, &P->d_eblk, (size_t)nblk)) != KLDI_OK) return fail(st);
   if ((st = dalloc(P, &P->d_exc, 1)) != KLDI_OK) return fail(st);
   if ((st = dalloc(P, &P->d_err, 1)) != KLDI_OK) return fail(st);
+  if ((st = dalloc(P, &P->d_vnext, 1)) != KLDI_OK) return fail(st);
   if (cudaMemset(P->d_err, 0, sizeof(int)) != cudaSuccess) { set_error("kldi_screen: memset failed"); return fail(KLDI_ECUDA); }
   *out = P;
   return KLDI_OK;

@@ -59,11 +59,12 @@ __host__ __device__ constexpr int tile_bytes(int ns) { return ns * kPlaneBytes; 
 // ---------------------------------------------------------------------------
 // slicing helpers
 __device__ __forceinline__ float pow2_ceil(float m) {
-  // smallest power of two >= m (m > 0), 1 for m <= 0
+  // smallest power of two >= m (m > 0), 1 for m <= 0, at least 2^-100 so that
+  // its reciprocal stays finite (values below 2^-124 then slice to zero)
   if (!(m > 0.f)) return 1.f;
   int e;
   const float f = frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
-  return ldexpf(1.f, f == 0.5f ? e - 1 : e);
+  return ldexpf(1.f, max(f == 0.5f ? e - 1 : e, -100));
 }
 
 template <int NS>
@@ -301,14 +302,17 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
   __syncthreads();
   // one scale per function for Phi~ and X~: they meet in one exact chain
   // (A = [Phi~ | X~], B = [X~ ; Phi~]); balancing keeps the two maxima alike
-  if (i < kBasisBlk) cp[i] = fmaxf(cp[i], cx[i]);
+  if (i < kBasisBlk) {
+    cp[i] = fmaxf(cp[i], cx[i]);
+    cx[i] = 1.f / cp[i];            // exact: the scales are powers of two
+  }
   __syncthreads();
   float v[kBasisBlk];
 #pragma unroll
-  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sp[nu][i] / cp[nu];
+  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sp[nu][i] * cx[nu];
   store_sliced_row<NS>(out_phi + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
 #pragma unroll
-  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sx[nu][i] / cp[nu];
+  for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sx[nu][i] * cx[nu];
   store_sliced_row<NS>(out_x + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
   if (i < kBasisBlk) {
     phi_scale[(t - t0) * kBasisBlk + i] = cp[i];
@@ -610,18 +614,23 @@ __global__ void __launch_bounds__(320, 1)
             for (int kk = 0; kk < 2; ++kk) {
               const int k4 = half * 2 + kk;
               if (k4 < nq) {
-                float acc[32];
+                const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + k4 * 32;
 #pragma unroll
-                for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+                for (int h = 0; h < 2; ++h) {
+                  // the NS levels of 16 columns, smallest first, one wait
+                  float t[16 * NS];
+                  if constexpr (NS == 3)
+                    tmem_ld16x3(ta + 2 * 128 + h * 16, ta + 128 + h * 16, ta + h * 16, t);
+                  else
+                    tmem_ld16x2(ta + 128 + h * 16, ta + h * 16, t);
 #pragma unroll
-                for (int l = NS - 1; l >= 0; --l) {  // smallest level first
-                  float lv[32];
-                  tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + l * 128 + k4 * 32, lv);
+                  for (int c = 0; c < 16; ++c) {
+                    float acc = t[c];
 #pragma unroll
-                  for (int c = 0; c < 32; ++c) acc[c] += lv[c];
+                    for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
+                    R[kk][h * 16 + c] += acc;
+                  }
                 }
-#pragma unroll
-                for (int c = 0; c < 32; ++c) R[kk][c] += acc[c];
               }
             }
           }
@@ -721,7 +730,9 @@ kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho_out, d
 // quarter = warp % 4, column half = warpgroup - 1) with compensated FP32 sums
 // per element (sums in registers, compensation terms in the TMEM columns after
 // the level accumulators) and an FP64 scatter-add at the end of each work
-// item.  Registers move from warpgroup 0 (kRegsLow) to the epilogue (kRegsHigh).
+// item.  Work items come from a global counter (a dynamic queue, so that CTAs
+// running together take neighbouring items).  Registers move from warpgroup 0
+// (kRegsLow) to the epilogue (kRegsHigh).
 template <int NS>
 struct VCfg {
   static constexpr int kChunk = 2048;                   // 32 points x 64 B of one plane of one tile
@@ -753,7 +764,7 @@ __global__ void __launch_bounds__(384, 1)
     k_v_tc(ListView L, const VWorkTC* __restrict__ work, int64_t nwork, const int32_t* __restrict__ glist,
            int64_t t0, const uint8_t* __restrict__ phic, const uint8_t* __restrict__ xs,
            const float* __restrict__ scale, const double* __restrict__ xmax, const uint8_t* __restrict__ zero,
-           int nbf, double t_b, double* V, int* err) {
+           int nbf, double t_b, double* V, int* next, int* err) {
   using C = VCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -761,8 +772,11 @@ __global__ void __launch_bounds__(384, 1)
   uint64_t* empty = full + C::kStages;
   uint64_t* tfull = empty + C::kStages;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* ifull = tempty + 2;       // work-item ring: index published by the producer
+  uint64_t* iempty = ifull + 4;       // ... and read by the MMA thread and the 8 epilogue warps
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(iempty + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* ring = reinterpret_cast<volatile int*>(tmem_slot + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -772,6 +786,10 @@ __global__ void __launch_bounds__(384, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 8);
+    }
+    for (int r = 0; r < 4; ++r) {
+      mbar_init(&ifull[r], 1);
+      mbar_init(&iempty[r], 9);
     }
     *abort_flag = 0;
     fence_barrier_init();
@@ -793,7 +811,20 @@ __global__ void __launch_bounds__(384, 1)
       const bool copier = lane < 8 * NS;
       uint32_t it = 0;
       bool ok = true;
-      for (int64_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+      for (uint32_t k = 0; ok; ++k) {
+        // next work item from the global counter: CTAs take neighbouring items
+        // and so share the tiles of the same grid-block range in L2
+        const int slot = k & 3;
+        if (!mbar_wait_warp(&iempty[slot], ((k >> 2) & 1) ^ 1, abort_flag, err, 125)) { ok = false; break; }
+        int wi = 0;
+        if (lane == 0) {
+          const int x = atomicAdd(next, 1);
+          wi = x < nwork ? x : -1;
+          ring[slot] = wi;
+          mbar_arrive(&ifull[slot]);
+        }
+        wi = __shfl_sync(0xffffffffu, wi, 0);
+        if (wi < 0) break;
         const VWorkTC wk = work[wi];
         for (int e = 0; e < wk.end - wk.beg && ok; ++e) {
           const int64_t gb = glist[wk.beg + e];
@@ -837,7 +868,12 @@ __global__ void __launch_bounds__(384, 1)
         const uint32_t idesc = instr_desc(128, 128, 1, 1, 1);
         uint32_t it = 0, job = 0;
         bool ok = true;
-        for (int64_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+        for (uint32_t k = 0; ok; ++k) {
+          const int slot = k & 3;
+          if (!mbar_wait(&ifull[slot], (k >> 2) & 1, abort_flag, err, 126)) { ok = false; break; }
+          const int wi = ring[slot];
+          mbar_arrive(&iempty[slot]);
+          if (wi < 0) break;
           const VWorkTC wk = work[wi];
           for (int e = 0; e < wk.end - wk.beg && ok; ++e, ++job) {
             if (!mbar_wait(&tempty[0], (job & 1) ^ 1, abort_flag, err, 124)) { ok = false; break; }
@@ -880,7 +916,13 @@ __global__ void __launch_bounds__(384, 1)
     const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16) + half * 64;
     uint32_t job = 0;
     bool ok = true;
-    for (int64_t wi = blockIdx.x; wi < nwork && ok; wi += gridDim.x) {
+    for (uint32_t k = 0; ok; ++k) {
+      const int slot = k & 3;
+      if (!mbar_wait_warp(&ifull[slot], (k >> 2) & 1, abort_flag, err, 127)) { ok = false; break; }
+      const int wi = ring[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&iempty[slot]);
+      if (wi < 0) break;
       const VWorkTC wk = work[wi];
       float S[64];
 #pragma unroll
@@ -916,20 +958,21 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
         for (int cq = 0; cq < 4; ++cq) {            // 16 columns at a time
           const int cc = cq >> 1;
-          float acc[16], cmp[16];
-          tmem_ld16(trow + (NS - 1) * 128 + cq * 16, acc);
-#pragma unroll
-          for (int l = NS - 2; l >= 0; --l) {
-            float lv[16];
-            tmem_ld16(trow + l * 128 + cq * 16, lv);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[c] += lv[c];
-          }
-          tmem_ld16(trow + C::kCcCol + cq * 16, cmp);
+          // levels (smallest first) and the compensation terms, one wait
+          float t[16 * (NS + 1)];
+          if constexpr (NS == 3)
+            tmem_ld16x4(trow + 2 * 128 + cq * 16, trow + 128 + cq * 16, trow + cq * 16, trow + C::kCcCol + cq * 16, t);
+          else
+            tmem_ld16x3(trow + 128 + cq * 16, trow + cq * 16, trow + C::kCcCol + cq * 16, t);
+          float cmp[16];
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
+            float acc = t[c];
+#pragma unroll
+            for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
+            cmp[c] = t[16 * NS + c];
             const float sc = rsc * __shfl_sync(0xffffffffu, csc[cc], (cq & 1) * 16 + c);
-            two_sum_acc(S[cq * 16 + c], cmp[c], acc[c] * sc);
+            two_sum_acc(S[cq * 16 + c], cmp[c], acc * sc);
           }
           tmem_st16(trow + C::kCcCol + cq * 16, cmp);
         }
@@ -968,10 +1011,11 @@ static kldi_status v_ns(const kldi_plan* P, const Batch& b, double* V, cudaStrea
   if (b.n_vtc_work == 0) return KLDI_OK;
   KLDI_TRY(prepare_tc_kernels());
   const unsigned grid = (unsigned)std::min<int64_t>(b.n_vtc_work, P->num_sms);
+  KLDI_TRY_CUDA(cudaMemsetAsync(P->d_vnext, 0, sizeof(int), s));
   k_v_tc<NS><<<grid, C::kThreads, C::kSmem, s>>>(
       P->list_view(), b.d_vtc_work, b.n_vtc_work, b.d_vtc_g, b.t0, reinterpret_cast<const uint8_t*>(P->d_phic_s),
       reinterpret_cast<const uint8_t*>(P->d_x_s), P->d_phic_scale, P->d_xmax,
-      reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, P->opt.t_b, V, P->d_err);
+      reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, P->opt.t_b, V, P->d_vnext, P->d_err);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
