@@ -27,11 +27,13 @@ weights (partition of unity); Morton key against a brute-force bit test.
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
 
 
+@functools.lru_cache(maxsize=None)
 def treutler_radial(n: int, xi: float = 1.0, alpha: float = 0.6):
     i = np.arange(1, n + 1)
     theta = i * math.pi / (n + 1)
@@ -45,8 +47,10 @@ def treutler_radial(n: int, xi: float = 1.0, alpha: float = 0.6):
     return r[order], w[order]
 
 
+@functools.lru_cache(maxsize=None)
 def angular_product(ntheta: int):
-    """Unit vectors and weights (summing to 4 pi), theta-major order."""
+    """Unit vectors and weights (summing to 4 pi), theta-major order (cached:
+    callers must not modify the returned arrays)."""
     t, wt = np.polynomial.legendre.leggauss(ntheta)
     nphi = 2 * ntheta
     phi = 2.0 * math.pi * np.arange(nphi) / nphi

@@ -1,7 +1,8 @@
 // kldi_make_grid: atom-centred molecular grid (App. A "Numerical integration
 // grids"), Becke partition, per-atom Morton order (App. B Eq. morton_code) and
 // 128-point blocks.  Host C++ with OpenMP: this is geometry-fixed
-// preprocessing, run once per geometry (Sec. III-D).
+// preprocessing, run once per geometry (Sec. III-D); the Becke weights run on
+// the GPU when one is present (grid_dev.cu), else on the host cores.
 //
 // Radial: Treutler-Ahlrichs M4 map r = (xi/ln2)(1+x)^0.6 ln(2/(1-x)), xi = 1, on
 // Chebyshev second-kind nodes x_i = cos(i pi/(n+1)) with weights
@@ -222,6 +223,18 @@ extern "C" kldi_status kldi_make_grid(const kldi_molecule* mol, const kldi_grid_
     std::iota(o, o + natm, 0);
     std::stable_sort(o, o + natm, [&](int32_t i, int32_t j) { return R[(int64_t)a * natm + i] < R[(int64_t)a * natm + j]; });
   }
+  // on the current CUDA device when there is one (same arithmetic), else on the host cores
+  int ndev = 0;
+  const bool use_dev = natm > 1 && cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0;
+  cudaGetLastError();
+  if (use_dev) {
+    const kldi_status st = becke_weights_device(natm, A, R.data(), nbr.data(), G->xyz.data(), G->atom.data(),
+                                                raw_w.data(), nreal, G->w.data());
+    if (st != KLDI_OK) {
+      delete G;
+      return st;
+    }
+  } else
 #pragma omp parallel
   {
     std::vector<double> d(natm);

@@ -244,6 +244,9 @@ kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho, doubl
 kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
 kldi_status prepare_tc_kernels();
+kldi_status becke_weights_device(int natm, const double* atom_xyz, const double* R, const int32_t* nbr,
+                                 const double* xyz, const int32_t* owner, const double* raw_w, int64_t nreal,
+                                 double* w);
 kldi_status ensure_tile_buffers(kldi_plan* P, int prec);
 kldi_status build_work(kldi_plan* P, int64_t cap);
 int64_t tile_bytes_max();

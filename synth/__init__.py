@@ -325,19 +325,27 @@ def overlap_matrix(xyz: np.ndarray, basis: Basis) -> np.ndarray:
         A = pc[i0:i1, None, :]
         B = pc[None, :, :]
         AB2 = np.sum((A - B) ** 2, axis=-1)
-        val = np.exp(-a * b / p * AB2) * pd[i0:i1, None] * pd[None, :]
+        x = a * b / p * AB2
+        # primitive pairs whose Gaussian-product factor exp(-x) is below 1e-30
+        # contribute nothing at double precision and are left out
+        r, c = np.nonzero(x < 69.0)
+        ap, bp = pa[i0 + r], pa[c]
+        pp = ap + bp
+        v = np.exp(-x[r, c]) * pd[i0 + r] * pd[c]
         for dim in range(3):
-            Pd = (a * A[..., dim] + b * B[..., dim]) / p
-            la = pw[i0:i1, dim]
-            lb = pw[:, dim]
-            comp = np.zeros_like(p)
+            Ad, Bd = pc[i0 + r, dim], pc[c, dim]
+            Pd = (ap * Ad + bp * Bd) / pp
+            PA, PB = Pd - Ad, Pd - Bd
+            la, lb = pw[i0 + r, dim], pw[c, dim]
+            comp = np.empty_like(v)
             for li in range(3):
                 for lj in range(3):
-                    m = (la[:, None] == li) & (lb[None, :] == lj)
-                    if not m.any():
-                        continue
-                    comp = np.where(m, _overlap_1d(li, lj, Pd - A[..., dim], Pd - B[..., dim], p), comp)
-            val = val * comp
+                    m = (la == li) & (lb == lj)
+                    if m.any():
+                        comp[m] = _overlap_1d(li, lj, PA[m], PB[m], pp[m])
+            v = v * comp
+        val = np.zeros(x.shape)
+        val[r, c] = v
         cols = np.add.reduceat(val, fstart, axis=1)
         S[f0:f1] = np.add.reduceat(cols, fstart[f0:f1] - i0, axis=0)
     # renormalise contractions to unit self-overlap
