@@ -391,12 +391,33 @@ __global__ void k_mirror(double* V, int nbf) {
   if (r > c) V[idx] = V[(int64_t)c * nbf + r];
 }
 
+// Tensor-core V: off-diagonal tile pairs hold V in the upper triangle, the
+// diagonal 128 x 128 tiles hold S with V = S + S^T.  One thread per pair r < c.
+__global__ void k_finish_tc(double* V, int nbf) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nbf * nbf) return;
+  const int r = (int)(idx / nbf), c = (int)(idx % nbf);
+  if (r > c) return;
+  if ((r >> 7) != (c >> 7)) {
+    V[(int64_t)c * nbf + r] = V[idx];
+  } else if (r == c) {
+    V[idx] = 2.0 * V[idx];
+  } else {
+    const double v = V[idx] + V[(int64_t)c * nbf + r];
+    V[idx] = v;
+    V[(int64_t)c * nbf + r] = v;
+  }
+}
+
 kldi_status launch_finish(const kldi_plan* P, double* V, double* exc, cudaStream_t s) {
   k_esum<<<1, 1024, 0, s>>>(P->d_eblk, P->nblocks, exc);
   KLDI_TRY_CUDA(cudaGetLastError());
   if (V) {
     const int64_t n = P->nbf * P->nbf;
-    k_mirror<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, (int)P->nbf);
+    if (P->prec == KLDI_FP64)
+      k_mirror<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, (int)P->nbf);
+    else
+      k_finish_tc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, (int)P->nbf);
     KLDI_TRY_CUDA(cudaGetLastError());
   }
   return KLDI_OK;

@@ -724,7 +724,9 @@ kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho_out, d
 // V product, persistent over work items (tile pair P <= Q of 128 functions,
 // segment of its grid-block list).  Per grid block one exact chain of K = 256:
 // A = [Phi~_P | X~_P]^T, B = [X~_Q ; Phi~_Q] (MN-major operands), so the chain
-// yields Phi^T X + X^T Phi of the tile pair at once.  384 threads in three
+// yields Phi^T X + X^T Phi of the tile pair at once.  A diagonal pair (P = Q)
+// runs the first half only (K = 128, S = Phi~_P^T X~_P): V_PP = S + S^T is
+// formed by the finish kernel.  384 threads in three
 // warpgroups: warpgroup 0 = warp 0 producer (one lane per bulk copy), warp 1
 // TMEM owner + MMA issue, warps 2-3 idle; warpgroups 1-2 = epilogue (lane
 // quarter = warp % 4, column half = warpgroup - 1) with compensated FP32 sums
@@ -839,7 +841,10 @@ __global__ void __launch_bounds__(384, 1)
               if (xmax[t] >= t_b) sx = xs + off;
             }
           }
-          for (int c = 0; c < 8; ++c) {
+          // a diagonal pair (P == Q) runs only the first half of the chain,
+          // S = Phi~_P^T X~_P (K = 128); the finish step adds S^T
+          const int nchunk = wk.P == wk.Q ? 4 : 8;
+          for (int c = 0; c < nchunk; ++c) {
             const int h = c >> 2, kc = c & 3;
             const int s = it % C::kStages;
             const uint32_t ph = (it / C::kStages) & 1;
@@ -882,7 +887,8 @@ __global__ void __launch_bounds__(384, 1)
             uint32_t started[NS];
 #pragma unroll
             for (int l = 0; l < NS; ++l) started[l] = 0;
-            for (int c = 0; c < 8; ++c) {
+            const int nchunk = wk.P == wk.Q ? 4 : 8;
+            for (int c = 0; c < nchunk; ++c) {
               const int s = it % C::kStages;
               const uint32_t ph = (it / C::kStages) & 1;
               if (!mbar_wait(&full[s], ph, abort_flag, err, 122)) { ok = false; break; }
