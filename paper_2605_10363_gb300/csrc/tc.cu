@@ -367,29 +367,33 @@ __device__ __forceinline__ void issue_levels(uint32_t d0, uint32_t lstride, cons
 }
 
 // Density product, persistent: one CTA per SM walks grid blocks g0 + c,
-// g0 + c + G, ...  320 threads: warp 0 = producer (all lanes build the next
+// g0 + c + G, ...  576 threads: warp 0 = producer (all lanes build the next
 // block's retained list and executed-pair bit matrix with warp ballots into a
 // double-buffered shared-memory record; lane 0 issues the bulk copies),
-// warp 1 = TMEM owner and MMA issuer, warps 2..9 = epilogue (lane quarter =
-// warp % 4; the two warps of a quarter split each N tile's four basis blocks).
+// warp 1 = TMEM owner and MMA issuer, warps 2..17 = epilogue (lane quarter =
+// warp % 4; the four warps of a quarter take one basis block of each N tile
+// each; their partial rho and grad rho are summed in a fixed order).
 template <int NS>
 struct RhoCfg {
   static constexpr int kNQ = 4;                                   // q blocks per N tile (N = 128)
+  static constexpr int kEpi = 16;                                 // epilogue warps: 4 lane quarters x 4 q blocks
   static constexpr int kBufCols = NS * 128;                       // NS level accumulators
   static constexpr int kBufs = NS == 2 ? 2 : 1;
   static constexpr int kStageBytes = NS * kPlaneBytes + NS * kNQ * kDPlane;
-  static constexpr int kStages = NS == 2 ? 4 : 3;
-  static constexpr int kOffR = kStages * kStageBytes;             // [2 halves][32][128] float
+  static constexpr int kStages = NS == 2 ? 3 : 2;
+  static constexpr int kOffR = kStages * kStageBytes;             // [4 q blocks][32][128] float
+  static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * 4;   // [4 q blocks][4][128] double
   static constexpr int kMetaWords = 4 + kMaxRet + kMaxRet * (kMaxRet / 32);
-  static constexpr int kOffMeta = kOffR + 2 * kBasisBlk * kBlockPts * 4;
+  static constexpr int kOffMeta = kOffRed + kNQ * 4 * kBlockPts * 8;
   static constexpr int kOffBar = kOffMeta + 2 * kMetaWords * 4;
   static constexpr int kSmem = kOffBar + 256 + 1024;
   static constexpr int kSegChunks = 8;                            // 8 x 32 = 256 K per exact accumulation
-  static constexpr int kThreads = 320;
+  static constexpr int kThreads = 64 + 32 * kEpi;
+  static_assert(kSmem <= 232448, "shared memory");
 };
 
 template <int NS, bool GRAD>
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(576, 1)
     k_rho_tc(BasisView B, GridView G, ListView L, int64_t g0, int64_t g1, int64_t t0,
              const uint8_t* __restrict__ phi, const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero,
              const double* __restrict__ dmax, const float* __restrict__ dscale, const float* __restrict__ rowscale,
@@ -404,7 +408,9 @@ __global__ void __launch_bounds__(320, 1)
   uint64_t* tempty = tfull + 2;
   uint64_t* mfull = tempty + 2;
   uint64_t* mempty = mfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mempty + 2);
+  uint64_t* rfull = mempty + 2;       // partial sums of the four q-block groups written
+  uint64_t* rempty = rfull + 1;       // ... and read by the combining warps
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rempty + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G_ = gridDim.x;
@@ -416,10 +422,12 @@ __global__ void __launch_bounds__(320, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 8);
+      mbar_init(&tempty[b], C::kEpi);
       mbar_init(&mfull[b], 1);
-      mbar_init(&mempty[b], 9);   // the MMA thread and the 8 epilogue warps
+      mbar_init(&mempty[b], 1 + C::kEpi);   // the MMA thread and the epilogue warps
     }
+    mbar_init(rfull, C::kEpi);
+    mbar_init(rempty, 4);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -574,10 +582,12 @@ __global__ void __launch_bounds__(320, 1)
       if (!ok) *abort_flag = 1;
     }
   } else {
+    // warp w: lane quarter w % 4 (its TMEM lanes), q block k4 of every N tile
     const int quarter = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int k4 = (warp - 2) >> 2;
     const int i = quarter * 32 + lane;
-    float* Rs = reinterpret_cast<float*>(sm + C::kOffR) + half * (kBasisBlk * kBlockPts);
+    float* Rs = reinterpret_cast<float*>(sm + C::kOffR) + k4 * (kBasisBlk * kBlockPts);
+    double* red = reinterpret_cast<double*>(sm + C::kOffRed);
     uint32_t job = 0;
     bool ok = true;
     for (int64_t k = 0; ok; ++k) {
@@ -599,38 +609,31 @@ __global__ void __launch_bounds__(320, 1)
         const int ns = nsegs(m, q0, nq);
         bool work = false;
         for (int jp = 0; jp < n && !work; ++jp) work = tile_bits(m, jp, q0, nq) != 0;
-        float R[2][32];
+        const bool mine = work && k4 < nq;
+        float R[32];
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-          for (int c = 0; c < 32; ++c) R[kk][c] = 0.f;
+        for (int c = 0; c < 32; ++c) R[c] = 0.f;
         for (int sg = 0; sg < ns; ++sg, ++job) {
           const int buf = job % C::kBufs;
           const uint32_t use = job / C::kBufs;
           if (!mbar_wait_warp(&tfull[buf], use & 1, abort_flag, err, 114)) { ok = false; break; }
           tc_fence_after();
-          if (work) {
+          if (mine) {
+            const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + k4 * 32;
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const int k4 = half * 2 + kk;
-              if (k4 < nq) {
-                const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + k4 * 32;
+            for (int h = 0; h < 2; ++h) {
+              // the NS levels of 16 columns, smallest first, one wait
+              float t[16 * NS];
+              if constexpr (NS == 3)
+                tmem_ld16x3(ta + 2 * 128 + h * 16, ta + 128 + h * 16, ta + h * 16, t);
+              else
+                tmem_ld16x2(ta + 128 + h * 16, ta + h * 16, t);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  // the NS levels of 16 columns, smallest first, one wait
-                  float t[16 * NS];
-                  if constexpr (NS == 3)
-                    tmem_ld16x3(ta + 2 * 128 + h * 16, ta + 128 + h * 16, ta + h * 16, t);
-                  else
-                    tmem_ld16x2(ta + 128 + h * 16, ta + h * 16, t);
+              for (int c = 0; c < 16; ++c) {
+                float acc = t[c];
 #pragma unroll
-                  for (int c = 0; c < 16; ++c) {
-                    float acc = t[c];
-#pragma unroll
-                    for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
-                    R[kk][h * 16 + c] += acc;
-                  }
-                }
+                for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
+                R[h * 16 + c] += acc;
               }
             }
           }
@@ -639,14 +642,11 @@ __global__ void __launch_bounds__(320, 1)
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         if (!ok) break;
-        // row-dot with this warp's basis blocks: R_i,nu = e_i f_nu R[kk][c]
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const int k4 = half * 2 + kk;
-          if (k4 >= nq) continue;
+        // row-dot with this warp's basis block: R_i,nu = e_i f_nu R[c]
+        if (k4 < nq) {
           const int q = plist[q0 + k4];
 #pragma unroll
-          for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[kk][c] * dscale[q * kBasisBlk + c];
+          for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * dscale[q * kBasisBlk + c];
           float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
           for_block_functions<float, GRAD>(
               B, q, prl.x, prl.y, prl.z,
@@ -668,15 +668,32 @@ __global__ void __launch_bounds__(320, 1)
           }
         }
       }
-      // the two halves of each point add into zeroed outputs: 0 + a + b is the
-      // same in either order, so the result is deterministic
+      if (!ok) break;
       __syncwarp();
       if (lane == 0) mbar_arrive(&mempty[b]);
-      atomicAdd(&rho[pt], r_i);
-      if (GRAD) {
-        atomicAdd(&grad[pt * 3], gx);
-        atomicAdd(&grad[pt * 3 + 1], gy);
-        atomicAdd(&grad[pt * 3 + 2], gz);
+      // combine the four q-block groups of each point in a fixed order
+      if (!mbar_wait_warp(rempty, (uint32_t)(k & 1) ^ 1u, abort_flag, err, 117)) break;
+      red[(k4 * 4 + 0) * kBlockPts + i] = r_i;
+      red[(k4 * 4 + 1) * kBlockPts + i] = gx;
+      red[(k4 * 4 + 2) * kBlockPts + i] = gy;
+      red[(k4 * 4 + 3) * kBlockPts + i] = gz;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(rfull);
+      if (k4 == 0) {
+        if (!mbar_wait_warp(rfull, (uint32_t)(k & 1), abort_flag, err, 118)) break;
+        double v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          v[c] = ((red[(0 * 4 + c) * kBlockPts + i] + red[(1 * 4 + c) * kBlockPts + i]) +
+                  red[(2 * 4 + c) * kBlockPts + i]) + red[(3 * 4 + c) * kBlockPts + i];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(rempty);
+        rho[pt] = v[0];
+        if (GRAD) {
+          grad[pt * 3] = v[1];
+          grad[pt * 3 + 1] = v[2];
+          grad[pt * 3 + 2] = v[3];
+        }
       }
     }
   }
@@ -697,8 +714,6 @@ static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, d
   if (n == 0) return KLDI_OK;
   KLDI_TRY(prepare_tc_kernels());
   const unsigned grid = (unsigned)std::min<int64_t>(n, P->num_sms);
-  KLDI_TRY_CUDA(cudaMemsetAsync(rho_out + b.g0 * kBlockPts, 0, sizeof(double) * n * kBlockPts, s));
-  if (P->gga) KLDI_TRY_CUDA(cudaMemsetAsync(grad_out + b.g0 * kBlockPts * 3, 0, sizeof(double) * n * kBlockPts * 3, s));
   const uint8_t* phi = reinterpret_cast<const uint8_t*>(P->d_phi_s);
   const uint8_t* ds = reinterpret_cast<const uint8_t*>(P->d_dsplit);
   const uint8_t* z = reinterpret_cast<const uint8_t*>(P->d_zero);
