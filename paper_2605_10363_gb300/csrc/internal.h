@@ -82,6 +82,7 @@ struct ListView {
   const int32_t* blk_idx;  // [ntiles] retained basis block p of tile t
   const double* bmax;      // [ntiles] b_gp
   const int32_t* tile_of;  // [nblocks*nbb] tile index of (g, p), -1 if not retained
+  const int32_t* tile_g;   // [ntiles] grid block g of tile t
   int32_t nbb;
 };
 
@@ -180,6 +181,7 @@ struct kldi_plan {
   int32_t* d_blk_idx = nullptr;
   double* d_bmax = nullptr;
   int32_t* d_tile_of = nullptr;
+  int32_t* d_tile_g = nullptr;
 
   // device: per-evaluation buffers
   double* d_D = nullptr;        // staging copy of a host D

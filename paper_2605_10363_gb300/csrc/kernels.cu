@@ -108,13 +108,7 @@ kldi_status launch_dmax(const kldi_plan* P, const double* D, cudaStream_t s) {
 // FP64 Phi tiles: tile t = (g, p) stored [32 functions][128 points].
 __global__ void k_phi64(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0, double* tiles) {
   const int64_t t = t0 + blockIdx.x;
-  // grid block of tile t: binary search in blk_ptr over [g0, nblocks]
-  int64_t lo = g0, hi = G.nblocks;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (L.blk_ptr[mid] <= t) lo = mid; else hi = mid;
-  }
-  const int64_t g = lo;
+  const int64_t g = L.tile_g[t];
   const int p = L.blk_idx[t];
   const int i = threadIdx.x;
   const int64_t pt = g * kBlockPts + i;
@@ -258,12 +252,7 @@ __global__ void k_x64(BasisView B, GridView G, ListView L, int64_t g0, int64_t t
                       double* xt, double* xmax) {
   __shared__ double red[4];
   const int64_t t = t0 + blockIdx.x;
-  int64_t lo = g0, hi = G.nblocks;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (L.blk_ptr[mid] <= t) lo = mid; else hi = mid;
-  }
-  const int64_t g = lo;
+  const int64_t g = L.tile_g[t];
   const int p = L.blk_idx[t];
   const int i = threadIdx.x;
   const int64_t pt = g * kBlockPts + i;

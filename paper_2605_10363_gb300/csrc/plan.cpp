@@ -51,6 +51,7 @@ ListView kldi_plan::list_view() const {
   v.blk_idx = d_blk_idx;
   v.bmax = d_bmax;
   v.tile_of = d_tile_of;
+  v.tile_g = d_tile_g;
   v.nbb = (int32_t)nbb;
   return v;
 }
@@ -81,7 +82,7 @@ kldi_status upload(kldi_plan* P, T** p, const T* h, size_t count) {
 void free_plan_buffers(kldi_plan* P) {
   free_own_tile_buffers(P);
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f,
-                  P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of,
+                  P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
                   P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
                   P->d_exc, P->d_err, P->d_vnext, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
   for (void* p : ptrs)
@@ -508,6 +509,12 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   if ((st = upload(P, &P->d_blk_idx, P->blk_idx.data(), P->blk_idx.size())) != KLDI_OK) return fail(st);
   if ((st = upload(P, &P->d_bmax, P->bmax.data(), P->bmax.size())) != KLDI_OK) return fail(st);
   if ((st = upload(P, &P->d_tile_of, tile_of.data(), tile_of.size())) != KLDI_OK) return fail(st);
+  {
+    std::vector<int32_t> tile_g(std::max<int64_t>(P->ntiles, 1), 0);
+    for (int64_t g = 0; g < nblk; ++g)
+      for (int32_t t = P->blk_ptr[g]; t < P->blk_ptr[g + 1]; ++t) tile_g[t] = (int32_t)g;
+    if ((st = upload(P, &P->d_tile_g, tile_g.data(), tile_g.size())) != KLDI_OK) return fail(st);
+  }
 
   // ---- batches and V work lists (tile buffers are allocated at first use)
   {
