@@ -120,6 +120,15 @@ __device__ __forceinline__ void store_sliced_row(uint8_t* base, int pstride, int
   }
 }
 
+// Row `row` of a chunk-major tile: rows 32 kc .. 32 kc + 31 of all NS planes
+// are contiguous ([kc][plane][32 rows x 64 B], each 2 KB chunk swizzled as a
+// plane), so one bulk copy of NS x 2 KB moves a K = 32 chunk of every plane.
+template <int NS>
+__device__ __forceinline__ void store_sliced_row_kc(uint8_t* base, int row, const float* v) {
+  store_sliced_row<NS>(base + (row >> 5) * (NS * 2048) - (row & ~31) * 64, 2048, row, v);
+}
+
+
 
 
 // ---------------------------------------------------------------------------
@@ -305,10 +314,10 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
   float v[kBasisBlk];
 #pragma unroll
   for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sp[nu][i] * cx[nu];
-  store_sliced_row<NS>(out_phi + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
+  store_sliced_row_kc<NS>(out_phi + (t - t0) * tile_bytes(NS), i, v);
 #pragma unroll
   for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = sx[nu][i] * cx[nu];
-  store_sliced_row<NS>(out_x + (t - t0) * tile_bytes(NS), kPlaneBytes, i, v);
+  store_sliced_row_kc<NS>(out_x + (t - t0) * tile_bytes(NS), i, v);
   if (i < kBasisBlk) {
     phi_scale[(t - t0) * kBasisBlk + i] = cp[i];
     x_scale[(t - t0) * kBasisBlk + i] = cp[i];
@@ -749,7 +758,7 @@ template <int NS>
 struct VCfg {
   static constexpr int kChunk = 2048;                   // 32 points x 64 B of one plane of one tile
   static constexpr int kOp = 4 * kChunk;                // 4 tiles (128 functions) of one plane
-  static constexpr int kStageBytes = 2 * NS * kOp;      // A planes then B planes
+  static constexpr int kStageBytes = 2 * NS * kOp;      // [side A, B][tile j][plane][32 points x 64 B]
   static constexpr int kStages = 4;
   static constexpr int kBufCols = NS * 128;
   static constexpr int kCcCol = NS * 128;               // TMEM columns of the compensation terms
@@ -818,9 +827,9 @@ __global__ void __launch_bounds__(384, 1)
   if (warp < 4) {
     regs_dec<C::kRegsLow>();
     if (warp == 0) {
-      // lane -> copy (plane l, side, tile j): lanes 0..8 NS-1, one bulk copy each per stage
-      const int q = lane & 7, side = q >> 2, j = q & 3, l = lane >> 3;
-      const bool copier = lane < 8 * NS;
+      // lane -> copy (side, tile j): lanes 0..7, one bulk copy of NS x 2 KB each per stage
+      const int side = (lane >> 2) & 1, j = lane & 3;
+      const bool copier = lane < 8;
       uint32_t it = 0;
       bool ok = true;
       for (uint32_t k = 0; ok; ++k) {
@@ -841,12 +850,12 @@ __global__ void __launch_bounds__(384, 1)
         for (int e = 0; e < wk.end - wk.beg && ok; ++e) {
           const int64_t gb = glist[wk.beg + e];
           const int p = (side == 0 ? wk.P : wk.Q) * 4 + j;
-          const uint8_t* sp = zero;   // Phi~ plane l of tile (gb, p), or zeros
-          const uint8_t* sx = zero;   // X~ plane l, or zeros (tile absent or x_gq < t_b)
+          const uint8_t* sp = zero;   // Phi~ tile (gb, p), or zeros
+          const uint8_t* sx = zero;   // X~ tile, or zeros (tile absent or x_gq < t_b)
           if (p < L.nbb) {
             const int t = L.tile_of[gb * L.nbb + p];
             if (t >= 0) {
-              const int64_t off = (int64_t)(t - t0) * tile_bytes(NS) + (int64_t)l * kPlaneBytes;
+              const int64_t off = (int64_t)(t - t0) * tile_bytes(NS);
               sp = phic + off;
               if (xmax[t] >= t_b) sx = xs + off;
             }
@@ -865,9 +874,8 @@ __global__ void __launch_bounds__(384, 1)
               // A = Phi~ then X~ along K; B = X~ then Phi~
               const bool use_x = (side == 0) == (h == 1);
               const uint8_t* src = use_x ? sx : sp;
-              if (src != zero) src += kc * C::kChunk;
-              bulk_g2s(sm + s * C::kStageBytes + (side * NS + l) * C::kOp + j * C::kChunk, src, C::kChunk,
-                       &full[s]);
+              if (src != zero) src += kc * (NS * C::kChunk);
+              bulk_g2s(sm + s * C::kStageBytes + (side * 4 + j) * (NS * C::kChunk), src, NS * C::kChunk, &full[s]);
             }
             ++it;
           }
@@ -909,8 +917,8 @@ __global__ void __launch_bounds__(384, 1)
                 uint64_t ad[NS], bd[NS];
 #pragma unroll
                 for (int l = 0; l < NS; ++l) {
-                  ad[l] = smem_desc(a + l * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
-                  bd[l] = smem_desc(a + (NS + l) * C::kOp + k * 1024, C::kChunk, 512, kSwz64);
+                  ad[l] = smem_desc(a + l * C::kChunk + k * 1024, NS * C::kChunk, 512, kSwz64);
+                  bd[l] = smem_desc(a + 4 * NS * C::kChunk + l * C::kChunk + k * 1024, NS * C::kChunk, 512, kSwz64);
                 }
                 issue_levels<NS>(d0, 128, ad, bd, idesc, started);
               }
