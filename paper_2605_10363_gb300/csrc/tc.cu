@@ -373,7 +373,8 @@ __device__ __forceinline__ void issue_levels(uint32_t d0, uint32_t lstride, cons
 // Density product, persistent: one CTA per SM walks grid blocks g0 + c,
 // g0 + c + G, ...  576 threads: warp 0 = producer (all lanes build the next
 // block's retained list and executed-pair bit matrix with warp ballots into a
-// double-buffered shared-memory record; lane 0 issues the bulk copies),
+// double-buffered shared-memory record, then issue each chunk's bulk copies
+// together),
 // warp 1 = TMEM owner and MMA issuer, warps 2..17 = epilogue (lane quarter =
 // warp % 4; the four warps of a quarter take one basis block of each N tile
 // each; their partial rho and grad rho are summed in a fixed order).
@@ -492,8 +493,10 @@ __global__ void __launch_bounds__(576, 1)
         m[1] = tb;
       }
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&mfull[b]);
+      if (lane == 0) mbar_arrive(&mfull[b]);
+      {
+        // the warp issues each chunk's copies together: lane 31 the Phi~ tile
+        // (its NS planes in one copy), lanes 0 .. NS nq - 1 one D plane each
         const int ntile = (n + C::kNQ - 1) / C::kNQ;
         bool ok = true;
         for (int nt = 0; nt < ntile && ok; ++nt) {
@@ -503,19 +506,18 @@ __global__ void __launch_bounds__(576, 1)
             if (!bits) continue;
             const int s = it % C::kStages;
             const uint32_t ph = (it / C::kStages) & 1;
-            if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, err, 111)) { ok = false; break; }
+            if (!mbar_wait_warp(&empty[s], ph ^ 1, abort_flag, err, 111)) { ok = false; break; }
             uint8_t* st = sm + s * C::kStageBytes;
-            mbar_arrive_expect_tx(&full[s], NS * kPlaneBytes + NS * nq * kDPlane);
-            const uint8_t* src = phi + (int64_t)(tb + jp - t0) * tile_bytes(NS);
-#pragma unroll
-            for (int l = 0; l < NS; ++l) bulk_g2s(st + l * kPlaneBytes, src + l * kPlaneBytes, kPlaneBytes, &full[s]);
-            uint8_t* bb = st + NS * kPlaneBytes;
-            for (int kq = 0; kq < nq; ++kq) {
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], NS * kPlaneBytes + NS * nq * kDPlane);
+            __syncwarp();
+            if (lane == 31) {
+              bulk_g2s(st, phi + (int64_t)(tb + jp - t0) * tile_bytes(NS), NS * kPlaneBytes, &full[s]);
+            } else if (lane < NS * nq) {
+              const int kq = lane / NS, l = lane % NS;
               const bool on = (bits >> kq) & 1u;
               const uint8_t* d = dsplit + ((int64_t)plist[jp] * L.nbb + plist[q0 + kq]) * (NS * kDPlane);
-#pragma unroll
-              for (int l = 0; l < NS; ++l)
-                bulk_g2s(bb + l * (C::kNQ * kDPlane) + kq * kDPlane, on ? d + l * kDPlane : zero, kDPlane, &full[s]);
+              bulk_g2s(st + NS * kPlaneBytes + l * (C::kNQ * kDPlane) + kq * kDPlane, on ? d + l * kDPlane : zero,
+                       kDPlane, &full[s]);
             }
             ++it;
           }
