@@ -191,6 +191,15 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
+# DRAM bytes per tensor FLOP of the two product kernels, from the ncu capture
+# summarised in profiles/ncu_full_water12_bf16x6.md (12-water case of the same
+# recipe; dram__bytes_read.sum + dram__bytes_write.sum over the launch's tensor
+# FLOPs).  The benchmark scales them by the launch's FLOPs.  Set an entry to
+# None when its kernel changes until it is captured again.
+DRAM_BYTES_PER_FLOP = {"k_v_tc": (1.586324e9 + 0.003784e9) / 4.159e11,
+                       "k_rho_tc": (0.722859e9 + 0.015395e9) / 3.0554e11}
+
+
 # ---------------------------------------------------------------------------- learned functional mode
 def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analytic):
     """Train the surrogate on the GPU on the grid points of the two-water and
@@ -330,8 +339,13 @@ def main():
     else:
         peak, peak_src = 1700.0, "fallback (bf16 sustained)"
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    dom_kernel = "k_rho_tc" if dom == "rho" else "k_v_tc"
+    bpf = DRAM_BYTES_PER_FLOP.get(dom_kernel) if args.prec == "bf16x6" else None
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_rho_tc" if dom == "rho" else "k_v_tc", "peak_source": peak_src,
+            "traffic": bpf * dom_flops if bpf else None,
+            "traffic_source": "ncu 12-water capture scaled by FLOPs (profiles/ncu_full_water12_bf16x6.md)"
+            if bpf else None,
+            "kernel": dom_kernel, "peak_source": peak_src,
             "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
             "other_kernel": {"kernel": "k_v_tc" if dom == "rho" else "k_rho_tc",
                              "achieved": (f_v if dom == "rho" else f_rho) /
