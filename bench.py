@@ -197,7 +197,7 @@ def run_reference(args, world, rank):
 # FLOPs).  The benchmark scales them by the launch's FLOPs.  Set an entry to
 # None when its kernel changes until it is captured again.
 DRAM_BYTES_PER_FLOP = {"k_v_tc": (1.586324e9 + 0.003784e9) / 4.159e11,
-                       "k_rho_tc": (0.722859e9 + 0.015395e9) / 3.0554e11}
+                       "k_rho_tc": None}   # changed since the capture (packed basis records)
 
 
 # ---------------------------------------------------------------------------- learned functional mode

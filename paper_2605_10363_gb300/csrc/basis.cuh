@@ -54,21 +54,17 @@ __device__ __forceinline__ void for_block_functions(const BasisView& B, int p, T
   const int sb = B.bb_shell_begin[p];
   const int se = B.bb_shell_end[p];
   for (int s = sb; s < se; ++s) {
-    const DevShell sh = B.shells[s];
     T dx, dy, dz;
+    int l, fn_off;
+    T g = T(0), gd = T(0);
     if constexpr (sizeof(T) == 8) {
+      const DevShell sh = B.shells[s];
+      l = sh.l;
+      fn_off = sh.fn_off;
       dx = px - sh.cx;
       dy = py - sh.cy;
       dz = pz - sh.cz;
-    } else {
-      const float* r = B.relatom + ((size_t)anchor * B.natm + sh.atom) * 8;
-      dx = (px - r[0]) - r[3];
-      dy = (py - r[1]) - r[4];
-      dz = (pz - r[2]) - r[5];
-    }
-    const T r2 = dx * dx + dy * dy + dz * dz;
-    T g = T(0), gd = T(0);
-    if constexpr (sizeof(T) == 8) {
+      const T r2 = dx * dx + dy * dy + dz * dz;
       for (int k = 0; k < sh.nprim; ++k) {
         const double a = B.alpha[sh.prim_off + k];
         const double e = B.coef[sh.prim_off + k] * exp(-a * r2);
@@ -76,12 +72,26 @@ __device__ __forceinline__ void for_block_functions(const BasisView& B, int p, T
         if (GRAD) gd += a * e;
       }
     } else {
-      // exponents, coefficients and their products as FP32 hi/lo pairs
-      for (int k = 0; k < sh.nprim; ++k) {
-        const int o = sh.prim_off + k;
-        const float e = exp_rn(fmaf(-B.alpha_f[o], r2, -B.alpha_lo[o] * r2));
-        g = fmaf(B.coef_f[o], e, fmaf(B.coef_lo[o], e, g));
-        if (GRAD) gd = fmaf(B.ac_f[o], e, fmaf(B.ac_lo[o], e, gd));
+      // packed shell record, anchor-relative centre (hi, lo), primitives as
+      // FP32 hi/lo pairs of the exponent, coefficient and their product
+      const int4 sh = B.shell_f[s];
+      l = sh.x & 255;
+      fn_off = sh.z;
+      const float4* r = reinterpret_cast<const float4*>(B.relatom + ((size_t)anchor * B.natm + sh.w) * 8);
+      const float4 r0 = r[0], r1 = r[1];
+      dx = (px - r0.x) - r0.w;
+      dy = (py - r0.y) - r1.x;
+      dz = (pz - r0.z) - r1.y;
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      const int np = sh.x >> 8;
+      for (int k = 0; k < np; ++k) {
+        const float4 pr = B.prim_f[sh.y + k];
+        const float e = exp_rn(fmaf(-pr.x, r2, -pr.y * r2));
+        g = fmaf(pr.z, e, fmaf(pr.w, e, g));
+        if (GRAD) {
+          const float2 ac = B.prim_ac[sh.y + k];
+          gd = fmaf(ac.x, e, fmaf(ac.y, e, gd));
+        }
       }
     }
     const T m2gd = T(-2) * gd;
@@ -93,10 +103,10 @@ __device__ __forceinline__ void for_block_functions(const BasisView& B, int p, T
           f(mu - lo, P * g, T(0), T(0), T(0));
       }
     };
-    const int b = sh.fn_off;
-    if (sh.l == 0) {
+    const int b = fn_off;
+    if (l == 0) {
       emit(b, T(1), T(0), T(0), T(0));
-    } else if (sh.l == 1) {
+    } else if (l == 1) {
       emit(b + 0, dx, T(1), T(0), T(0));
       emit(b + 1, dy, T(0), T(1), T(0));
       emit(b + 2, dz, T(0), T(0), T(1));

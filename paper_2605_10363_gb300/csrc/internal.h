@@ -63,6 +63,12 @@ struct BasisView {
   // FP32 evaluation in coordinates relative to an anchor atom: relatom[(a * natm + b) * 8 + 0..5]
   // = A_b - A_a as hi (0..2) and lo (3..5) FP32 parts
   const float* relatom;
+  // packed copies for the FP32 kernels: per shell {l | nprim << 8, prim_off,
+  // fn_off, atom}; per primitive {alpha hi, alpha lo, coef hi, coef lo} and
+  // {alpha coef hi, lo}
+  const int4* shell_f;
+  const float4* prim_f;
+  const float2* prim_ac;
   int32_t natm;
   int32_t nbf;
   int32_t nbb;
@@ -175,6 +181,9 @@ struct kldi_plan {
   double* d_coef = nullptr;
   float* d_alpha_f = nullptr;   // [4][nprim]: alpha hi, alpha lo, coef hi, coef lo
   float* d_coef_f = nullptr;    // [2][nprim]: (alpha coef) hi, lo
+  int4* d_shell_f = nullptr;    // packed per shell (BasisView::shell_f)
+  float4* d_prim_f = nullptr;   // packed per primitive
+  float2* d_prim_ac = nullptr;
   int32_t* d_bb_begin = nullptr;
   int32_t* d_bb_end = nullptr;
   int32_t* d_blk_ptr = nullptr;

@@ -25,6 +25,9 @@ BasisView kldi_plan::basis_view() const {
   v.coef_lo = d_alpha_f ? d_alpha_f + 3 * nprim_total : nullptr;
   v.ac_f = d_coef_f;
   v.ac_lo = d_coef_f ? d_coef_f + nprim_total : nullptr;
+  v.shell_f = d_shell_f;
+  v.prim_f = d_prim_f;
+  v.prim_ac = d_prim_ac;
   v.bb_shell_begin = d_bb_begin;
   v.bb_shell_end = d_bb_end;
   v.relatom = d_relatom;
@@ -81,7 +84,7 @@ kldi_status upload(kldi_plan* P, T** p, const T* h, size_t count) {
 
 void free_plan_buffers(kldi_plan* P) {
   free_own_tile_buffers(P);
-  void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f,
+  void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
                   P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
                   P->d_exc, P->d_err, P->d_vnext, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
@@ -403,6 +406,22 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   if ((st = upload(P, &P->d_coef, coef.data(), coef.size())) != KLDI_OK) return fail(st);
   if ((st = upload(P, &P->d_alpha_f, alpha_f.data(), alpha_f.size())) != KLDI_OK) return fail(st);
   if ((st = upload(P, &P->d_coef_f, coef_f.data(), coef_f.size())) != KLDI_OK) return fail(st);
+  {
+    // packed copies for the FP32 kernels (one vector load per shell / primitive)
+    std::vector<int4> shf(ns);
+    for (int s2 = 0; s2 < ns; ++s2)
+      shf[s2] = make_int4(shells[s2].l | (shells[s2].nprim << 8), shells[s2].prim_off, shells[s2].fn_off,
+                          shells[s2].atom);
+    std::vector<float4> prf(npr);
+    std::vector<float2> pac(npr);
+    for (size_t k = 0; k < (size_t)npr; ++k) {
+      prf[k] = make_float4(alpha_f[k], alpha_f[npr + k], alpha_f[2 * npr + k], alpha_f[3 * npr + k]);
+      pac[k] = make_float2(coef_f[k], coef_f[npr + k]);
+    }
+    if ((st = upload(P, &P->d_shell_f, shf.data(), shf.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_prim_f, prf.data(), prf.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_prim_ac, pac.data(), pac.size())) != KLDI_OK) return fail(st);
+  }
   if ((st = upload(P, &P->d_bb_begin, bb_begin.data(), bb_begin.size())) != KLDI_OK) return fail(st);
   if ((st = upload(P, &P->d_bb_end, bb_end.data(), bb_end.size())) != KLDI_OK) return fail(st);
 

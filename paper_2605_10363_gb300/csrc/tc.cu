@@ -212,14 +212,19 @@ __global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, List
   for (int j = tb; j < te; ++j) {
     const int p = L.blk_idx[j];
     for (int s = B.bb_shell_begin[p]; s < B.bb_shell_end[p]; ++s) {
-      const DevShell sh = B.shells[s];
-      const float* ra = B.relatom + ((size_t)anc * B.natm + sh.atom) * 8;
-      const float dx = (px - ra[0]) - ra[3], dy = (py - ra[1]) - ra[4], dz = (pz - ra[2]) - ra[5];
+      const int4 sh = B.shell_f[s];
+      const float4* ra = reinterpret_cast<const float4*>(B.relatom + ((size_t)anc * B.natm + sh.w) * 8);
+      const float4 r0 = ra[0], r1 = ra[1];
+      const float dx = (px - r0.x) - r0.w, dy = (py - r0.y) - r1.x, dz = (pz - r0.z) - r1.y;
       const float r2 = dx * dx + dy * dy + dz * dz;
       float sum = 0.f;
-      for (int k = 0; k < sh.nprim; ++k)
-        sum += fabsf(B.coef_f[sh.prim_off + k]) * __expf(-B.alpha_f[sh.prim_off + k] * r2);
-      const float poly = sh.l == 0 ? 1.f : (sh.l == 1 ? sqrtf(r2) : r2);
+      const int np = sh.x >> 8;
+      for (int k = 0; k < np; ++k) {
+        const float4 pr = B.prim_f[sh.y + k];
+        sum += fabsf(pr.z) * __expf(-pr.x * r2);
+      }
+      const int l = sh.x & 255;
+      const float poly = l == 0 ? 1.f : (l == 1 ? sqrtf(r2) : r2);
       M = fmaxf(M, poly * sum);
     }
   }
