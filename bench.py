@@ -113,10 +113,12 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- work counts
-def work_counts(plan, system, splits):
+def work_counts(plan, system, splits, counts=None):
     """Tensor-pipe FLOPs of one evaluation per product (algorithmic: executed
     block pairs x 2 x 128 x d_p d_q x slice products), from the retained lists
-    and the D block maxima."""
+    and the D block maxima; `counts` (a dict) also receives the executed tensor
+    FLOPs including the padding of the 128-wide tiles."""
+    counts = {} if counts is None else counts
     ptr, idx, b = plan.lists()
     D = system.D
     n = D.shape[0]
@@ -127,6 +129,8 @@ def work_counts(plan, system, splits):
     dmax = pad.reshape(nbb, 32, nbb, 32).max(axis=(1, 3))
     f_rho = 0.0
     f_v = 0.0
+    x_rho = 0.0
+    x_v = 0.0
     for g in range(len(ptr) - 1):
         S = idx[ptr[g]:ptr[g + 1]]
         if S.size == 0:
@@ -137,6 +141,14 @@ def work_counts(plan, system, splits):
         dd = np.outer(dsz[S], dsz[S])
         f_rho += 2.0 * 128 * float((dd * e1).sum())
         f_v += 2.0 * 128 * float(dd.sum())
+        # executed tensor work (tile padding included): density chunks of
+        # 128 x 128 x 32 per (N tile of 4 retained blocks, p with any executed
+        # pair); V jobs of 128 x 128 x 256 per tile pair P < Q, x 128 for P = Q
+        for q0 in range(0, S.size, 4):
+            x_rho += 2.0 * 128 * 128 * 32 * float(np.any(e1[:, q0:q0 + 4], axis=1).sum())
+        nvt = len(set((S // 4).tolist()))
+        x_v += 2.0 * 128 * 128 * (256 * nvt * (nvt - 1) / 2 + 128 * nvt)
+    counts.update(executed_rho=splits * x_rho, executed_v=splits * x_v)
     return splits * f_rho, splits * f_v
 
 
@@ -325,7 +337,8 @@ def main():
                                                              - vs[:, 2]).max())
 
     splits = {"bf16x3": 3, "bf16x6": 6, "fp64": 1}[args.prec]
-    f_rho, f_v = work_counts(plan, s, splits)
+    executed = {}
+    f_rho, f_v = work_counts(plan, s, splits, executed)
     names = kldi.STAGES
     per_stage = {names[k]: round(stage_ms[k] / args.steps, 4) for k in range(len(names))}
     dom = "rho" if stage_ms[2] >= stage_ms[5] else "v"
@@ -347,6 +360,8 @@ def main():
             if bpf else None,
             "kernel": dom_kernel, "peak_source": peak_src,
             "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
+            "executed_flops_per_launch": executed["executed_rho" if dom == "rho" else "executed_v"],
+            "executed_tflops": executed["executed_rho" if dom == "rho" else "executed_v"] / (dom_ms * 1e-3) / 1e12,
             "other_kernel": {"kernel": "k_v_tc" if dom == "rho" else "k_rho_tc",
                              "achieved": (f_v if dom == "rho" else f_rho) /
                              ((stage_ms[5] if dom == "rho" else stage_ms[2]) / max(1, stage_n[5] if dom == "rho"
