@@ -94,3 +94,67 @@ def test_cnoh1000_full_grid_sampled_ranges(cnoh):
         assert abs(Er.item() - ref.E) <= 1e-6, (g0, Er.item(), ref.E)
         assert np.abs(Vr.cpu().numpy() - ref.V).max() <= 3e-7, g0
         assert np.all(ratio <= 1.0), g0
+
+
+def _density_points(system):
+    kldi = _kldi()
+    plan = kldi.plan_for_system(system, prec="fp64", xc="pbe")
+    rho = np.zeros(plan.npoints)
+    grad = np.zeros((plan.npoints, 3))
+    kldi.density(plan, system.D, rho, grad)
+    return rho, np.einsum("ic,ic->i", grad, grad)
+
+
+def test_water167_learned_functional_fused():
+    """The learned-functional workload: the network trained on the GPU on the
+    grid points of the two-water and 33-water systems, fused between the
+    products on the 167-water cluster (501 atoms, 4175 functions, 5.84M points).
+    The whole-grid E_xc against the analytic functional is measured and
+    stated; on seeded 6-block ranges the fused path is held to the oracle
+    evaluating the same network (FP16 weights) at the learned functional's
+    tolerances: |dE| <= 2e-5 sum |w e0|, max|dV| <= 2e-5 max|V| + 3e-7."""
+    import torch
+    from oracle import mlp as om
+    kldi = _kldi()
+    pts = [_density_points(synth.make_system(1)), _density_points(synth.make_system(2))]
+    rho = np.concatenate([a for a, _ in pts])
+    sig = np.concatenate([b for _, b in pts])
+    box = synth.mlp_box(rho, sig)
+    net = kldi.Mlp(synth.mlp_init(42), box)
+    hist = net.train(rho, sig, epochs=100, batch=8192, lr0=3e-3, lr1=1e-5)
+    assert hist[-1] < 1e-3 * hist[0]
+    s = synth.make_system(5)
+    plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe")
+    D = torch.from_numpy(s.D).cuda()
+    V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    kldi.exc(plan, "pbe", D, V, E)
+    E_pbe = E.item()
+    kldi.plan_set_mlp(plan, net)
+    kldi.exc(plan, "mlp", D, V, E)
+    torch.cuda.synchronize()
+    E_mlp = E.item()
+    print(f"water167: E_xc analytic {E_pbe:.6f} Ha, learned {E_mlp:.6f} Ha, difference {E_mlp - E_pbe:.3e} Ha "
+          f"({(E_mlp - E_pbe) / abs(E_pbe):.2e} relative)")
+    assert abs(E_mlp - E_pbe) < 1e-3 * abs(E_pbe)
+    nb = plan.stats["nblocks"]
+    rng = np.random.default_rng(41)
+    starts = sorted(rng.choice(nb - 6, size=2, replace=False).tolist())
+    blocks = [b for g0 in starts for b in range(g0, g0 + 6)]
+    go = og.build_grid(s.Z, s.xyz, s.grid, weight_blocks=blocks)
+    sh = ob.build_shells(s.xyz, s.basis)
+    p16 = om.fp16_weights(net.params())
+    for g0 in starts:
+        ref = oe.evaluate(s, go, sh, screened=True, blocks=range(g0, g0 + 6), xc_kind="mlp", mlp=(p16, om.Box(*box)))
+        plan.set_block_range(g0, g0 + 6)
+        Vr = torch.zeros_like(V)
+        Er = torch.zeros_like(E)
+        kldi.exc(plan, "mlp", D, Vr, Er)
+        torch.cuda.synchronize()
+        pts_ = slice(g0 * 128, (g0 + 6) * 128)
+        e0 = np.abs(om.slater(np.maximum(ref.rho[pts_], 1e-300))[0]) * (ref.rho[pts_] >= 1e-14)
+        scaleE = float(np.sum(np.abs(go.weights[pts_]) * e0))
+        dV = np.abs(Vr.cpu().numpy() - ref.V).max()
+        print(f"range {g0}: dE {Er.item() - ref.E:.2e} (bound {2e-5 * scaleE:.1e}), max|dV| {dV:.2e}")
+        assert abs(Er.item() - ref.E) <= 2e-5 * scaleE
+        assert dV <= 2e-5 * np.abs(ref.V).max() + 3e-7
