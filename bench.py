@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-side-modes", action="store_true", help="skip the FP64 / BF16x3 side measurements")
     ap.add_argument("--nwaters", type=int, default=0,
                     help="profiling case: a smaller water cluster of the same recipe (not a bench line)")
+    ap.add_argument("--workload", default="water33", choices=["water33", "frames"],
+                    help="frames: the first --frames frames of the 20-130-water trajectory recipe through one "
+                         "CUDA-graph batch (a side measurement, not the headline line)")
+    ap.add_argument("--frames", type=int, default=8)
     return ap.parse_args()
 
 
@@ -261,12 +265,67 @@ def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analyt
                          "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1])}}
 
 
+# ---------------------------------------------------------------------------- batched frames
+def run_frames(args, dev, stream):
+    """Frames of uneven size (20-130 waters, own D each) through one CUDA-graph
+    batch with a shared tile workspace and the tuned V decomposition."""
+    import torch
+
+    import synth
+    from paper_2605_10363_gb300 import kldi
+    t0 = time.perf_counter()
+    systems = [synth.make_system(4, frame=k) for k in range(args.frames)]
+    plans = [kldi.plan_for_system(s, prec=args.prec, xc="pbe", stream=stream.cuda_stream) for s in systems]
+    t_plan = time.perf_counter() - t0
+    free, _ = torch.cuda.mem_get_info(dev)
+    ws = kldi.Workspace(int(0.5 * free) // 73984 * 73984)
+    for p in plans:
+        p.set_workspace(ws)
+    Ds = [torch.from_numpy(s.D).to(dev) for s in systems]
+    Vs = [torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device=dev) for s in systems]
+    E = torch.zeros(len(systems), dtype=torch.float64, device=dev)
+    big = int(np.argmax([p.npoints for p in plans]))
+    tuning, _ = plans[big].autotune("pbe", Ds[big], reps=2)
+    for p in plans:
+        p.set_tuning(tuning["v_seg"])
+    batch = kldi.Batch(plans, "pbe", Ds, Vs, E, stream=stream.cuda_stream)
+    for _ in range(max(1, args.warmup)):
+        batch.launch()
+    batch.sync()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        batch.launch()
+    b.record(stream)
+    batch.sync()
+    ms = a.elapsed_time(b) / args.steps
+    npts = sum(p.grid.nreal for p in plans)
+    print(json.dumps({
+        "metric": METRIC, "value": npts / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"frames: the first {args.frames} frames of the trajectory recipe "
+                               f"(waters {[int(x) for x in synth.frame_sizes(args.frames)]}), PBE-form, one CUDA-graph "
+                               f"launch per step", "precision": args.prec, "points": int(npts),
+                   "tuned_v_seg": tuning["v_seg"], "plan_seconds": round(t_plan, 1)},
+        "E_xc": E.cpu().numpy().tolist()}), flush=True)
+
+
 # ---------------------------------------------------------------------------- our arm
 def main():
     args = parse()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "frames":
+        import torch
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        side = torch.cuda.Stream(dev)      # a real stream: the graph launches and the events share it
+        with torch.cuda.stream(side):
+            run_frames(args, dev, side)
         return
     import torch
 
