@@ -188,6 +188,16 @@ kldi_status kldi_exc(kldi_plan* plan, int xc, const double* D, double* V, double
 kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
                              double* const* V, double* Exc);
 
+/* Nuclear gradient of E_xc (the paper's energy + gradient workload, Sec. IV),
+ * on the fixed grid (no grid-weight response), through the basis centres:
+ *   dE/dR_A = -2 sum_{mu on A} sum_i [grad chi_mu Q_mu,i + (b_i . grad grad chi_mu) R_mu,i],
+ *   R = Phi D, Q = Z D over the executed pairs E1_g,
+ *   Z = w v_rho chi + 2 w v_sigma grad rho . grad chi, b = 2 w v_sigma grad rho.
+ * G[natm*3] (row-major per atom, bohr, Hartree/bohr) and Exc[1]: host or device
+ * (both the same kind).  FP64 plans only (KLDI_EUNSUPPORTED otherwise).  D as in
+ * kldi_exc. */
+kldi_status kldi_exc_grad(kldi_plan* plan, int xc, const double* D, double* G, double* Exc);
+
 /* Stages of one evaluation, for kldi_plan_stage_times. */
 typedef enum {
   KLDI_STAGE_DPREP = 0,   /* D block maxima (and slicing for tensor modes)        */

@@ -1,5 +1,6 @@
 // Compute entry points: kldi_density, kldi_vxc, kldi_exc, kldi_exc_batched.
 // Every step runs in this library's CUDA kernels on the plan's stream.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -194,6 +195,45 @@ extern "C" kldi_status kldi_exc(kldi_plan* P, int xc, const double* D, double* V
   if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, nbf2 * 8, cudaMemcpyDeviceToHost, P->stream));
   if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
   if (hostV || hostE) {
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    KLDI_TRY(check_device_error(P));
+  }
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
+extern "C" kldi_status kldi_exc_grad(kldi_plan* P, int xc, const double* D, double* G, double* Exc) {
+  if (!P || !D || !G || !Exc) { set_error("kldi_exc_grad: null argument"); return KLDI_EINVAL; }
+  if (P->prec != KLDI_FP64) {
+    set_error("kldi_exc_grad: the gradient is provided for FP64 plans (kldi_plan_set_precision(plan, KLDI_FP64))");
+    return KLDI_EUNSUPPORTED;
+  }
+  KLDI_TRY(check_xc(P, xc));
+  const size_t nbf2 = (size_t)P->nbf * P->nbf;
+  const double* dD = D;
+  if (!is_device_ptr(D)) {
+    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
+    dD = P->d_D;
+  }
+  const bool host_out = !is_device_ptr(G);
+  if (!P->d_G) {
+    KLDI_TRY_CUDA(cudaMalloc(&P->d_G, sizeof(double) * 3 * std::max(P->natm, 1)));
+  }
+  double* dG = host_out ? P->d_G : G;
+  double* dE = host_out ? P->d_exc : Exc;
+  KLDI_TRY(ensure_tile_buffers(P, P->prec));
+  KLDI_TRY(prepare_D(P, dD));
+  KLDI_TRY_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * 3 * P->natm, P->stream));
+  for (const Batch& b : P->batches) {
+    KLDI_TRY(density_batch(P, b, dD, P->d_rho, P->d_grad));
+    KLDI_TRY(staged(P, KLDI_STAGE_XC, 1, [&] { return launch_xc(P, b, xc, P->d_rho, P->d_grad, P->stream); }));
+    KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x64(P, b, P->stream); }));
+    KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_grad64(P, b, dD, dG, P->stream); }));
+  }
+  KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_finish(P, nullptr, dE, P->stream); }));
+  if (host_out) {
+    KLDI_TRY_CUDA(cudaMemcpyAsync(G, dG, sizeof(double) * 3 * P->natm, cudaMemcpyDeviceToHost, P->stream));
+    KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
     KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
     KLDI_TRY(check_device_error(P));
   }

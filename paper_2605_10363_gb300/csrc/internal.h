@@ -164,6 +164,7 @@ struct kldi_plan {
   int64_t nvt = 0;  // 128-function V tiles per edge (ceil(nbb / 4))
   int* d_err = nullptr;         // device error word (bounded-wait timeouts)
   int* d_vnext = nullptr;       // work-item counter of the tensor-core V product
+  double* d_G = nullptr;        // [natm][3] nuclear gradient (allocated by the first kldi_exc_grad)
 
   // host copies of the retained lists
   std::vector<int32_t> blk_ptr, blk_idx;
@@ -255,6 +256,7 @@ kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho, doubl
 kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
 kldi_status prepare_tc_kernels();
+kldi_status launch_grad64(const kldi_plan* P, const Batch& b, const double* D, double* G, cudaStream_t s);
 kldi_status becke_weights_device(int natm, const double* atom_xyz, const double* R, const int32_t* nbr,
                                  const double* xyz, const int32_t* owner, const double* raw_w, int64_t nreal,
                                  double* w);

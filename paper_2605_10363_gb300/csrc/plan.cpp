@@ -87,7 +87,7 @@ void free_plan_buffers(kldi_plan* P) {
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
                   P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
-                  P->d_exc, P->d_err, P->d_vnext, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
+                  P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& b : P->batches) {

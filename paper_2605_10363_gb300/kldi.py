@@ -78,6 +78,7 @@ def _load():
         "kldi_vxc": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
         "kldi_exc": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "kldi_exc_batched": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), vp]),
+        "kldi_exc_grad": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "kldi_plan_set_precision": (C.c_int, [vp, C.c_int]),
         "kldi_plan_profile": (C.c_int, [vp, C.c_int]),
         "kldi_plan_stage_times": (C.c_int, [vp, vp, vp]),
@@ -265,6 +266,11 @@ def vxc(plan: Plan, xc, rho, grad, V, Exc):
 
 def exc(plan: Plan, xc, D, V, Exc):
     _check(LIB.kldi_exc(plan.h, XC[xc] if isinstance(xc, str) else int(xc), _ptr(D), _ptr(V), _ptr(Exc)))
+
+
+def exc_grad(plan: Plan, xc, D, G, Exc):
+    """Nuclear gradient G[natm, 3] of E_xc on the fixed grid (FP64 plans)."""
+    _check(LIB.kldi_exc_grad(plan.h, XC[xc] if isinstance(xc, str) else int(xc), _ptr(D), _ptr(G), _ptr(Exc)))
 
 
 def exc_batched(plans, xc, Ds, Vs, Exc):
