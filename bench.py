@@ -447,6 +447,22 @@ def main():
             modes[pm] = m
             del p2
         out_extra["speedup_vs_fp64"] = modes["fp64"]["ms_per_step"] / ms_step
+        # nuclear gradient of E_xc (FP64 block form)
+        pg = kldi.plan_for_system(s, prec="fp64", xc="pbe", stream=stream.cuda_stream)
+        Gd = torch.zeros((len(s.Z), 3), dtype=torch.float64, device=dev)
+        kldi.exc_grad(pg, "pbe", D, Gd, E)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        bb = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            kldi.exc_grad(pg, "pbe", D, Gd, E)
+        bb.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(bb) / 2
+        modes["gradient_fp64"] = {"ms_per_step": ms, "value": npts_real / (ms * 1e-3),
+                                  "max_abs_gradient": float(Gd.abs().max().item())}
+        del pg
         modes["mlp"] = mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, stage_ms[3] / args.steps, E_ours)
 
     cpu = None
