@@ -39,6 +39,55 @@ __device__ __forceinline__ float exp_rn(float x) {
 __device__ __forceinline__ double mul_s3(double v) { return v * 0.57735026918962576451; }
 __device__ __forceinline__ float mul_s3(float v) { return fmaf(v, 0.5773502588272095f, v * 1.0362416702491828e-08f); }
 
+// Calls f(local index, value, dx, dy, dz) for the functions of one shell
+// whose index relative to the basis block, first + c, lies in [0, 32):
+// chi = P g, d chi / dr_a = (d_a P) g - 2 r_a P gd with gd = sum_k c_k a_k e^{-a_k r^2}.
+template <typename T, bool GRAD, typename F>
+__device__ __forceinline__ void emit_shell(int l, int first, T dx, T dy, T dz, T g, T gd, F&& f) {
+  const T m2gd = T(-2) * gd;
+  auto emit = [&](int c, T P, T px_, T py_, T pz_) {
+    const int mu = first + c;
+    if (mu >= 0 && mu < kBasisBlk) {
+      if (GRAD)
+        f(mu, P * g, px_ * g + dx * m2gd * P, py_ * g + dy * m2gd * P, pz_ * g + dz * m2gd * P);
+      else
+        f(mu, P * g, T(0), T(0), T(0));
+    }
+  };
+  if (l == 0) {
+    emit(0, T(1), T(0), T(0), T(0));
+  } else if (l == 1) {
+    emit(0, dx, T(1), T(0), T(0));
+    emit(1, dy, T(0), T(1), T(0));
+    emit(2, dz, T(0), T(0), T(1));
+  } else {
+    emit(0, mul_s3(dx * dx), mul_s3(T(2) * dx), T(0), T(0));
+    emit(1, dx * dy, dy, dx, T(0));
+    emit(2, dx * dz, dz, T(0), dx);
+    emit(3, mul_s3(dy * dy), T(0), mul_s3(T(2) * dy), T(0));
+    emit(4, dy * dz, T(0), dz, dy);
+    emit(5, mul_s3(dz * dz), T(0), T(0), mul_s3(T(2) * dz));
+  }
+}
+
+// Contracted radial factor of the FP32 path: g = sum_k c_k e^{-a_k r^2} and
+// gd = sum_k c_k a_k e^{-a_k r^2} from hi/lo pairs of a, c and a c.
+template <bool GRAD>
+__device__ __forceinline__ void radial_f(const float4* pf, const float2* pac, int np, float r2, float& g,
+                                         float& gd) {
+  g = 0.f;
+  gd = 0.f;
+  for (int k = 0; k < np; ++k) {
+    const float4 pr = pf[k];
+    const float e = exp_rn(fmaf(-pr.x, r2, -pr.y * r2));
+    g = fmaf(pr.z, e, fmaf(pr.w, e, g));
+    if (GRAD) {
+      const float2 ac = pac[k];
+      gd = fmaf(ac.x, e, fmaf(ac.y, e, gd));
+    }
+  }
+}
+
 // Calls f(local_index, value, dx, dy, dz) for every basis function of basis
 // block p (functions [32 p, 32 p + 32) that exist) at point (px, py, pz).
 // Gradients are zero when GRAD is false.
@@ -50,74 +99,101 @@ template <typename T, bool GRAD, typename F>
 __device__ __forceinline__ void for_block_functions(const BasisView& B, int p, T px, T py, T pz, F&& f,
                                                     int anchor = 0) {
   const int lo = p * kBasisBlk;
-  const int hi = lo + kBasisBlk;
   const int sb = B.bb_shell_begin[p];
   const int se = B.bb_shell_end[p];
   for (int s = sb; s < se; ++s) {
-    T dx, dy, dz;
-    int l, fn_off;
-    T g = T(0), gd = T(0);
     if constexpr (sizeof(T) == 8) {
       const DevShell sh = B.shells[s];
-      l = sh.l;
-      fn_off = sh.fn_off;
-      dx = px - sh.cx;
-      dy = py - sh.cy;
-      dz = pz - sh.cz;
+      const T dx = px - sh.cx, dy = py - sh.cy, dz = pz - sh.cz;
       const T r2 = dx * dx + dy * dy + dz * dz;
+      T g = T(0), gd = T(0);
       for (int k = 0; k < sh.nprim; ++k) {
         const double a = B.alpha[sh.prim_off + k];
         const double e = B.coef[sh.prim_off + k] * exp(-a * r2);
         g += e;
         if (GRAD) gd += a * e;
       }
+      emit_shell<T, GRAD>(sh.l, sh.fn_off - lo, dx, dy, dz, g, gd, f);
     } else {
       // packed shell record, anchor-relative centre (hi, lo), primitives as
       // FP32 hi/lo pairs of the exponent, coefficient and their product
       const int4 sh = B.shell_f[s];
-      l = sh.x & 255;
-      fn_off = sh.z;
       const float4* r = reinterpret_cast<const float4*>(B.relatom + ((size_t)anchor * B.natm + sh.w) * 8);
       const float4 r0 = r[0], r1 = r[1];
-      dx = (px - r0.x) - r0.w;
-      dy = (py - r0.y) - r1.x;
-      dz = (pz - r0.z) - r1.y;
-      const T r2 = dx * dx + dy * dy + dz * dz;
-      const int np = sh.x >> 8;
-      for (int k = 0; k < np; ++k) {
-        const float4 pr = B.prim_f[sh.y + k];
-        const float e = exp_rn(fmaf(-pr.x, r2, -pr.y * r2));
-        g = fmaf(pr.z, e, fmaf(pr.w, e, g));
-        if (GRAD) {
-          const float2 ac = B.prim_ac[sh.y + k];
-          gd = fmaf(ac.x, e, fmaf(ac.y, e, gd));
-        }
-      }
+      const float dx = (px - r0.x) - r0.w, dy = (py - r0.y) - r1.x, dz = (pz - r0.z) - r1.y;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      float g, gd;
+      radial_f<GRAD>(B.prim_f + sh.y, B.prim_ac + sh.y, sh.x >> 8, r2, g, gd);
+      emit_shell<float, GRAD>(sh.x & 255, sh.z - lo, dx, dy, dz, g, gd, f);
     }
-    const T m2gd = T(-2) * gd;
-    auto emit = [&](int mu, T P, T px_, T py_, T pz_) {
-      if (mu >= lo && mu < hi) {
-        if (GRAD)
-          f(mu - lo, P * g, px_ * g + dx * m2gd * P, py_ * g + dy * m2gd * P, pz_ * g + dz * m2gd * P);
-        else
-          f(mu - lo, P * g, T(0), T(0), T(0));
-      }
-    };
-    const int b = fn_off;
-    if (l == 0) {
-      emit(b, T(1), T(0), T(0), T(0));
-    } else if (l == 1) {
-      emit(b + 0, dx, T(1), T(0), T(0));
-      emit(b + 1, dy, T(0), T(1), T(0));
-      emit(b + 2, dz, T(0), T(0), T(1));
-    } else {
-      emit(b + 0, mul_s3(dx * dx), mul_s3(T(2) * dx), T(0), T(0));
-      emit(b + 1, dx * dy, dy, dx, T(0));
-      emit(b + 2, dx * dz, dz, T(0), dx);
-      emit(b + 3, mul_s3(dy * dy), T(0), mul_s3(T(2) * dy), T(0));
-      emit(b + 4, dy * dz, T(0), dz, dy);
-      emit(b + 5, mul_s3(dz * dz), T(0), T(0), mul_s3(T(2) * dz));
-    }
+  }
+}
+
+// Shared-memory copy of one basis block's shells, for the FP32 evaluation at
+// the points of one grid block: shell centres relative to the grid block's
+// anchor atom (hi, lo), a packed header and the primitives.  Every thread of
+// the evaluation reads the same record, so the reads are broadcasts, and no
+// load depends on another (the global tables chain shell -> centre and
+// shell -> primitives).  Blocks with more shells or primitives than the
+// record holds are evaluated from the global tables; both give the same bits.
+constexpr int kRecShells = 40;
+constexpr int kRecPrims = 80;
+struct BlockRec {
+  float4 c0[kRecShells];   // x hi, y hi, z hi, x lo of A_atom - A_anchor
+  float4 c1[kRecShells];   // y lo, z lo, header (l | nprim << 8 | (first + 64) << 16), first primitive
+  float4 pf[kRecPrims];    // alpha hi, alpha lo, coef hi, coef lo
+  float2 pac[kRecPrims];   // alpha coef hi, lo
+  float ds[kBasisBlk];     // per-function factor, filled by the caller where needed
+  int nshell;
+  int pad[3];
+};
+
+// True when basis block p fits a BlockRec (the same answer on every thread).
+__device__ __forceinline__ bool block_rec_fits(const BasisView& B, int p) {
+  const int sb = B.bb_shell_begin[p], se = B.bb_shell_end[p];
+  if (se - sb > kRecShells) return false;
+  if (se == sb) return true;
+  const int4 a = B.shell_f[sb], z = B.shell_f[se - 1];
+  return (z.y + (z.x >> 8)) - a.y <= kRecPrims;
+}
+
+// Fills rec for basis block p at anchor atom `anchor`, cooperatively over
+// threads t = 0 .. nthr - 1 (the caller synchronises before the reads).
+__device__ __forceinline__ void stage_block_rec(const BasisView& B, int p, int anchor, BlockRec* rec, int t,
+                                                int nthr) {
+  const int sb = B.bb_shell_begin[p], se = B.bb_shell_end[p];
+  if (t == 0) rec->nshell = se - sb;
+  if (se == sb) return;
+  const int pbase = B.shell_f[sb].y;
+  const int4 z = B.shell_f[se - 1];
+  const int np = z.y + (z.x >> 8) - pbase;
+  const int lo = p * kBasisBlk;
+  for (int s = t; s < se - sb; s += nthr) {
+    const int4 sh = B.shell_f[sb + s];
+    const float4* r = reinterpret_cast<const float4*>(B.relatom + ((size_t)anchor * B.natm + sh.w) * 8);
+    const float4 r0 = r[0], r1 = r[1];
+    const int hdr = (sh.x & 0xffff) | ((sh.z - lo + 64) << 16);
+    rec->c0[s] = r0;
+    rec->c1[s] = make_float4(r1.x, r1.y, __int_as_float(hdr), __int_as_float(sh.y - pbase));
+  }
+  for (int k = t; k < np; k += nthr) {
+    rec->pf[k] = B.prim_f[pbase + k];
+    rec->pac[k] = B.prim_ac[pbase + k];
+  }
+}
+
+// for_block_functions<float> from a staged record (same arithmetic, same bits).
+template <bool GRAD, typename F>
+__device__ __forceinline__ void for_rec_functions(const BlockRec* rec, float px, float py, float pz, F&& f) {
+  const int ns = rec->nshell;
+  for (int s = 0; s < ns; ++s) {
+    const float4 c0 = rec->c0[s], c1 = rec->c1[s];
+    const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
+    const float dx = (px - c0.x) - c0.w, dy = (py - c0.y) - c1.x, dz = (pz - c0.z) - c1.y;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    float g, gd;
+    radial_f<GRAD>(rec->pf + pi, rec->pac + pi, (hdr >> 8) & 255, r2, g, gd);
+    emit_shell<float, GRAD>(hdr & 255, (hdr >> 16) - 64, dx, dy, dz, g, gd, f);
   }
 }
 

@@ -198,6 +198,7 @@ template <int NS>
 __global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
                                                    uint8_t* out_row, float* rowscale) {
   __shared__ float st[kBasisBlk][kBlockPts + 1];
+  __shared__ BlockRec rec[2];
   const int64_t g = g0 + blockIdx.x;
   const int i = threadIdx.x;
   const int64_t pt = g * kBlockPts + i;
@@ -207,25 +208,37 @@ __global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, List
   const int tb = L.blk_ptr[g], te = L.blk_ptr[g + 1];
   // pass 1: point scale from the shell bound r^l sum_k |c_k| exp(-a_k r^2) >= |phi_mu(r_i)|;
   // a bound needs no unbiased exp: the hardware exp's ~1e-6 relative error is
-  // covered by the 1.001 margin below
+  // covered by the 1.001 margin below.  Shell records are staged in shared
+  // memory per basis block (double-buffered: one barrier per block).
+  auto shell_bound = [&](int l, int np, const float4* pf, float dx, float dy, float dz) {
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    float sum = 0.f;
+    for (int k = 0; k < np; ++k) sum += fabsf(pf[k].z) * __expf(-pf[k].x * r2);
+    const float poly = l == 0 ? 1.f : (l == 1 ? sqrtf(r2) : r2);
+    return poly * sum;
+  };
   float M = 0.f;
   for (int j = tb; j < te; ++j) {
     const int p = L.blk_idx[j];
-    for (int s = B.bb_shell_begin[p]; s < B.bb_shell_end[p]; ++s) {
-      const int4 sh = B.shell_f[s];
-      const float4* ra = reinterpret_cast<const float4*>(B.relatom + ((size_t)anc * B.natm + sh.w) * 8);
-      const float4 r0 = ra[0], r1 = ra[1];
-      const float dx = (px - r0.x) - r0.w, dy = (py - r0.y) - r1.x, dz = (pz - r0.z) - r1.y;
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      float sum = 0.f;
-      const int np = sh.x >> 8;
-      for (int k = 0; k < np; ++k) {
-        const float4 pr = B.prim_f[sh.y + k];
-        sum += fabsf(pr.z) * __expf(-pr.x * r2);
+    BlockRec* rc = rec + ((j - tb) & 1);
+    if (block_rec_fits(B, p)) {
+      stage_block_rec(B, p, anc, rc, i, kBlockPts);
+      __syncthreads();
+      for (int s = 0; s < rc->nshell; ++s) {
+        const float4 c0 = rc->c0[s], c1 = rc->c1[s];
+        const int hdr = __float_as_int(c1.z);
+        M = fmaxf(M, shell_bound(hdr & 255, (hdr >> 8) & 255, rc->pf + __float_as_int(c1.w), (px - c0.x) - c0.w,
+                                 (py - c0.y) - c1.x, (pz - c0.z) - c1.y));
       }
-      const int l = sh.x & 255;
-      const float poly = l == 0 ? 1.f : (l == 1 ? sqrtf(r2) : r2);
-      M = fmaxf(M, poly * sum);
+    } else {
+      __syncthreads();
+      for (int s = B.bb_shell_begin[p]; s < B.bb_shell_end[p]; ++s) {
+        const int4 sh = B.shell_f[s];
+        const float4* ra = reinterpret_cast<const float4*>(B.relatom + ((size_t)anc * B.natm + sh.w) * 8);
+        const float4 r0 = ra[0], r1 = ra[1];
+        M = fmaxf(M, shell_bound(sh.x & 255, sh.x >> 8, B.prim_f + sh.y, (px - r0.x) - r0.w, (py - r0.y) - r1.x,
+                                 (pz - r0.z) - r1.y));
+      }
     }
   }
   const float rs = pow2_ceil(M * 1.001f);
@@ -234,11 +247,18 @@ __global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, List
   // pass 2: per-point slicing of every retained tile
   for (int j = tb; j < te; ++j) {
     const int p = L.blk_idx[j];
+    BlockRec* rc = rec + ((j - tb + te - tb) & 1);
+    const bool fits = block_rec_fits(B, p);
+    if (fits) stage_block_rec(B, p, anc, rc, i, kBlockPts);
+    __syncthreads();
     float v[kBasisBlk];
 #pragma unroll
     for (int nu = 0; nu < kBasisBlk; ++nu) st[nu][i] = 0.f;
-    for_block_functions<float, false>(
-        B, p, px, py, pz, [&](int nu, float x, float, float, float) { st[nu][i] = x; }, anc);
+    auto put = [&](int nu, float x, float, float, float) { st[nu][i] = x; };
+    if (fits)
+      for_rec_functions<false>(rc, px, py, pz, put);
+    else
+      for_block_functions<float, false>(B, p, px, py, pz, put, anc);
 #pragma unroll
     for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = st[nu][i] * rinv;
     store_sliced_row<NS>(out_row + (int64_t)(j - t0) * tile_bytes(NS), kPlaneBytes, i, v);
@@ -285,6 +305,7 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
   __shared__ float sp[kBasisBlk][kBlockPts + 1];
   __shared__ float sx[kBasisBlk][kBlockPts + 1];
   __shared__ float cp[kBasisBlk], cx[kBasisBlk], rawx[kBasisBlk];
+  __shared__ BlockRec rec;
   const int64_t t = t0 + blockIdx.x;
   const int64_t g = L.tile_g[t];
   const int p = L.blk_idx[t];
@@ -296,15 +317,19 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
 #pragma unroll
   for (int nu = 0; nu < kBasisBlk; ++nu) sp[nu][i] = sx[nu][i] = 0.f;
   const float4 pr = G.prel[pt];
-  for_block_functions<float, GRAD>(
-      B, p, pr.x, pr.y, pr.z,
-      [&](int nu, float v, float dx, float dy, float dz) {
-        float x = a * v;
-        if (GRAD) x = fmaf(bx, dx, fmaf(by, dy, fmaf(bz, dz, x)));
-        sp[nu][i] = v * c;
-        sx[nu][i] = x * cinv;
-      },
-      G.anchor[g]);
+  const bool fits = block_rec_fits(B, p);
+  if (fits) stage_block_rec(B, p, G.anchor[g], &rec, i, kBlockPts);
+  __syncthreads();
+  auto put = [&](int nu, float v, float dx, float dy, float dz) {
+    float x = a * v;
+    if (GRAD) x = fmaf(bx, dx, fmaf(by, dy, fmaf(bz, dz, x)));
+    sp[nu][i] = v * c;
+    sx[nu][i] = x * cinv;
+  };
+  if (fits)
+    for_rec_functions<GRAD>(&rec, pr.x, pr.y, pr.z, put);
+  else
+    for_block_functions<float, GRAD>(B, p, pr.x, pr.y, pr.z, put, G.anchor[g]);
   __syncthreads();
   column_scales(sp, cp, nullptr);
   column_scales(sx, cx, rawx);
@@ -395,7 +420,8 @@ struct RhoCfg {
   static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * 4;   // [4 q blocks][4][128] double
   static constexpr int kMetaWords = 4 + kMaxRet + kMaxRet * (kMaxRet / 32);
   static constexpr int kOffMeta = kOffRed + kNQ * 4 * kBlockPts * 8;
-  static constexpr int kOffBar = kOffMeta + 2 * kMetaWords * 4;
+  static constexpr int kOffRec = kOffMeta + 2 * kMetaWords * 4;  // [4 q blocks][2] BlockRec
+  static constexpr int kOffBar = kOffRec + 2 * kNQ * (int)sizeof(BlockRec);
   static constexpr int kSmem = kOffBar + 256 + 1024;
   static constexpr int kSegChunks = 8;                            // 8 x 32 = 256 K per exact accumulation
   static constexpr int kThreads = 64 + 32 * kEpi;
@@ -599,7 +625,8 @@ __global__ void __launch_bounds__(576, 1)
     const int i = quarter * 32 + lane;
     float* Rs = reinterpret_cast<float*>(sm + C::kOffR) + k4 * (kBasisBlk * kBlockPts);
     double* red = reinterpret_cast<double*>(sm + C::kOffRed);
-    uint32_t job = 0;
+    BlockRec* recs = reinterpret_cast<BlockRec*>(sm + C::kOffRec) + 2 * k4;
+    uint32_t job = 0, ruse = 0;
     bool ok = true;
     for (int64_t k = 0; ok; ++k) {
       const int64_t g = g0 + blockIdx.x + k * G_;
@@ -621,6 +648,15 @@ __global__ void __launch_bounds__(576, 1)
         bool work = false;
         for (int jp = 0; jp < n && !work; ++jp) work = tile_bits(m, jp, q0, nq) != 0;
         const bool mine = work && k4 < nq;
+        // the four warps of this q block stage its shells (double-buffered
+        // record, one named barrier per use) while the products run
+        BlockRec* rec = recs + (ruse & 1);
+        const int qb = mine ? plist[q0 + k4] : 0;
+        const bool staged = mine && block_rec_fits(B, qb);
+        if (staged) {
+          stage_block_rec(B, qb, anc, rec, quarter * 32 + lane, 128);
+          if (quarter == 0) rec->ds[lane] = dscale[qb * kBasisBlk + lane];
+        }
         float R[32];
 #pragma unroll
         for (int c = 0; c < 32; ++c) R[c] = 0.f;
@@ -654,23 +690,32 @@ __global__ void __launch_bounds__(576, 1)
         }
         if (!ok) break;
         // row-dot with this warp's basis block: R_i,nu = e_i f_nu R[c]
-        if (k4 < nq) {
-          const int q = plist[q0 + k4];
+        // (a tile without executed pairs has R = 0 and adds nothing)
+        if (mine) {
+          const int q = qb;
+          named_bar_sync(1 + k4, 128);
+          ++ruse;
+          if (staged) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * dscale[q * kBasisBlk + c];
+            for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * rec->ds[c];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * dscale[q * kBasisBlk + c];
+          }
           float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
-          for_block_functions<float, GRAD>(
-              B, q, prl.x, prl.y, prl.z,
-              [&](int nu, float v, float dx, float dy, float dz) {
-                const float rr = Rs[nu * kBlockPts + i];
-                pr = fmaf(v, rr, pr);
-                if (GRAD) {
-                  px_ = fmaf(dx, rr, px_);
-                  py_ = fmaf(dy, rr, py_);
-                  pz_ = fmaf(dz, rr, pz_);
-                }
-              },
-              anc);
+          auto acc = [&](int nu, float v, float dx, float dy, float dz) {
+            const float rr = Rs[nu * kBlockPts + i];
+            pr = fmaf(v, rr, pr);
+            if (GRAD) {
+              px_ = fmaf(dx, rr, px_);
+              py_ = fmaf(dy, rr, py_);
+              pz_ = fmaf(dz, rr, pz_);
+            }
+          };
+          if (staged)
+            for_rec_functions<GRAD>(rec, prl.x, prl.y, prl.z, acc);
+          else
+            for_block_functions<float, GRAD>(B, q, prl.x, prl.y, prl.z, acc, anc);
           r_i += rsc * (double)pr;
           if (GRAD) {
             gx += 2.0 * rsc * (double)px_;

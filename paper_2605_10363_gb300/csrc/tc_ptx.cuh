@@ -111,6 +111,10 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// barrier `id` (1 .. 15; 0 is __syncthreads) over `nthreads` threads (whole warps)
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 // ---- descriptors
 // Shared-memory matrix descriptor: start address, leading / stride byte
