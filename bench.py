@@ -411,6 +411,8 @@ def main():
     else:
         peak, peak_src = 1700.0, "fallback (bf16 sustained)"
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    oth = 5 if dom == "rho" else 2
+    oth_ms = stage_ms[oth] / max(1, stage_n[oth])
     dom_kernel = "k_rho_tc" if dom == "rho" else "k_v_tc"
     bpf = DRAM_BYTES_PER_FLOP.get(dom_kernel) if args.prec == "bf16x6" else None
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -422,9 +424,11 @@ def main():
             "executed_flops_per_launch": executed["executed_rho" if dom == "rho" else "executed_v"],
             "executed_tflops": executed["executed_rho" if dom == "rho" else "executed_v"] / (dom_ms * 1e-3) / 1e12,
             "other_kernel": {"kernel": "k_v_tc" if dom == "rho" else "k_rho_tc",
-                             "achieved": (f_v if dom == "rho" else f_rho) /
-                             ((stage_ms[5] if dom == "rho" else stage_ms[2]) / max(1, stage_n[5] if dom == "rho"
-                                                                                   else stage_n[2]) * 1e-3) / 1e12}}
+                             "ms_per_launch": oth_ms,
+                             "achieved": (f_v if dom == "rho" else f_rho) / (oth_ms * 1e-3) / 1e12,
+                             "executed_flops_per_launch": executed["executed_v" if dom == "rho" else "executed_rho"],
+                             "executed_tflops": executed["executed_v" if dom == "rho" else "executed_rho"]
+                             / (oth_ms * 1e-3) / 1e12}}
 
     # side modes: the FP64 block form (speedup denominator) and BF16x3
     modes = {}

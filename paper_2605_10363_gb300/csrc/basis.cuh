@@ -17,8 +17,11 @@ namespace kldi {
 // e^r to degree 8 (remainder below 2e-10 relative) by Horner's rule, times 2^n.
 // The last Horner step rounds to nearest, so the error is close to a single
 // round-to-nearest and symmetric.  Results below 2^-125 are flushed to zero.
+// n = rint(x log2 e) as (y + 1.5 x 2^23) - 1.5 x 2^23 with y = x log2 e rounded
+// (exact for |y| < 2^22, ties to even); the bits of y + 1.5 x 2^23 hold n.
 __device__ __forceinline__ float exp_rn(float x) {
-  const float n = rintf(x * 1.4426950216293335f);
+  const float t = __fadd_rn(__fmul_rn(x, 1.4426950216293335f), 12582912.f);
+  const float n = __fsub_rn(t, 12582912.f);
   float r = fmaf(-n, 0.693145751953125f, x);
   r = fmaf(-n, 1.428606765330187e-06f, r);
   float p = 2.4801587642286904e-05f;        // 1/8!
@@ -31,7 +34,7 @@ __device__ __forceinline__ float exp_rn(float x) {
   p = fmaf(p, r, 1.0f);
   p = fmaf(p, r, 1.0f);
   if (n < -125.f) return 0.f;
-  return p * __int_as_float(((int)n + 127) << 23);
+  return p * __int_as_float((__float_as_int(t) - 0x4B400000 + 127) << 23);
 }
 
 // 1/sqrt(3) for the xx, yy, zz components: one FP64 constant, or an FP32

@@ -67,17 +67,25 @@ __device__ __forceinline__ float pow2_ceil(float m) {
   return ldexpf(1.f, max(f == 0.5f ? e - 1 : e, -100));
 }
 
+// Balanced digits of a on the grids 2^-7, 2^-15, 2^-23: s0 = rint(a 2^7) 2^-7,
+// s1 = rint((a - s0) 2^15) 2^-15, s2 = rint((a - s0 - s1) 2^23) 2^-23.  Each
+// rint is one addition and one subtraction of 1.5 x 2^(23 - e) (e = 7, 15,
+// 23): the sum lies in [2^(23-e), 2^(24-e)), where the spacing of FP32 numbers
+// is 2^-e, so the addition rounds to the grid (ties to even) and the
+// subtraction is exact.  Valid for |a| <= 1 (the residuals are then below
+// 2^-8 and 2^-16).
 template <int NS>
 __device__ __forceinline__ void slice(float a, float* s) {  // |a| <= 1
-  const float s0 = rintf(a * 128.f) * (1.f / 128.f);
-  float r = a - s0;
+  constexpr float C0 = 98304.f, C1 = 384.f, C2 = 1.5f;   // 1.5 x 2^16, 1.5 x 2^8, 1.5
+  const float s0 = __fsub_rn(__fadd_rn(a, C0), C0);
+  float r = __fsub_rn(a, s0);
   s[0] = s0;
   if (NS >= 2) {
-    const float s1 = rintf(r * 32768.f) * (1.f / 32768.f);
-    r = r - s1;
+    const float s1 = __fsub_rn(__fadd_rn(r, C1), C1);
+    r = __fsub_rn(r, s1);
     s[1] = s1;
   }
-  if (NS >= 3) s[2] = rintf(r * 8388608.f) * (1.f / 8388608.f);
+  if (NS >= 3) s[2] = __fsub_rn(__fadd_rn(r, C2), C2);
 }
 
 template <int NS>
@@ -93,9 +101,9 @@ __device__ __forceinline__ void slice_d(double a, float* s) {  // |a| <= 1, FP64
   if (NS >= 3) s[2] = (float)(rint(r * 8388608.0) / 8388608.0);
 }
 
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+__device__ __forceinline__ uint32_t pack2(float a, float b) {   // a in the low half
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 // Row `row` of NS swizzled [rows][32] planes (plane stride `pstride` bytes)
@@ -507,17 +515,29 @@ __global__ void __launch_bounds__(576, 1)
       uint32_t* mask = reinterpret_cast<uint32_t*>(m + 4 + kMaxRet);
       for (int j = lane; j < n; j += 32) plist[j] = L.blk_idx[tb + j];
       __syncwarp();
-      // executed pairs E1_g: one ballot per 32 (jp, jq) predicates
-      for (int wi = 0; wi < n * nw; ++wi) {
-        const int jp = wi / nw, w = wi % nw;
+      // executed pairs E1_g: one ballot per 32 (jp, jq) predicates; lane owns
+      // column jq = 32 w + lane, the loads of eight rows are issued together
+      for (int w = 0; w < nw; ++w) {
         const int jq = w * 32 + lane;
-        bool pred = false;
-        if (jq < n) {
-          const double dm = dmax[plist[jp] * L.nbb + plist[jq]];
-          pred = dm >= t_b && L.bmax[tb + jp] * dm * L.bmax[tb + jq] >= t_d;
+        const bool in = jq < n;
+        const int qblk = in ? plist[jq] : 0;
+        const double bq = in ? L.bmax[tb + jq] : 0.0;
+        for (int jp0 = 0; jp0 < n; jp0 += 8) {
+          double dm[8], bp[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int jp = jp0 + u;
+            dm[u] = (in && jp < n) ? dmax[plist[jp] * L.nbb + qblk] : 0.0;
+            bp[u] = jp < n ? L.bmax[tb + jp] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int jp = jp0 + u;
+            const bool pred = in && jp < n && dm[u] >= t_b && bp[u] * dm[u] * bq >= t_d;
+            const uint32_t word = __ballot_sync(0xffffffffu, pred);
+            if (lane == 0 && jp < n) mask[jp * nw + w] = word;
+          }
         }
-        const uint32_t word = __ballot_sync(0xffffffffu, pred);
-        if (lane == 0) mask[wi] = word;
       }
       if (lane == 0) {
         m[0] = n;
