@@ -194,8 +194,13 @@ kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, int xc, const
  *   R = Phi D, Q = Z D over the executed pairs E1_g,
  *   Z = w v_rho chi + 2 w v_sigma grad rho . grad chi, b = 2 w v_sigma grad rho.
  * G[natm*3] (row-major per atom, bohr, Hartree/bohr) and Exc[1]: host or device
- * (both the same kind).  FP64 plans only (KLDI_EUNSUPPORTED otherwise).  D as in
- * kldi_exc. */
+ * (both the same kind).  D as in kldi_exc.  FP64 plans use the FP64 block form;
+ * BF16X3 / BF16X6 plans run R and Q through the tensor-core density product
+ * (Z sliced per point like Phi) and contract them with FP32 first and second
+ * basis derivatives, one FP64 atomic per atom, component and warp (summation
+ * order, hence the last bits, vary between calls).  KLDI_EUNSUPPORTED for a
+ * tensor-core plan whose basis has a 32-function block with more than 40 shells
+ * or 80 primitives.  The V product is not evaluated. */
 kldi_status kldi_exc_grad(kldi_plan* plan, int xc, const double* D, double* G, double* Exc);
 
 /* Stages of one evaluation, for kldi_plan_stage_times. */

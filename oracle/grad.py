@@ -95,8 +95,11 @@ def function_atoms(system) -> np.ndarray:
 
 
 def exc_gradient(system, grid, shells=None, screened=True, xc_kind=None, t_b=None, t_d=None,
-                 rho_min=oxc.RHO_MIN, mlp=None):
-    """dE_xc/dR_A (natm x 3) on the fixed grid, the formula of the module docstring."""
+                 rho_min=oxc.RHO_MIN, mlp=None, return_magnitude=False):
+    """dE_xc/dR_A (natm x 3) on the fixed grid, the formula of the module docstring.
+    With return_magnitude, also the sums of the terms' magnitudes per atom and
+    component, 2 sum_{mu on A} sum_i (|d_x chi Q| + |b . grad d_x chi| |R|): the
+    scale against which rounding errors of the terms are measured."""
     from . import mlp as omlp
     if shells is None:
         shells = obasis.build_shells(system.xyz, system.basis)
@@ -109,6 +112,7 @@ def exc_gradient(system, grid, shells=None, screened=True, xc_kind=None, t_b=Non
     fatom = function_atoms(system)
     natm = len(system.Z)
     G = np.zeros((natm, 3))
+    Gmag = np.zeros((natm, 3))
     dmax = oscreen.d_block_max(D)
     dsz = oscreen.D_BASIS
     nb = oscreen.nbasis_blocks(nbf)
@@ -159,4 +163,8 @@ def exc_gradient(system, grid, shells=None, screened=True, xc_kind=None, t_b=Non
         t2 = np.einsum("ic,xcim,im->xm", bvec, hph, R)
         contrib = -2.0 * (t1 + t2)                                   # [3, n_cols]
         np.add.at(G, fatom[cols], contrib.T)
-    return G
+        if return_magnitude:
+            m1 = np.einsum("xim,im->xm", np.abs(dph), np.abs(Q))
+            m2 = np.einsum("xim,im->xm", np.abs(np.einsum("ic,xcim->xim", bvec, hph)), np.abs(R))
+            np.add.at(Gmag, fatom[cols], (2.0 * (m1 + m2)).T)
+    return (G, Gmag) if return_magnitude else G

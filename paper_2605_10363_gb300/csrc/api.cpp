@@ -204,11 +204,11 @@ extern "C" kldi_status kldi_exc(kldi_plan* P, int xc, const double* D, double* V
 
 extern "C" kldi_status kldi_exc_grad(kldi_plan* P, int xc, const double* D, double* G, double* Exc) {
   if (!P || !D || !G || !Exc) { set_error("kldi_exc_grad: null argument"); return KLDI_EINVAL; }
-  if (P->prec != KLDI_FP64) {
-    set_error("kldi_exc_grad: the gradient is provided for FP64 plans (kldi_plan_set_precision(plan, KLDI_FP64))");
+  KLDI_TRY(check_xc(P, xc));
+  if (P->prec != KLDI_FP64 && !P->rec_fit_all) {
+    set_error("kldi_exc_grad: a basis block has more than 40 shells or 80 primitives (tensor-core gradient)");
     return KLDI_EUNSUPPORTED;
   }
-  KLDI_TRY(check_xc(P, xc));
   const size_t nbf2 = (size_t)P->nbf * P->nbf;
   const double* dD = D;
   if (!is_device_ptr(D)) {
@@ -222,13 +222,23 @@ extern "C" kldi_status kldi_exc_grad(kldi_plan* P, int xc, const double* D, doub
   double* dG = host_out ? P->d_G : G;
   double* dE = host_out ? P->d_exc : Exc;
   KLDI_TRY(ensure_tile_buffers(P, P->prec));
+  if (P->prec != KLDI_FP64 && !P->d_zscale) {
+    KLDI_TRY_CUDA(cudaMalloc(&P->d_zscale, sizeof(float) * std::max<int64_t>(P->npoints, 1)));
+  }
   KLDI_TRY(prepare_D(P, dD));
   KLDI_TRY_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * 3 * P->natm, P->stream));
   for (const Batch& b : P->batches) {
     KLDI_TRY(density_batch(P, b, dD, P->d_rho, P->d_grad));
     KLDI_TRY(staged(P, KLDI_STAGE_XC, 1, [&] { return launch_xc(P, b, xc, P->d_rho, P->d_grad, P->stream); }));
-    KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x64(P, b, P->stream); }));
-    KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_grad64(P, b, dD, dG, P->stream); }));
+    if (P->prec == KLDI_FP64) {
+      KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x64(P, b, P->stream); }));
+      KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_grad64(P, b, dD, dG, P->stream); }));
+    } else {
+      // Z tiles (X stage), then the Q and R terms through the density-product kernel (V stage)
+      const bool gga_xc = xc != KLDI_XC_LDA_X;
+      KLDI_TRY(staged(P, KLDI_STAGE_V, gga_xc ? 3 : 2,
+                      [&] { return launch_grad_tc(P, b, gga_xc, dG, P->stream); }));
+    }
   }
   KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_finish(P, nullptr, dE, P->stream); }));
   if (host_out) {

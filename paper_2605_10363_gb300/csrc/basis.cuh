@@ -147,6 +147,7 @@ struct BlockRec {
   float4 pf[kRecPrims];    // alpha hi, alpha lo, coef hi, coef lo
   float2 pac[kRecPrims];   // alpha coef hi, lo
   float ds[kBasisBlk];     // per-function factor, filled by the caller where needed
+  int atom[kRecShells];    // atom of each shell
   int nshell;
   int pad[3];
 };
@@ -178,6 +179,7 @@ __device__ __forceinline__ void stage_block_rec(const BasisView& B, int p, int a
     const int hdr = (sh.x & 0xffff) | ((sh.z - lo + 64) << 16);
     rec->c0[s] = r0;
     rec->c1[s] = make_float4(r1.x, r1.y, __int_as_float(hdr), __int_as_float(sh.y - pbase));
+    rec->atom[s] = sh.w;
   }
   for (int k = t; k < np; k += nthr) {
     rec->pf[k] = B.prim_f[pbase + k];
@@ -197,6 +199,86 @@ __device__ __forceinline__ void for_rec_functions(const BlockRec* rec, float px,
     float g, gd;
     radial_f<GRAD>(rec->pf + pi, rec->pac + pi, (hdr >> 8) & 255, r2, g, gd);
     emit_shell<float, GRAD>(hdr & 255, (hdr >> 16) - 64, dx, dy, dz, g, gd, f);
+  }
+}
+
+// First and second derivatives of the functions of a staged block, FP32, for
+// the nuclear gradient (accuracy ~1e-7 relative; no hi/lo compensation).
+// With chi = P g(r^2), g = sum c e^{-a r^2}, g1 = sum c a e, g2 = sum c a^2 e:
+//   d_a chi = (d_a P) g - 2 r_a P g1
+//   d_a d_b chi = (d_a d_b P) g - 2 (d_a P r_b + d_b P r_a) g1 + P (4 r_a r_b g2 - 2 delta_ab g1)
+// Calls f(atom, nu, d[3], h[6]) with h = (xx, xy, xz, yy, yz, zz) (zero when
+// HESS is false).
+template <bool HESS, typename F>
+__device__ __forceinline__ void for_rec_derivatives(const BlockRec* rec, float px, float py, float pz, F&& f) {
+  const int ns = rec->nshell;
+  for (int s = 0; s < ns; ++s) {
+    const float4 c0 = rec->c0[s], c1 = rec->c1[s];
+    const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
+    const int l = hdr & 255, np = (hdr >> 8) & 255, first = (hdr >> 16) - 64;
+    const int atom = rec->atom[s];
+    const float r[3] = {(px - c0.x) - c0.w, (py - c0.y) - c1.x, (pz - c0.z) - c1.y};
+    const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    float g = 0.f, g1 = 0.f, g2 = 0.f;
+    for (int k = 0; k < np; ++k) {
+      const float4 pr = rec->pf[pi + k];
+      const float2 ac = rec->pac[pi + k];
+      const float e = exp_rn(fmaf(-pr.x, r2, -pr.y * r2));
+      g = fmaf(pr.z, e, fmaf(pr.w, e, g));
+      const float ace = (ac.x + ac.y) * e;
+      g1 += ace;
+      if (HESS) g2 = fmaf(pr.x + pr.y, ace, g2);
+    }
+    const int ncomp = (l + 1) * (l + 2) / 2;
+    for (int c = 0; c < ncomp; ++c) {
+      const int nu = first + c;
+      if (nu < 0 || nu >= kBasisBlk) continue;
+      // exponents of x, y, z and the normalisation of this component
+      int e[3];
+      float fc = 1.f;
+      if (l == 0) {
+        e[0] = e[1] = e[2] = 0;
+      } else if (l == 1) {
+        e[0] = c == 0; e[1] = c == 1; e[2] = c == 2;
+      } else {
+        e[0] = (c == 0) * 2 + (c == 1) + (c == 2);
+        e[1] = (c == 3) * 2 + (c == 1) + (c == 4);
+        e[2] = (c == 5) * 2 + (c == 2) + (c == 4);
+        if (c == 0 || c == 3 || c == 5) fc = 0.57735026918962576f;
+      }
+      float p0[3], p1[3], p2[3];   // per axis: r^e, d/dr, d2/dr2
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        p0[a] = e[a] == 0 ? 1.f : (e[a] == 1 ? r[a] : r[a] * r[a]);
+        p1[a] = e[a] == 0 ? 0.f : (e[a] == 1 ? 1.f : 2.f * r[a]);
+        p2[a] = e[a] == 2 ? 2.f : 0.f;
+      }
+      const float P = fc * p0[0] * p0[1] * p0[2];
+      float dP[3];
+      dP[0] = fc * p1[0] * p0[1] * p0[2];
+      dP[1] = fc * p0[0] * p1[1] * p0[2];
+      dP[2] = fc * p0[0] * p0[1] * p1[2];
+      float d[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d[a] = dP[a] * g - 2.f * r[a] * P * g1;
+      float h[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (HESS) {
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int a = ia[k], b = ib[k];
+          float ddP;
+          if (a == b)
+            ddP = fc * (a == 0 ? p2[0] * p0[1] * p0[2] : a == 1 ? p0[0] * p2[1] * p0[2] : p0[0] * p0[1] * p2[2]);
+          else
+            ddP = fc * (3 - a - b == 2 ? p1[0] * p1[1] * p0[2] : 3 - a - b == 1 ? p1[0] * p0[1] * p1[2]
+                                                                               : p0[0] * p1[1] * p1[2]);
+          h[k] = ddP * g - 2.f * (dP[a] * r[b] + dP[b] * r[a]) * g1 +
+                 P * (4.f * r[a] * r[b] * g2 - (a == b ? 2.f * g1 : 0.f));
+        }
+      }
+      f(atom, nu, d, h);
+    }
   }
 }
 

@@ -213,6 +213,8 @@ struct kldi_plan {
   float* d_x_scale = nullptr;   // [tiles][32] function scales of d_x_s
   float* d_rowscale = nullptr;  // [npoints] point scales of d_phi_s
   float* d_pscale = nullptr;    // [npoints] per-point balance c_i: Phi c and X / c in the V product
+  float* d_zscale = nullptr;    // [npoints] point scales of the gradient's Z tiles (first tensor-core gradient)
+  bool rec_fit_all = true;      // every basis block fits a shared-memory shell record (40 shells, 80 primitives)
   float* d_dscale = nullptr;    // [nbf_pad] column scales of d_dsplit
   uint16_t* d_dsplit = nullptr; // sliced D block pairs [nbb*nbb][NS planes][32][32]
   uint16_t* d_zero = nullptr;   // zero block (bulk-copy source for masked / absent blocks)
@@ -257,6 +259,7 @@ kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
 kldi_status prepare_tc_kernels();
 kldi_status launch_grad64(const kldi_plan* P, const Batch& b, const double* D, double* G, cudaStream_t s);
+kldi_status launch_grad_tc(const kldi_plan* P, const Batch& b, bool gga_xc, double* G, cudaStream_t s);
 kldi_status becke_weights_device(int natm, const double* atom_xyz, const double* R, const int32_t* nbr,
                                  const double* xyz, const int32_t* owner, const double* raw_w, int64_t nreal,
                                  double* w);

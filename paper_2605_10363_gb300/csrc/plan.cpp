@@ -87,7 +87,7 @@ void free_plan_buffers(kldi_plan* P) {
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
                   P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
-                  P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_dscale, P->d_dsplit, P->d_zero};
+                  P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& b : P->batches) {
@@ -355,6 +355,14 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
       bb_begin[p] = std::min(bb_begin[p], s);
       bb_end[p] = std::max(bb_end[p], s + 1);
     }
+  }
+  for (int64_t p = 0; p < nbb; ++p) {
+    int npr_blk = 0;
+    for (int s = bb_begin[p]; s < bb_end[p]; ++s) {
+      npr_blk += shells[s].nprim;
+      if (shells[s].nprim > 255) npr_blk += 1 << 20;
+    }
+    if (bb_end[p] - bb_begin[p] > 40 || npr_blk > 80) P->rec_fit_all = false;
   }
   // FP32 hi/lo pairs: hi = fp32(v), lo = fp32(v - hi)
   const size_t npr = alpha.size();

@@ -273,6 +273,73 @@ __global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, List
   }
 }
 
+// Z tiles of the nuclear gradient: Z_nu,i = 2 a_i chi_nu(r_i) + b_i . grad chi_nu(r_i)
+// (a = w v_rho / 2, b = 2 w v_sigma grad rho), sliced per point like the Phi
+// tiles, so that Q = Z D runs through the density product.  Point scale from
+// the shell bounds |chi| <= r^l S0 and |d_a chi| <= l r^(l-1) S0 + 2 r^(l+1) S1
+// (S0 = sum |c| e^{-a r^2}, S1 = sum |c| a e^{-a r^2}; |P| <= r^l and
+// |d_a P| <= l r^(l-1) for the Cartesian components):
+// |Z| <= 2 |a| r^l S0 + (|b_x| + |b_y| + |b_z|) (l r^(l-1) S0 + 2 r^(l+1) S1).
+template <int NS>
+__global__ void __launch_bounds__(128) k_z_split(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
+                                                 const double* __restrict__ xcoef, uint8_t* out_row,
+                                                 float* zscale) {
+  __shared__ float st[kBasisBlk][kBlockPts + 1];
+  __shared__ BlockRec rec[2];
+  const int64_t g = g0 + blockIdx.x;
+  const int i = threadIdx.x;
+  const int64_t pt = g * kBlockPts + i;
+  const float4 pr = G.prel[pt];
+  const float px = pr.x, py = pr.y, pz = pr.z;
+  const int anc = G.anchor[g];
+  const int tb = L.blk_ptr[g], te = L.blk_ptr[g + 1];
+  const float a2 = 2.f * (float)xcoef[pt * 4];
+  const float bx = (float)xcoef[pt * 4 + 1], by = (float)xcoef[pt * 4 + 2], bz = (float)xcoef[pt * 4 + 3];
+  const float bsum = fabsf(bx) + fabsf(by) + fabsf(bz);
+  float M = 0.f;
+  for (int j = tb; j < te; ++j) {
+    const int p = L.blk_idx[j];
+    BlockRec* rc = rec + ((j - tb) & 1);
+    stage_block_rec(B, p, anc, rc, i, kBlockPts);   // every block fits (checked on the host)
+    __syncthreads();
+    for (int s = 0; s < rc->nshell; ++s) {
+      const float4 c0 = rc->c0[s], c1 = rc->c1[s];
+      const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
+      const int l = hdr & 255, np = (hdr >> 8) & 255;
+      const float dx = (px - c0.x) - c0.w, dy = (py - c0.y) - c1.x, dz = (pz - c0.z) - c1.y;
+      const float r2 = dx * dx + dy * dy + dz * dz, r = sqrtf(r2);
+      float s0 = 0.f, s1 = 0.f;
+      for (int k = 0; k < np; ++k) {
+        const float4 q = rc->pf[pi + k];
+        const float e = fabsf(q.z) * __expf(-q.x * r2);
+        s0 += e;
+        s1 += q.x * e;
+      }
+      const float rl = l == 0 ? 1.f : (l == 1 ? r : r2);                 // r^l
+      const float dl = l == 0 ? 0.f : (l == 1 ? 1.f : 2.f * r);          // l r^(l-1)
+      M = fmaxf(M, fabsf(a2) * rl * s0 + bsum * (dl * s0 + 2.f * r * rl * s1));
+    }
+  }
+  const float zs = pow2_ceil(M * 1.001f);
+  zscale[pt] = zs;
+  const float rinv = 1.f / zs;
+  for (int j = tb; j < te; ++j) {
+    const int p = L.blk_idx[j];
+    BlockRec* rc = rec + ((j - tb + te - tb) & 1);
+    stage_block_rec(B, p, anc, rc, i, kBlockPts);
+    __syncthreads();
+    float v[kBasisBlk];
+#pragma unroll
+    for (int nu = 0; nu < kBasisBlk; ++nu) st[nu][i] = 0.f;
+    for_rec_functions<true>(rc, px, py, pz, [&](int nu, float x, float gx, float gy, float gz) {
+      st[nu][i] = fmaf(bx, gx, fmaf(by, gy, fmaf(bz, gz, a2 * x)));
+    });
+#pragma unroll
+    for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = st[nu][i] * rinv;
+    store_sliced_row<NS>(out_row + (int64_t)(j - t0) * tile_bytes(NS), kPlaneBytes, i, v);
+  }
+}
+
 template <int NS>
 static kldi_status phi_ns(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   const int64_t n = b.g1 - b.g0;
@@ -436,12 +503,21 @@ struct RhoCfg {
   static_assert(kSmem <= 232448, "shared memory");
 };
 
-template <int NS, bool GRAD>
+// Epilogue of the density-product kernel: the row-dot (rho, grad rho), or
+// one of the two terms of the nuclear gradient of E_xc on a fixed grid,
+//   dE/dR_A = -2 sum_{mu on A} sum_i [ grad chi_mu Q_mu,i + (b_i . grad grad chi_mu) R_mu,i ]
+// with R = Phi D and Q = Z D (Z = 2 a phi + b . grad phi) over the executed pairs:
+// kGradQ takes the Z~ tiles as operand A and contracts Q with grad chi,
+// kGradR takes the Phi~ tiles and contracts R with b . grad grad chi.
+enum { kRowDot = 0, kGradR = 1, kGradQ = 2 };
+
+template <int NS, bool GRAD, int MODE = kRowDot>
 __global__ void __launch_bounds__(576, 1)
     k_rho_tc(BasisView B, GridView G, ListView L, int64_t g0, int64_t g1, int64_t t0,
              const uint8_t* __restrict__ phi, const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero,
              const double* __restrict__ dmax, const float* __restrict__ dscale, const float* __restrict__ rowscale,
-             double t_b, double t_d, double* rho, double* grad, int* err) {
+             double t_b, double t_d, double* rho, double* grad, const double* __restrict__ xcoef, double* gout,
+             int* err) {
   using C = RhoCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -661,6 +737,12 @@ __global__ void __launch_bounds__(576, 1)
       const int anc = G.anchor[g];
       const double rsc = (double)rowscale[pt];
       double r_i = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+      float bx = 0.f, by = 0.f, bz = 0.f;   // b_i of the gradient's Hessian term
+      if constexpr (MODE == kGradR) {
+        bx = (float)xcoef[pt * 4 + 1];
+        by = (float)xcoef[pt * 4 + 2];
+        bz = (float)xcoef[pt * 4 + 3];
+      }
       const int ntile = (n + C::kNQ - 1) / C::kNQ;
       for (int nt = 0; nt < ntile && ok; ++nt) {
         const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
@@ -722,31 +804,72 @@ __global__ void __launch_bounds__(576, 1)
 #pragma unroll
             for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * dscale[q * kBasisBlk + c];
           }
-          float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
-          auto acc = [&](int nu, float v, float dx, float dy, float dz) {
-            const float rr = Rs[nu * kBlockPts + i];
-            pr = fmaf(v, rr, pr);
+          if constexpr (MODE == kRowDot) {
+            float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
+            auto acc = [&](int nu, float v, float dx, float dy, float dz) {
+              const float rr = Rs[nu * kBlockPts + i];
+              pr = fmaf(v, rr, pr);
+              if (GRAD) {
+                px_ = fmaf(dx, rr, px_);
+                py_ = fmaf(dy, rr, py_);
+                pz_ = fmaf(dz, rr, pz_);
+              }
+            };
+            if (staged)
+              for_rec_functions<GRAD>(rec, prl.x, prl.y, prl.z, acc);
+            else
+              for_block_functions<float, GRAD>(B, q, prl.x, prl.y, prl.z, acc, anc);
+            r_i += rsc * (double)pr;
             if (GRAD) {
-              px_ = fmaf(dx, rr, px_);
-              py_ = fmaf(dy, rr, py_);
-              pz_ = fmaf(dz, rr, pz_);
+              gx += 2.0 * rsc * (double)px_;
+              gy += 2.0 * rsc * (double)py_;
+              gz += 2.0 * rsc * (double)pz_;
             }
-          };
-          if (staged)
-            for_rec_functions<GRAD>(rec, prl.x, prl.y, prl.z, acc);
-          else
-            for_block_functions<float, GRAD>(B, q, prl.x, prl.y, prl.z, acc, anc);
-          r_i += rsc * (double)pr;
-          if (GRAD) {
-            gx += 2.0 * rsc * (double)px_;
-            gy += 2.0 * rsc * (double)py_;
-            gz += 2.0 * rsc * (double)pz_;
+          } else if (staged) {
+            // per atom of the block's shells: the warp's sum over its 32
+            // points, one FP64 atomic per atom and component
+            const float rscf = (float)rsc;
+            int cur = -1;
+            float tx = 0.f, ty = 0.f, tz = 0.f;
+            auto flush = [&]() {
+              float v[3] = {tx * rscf, ty * rscf, tz * rscf};
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+              if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(&gout[cur * 3 + c], -2.0 * (double)v[c]);
+            };
+            for_rec_derivatives<MODE == kGradR>(rec, prl.x, prl.y, prl.z,
+                                                [&](int atom, int nu, const float* d, const float* h) {
+              if (atom != cur) {
+                if (cur >= 0) flush();
+                cur = atom;
+                tx = ty = tz = 0.f;
+              }
+              const float rr = Rs[nu * kBlockPts + i];
+              if constexpr (MODE == kGradQ) {
+                tx = fmaf(d[0], rr, tx);
+                ty = fmaf(d[1], rr, ty);
+                tz = fmaf(d[2], rr, tz);
+              } else {
+                // (b . grad d_x chi) = b_x h_xx + b_y h_xy + b_z h_xz, ...
+                tx = fmaf(fmaf(bx, h[0], fmaf(by, h[1], bz * h[2])), rr, tx);
+                ty = fmaf(fmaf(bx, h[1], fmaf(by, h[3], bz * h[4])), rr, ty);
+                tz = fmaf(fmaf(bx, h[2], fmaf(by, h[4], bz * h[5])), rr, tz);
+              }
+            });
+            if (cur >= 0) flush();
+          } else if (lane == 0) {
+            atomicCAS(err, 0, 102);   // the gradient epilogue needs staged shell records
           }
         }
       }
       if (!ok) break;
       __syncwarp();
       if (lane == 0) mbar_arrive(&mempty[b]);
+      if constexpr (MODE != kRowDot) continue;
       // combine the four q-block groups of each point in a fixed order
       if (!mbar_wait_warp(rempty, (uint32_t)(k & 1) ^ 1u, abort_flag, err, 117)) break;
       red[(k4 * 4 + 0) * kBlockPts + i] = r_i;
@@ -797,18 +920,52 @@ static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, d
     k_rho_tc<NS, true><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                            b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                            P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
-                                                           P->d_err);
+                                                           nullptr, nullptr, P->d_err);
   else
     k_rho_tc<NS, false><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                             b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                             P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
-                                                            P->d_err);
+                                                            nullptr, nullptr, P->d_err);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
 
 kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho_out, double* grad_out, cudaStream_t s) {
   return P->prec == KLDI_BF16X6 ? rho_ns<3>(P, b, rho_out, grad_out, s) : rho_ns<2>(P, b, rho_out, grad_out, s);
+}
+
+// Nuclear gradient of one batch (after its density and functional stages):
+// Z tiles into the X-tile buffer, then the Q term (operand Z~) and, for a GGA
+// functional, the R term (operand Phi~) of the density-product kernel.
+template <int NS>
+static kldi_status grad_ns(const kldi_plan* P, const Batch& b, bool gga_xc, double* G, cudaStream_t s) {
+  using C = RhoCfg<NS>;
+  const int64_t n = b.g1 - b.g0;
+  if (n == 0) return KLDI_OK;
+  KLDI_TRY(prepare_tc_kernels());
+  uint8_t* zt = reinterpret_cast<uint8_t*>(P->d_x_s);
+  k_z_split<NS><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.t0,
+                                                  P->d_xcoef, zt, P->d_zscale);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  const unsigned grid = (unsigned)std::min<int64_t>(n, P->num_sms);
+  const uint8_t* ds = reinterpret_cast<const uint8_t*>(P->d_dsplit);
+  const uint8_t* z = reinterpret_cast<const uint8_t*>(P->d_zero);
+  k_rho_tc<NS, false, kGradQ><<<grid, C::kThreads, C::kSmem, s>>>(
+      P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.g1, b.t0, zt, ds, z, P->d_dmax, P->d_dscale,
+      P->d_zscale, P->opt.t_b, P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  if (gga_xc) {
+    k_rho_tc<NS, false, kGradR><<<grid, C::kThreads, C::kSmem, s>>>(
+        P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.g1, b.t0,
+        reinterpret_cast<const uint8_t*>(P->d_phi_s), ds, z, P->d_dmax, P->d_dscale, P->d_rowscale, P->opt.t_b,
+        P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err);
+    KLDI_TRY_CUDA(cudaGetLastError());
+  }
+  return KLDI_OK;
+}
+
+kldi_status launch_grad_tc(const kldi_plan* P, const Batch& b, bool gga_xc, double* G, cudaStream_t s) {
+  return P->prec == KLDI_BF16X6 ? grad_ns<3>(P, b, gga_xc, G, s) : grad_ns<2>(P, b, gga_xc, G, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1135,6 +1292,10 @@ static kldi_status prepare_rho_kernel() {
   using C = RhoCfg<NS>;
   KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
   KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+  KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false, kGradQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     C::kSmem));
+  KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false, kGradR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     C::kSmem));
   return KLDI_OK;
 }
 
