@@ -95,11 +95,12 @@ def function_atoms(system) -> np.ndarray:
 
 
 def exc_gradient(system, grid, shells=None, screened=True, xc_kind=None, t_b=None, t_d=None,
-                 rho_min=oxc.RHO_MIN, mlp=None, return_magnitude=False):
+                 rho_min=oxc.RHO_MIN, mlp=None, return_magnitude=False, blocks=None):
     """dE_xc/dR_A (natm x 3) on the fixed grid, the formula of the module docstring.
     With return_magnitude, also the sums of the terms' magnitudes per atom and
     component, 2 sum_{mu on A} sum_i (|d_x chi Q| + |b . grad d_x chi| |R|): the
-    scale against which rounding errors of the terms are measured."""
+    scale against which rounding errors of the terms are measured.  `blocks`
+    restricts the sum to those grid blocks (a rank's share of the grid)."""
     from . import mlp as omlp
     if shells is None:
         shells = obasis.build_shells(system.xyz, system.basis)
@@ -117,7 +118,7 @@ def exc_gradient(system, grid, shells=None, screened=True, xc_kind=None, t_b=Non
     dsz = oscreen.D_BASIS
     nb = oscreen.nbasis_blocks(nbf)
     B = grid.block
-    for g in range(grid.nblocks):
+    for g in (range(grid.nblocks) if blocks is None else blocks):
         sl = slice(g * B, (g + 1) * B)
         pts = grid.points[sl]
         w = grid.weights[sl]

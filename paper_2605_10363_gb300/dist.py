@@ -61,3 +61,23 @@ def exc_sharded(plan, xc, D, V, E, rank: int, world: int, group=None):
     plan.set_block_range(g0, g1)
     kldi.exc(plan, xc, D, V, E)
     return reduce_exc(V, E, group)
+
+
+def reduce_grad(G, E, group=None):
+    """Sum the ranks' partial nuclear gradients (natm x 3) and E_xc in place."""
+    import torch.distributed as dist
+    dist.all_reduce(G, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(E, op=dist.ReduceOp.SUM, group=group)
+    return G, E
+
+
+def exc_grad_sharded(plan, xc, D, G, E, rank: int, world: int, group=None):
+    """This rank's share of kldi_exc_grad (its balanced block range) followed by
+    the reduction: G and E (device tensors) receive the full result on every
+    rank.  The gradient is a sum over grid blocks like E_xc, so the partials add."""
+    from . import kldi
+    ptr, _, _ = plan.lists()
+    g0, g1 = partition_blocks(block_weights(ptr), world)[rank]
+    plan.set_block_range(g0, g1)
+    kldi.exc_grad(plan, xc, D, G, E)
+    return reduce_grad(G, E, group)

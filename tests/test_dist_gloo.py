@@ -10,6 +10,7 @@ import pytest
 import synth
 from oracle import basis as ob
 from oracle import exc as oe
+from oracle import grad as ogr
 from oracle import grid as og
 from paper_2605_10363_gb300 import dist as kdist
 
@@ -77,3 +78,38 @@ def test_two_ranks_reduce_to_the_single_process_result(tmp_path):
         E = np.load(tmp_path / f"E{r}.npy")[0]
         assert E == pytest.approx(ref.E, rel=1e-13)
         assert np.abs(V - ref.V).max() <= 1e-13 * np.abs(ref.V).max()
+
+
+def _rank_grad(rank, world, port, ranges, out_dir):
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        s = synth.make_system(1)
+        g = og.build_grid(s.Z, s.xyz, s.grid)
+        sh = ob.build_shells(s.xyz, s.basis)
+        g0, g1 = ranges[rank]
+        G = torch.from_numpy(ogr.exc_gradient(s, g, sh, screened=True, blocks=range(g0, g1)).copy())
+        E = torch.tensor([oe.evaluate(s, g, sh, screened=True, want_v=False, blocks=range(g0, g1)).E],
+                         dtype=torch.float64)
+        kdist.reduce_grad(G, E)
+        np.save(os.path.join(out_dir, f"G{rank}.npy"), G.numpy())
+        np.save(os.path.join(out_dir, f"E{rank}.npy"), E.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_reduce_the_gradient(tmp_path):
+    """The nuclear gradient is a sum over grid blocks: two ranks' partial
+    gradients over complementary block ranges reduce to the full gradient."""
+    import torch.multiprocessing as mp
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    Gref = ogr.exc_gradient(s, g, sh, screened=True)
+    ranges = [(0, g.nblocks // 3), (g.nblocks // 3, g.nblocks)]
+    mp.start_processes(_rank_grad, args=(2, _free_port(), ranges, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    for r in range(2):
+        G = np.load(tmp_path / f"G{r}.npy")
+        assert np.abs(G - Gref).max() <= 1e-13 * np.abs(Gref).max()

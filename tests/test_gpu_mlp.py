@@ -189,3 +189,28 @@ def test_what_training_gains(trained):
     print(f"E_xc error vs analytic: trained {d_tr:.3e} Ha, untrained {d_un:.3e} Ha; "
           f"functional stage ms: mlp {times['trained']:.4f}, analytic {times['analytic']:.4f}")
     assert d_tr < d_un / 20.0
+
+
+def test_gradient_with_learned_functional(trained):
+    """Nuclear gradient with the fused network: the X coefficients a, b come from
+    the FP32 network (relative error <= 2e-5 of the Slater scale, above), and
+    the gradient is linear in them, so |dG| <= 2e-5 Gmag (the oracle's term
+    magnitudes) in both the FP64 and the BF16x6 forms."""
+    from oracle import grad as ogr
+    kldi = _kldi()
+    net, box, _ = trained
+    s = synth.make_system(1)
+    p16 = om.fp16_weights(net.params())
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    Gref, Gmag = ogr.exc_gradient(s, g, sh, screened=True, xc_kind="mlp", mlp=(p16, om.Box(*box)),
+                                  return_magnitude=True)
+    for prec in ("fp64", "bf16x6"):
+        plan = kldi.plan_for_system(s, prec=prec, xc="pbe")
+        kldi.plan_set_mlp(plan, net)
+        G = np.zeros((len(s.Z), 3))
+        E = np.zeros(1)
+        kldi.exc_grad(plan, "mlp", s.D, G, E)
+        d = np.abs(G - Gref)
+        print(f"learned functional gradient {prec}: max|dG| {d.max():.2e}, max dG/Gmag {(d / Gmag).max():.2e}")
+        assert np.all(d <= 2e-5 * Gmag), prec
