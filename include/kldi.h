@@ -140,6 +140,21 @@ typedef struct {
   int64_t workspace_bytes;/* device bytes held by the plan                    */
 } kldi_plan_stats;
 
+/* Basis order by overlap signatures (Sec. III-B, appendix "Overlap-Signature
+ * Construction and Basis-Function Clustering"), host preprocessing once per
+ * geometry.  Units are shells (a Cartesian shell's functions stay together):
+ * shell signature T_s = (||S[s,t]||_F)_t, cosine distance
+ * d(s,t) = 1 - T_s.T_t / (|T_s||T_t|), agglomerative clustering with average
+ * linkage, each merge orienting the two leaf sequences so that their closest end
+ * leaves are adjacent.  nfn[nshell]: functions per shell in the current order;
+ * S: the nbf x nbf overlap matrix in that order (row-major, host); perm[nshell]
+ * (host, caller-owned) receives the new order: position k holds old shell
+ * perm[k].  Ties are broken by the lower index, so the result is reproducible.
+ * O(nshell^2) memory.  KLDI_EINVAL for a non-positive size or a shell with a
+ * zero signature.  The caller reorders its basis and D with perm (the plan is
+ * then built from the reordered basis). */
+kldi_status kldi_order_shells(int nshell, const int* nfn, const double* S, int* perm);
+
 /* Build the molecular grid on the host (preprocessing, run once per
  * geometry; Sec. III-D).  *out is library-owned. */
 kldi_status kldi_make_grid(const kldi_molecule* mol, const kldi_grid_spec* spec, kldi_grid** out);

@@ -39,7 +39,7 @@ def _compile(src: str, extra: list[str]) -> str:
         return obj
     cmd = [nvcc(), "-c", src, "-o", obj, "-O3", "-std=c++17", "-lineinfo", *ARCH,
            "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-           "-Xcompiler", "-fPIC,-fopenmp,-O3", "--expt-relaxed-constexpr", *extra]
+           "-Xcompiler", "-fPIC,-fopenmp,-O3,-ffp-contract=off", "--expt-relaxed-constexpr", *extra]
     if src.endswith(".cpp"):
         cmd += ["-x", "cu"]
     r = subprocess.run(cmd, capture_output=True, text=True)

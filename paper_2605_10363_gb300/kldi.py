@@ -69,6 +69,7 @@ def _load():
     vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
     sig = {
         "kldi_make_grid": (C.c_int, [C.POINTER(Molecule), C.POINTER(GridSpec), C.POINTER(vp)]),
+        "kldi_order_shells": (C.c_int, [C.c_int, vp, vp, vp]),
         "kldi_grid_info": (C.c_int, [vp, i64p, i64p, i64p]),
         "kldi_grid_export": (C.c_int, [vp, vp, vp, vp]),
         "kldi_screen": (C.c_int, [vp, C.POINTER(Molecule), C.POINTER(Basis), C.POINTER(Options), C.POINTER(vp)]),
@@ -163,6 +164,19 @@ def _molecule(Z, xyz):
     xyz = np.ascontiguousarray(xyz, np.float64)
     m = Molecule(len(Z), Z.ctypes.data_as(C.POINTER(C.c_int32)), xyz.ctypes.data_as(C.POINTER(C.c_double)))
     return m, (Z, xyz)
+
+
+def order_shells(S, nfn):
+    """Shell order by overlap signatures (kldi_order_shells): S the nbf x nbf
+    overlap matrix, nfn the functions per shell; returns perm (position k holds
+    old shell perm[k])."""
+    S = np.ascontiguousarray(S, np.float64)
+    nfn = np.ascontiguousarray(nfn, np.int32)
+    if S.shape != (int(nfn.sum()), int(nfn.sum())):
+        raise ValueError("S must be nbf x nbf with nbf = sum(nfn)")
+    perm = np.zeros(nfn.size, np.int32)
+    _check(LIB.kldi_order_shells(int(nfn.size), _ptr(nfn), _ptr(S), _ptr(perm)))
+    return perm
 
 
 def make_grid(Z, xyz, nrad, ntheta, block=128) -> Grid:

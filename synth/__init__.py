@@ -454,6 +454,27 @@ def frame_sizes(nframes: int = 256) -> np.ndarray:
     return np.random.default_rng(31).integers(20, 131, size=256)[:nframes]
 
 
+def shell_sizes(basis: Basis) -> np.ndarray:
+    """Cartesian functions per shell."""
+    return np.array([len(CART[int(l)]) for l in basis.l], dtype=np.int32)
+
+
+def permute_shells(system: System, perm) -> System:
+    """The same system with its shells in the order perm (position k holds old
+    shell perm[k]); D is permuted to match.  Array bookkeeping only."""
+    perm = np.asarray(perm, dtype=np.int64)
+    b = system.basis
+    pp = b.prim_ptr
+    nfn = shell_sizes(b)
+    foff = np.concatenate([[0], np.cumsum(nfn)]).astype(np.int64)
+    prim_idx = np.concatenate([np.arange(pp[s], pp[s + 1]) for s in perm])
+    fn_idx = np.concatenate([np.arange(foff[s], foff[s + 1]) for s in perm])
+    nb = Basis(b.atom[perm].copy(), b.l[perm].copy(), b.nprim[perm].copy(), b.exps[prim_idx].copy(),
+               b.coefs[prim_idx].copy())
+    D = system.D[np.ix_(fn_idx, fn_idx)].copy()
+    return System(system.name + "_reordered", system.Z, system.xyz, nb, D, system.grid, system.t_b, system.t_d,
+                  system.xc, meta=dict(system.meta, shell_perm=perm, fn_perm=fn_idx))
+
 # ---------------------------------------------------------------------------- learned functional inputs
 MLP_HIDDEN = 64
 MLP_NPARAMS = MLP_HIDDEN * 2 + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + 2 * MLP_HIDDEN + 2
