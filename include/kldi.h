@@ -118,7 +118,13 @@ typedef struct {
  * t_d: block-pair execution threshold (Eq. block_pair_filter); rho_min: points
  * with rho < rho_min contribute nothing; prec: kldi_prec; xc: the kldi_xc the
  * plan will serve (KLDI_XC_PBE/MLP need basis gradients, LDA does not);
- * stream: a cudaStream_t, or NULL for the legacy default stream. */
+ * stream: a cudaStream_t, or NULL for the legacy default stream;
+ * shell_order: NULL, or a permutation of the nshell shells (e.g. from
+ * kldi_order_shells; caller-owned, read during kldi_screen only) in which the
+ * plan lays out its basis blocks (Sec. III-B).  The caller's D, V and any
+ * other matrix stay in the caller's order: the compute calls permute D on the
+ * way in and V on the way out (two gather kernels and two nbf x nbf buffers
+ * held by the plan). */
 typedef struct {
   double t_b;
   double t_d;
@@ -126,6 +132,7 @@ typedef struct {
   int prec;
   int xc;
   void* stream;
+  const int32_t* shell_order;
 } kldi_options;
 
 /* Plan statistics (kldi_plan_info). */

@@ -104,7 +104,33 @@ kldi_status check_xc(const kldi_plan* P, int xc) {
   return KLDI_OK;
 }
 
+// D in the caller's function order (device) -> the plan's order.
+kldi_status internal_D(kldi_plan* P, const double*& D) {
+  if (!P->d_fnperm) return KLDI_OK;
+  KLDI_TRY(launch_permute(P, D, P->d_Dint, true, P->stream));
+  D = P->d_Dint;
+  return KLDI_OK;
+}
+
 kldi_status exc_device(kldi_plan* P, int xc, const double* D, double* V, double* exc) {
+  if (P->d_fnperm) {
+    // reordered plan: evaluate in the internal order, then V to the caller's order
+    KLDI_TRY(internal_D(P, D));
+    double* Vc = V;
+    V = P->d_Vint;
+    KLDI_TRY(ensure_tile_buffers(P, P->prec));
+    KLDI_TRY(prepare_D(P, D));
+    KLDI_TRY_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
+    for (const Batch& b : P->batches) {
+      KLDI_TRY(density_batch(P, b, D, P->d_rho, P->d_grad));
+      KLDI_TRY(potential_batch(P, b, xc, P->d_rho, P->d_grad, V, true));
+    }
+    KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 3, [&]() -> kldi_status {
+      KLDI_TRY(launch_finish(P, V, exc, P->stream));
+      return launch_permute(P, V, Vc, false, P->stream);
+    }));
+    return KLDI_OK;
+  }
   KLDI_TRY(ensure_tile_buffers(P, P->prec));
   KLDI_TRY(prepare_D(P, D));
   KLDI_TRY_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
@@ -131,6 +157,7 @@ extern "C" kldi_status kldi_density(kldi_plan* P, const double* D, double* rho, 
   double* drho = host_out ? P->d_rho : rho;
   double* dgrad = P->gga ? (host_out ? P->d_grad : grad) : P->d_grad;
   KLDI_TRY(ensure_tile_buffers(P, P->prec));
+  KLDI_TRY(internal_D(P, dD));
   KLDI_TRY(prepare_D(P, dD));
   for (const Batch& b : P->batches) KLDI_TRY(density_batch(P, b, dD, drho, dgrad));
   if (host_out) {
@@ -166,9 +193,15 @@ extern "C" kldi_status kldi_vxc(kldi_plan* P, int xc, const double* rho, const d
   const bool hostV = !is_device_ptr(V), hostE = !is_device_ptr(Exc);
   double* dV = hostV ? P->d_V : V;
   double* dE = hostE ? P->d_exc : Exc;
+  double* dVc = dV;
+  if (P->d_fnperm) dV = P->d_Vint;   // reordered plan: V to the caller's order at the end
   KLDI_TRY_CUDA(cudaMemsetAsync(dV, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
   for (const Batch& b : P->batches) KLDI_TRY(potential_batch(P, b, xc, drho, dgrad, dV, false));
   KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 2, [&] { return launch_finish(P, dV, dE, P->stream); }));
+  if (P->d_fnperm) {
+    KLDI_TRY(launch_permute(P, dV, dVc, false, P->stream));
+    dV = dVc;
+  }
   if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, sizeof(double) * P->nbf * P->nbf, cudaMemcpyDeviceToHost, P->stream));
   if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
   if (hostV || hostE) {
@@ -225,6 +258,7 @@ extern "C" kldi_status kldi_exc_grad(kldi_plan* P, int xc, const double* D, doub
   if (P->prec != KLDI_FP64 && !P->d_zscale) {
     KLDI_TRY_CUDA(cudaMalloc(&P->d_zscale, sizeof(float) * std::max<int64_t>(P->npoints, 1)));
   }
+  KLDI_TRY(internal_D(P, dD));
   KLDI_TRY(prepare_D(P, dD));
   KLDI_TRY_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * 3 * P->natm, P->stream));
   for (const Batch& b : P->batches) {

@@ -196,6 +196,9 @@ struct kldi_plan {
   // device: per-evaluation buffers
   double* d_D = nullptr;        // staging copy of a host D
   double* d_V = nullptr;        // staging V when the caller passes host memory
+  int32_t* d_fnperm = nullptr;  // [nbf] caller's index of each internal function (reordered plans)
+  double* d_Dint = nullptr;     // D and V in the internal function order (reordered plans)
+  double* d_Vint = nullptr;
   double* d_dmax = nullptr;     // [nbb*nbb]
   double* d_rho = nullptr;      // [npoints]
   double* d_grad = nullptr;     // [npoints*3]
@@ -259,6 +262,8 @@ kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s);
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s);
 kldi_status prepare_tc_kernels();
 kldi_status launch_grad64(const kldi_plan* P, const Batch& b, const double* D, double* G, cudaStream_t s);
+// Reordered plans: dst[i][j] = src[fp[i]][fp[j]] (gather) or dst[fp[i]][fp[j]] = src[i][j].
+kldi_status launch_permute(const kldi_plan* P, const double* src, double* dst, bool gather, cudaStream_t s);
 kldi_status launch_grad_tc(const kldi_plan* P, const Batch& b, bool gga_xc, double* G, cudaStream_t s);
 kldi_status becke_weights_device(int natm, const double* atom_xyz, const double* R, const int32_t* nbr,
                                  const double* xyz, const int32_t* owner, const double* raw_w, int64_t nreal,

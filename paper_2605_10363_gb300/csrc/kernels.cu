@@ -412,4 +412,24 @@ kldi_status launch_finish(const kldi_plan* P, double* V, double* exc, cudaStream
   return KLDI_OK;
 }
 
+// Reordered plans: D into the internal function order, V back to the caller's.
+__global__ void k_permute(const double* __restrict__ src, double* __restrict__ dst, const int32_t* __restrict__ fp,
+                          int n, int gather) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  const int64_t o = (int64_t)fp[i] * n + fp[j];
+  if (gather)
+    dst[idx] = src[o];
+  else
+    dst[o] = src[idx];
+}
+
+kldi_status launch_permute(const kldi_plan* P, const double* src, double* dst, bool gather, cudaStream_t s) {
+  const int64_t n2 = P->nbf * P->nbf;
+  k_permute<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(src, dst, P->d_fnperm, (int)P->nbf, gather ? 1 : 0);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
 }  // namespace kldi

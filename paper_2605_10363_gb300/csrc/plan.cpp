@@ -86,7 +86,7 @@ void free_plan_buffers(kldi_plan* P) {
   free_own_tile_buffers(P);
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
-                  P->d_D, P->d_V, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
+                  P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
                   P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -295,9 +295,47 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     set_error("KLDI_TF32X3 is not provided: 11-bit slices cannot keep the tensor-core sums exact");
     return KLDI_EUNSUPPORTED;
   }
+  // optional shell order: the plan works on the permuted basis; fnperm maps an
+  // internal function index to the caller's
+  std::vector<int32_t> p_atom, p_l, p_nprim, fnperm;
+  std::vector<double> p_exps, p_coefs;
+  kldi_basis permuted;
+  if (opt->shell_order) {
+    const int ns0 = basis->nshell;
+    std::vector<char> seen(ns0, 0);
+    std::vector<int64_t> poff(ns0 + 1, 0), foff(ns0 + 1, 0);
+    for (int s = 0; s < ns0; ++s) {
+      const int l = basis->l[s];
+      if (l < 0 || l > 2 || basis->nprim[s] <= 0) {
+        set_error("kldi_screen: shell %d has l=%d nprim=%d (supported: l <= 2)", s, l, basis->nprim[s]);
+        return l > 2 ? KLDI_EUNSUPPORTED : KLDI_EINVAL;
+      }
+      poff[s + 1] = poff[s] + basis->nprim[s];
+      foff[s + 1] = foff[s] + (l + 1) * (l + 2) / 2;
+    }
+    for (int k = 0; k < ns0; ++k) {
+      const int s = opt->shell_order[k];
+      if (s < 0 || s >= ns0 || seen[s]) {
+        set_error("kldi_screen: shell_order is not a permutation of 0 .. %d", ns0 - 1);
+        return KLDI_EINVAL;
+      }
+      seen[s] = 1;
+      p_atom.push_back(basis->atom[s]);
+      p_l.push_back(basis->l[s]);
+      p_nprim.push_back(basis->nprim[s]);
+      for (int64_t i = poff[s]; i < poff[s + 1]; ++i) {
+        p_exps.push_back(basis->exps[i]);
+        p_coefs.push_back(basis->coefs[i]);
+      }
+      for (int64_t f = foff[s]; f < foff[s + 1]; ++f) fnperm.push_back((int32_t)f);
+    }
+    permuted = kldi_basis{ns0, p_atom.data(), p_l.data(), p_nprim.data(), p_exps.data(), p_coefs.data()};
+    basis = &permuted;
+  }
   kldi_plan* P = new (std::nothrow) kldi_plan;
   if (!P) { set_error("kldi_screen: out of host memory"); return KLDI_ENOMEM; }
   P->opt = *opt;
+  P->opt.shell_order = nullptr;   // read here only
   P->gga = opt->xc != KLDI_XC_LDA_X;
   P->prec = opt->prec;
   P->stream = (cudaStream_t)opt->stream;
@@ -556,6 +594,11 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
   const size_t nbf2 = (size_t)P->nbf * P->nbf;
   if ((st = dalloc(P, &P->d_D, nbf2)) != KLDI_OK) return fail(st);
   if ((st = dalloc(P, &P->d_V, nbf2)) != KLDI_OK) return fail(st);
+  if (!fnperm.empty()) {
+    if ((st = upload(P, &P->d_fnperm, fnperm.data(), fnperm.size())) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_Dint, nbf2)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_Vint, nbf2)) != KLDI_OK) return fail(st);
+  }
   if ((st = dalloc(P, &P->d_dmax, (size_t)nbb * nbb)) != KLDI_OK) return fail(st);
   if ((st = dalloc(P, &P->d_rho, (size_t)P->npoints)) != KLDI_OK) return fail(st);
   if ((st = dalloc(P, &P->d_grad, (size_t)P->npoints * 3)) != KLDI_OK) return fail(st);

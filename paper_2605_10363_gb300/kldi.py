@@ -45,7 +45,7 @@ class GridSpec(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("t_b", C.c_double), ("t_d", C.c_double), ("rho_min", C.c_double), ("prec", C.c_int),
-                ("xc", C.c_int), ("stream", C.c_void_p)]
+                ("xc", C.c_int), ("stream", C.c_void_p), ("shell_order", C.c_void_p)]
 
 
 class TrainOptions(C.Structure):
@@ -255,15 +255,17 @@ class Plan:
 
 
 def screen(grid: Grid, Z, xyz, shells_atom, shells_l, shells_nprim, exps, coefs, t_b, t_d,
-           rho_min=1e-14, prec="bf16x3", xc="pbe", stream=0) -> Plan:
+           rho_min=1e-14, prec="bf16x3", xc="pbe", stream=0, shell_order=None) -> Plan:
     m, keepm = _molecule(Z, xyz)
     arrs = [np.ascontiguousarray(a, np.int32) for a in (shells_atom, shells_l, shells_nprim)]
     ex = np.ascontiguousarray(exps, np.float64)
     co = np.ascontiguousarray(coefs, np.float64)
     b = Basis(len(arrs[0]), *[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs],
               ex.ctypes.data_as(C.POINTER(C.c_double)), co.ctypes.data_as(C.POINTER(C.c_double)))
+    order = None if shell_order is None else np.ascontiguousarray(shell_order, np.int32)
     opt = Options(float(t_b), float(t_d), float(rho_min), PREC[prec] if isinstance(prec, str) else int(prec),
-                  XC[xc] if isinstance(xc, str) else int(xc), C.c_void_p(int(stream)))
+                  XC[xc] if isinstance(xc, str) else int(xc), C.c_void_p(int(stream)),
+                  C.c_void_p(None if order is None else order.ctypes.data))
     h = C.c_void_p()
     _check(LIB.kldi_screen(grid.h, C.byref(m), C.byref(b), C.byref(opt), C.byref(h)))
     return Plan(h.value, grid, (keepm, arrs, ex, co))
@@ -410,8 +412,8 @@ def version() -> str:
 
 # ----------------------------------------------------------------------------
 # convenience: build grid + plan for a ``synth.System``
-def plan_for_system(system, prec="bf16x3", xc=None, stream=0, rho_min=1e-14):
+def plan_for_system(system, prec="bf16x3", xc=None, stream=0, rho_min=1e-14, shell_order=None):
     g = make_grid(system.Z, system.xyz, system.grid.nrad, system.grid.ntheta, system.grid.block)
     b = system.basis
     return screen(g, system.Z, system.xyz, b.atom, b.l, b.nprim, b.exps, b.coefs, system.t_b, system.t_d,
-                  rho_min=rho_min, prec=prec, xc=xc or system.xc, stream=stream)
+                  rho_min=rho_min, prec=prec, xc=xc or system.xc, stream=stream, shell_order=shell_order)
