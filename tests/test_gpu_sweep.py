@@ -47,3 +47,42 @@ def test_threshold_sweep_water33():
     assert errs[0] > errs[2]                      # coarse thresholds err more
     assert abs(rows[3][1]) <= 1e-6                # the workload's threshold
     assert rows[4][2] >= rows[0][2]               # retained work grows as t falls
+
+
+def test_size_series_screened_vs_dense():
+    """The crossover study (Sec. IV, Fig. 5): water clusters of growing size,
+    BF16x6, the workload's thresholds (t_b = t_d = 1e-10) against the same
+    kernels with every block and block pair kept (t_b = t_d = 0, the dense
+    form).  Dense work grows with N_points x N_basis^2, screened work with
+    N_points x n_g^2 where n_g saturates, so the advantage of screening must
+    grow with the system size."""
+    import torch
+    from paper_2605_10363_gb300 import kldi
+    rows = []
+    for nw in (4, 8, 16, 33, 66, 100):
+        s = synth.make_system(2, nwaters=nw)
+        order = kldi.order_shells(synth.overlap_matrix(s.xyz, s.basis), synth.shell_sizes(s.basis))
+        D = torch.from_numpy(s.D).cuda()
+        V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda")
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ms, Es, npts = [], [], 0
+        for t in (1e-10, 0.0):
+            s.t_b = s.t_d = t
+            plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe", shell_order=order)
+            npts = plan.grid.nreal
+            kldi.exc(plan, "pbe", D, V, E)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(2):
+                kldi.exc(plan, "pbe", D, V, E)
+            torch.cuda.synchronize()
+            ms.append((time.perf_counter() - t0) / 2 * 1e3)
+            Es.append(E.item())
+            del plan
+        rows.append((nw, 3 * nw, s.nbf, npts, ms[0], ms[1], Es[0] - Es[1]))
+    print("\n   waters  atoms  N_basis   points     screened ms   dense ms   dense/screened   E_scr - E_dense")
+    for nw, na, nb, npts, m0, m1, dE in rows:
+        print(f"   {nw:6d} {na:6d} {nb:8d} {npts:10d} {m0:12.2f} {m1:10.2f} {m1 / m0:14.2f}     {dE:+.2e}")
+    ratios = [r[5] / r[4] for r in rows]
+    assert ratios[-1] > ratios[2] > 1.0             # screening pays more as the system grows
+    assert all(abs(r[6]) <= 1e-6 for r in rows)    # and changes E_xc by less than the tolerance
