@@ -1,6 +1,10 @@
 """Multi-process form of the quadrature: grid blocks are independent work
 units (paper Sec. III-E), so ranks evaluate disjoint block ranges and the
-single exchange step is a sum of the partial V_xc and E_xc.
+single exchange step is a sum of the partial V_xc and E_xc.  Two ways to hand
+out the blocks: a static partition balanced by the retained-list work
+(partition_blocks), or dynamic pulling of fixed-size chunks from a counter
+shared through the torch.distributed store (BlockQueue), the paper's runtime
+for heterogeneous grid-batch tasks.
 
 Host logic only (partitioning and the reduction through torch.distributed);
 every rank's evaluation runs in the library's kernels.  One GPU per process;
@@ -81,3 +85,51 @@ def exc_grad_sharded(plan, xc, D, G, E, rank: int, world: int, group=None):
     plan.set_block_range(g0, g1)
     kldi.exc_grad(plan, xc, D, G, E)
     return reduce_grad(G, E, group)
+
+
+class BlockQueue:
+    """Dynamic pull scheduler: chunk c covers grid blocks [c chunk, min((c + 1)
+    chunk, nblocks)); ranks take the next chunk with one atomic Store.add, so
+    every chunk goes to exactly one rank and faster ranks take more.  `key`
+    names the counter; use a fresh key per evaluation (the store keeps it)."""
+
+    def __init__(self, store, nblocks: int, chunk: int, key: str):
+        if chunk < 1:
+            raise ValueError("chunk must be >= 1")
+        self.store, self.nblocks, self.chunk, self.key = store, int(nblocks), int(chunk), key
+
+    def take(self):
+        c = int(self.store.add(self.key, 1)) - 1
+        g0 = c * self.chunk
+        if g0 >= self.nblocks:
+            return None
+        return g0, min(g0 + self.chunk, self.nblocks)
+
+
+def exc_pulled(plan, xc, D, V, E, queue: BlockQueue, group=None):
+    """kldi_exc over the chunks this rank pulls from `queue`, summed, then the
+    sum-reduce over ranks (device tensors V, E receive the full result).
+    Returns the block ranges this rank evaluated; the plan is left on all its
+    grid blocks.  Without an initialised process group of more than one rank
+    there is nothing to reduce."""
+    import torch
+    from . import kldi
+    Vp = torch.zeros_like(V)
+    Ep = torch.zeros_like(E)
+    V.zero_()
+    E.zero_()
+    done = []
+    while True:
+        r = queue.take()
+        if r is None:
+            break
+        plan.set_block_range(*r)
+        kldi.exc(plan, xc, D, Vp, Ep)
+        V += Vp
+        E += Ep
+        done.append(r)
+    plan.set_block_range(0, plan.stats["nblocks"])
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        reduce_exc(V, E, group)
+    return done

@@ -113,3 +113,62 @@ def test_two_ranks_reduce_the_gradient(tmp_path):
     for r in range(2):
         G = np.load(tmp_path / f"G{r}.npy")
         assert np.abs(G - Gref).max() <= 1e-13 * np.abs(Gref).max()
+
+
+def _rank_pull(rank, world, port, nblocks, chunk, out_dir):
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        s = synth.make_system(1)
+        g = og.build_grid(s.Z, s.xyz, s.grid)
+        sh = ob.build_shells(s.xyz, s.basis)
+        store = dist.distributed_c10d._get_default_store()
+        q = kdist.BlockQueue(store, nblocks, chunk, key="exc_blocks_0")
+        V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64)
+        E = torch.zeros(1, dtype=torch.float64)
+        done = []
+        while True:                      # the loop of kdist.exc_pulled, with the oracle as the worker
+            r = q.take()
+            if r is None:
+                break
+            part = oe.evaluate(s, g, sh, screened=True, blocks=range(*r))
+            V += torch.from_numpy(part.V)
+            E += part.E
+            done.append(r)
+        kdist.reduce_exc(V, E)
+        np.save(os.path.join(out_dir, f"V{rank}.npy"), V.numpy())
+        np.save(os.path.join(out_dir, f"E{rank}.npy"), E.numpy())
+        np.save(os.path.join(out_dir, f"done{rank}.npy"), np.array(done, dtype=np.int64).reshape(-1, 2))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_pull_queue_covers_every_block_once(tmp_path):
+    """Three ranks pull chunks of 16 grid blocks from the shared counter: the
+    chunks they took are disjoint, cover all blocks, and the reduced E_xc and V
+    equal the single-process oracle."""
+    import torch.multiprocessing as mp
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    ref = oe.evaluate(s, g, sh, screened=True)
+    world = 3
+    mp.start_processes(_rank_pull, args=(world, _free_port(), g.nblocks, 16, str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    taken = np.concatenate([np.load(tmp_path / f"done{r}.npy") for r in range(world)])
+    taken = taken[np.argsort(taken[:, 0])]
+    assert taken[0, 0] == 0 and taken[-1, 1] == g.nblocks
+    assert np.all(taken[1:, 0] == taken[:-1, 1])
+    for r in range(world):
+        assert np.load(tmp_path / f"E{r}.npy")[0] == pytest.approx(ref.E, rel=1e-13)
+        assert np.abs(np.load(tmp_path / f"V{r}.npy") - ref.V).max() <= 1e-13 * np.abs(ref.V).max()
+
+
+def test_block_queue_single_process():
+    import torch.distributed as dist
+    store = dist.HashStore()
+    q = kdist.BlockQueue(store, 10, 4, key="k")
+    assert [q.take() for _ in range(4)] == [(0, 4), (4, 8), (8, 10), None]
+    with pytest.raises(ValueError):
+        kdist.BlockQueue(store, 10, 0, key="k2")

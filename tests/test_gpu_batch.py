@@ -147,3 +147,30 @@ def test_block_ranges_sum_to_the_whole(frames):
     assert np.abs(Vt - V1).max() <= 1e-12 * np.abs(V1).max()
     with pytest.raises(kldi.KldiError):
         ref_plan.set_block_range(5, 2)
+
+
+def test_pulled_chunks_equal_one_evaluation():
+    """exc_pulled (the dynamic chunk scheduler's per-rank loop) on one process:
+    the summed chunks equal one whole-grid evaluation."""
+    import torch
+    import torch.distributed as dist
+    from paper_2605_10363_gb300 import dist as kdist
+    from paper_2605_10363_gb300 import kldi
+    s = synth.make_system(2, nwaters=4)
+    plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe")
+    D = torch.from_numpy(s.D).cuda()
+    V1 = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda")
+    E1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    kldi.exc(plan, "pbe", D, V1, E1)
+    V = torch.zeros_like(V1)
+    E = torch.zeros_like(E1)
+    q = kdist.BlockQueue(dist.HashStore(), plan.stats["nblocks"], 37, key="exc0")
+    done = kdist.exc_pulled(plan, "pbe", D, V, E, q)
+    torch.cuda.synchronize()
+    assert len(done) == -(-plan.stats["nblocks"] // 37)
+    assert E.item() == pytest.approx(E1.item(), rel=1e-13)
+    assert (V - V1).abs().max().item() <= 1e-12 * V1.abs().max().item()
+    # the plan is back on all its blocks
+    kldi.exc(plan, "pbe", D, V, E)
+    torch.cuda.synchronize()
+    assert E.item() == pytest.approx(E1.item(), rel=1e-14)
