@@ -312,7 +312,10 @@ def run_frames(args, dev, stream):
     from paper_2605_10363_gb300 import kldi
     t0 = time.perf_counter()
     systems = [synth.make_system(4, frame=k) for k in range(args.frames)]
-    plans = [kldi.plan_for_system(s, prec=args.prec, xc="pbe", stream=stream.cuda_stream) for s in systems]
+    orders = [kldi.order_shells(synth.overlap_matrix(s.xyz, s.basis), synth.shell_sizes(s.basis))
+              if args.basis_order == "overlap" else None for s in systems]
+    plans = [kldi.plan_for_system(s, prec=args.prec, xc="pbe", stream=stream.cuda_stream, shell_order=o)
+             for s, o in zip(systems, orders)]
     t_plan = time.perf_counter() - t0
     free, _ = torch.cuda.mem_get_info(dev)
     ws = kldi.Workspace(int(0.5 * free) // 73984 * 73984)
@@ -345,7 +348,8 @@ def run_frames(args, dev, stream):
         "config": {"workload": f"frames: the first {args.frames} frames of the trajectory recipe "
                                f"(waters {[int(x) for x in synth.frame_sizes(args.frames)]}), PBE-form, one CUDA-graph "
                                f"launch per step", "precision": args.prec, "points": int(npts),
-                   "tuned_v_seg": tuning["v_seg"], "plan_seconds": round(t_plan, 1)},
+                   "tuned_v_seg": tuning["v_seg"], "plan_seconds": round(t_plan, 1),
+                   "basis_order": "overlap-signature clustering" if args.basis_order == "overlap" else "atom order"},
         "E_xc": E.cpu().numpy().tolist()}), flush=True)
 
 

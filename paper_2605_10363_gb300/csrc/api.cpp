@@ -107,7 +107,8 @@ kldi_status check_xc(const kldi_plan* P, int xc) {
 // D in the caller's function order (device) -> the plan's order.
 kldi_status internal_D(kldi_plan* P, const double*& D) {
   if (!P->d_fnperm) return KLDI_OK;
-  KLDI_TRY(launch_permute(P, D, P->d_Dint, true, P->stream));
+  const double* src = D;
+  KLDI_TRY(staged(P, KLDI_STAGE_DPREP, 1, [&] { return launch_permute(P, src, P->d_Dint, true, P->stream); }));
   D = P->d_Dint;
   return KLDI_OK;
 }
@@ -199,7 +200,7 @@ extern "C" kldi_status kldi_vxc(kldi_plan* P, int xc, const double* rho, const d
   for (const Batch& b : P->batches) KLDI_TRY(potential_batch(P, b, xc, drho, dgrad, dV, false));
   KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 2, [&] { return launch_finish(P, dV, dE, P->stream); }));
   if (P->d_fnperm) {
-    KLDI_TRY(launch_permute(P, dV, dVc, false, P->stream));
+    KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_permute(P, dV, dVc, false, P->stream); }));
     dV = dVc;
   }
   if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, sizeof(double) * P->nbf * P->nbf, cudaMemcpyDeviceToHost, P->stream));
