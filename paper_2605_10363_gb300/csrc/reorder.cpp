@@ -44,6 +44,7 @@ extern "C" kldi_status kldi_order_shells(int nshell, const int* nfn, const doubl
   const int n = nshell;
   // shell signatures
   std::vector<double> T((size_t)n * n);
+#pragma omp parallel for schedule(dynamic, 8)
   for (int s = 0; s < n; ++s)
     for (int t = 0; t < n; ++t) {
       double acc = 0.0;
@@ -69,18 +70,33 @@ extern "C" kldi_status kldi_order_shells(int nshell, const int* nfn, const doubl
       return KLDI_EINVAL;
     }
   }
-  // leaf (shell) cosine distances, and the cluster distance matrix
-  std::vector<double> d0((size_t)n * n), D((size_t)n * n);
+  // leaf (shell) cosine distances, and the cluster distance matrix.  The
+  // dot products T_s . T_t run over u in order for every t at once (a row of
+  // the transposed signatures per u), so each sum has the sequential order.
+  std::vector<double> TT((size_t)n * n);
   for (int s = 0; s < n; ++s)
-    for (int t = 0; t < n; ++t) {
-      double acc = 0.0;
+    for (int t = 0; t < n; ++t) TT[(size_t)t * n + s] = T[(size_t)s * n + t];
+  std::vector<double> d0((size_t)n * n), D((size_t)n * n);
+#pragma omp parallel
+  {
+    std::vector<double> acc(n);
+#pragma omp for schedule(dynamic, 4)
+    for (int s = 0; s < n; ++s) {
+      std::fill(acc.begin(), acc.end(), 0.0);
       for (int u = 0; u < n; ++u) {
-        const double pr = T[(size_t)s * n + u] * T[(size_t)t * n + u];
-        acc = acc + pr;
+        const double a = T[(size_t)s * n + u];
+        const double* row = &TT[(size_t)u * n];
+        for (int t = 0; t < n; ++t) {
+          const double pr = a * row[t];
+          acc[t] = acc[t] + pr;
+        }
       }
-      const double den = norm[s] * norm[t];
-      d0[(size_t)s * n + t] = 1.0 - acc / den;
+      for (int t = 0; t < n; ++t) {
+        const double den = norm[s] * norm[t];
+        d0[(size_t)s * n + t] = 1.0 - acc[t] / den;
+      }
     }
+  }
   D = d0;
   std::vector<char> active(n, 1);
   std::vector<double> size(n, 1.0);
