@@ -182,12 +182,11 @@ kldi_status launch_grad64(const kldi_plan* P, const Batch& b, const double* D, d
   const int64_t n = b.g1 - b.g0;
   if (n == 0) return KLDI_OK;
   constexpr int kDyn = 2 * kBasisBlk * kBlockPts * (int)sizeof(double);
-  static bool attr = false;
-  if (!attr) {
+  KLDI_TRY(once_per_device([&]() -> kldi_status {
     KLDI_TRY_CUDA(cudaFuncSetAttribute(k_grad64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn));
     KLDI_TRY_CUDA(cudaFuncSetAttribute(k_grad64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn));
-    attr = true;
-  }
+    return KLDI_OK;
+  }));
   if (P->gga)
     k_grad64<true><<<(unsigned)n, kBlockPts, kDyn, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.t0,
                                                      P->d_phi64, P->d_x64, P->d_xcoef, D, P->d_dmax, (int)P->nbf,

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -33,6 +35,22 @@ void set_error(const char* fmt, ...);
     kldi_status s_ = (expr);      \
     if (s_ != KLDI_OK) return s_; \
   } while (0)
+
+// Runs f() once per device for the call site (each lambda type has its own
+// state): kernel attributes such as the shared-memory opt-in belong to a
+// device; the lock keeps plans built on several host threads from racing.
+template <typename F>
+kldi_status once_per_device(F&& f) {
+  static std::mutex mu;
+  static std::set<int> ready;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return KLDI_ECUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (ready.count(dev)) return KLDI_OK;
+  const kldi_status st = f();
+  if (st == KLDI_OK) ready.insert(dev);
+  return st;
+}
 
 // One shell as the kernels see it.  coef[k] already carries the primitive norm
 // (2a/pi)^(3/4) (4a)^(l/2) and the contraction rescale; the per-component factor

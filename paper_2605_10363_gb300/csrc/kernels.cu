@@ -344,11 +344,10 @@ __global__ void __launch_bounds__(256) k_v64(ListView L, const VWork64* work, co
 kldi_status launch_v64(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
   if (b.n_v64_work == 0) return KLDI_OK;
   const size_t smem = 4 * kBlockPts * (kBasisBlk + 1) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
+  KLDI_TRY(once_per_device([&]() -> kldi_status {
     KLDI_TRY_CUDA(cudaFuncSetAttribute(k_v64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+    return KLDI_OK;
+  }));
   k_v64<<<(unsigned)b.n_v64_work, 256, smem, s>>>(P->list_view(), b.d_v64_work, b.d_v64_g, P->d_phi64, P->d_x64,
                                                    P->d_xmax, b.t0, (int)P->nbf, P->opt.t_b, P->opt.t_d, V);
   KLDI_TRY_CUDA(cudaGetLastError());

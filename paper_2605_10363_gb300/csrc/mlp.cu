@@ -438,13 +438,11 @@ kldi_status ensure_parts(kldi_mlp* M, int64_t nctas) {
 }
 
 kldi_status set_train_smem() {
-  static bool done = false;
-  if (!done) {
+  return once_per_device([]() -> kldi_status {
     KLDI_TRY_CUDA(cudaFuncSetAttribute(k_mlp_partials, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kTrainSmemFloats * (int)sizeof(float)));
-    done = true;
-  }
-  return KLDI_OK;
+    return KLDI_OK;
+  });
 }
 
 kldi_status launch_partials(kldi_mlp* M, const float4* data, const uint8_t* valid, int64_t n, int64_t A, int64_t C,

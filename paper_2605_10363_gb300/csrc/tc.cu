@@ -41,6 +41,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "basis.cuh"
 #include "internal.h"
@@ -1300,20 +1302,25 @@ static kldi_status prepare_rho_kernel() {
 }
 
 // Kernel attributes set once per process (outside any stream capture).
+// Kernel attributes belong to a device: set once per device, under a lock so
+// that plans created on several host threads do not race.
 kldi_status prepare_tc_kernels() {
-  static kldi_status done = KLDI_EINVAL;
-  static bool tried = false;
-  if (tried) {
-    if (done != KLDI_OK) set_error("tensor-core kernels could not be prepared");
-    return done;
+  static std::mutex mu;
+  static std::map<int, kldi_status> done;
+  int dev = 0;
+  KLDI_TRY_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(dev);
+  if (it != done.end()) {
+    if (it->second != KLDI_OK) set_error("tensor-core kernels could not be prepared on device %d", dev);
+    return it->second;
   }
-  tried = true;
-  done = KLDI_OK;
-  if ((done = prepare_rho_kernel<2>()) != KLDI_OK) return done;
-  if ((done = prepare_rho_kernel<3>()) != KLDI_OK) return done;
-  if ((done = prepare_v_kernel<2>()) != KLDI_OK) return done;
-  done = prepare_v_kernel<3>();
-  return done;
+  kldi_status st = prepare_rho_kernel<2>();
+  if (st == KLDI_OK) st = prepare_rho_kernel<3>();
+  if (st == KLDI_OK) st = prepare_v_kernel<2>();
+  if (st == KLDI_OK) st = prepare_v_kernel<3>();
+  done[dev] = st;
+  return st;
 }
 
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
