@@ -255,9 +255,10 @@ def order_mode(kldi, s, plan, order, stream, dev, args, E_main):
 
 
 def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analytic):
-    """Train the surrogate on the GPU on the grid points of the two-water and
-    33-water systems (their densities from the library), then time the same
-    evaluation with the network fused between the products."""
+    """Train the surrogate on the GPU on ~50M grid points of the two-water and
+    33-water systems (their densities from the library; the 33-water grid under
+    44 density matrices of its recipe), then time the same evaluation with the
+    network fused between the products."""
     import torch
 
     import synth
@@ -269,13 +270,23 @@ def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analyt
         kldi.density(p, system.D, rho, grad)
         return rho, np.einsum("ic,ic->i", grad, grad)
 
+    # ~50M training points: the two-water system and the 33-water system under
+    # its own density and 43 further densities of the same recipe
     r1, s1 = points(synth.make_system(1))
-    r2, s2 = points(s, plan)
-    rho = np.concatenate([r1, r2])
-    sig = np.concatenate([s1, s2])
+    rs, ss = [r1], [s1]
+    Dv = [s.D] + synth.density_variants(s, 43)
+    for Dk in Dv:
+        rho_k = np.zeros(plan.npoints)
+        grad_k = np.zeros((plan.npoints, 3))
+        kldi.density(plan, Dk, rho_k, grad_k)
+        rs.append(rho_k)
+        ss.append(np.einsum("ic,ic->i", grad_k, grad_k))
+    rho = np.concatenate(rs)
+    sig = np.concatenate(ss)
+    del rs, ss
     box = synth.mlp_box(rho, sig)
     net = kldi.Mlp(synth.mlp_init(42), box)
-    epochs = 200
+    epochs = 6
     t0 = time.perf_counter()
     hist = net.train(rho, sig, epochs=epochs, batch=8192, lr0=3e-3, lr1=1e-5)
     t_train = time.perf_counter() - t0

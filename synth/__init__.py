@@ -377,6 +377,16 @@ def density_localised(supports: list, nbf: int, S: np.ndarray, seed: int) -> np.
     return 0.5 * (D + D.T)
 
 
+def density_variants(system: System, n: int, seed0: int = 100) -> list:
+    """n further density matrices of a water-cluster system from its own recipe
+    (one random orbital per occupied pair on each molecule, Loewdin-
+    orthonormalised), seeds seed0 .. seed0 + n - 1: the densities an SCF or a
+    trajectory passes through on the same geometry and grid."""
+    S = overlap_matrix(system.xyz, system.basis)
+    sups = _water_supports(system.Z, system.basis)
+    return [density_localised(sups, system.nbf, S, seed0 + k) for k in range(n)]
+
+
 def _water_supports(Z: np.ndarray, basis: Basis):
     fa = basis_function_atoms(Z, basis)
     sups = []
