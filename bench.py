@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-side-modes", action="store_true", help="skip the FP64 / BF16x3 side measurements")
     ap.add_argument("--nwaters", type=int, default=0,
                     help="profiling case: a smaller water cluster of the same recipe (not a bench line)")
-    ap.add_argument("--workload", default="water33", choices=["water33", "frames"],
+    ap.add_argument("--workload", default="water33", choices=["water33", "frames", "cnoh1000"],
                     help="frames: the first --frames frames of the 20-130-water trajectory recipe through one "
                          "CUDA-graph batch (a side measurement, not the headline line)")
     ap.add_argument("--frames", type=int, default=8)
@@ -314,6 +314,66 @@ def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analyt
 
 
 # ---------------------------------------------------------------------------- batched frames
+def run_large(args, dev, stream):
+    """The 1000-atom C/N/O/H cluster (9000 functions, 11.55M points): one
+    evaluation per precision mode (BF16x6, BF16x3, the FP64 block form; the
+    tensor modes after one untimed evaluation), with the plan statistics.  The overlap matrix
+    (for the shell order) is the Kohn-Sham setup's input; building it in numpy
+    and the plans are preprocessing, reported separately."""
+    import torch
+
+    import synth
+    from paper_2605_10363_gb300 import kldi
+    t0 = time.perf_counter()
+    s = synth.make_system(3, keep_overlap=True)
+    t_sys = time.perf_counter() - t0
+    order = None
+    t_order = 0.0
+    if args.basis_order == "overlap":
+        t1 = time.perf_counter()
+        order = kldi.order_shells(s.meta["S"], synth.shell_sizes(s.basis))
+        t_order = time.perf_counter() - t1
+    s.meta.pop("S")
+    D = torch.from_numpy(s.D).to(dev)
+    V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    modes = {}
+    npts = 0
+    for prec in ("bf16x6", "bf16x3", "fp64"):
+        t1 = time.perf_counter()
+        plan = kldi.plan_for_system(s, prec=prec, xc="pbe", stream=stream.cuda_stream, shell_order=order)
+        t_plan = time.perf_counter() - t1
+        npts = plan.grid.nreal
+        if prec != "fp64":                 # the FP64 form takes tens of seconds: one evaluation
+            kldi.exc(plan, "pbe", D, V, E)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kldi.exc(plan, "pbe", D, V, E)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        st = plan.stats
+        modes[prec] = {"ms_per_step": ms, "value": npts / (ms * 1e-3), "E_xc": float(E.item()),
+                       "plan_seconds": round(t_plan, 1),
+                       "retained_fraction": st["pair_slots"] / (st["nblocks"] * st["nbasis_blocks"] ** 2)}
+        del plan
+    main = modes["bf16x6"]
+    print(json.dumps({
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "cnoh1000_pbe: 1000 atoms (240 C, 80 N, 80 O, 600 H, 0.1 atoms/A^3), 9000 "
+                               "Cartesian s/p/d functions, 11.55M points, PBE-form, t_b = t_d = 1e-10",
+                   "precision": "bf16x6", "system_seconds": round(t_sys, 1), "order_seconds": round(t_order, 1),
+                   "basis_order": "overlap-signature clustering" if order is not None else "atom order"},
+        "speedup_vs_fp64": modes["fp64"]["ms_per_step"] / main["ms_per_step"],
+        "dE_bf16x6_vs_fp64": modes["bf16x6"]["E_xc"] - modes["fp64"]["E_xc"],
+        "dE_bf16x3_vs_fp64": modes["bf16x3"]["E_xc"] - modes["fp64"]["E_xc"],
+        "modes": modes}), flush=True)
+
+
 def run_frames(args, dev, stream):
     """Frames of uneven size (20-130 waters, own D each) through one CUDA-graph
     batch with a shared tile workspace and the tuned V decomposition."""
@@ -370,6 +430,12 @@ def main():
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "cnoh1000":
+        import torch
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        run_large(args, dev, torch.cuda.current_stream(dev))
         return
     if args.workload == "frames":
         import torch

@@ -420,17 +420,25 @@ GRID_SMALL = GridSpec(nrad=30, ntheta=(8,))
 GRID_PRUNED = GridSpec(nrad=75, ntheta=(5, 8, 12))
 
 
-def make_system(config: int, frame: int = 0, nwaters: int | None = None) -> System:
+def make_system(config: int, frame: int = 0, nwaters: int | None = None, keep_overlap: bool = False) -> System:
     """The seeded synthetic system for one of the five workloads.
 
     ``nwaters`` overrides the cluster size (water workloads only) for small
-    test variants of the same recipe."""
+    test variants of the same recipe.  ``keep_overlap`` keeps the overlap
+    matrix built for D in ``meta["S"]``."""
+    sysm = _make_system(config, frame, nwaters)
+    if not keep_overlap:
+        sysm.meta.pop("S", None)
+    return sysm
+
+
+def _make_system(config: int, frame: int, nwaters: int | None) -> System:
     if config == 1:
         Z, xyz = two_waters(1)
         basis = make_basis(Z, RECIPE_SP, 2)
         S = overlap_matrix(xyz, basis)
         D = density_random(basis.nbf, 10, S, 3)
-        return System("two_waters_lda", Z, xyz, basis, D, GRID_SMALL, 1e-12, 1e-12, "lda_x")
+        return System("two_waters_lda", Z, xyz, basis, D, GRID_SMALL, 1e-12, 1e-12, "lda_x", meta={"S": S})
     if config in (2, 5):
         nw = nwaters if nwaters is not None else (33 if config == 2 else 167)
         Z, xyz = water_cluster(nw, 11 if config == 2 else 41)
@@ -438,13 +446,13 @@ def make_system(config: int, frame: int = 0, nwaters: int | None = None) -> Syst
         S = overlap_matrix(xyz, basis)
         D = density_localised(_water_supports(Z, basis), basis.nbf, S, 12 if config == 2 else 43)
         name = f"water{nw}_pbe"
-        return System(name, Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe")
+        return System(name, Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe", meta={"S": S})
     if config == 3:
         Z, xyz = organic_cluster(21)
         basis = make_basis(Z, RECIPE_SVP, 2)
         S = overlap_matrix(xyz, basis)
         D = density_localised(_atom_supports(Z, xyz, basis), basis.nbf, S, 22)
-        return System("cnoh1000_pbe", Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe")
+        return System("cnoh1000_pbe", Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe", meta={"S": S})
     if config == 4:
         sizes = np.random.default_rng(31).integers(20, 131, size=256)
         nw = int(sizes[frame]) if nwaters is None else nwaters
@@ -455,7 +463,7 @@ def make_system(config: int, frame: int = 0, nwaters: int | None = None) -> Syst
         S = overlap_matrix(xyz, basis)
         D = density_localised(_water_supports(Z, basis), basis.nbf, S, 33 + frame)
         return System(f"frame{frame}_water{nw}_pbe", Z, xyz, basis, D, GRID_PRUNED, 1e-10, 1e-10, "pbe",
-                      meta={"frame": frame})
+                      meta={"frame": frame, "S": S})
     raise ValueError(f"unknown workload {config}")
 
 
