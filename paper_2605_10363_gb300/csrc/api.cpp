@@ -146,197 +146,211 @@ kldi_status exc_device(kldi_plan* P, int xc, const double* D, double* V, double*
 }  // namespace
 
 extern "C" kldi_status kldi_density(kldi_plan* P, const double* D, double* rho, double* grad) {
-  if (!P || !D || !rho) { set_error("kldi_density: null argument"); return KLDI_EINVAL; }
-  if (P->gga && !grad) { set_error("kldi_density: a GGA plan needs grad"); return KLDI_EINVAL; }
-  const size_t nbf2 = (size_t)P->nbf * P->nbf;
-  const double* dD = D;
-  if (!is_device_ptr(D)) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
-    dD = P->d_D;
-  }
-  const bool host_out = !is_device_ptr(rho);
-  double* drho = host_out ? P->d_rho : rho;
-  double* dgrad = P->gga ? (host_out ? P->d_grad : grad) : P->d_grad;
-  KLDI_TRY(ensure_tile_buffers(P, P->prec));
-  KLDI_TRY(internal_D(P, dD));
-  KLDI_TRY(prepare_D(P, dD));
-  for (const Batch& b : P->batches) KLDI_TRY(density_batch(P, b, dD, drho, dgrad));
-  if (host_out) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(rho, drho, P->npoints * 8, cudaMemcpyDeviceToHost, P->stream));
-    if (P->gga) KLDI_TRY_CUDA(cudaMemcpyAsync(grad, dgrad, P->npoints * 24, cudaMemcpyDeviceToHost, P->stream));
-    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-    KLDI_TRY(check_device_error(P));
-  } else if (P->gga && !is_device_ptr(grad)) {
-    set_error("kldi_density: rho and grad must both be device or both host memory");
-    return KLDI_EINVAL;
-  }
-  KLDI_TRY_CUDA(cudaGetLastError());
-  return KLDI_OK;
+  return kldi::guarded("kldi_density", [&]() -> kldi_status {
+    if (!P || !D || !rho) { set_error("kldi_density: null argument"); return KLDI_EINVAL; }
+    if (P->gga && !grad) { set_error("kldi_density: a GGA plan needs grad"); return KLDI_EINVAL; }
+    const size_t nbf2 = (size_t)P->nbf * P->nbf;
+    const double* dD = D;
+    if (!is_device_ptr(D)) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
+      dD = P->d_D;
+    }
+    const bool host_out = !is_device_ptr(rho);
+    double* drho = host_out ? P->d_rho : rho;
+    double* dgrad = P->gga ? (host_out ? P->d_grad : grad) : P->d_grad;
+    KLDI_TRY(ensure_tile_buffers(P, P->prec));
+    KLDI_TRY(internal_D(P, dD));
+    KLDI_TRY(prepare_D(P, dD));
+    for (const Batch& b : P->batches) KLDI_TRY(density_batch(P, b, dD, drho, dgrad));
+    if (host_out) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(rho, drho, P->npoints * 8, cudaMemcpyDeviceToHost, P->stream));
+      if (P->gga) KLDI_TRY_CUDA(cudaMemcpyAsync(grad, dgrad, P->npoints * 24, cudaMemcpyDeviceToHost, P->stream));
+      KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+      KLDI_TRY(check_device_error(P));
+    } else if (P->gga && !is_device_ptr(grad)) {
+      set_error("kldi_density: rho and grad must both be device or both host memory");
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY_CUDA(cudaGetLastError());
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_vxc(kldi_plan* P, int xc, const double* rho, const double* grad, double* V,
                                 double* Exc) {
-  if (!P || !rho || !V || !Exc) { set_error("kldi_vxc: null argument"); return KLDI_EINVAL; }
-  KLDI_TRY(check_xc(P, xc));
-  if (xc != KLDI_XC_LDA_X && !grad) { set_error("kldi_vxc: the GGA needs grad"); return KLDI_EINVAL; }
-  KLDI_TRY(ensure_tile_buffers(P, P->prec));
-  const double* drho = rho;
-  const double* dgrad = grad;
-  if (!is_device_ptr(rho)) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_rho, rho, P->npoints * 8, cudaMemcpyHostToDevice, P->stream));
-    drho = P->d_rho;
-  }
-  if (grad && !is_device_ptr(grad)) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_grad, grad, P->npoints * 24, cudaMemcpyHostToDevice, P->stream));
-    dgrad = P->d_grad;
-  }
-  if (!dgrad) dgrad = P->d_grad;
-  const bool hostV = !is_device_ptr(V), hostE = !is_device_ptr(Exc);
-  double* dV = hostV ? P->d_V : V;
-  double* dE = hostE ? P->d_exc : Exc;
-  double* dVc = dV;
-  if (P->d_fnperm) dV = P->d_Vint;   // reordered plan: V to the caller's order at the end
-  KLDI_TRY_CUDA(cudaMemsetAsync(dV, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
-  for (const Batch& b : P->batches) KLDI_TRY(potential_batch(P, b, xc, drho, dgrad, dV, false));
-  KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 2, [&] { return launch_finish(P, dV, dE, P->stream); }));
-  if (P->d_fnperm) {
-    KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_permute(P, dV, dVc, false, P->stream); }));
-    dV = dVc;
-  }
-  if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, sizeof(double) * P->nbf * P->nbf, cudaMemcpyDeviceToHost, P->stream));
-  if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
-  if (hostV || hostE) {
-    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-    KLDI_TRY(check_device_error(P));
-  }
-  KLDI_TRY_CUDA(cudaGetLastError());
-  return KLDI_OK;
+  return kldi::guarded("kldi_vxc", [&]() -> kldi_status {
+    if (!P || !rho || !V || !Exc) { set_error("kldi_vxc: null argument"); return KLDI_EINVAL; }
+    KLDI_TRY(check_xc(P, xc));
+    if (xc != KLDI_XC_LDA_X && !grad) { set_error("kldi_vxc: the GGA needs grad"); return KLDI_EINVAL; }
+    KLDI_TRY(ensure_tile_buffers(P, P->prec));
+    const double* drho = rho;
+    const double* dgrad = grad;
+    if (!is_device_ptr(rho)) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_rho, rho, P->npoints * 8, cudaMemcpyHostToDevice, P->stream));
+      drho = P->d_rho;
+    }
+    if (grad && !is_device_ptr(grad)) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_grad, grad, P->npoints * 24, cudaMemcpyHostToDevice, P->stream));
+      dgrad = P->d_grad;
+    }
+    if (!dgrad) dgrad = P->d_grad;
+    const bool hostV = !is_device_ptr(V), hostE = !is_device_ptr(Exc);
+    double* dV = hostV ? P->d_V : V;
+    double* dE = hostE ? P->d_exc : Exc;
+    double* dVc = dV;
+    if (P->d_fnperm) dV = P->d_Vint;   // reordered plan: V to the caller's order at the end
+    KLDI_TRY_CUDA(cudaMemsetAsync(dV, 0, sizeof(double) * P->nbf * P->nbf, P->stream));
+    for (const Batch& b : P->batches) KLDI_TRY(potential_batch(P, b, xc, drho, dgrad, dV, false));
+    KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 2, [&] { return launch_finish(P, dV, dE, P->stream); }));
+    if (P->d_fnperm) {
+      KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_permute(P, dV, dVc, false, P->stream); }));
+      dV = dVc;
+    }
+    if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, sizeof(double) * P->nbf * P->nbf, cudaMemcpyDeviceToHost, P->stream));
+    if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
+    if (hostV || hostE) {
+      KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+      KLDI_TRY(check_device_error(P));
+    }
+    KLDI_TRY_CUDA(cudaGetLastError());
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_exc(kldi_plan* P, int xc, const double* D, double* V, double* Exc) {
-  if (!P || !D || !V || !Exc) { set_error("kldi_exc: null argument"); return KLDI_EINVAL; }
-  KLDI_TRY(check_xc(P, xc));
-  const size_t nbf2 = (size_t)P->nbf * P->nbf;
-  const double* dD = D;
-  if (!is_device_ptr(D)) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
-    dD = P->d_D;
-  }
-  const bool hostV = !is_device_ptr(V), hostE = !is_device_ptr(Exc);
-  double* dV = hostV ? P->d_V : V;
-  double* dE = hostE ? P->d_exc : Exc;
-  KLDI_TRY(exc_device(P, xc, dD, dV, dE));
-  if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, nbf2 * 8, cudaMemcpyDeviceToHost, P->stream));
-  if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
-  if (hostV || hostE) {
-    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-    KLDI_TRY(check_device_error(P));
-  }
-  KLDI_TRY_CUDA(cudaGetLastError());
-  return KLDI_OK;
+  return kldi::guarded("kldi_exc", [&]() -> kldi_status {
+    if (!P || !D || !V || !Exc) { set_error("kldi_exc: null argument"); return KLDI_EINVAL; }
+    KLDI_TRY(check_xc(P, xc));
+    const size_t nbf2 = (size_t)P->nbf * P->nbf;
+    const double* dD = D;
+    if (!is_device_ptr(D)) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
+      dD = P->d_D;
+    }
+    const bool hostV = !is_device_ptr(V), hostE = !is_device_ptr(Exc);
+    double* dV = hostV ? P->d_V : V;
+    double* dE = hostE ? P->d_exc : Exc;
+    KLDI_TRY(exc_device(P, xc, dD, dV, dE));
+    if (hostV) KLDI_TRY_CUDA(cudaMemcpyAsync(V, dV, nbf2 * 8, cudaMemcpyDeviceToHost, P->stream));
+    if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
+    if (hostV || hostE) {
+      KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+      KLDI_TRY(check_device_error(P));
+    }
+    KLDI_TRY_CUDA(cudaGetLastError());
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_exc_grad(kldi_plan* P, int xc, const double* D, double* G, double* Exc) {
-  if (!P || !D || !G || !Exc) { set_error("kldi_exc_grad: null argument"); return KLDI_EINVAL; }
-  KLDI_TRY(check_xc(P, xc));
-  if (P->prec != KLDI_FP64 && !P->rec_fit_all) {
-    set_error("kldi_exc_grad: a basis block has more than 40 shells or 80 primitives (tensor-core gradient)");
-    return KLDI_EUNSUPPORTED;
-  }
-  const size_t nbf2 = (size_t)P->nbf * P->nbf;
-  const double* dD = D;
-  if (!is_device_ptr(D)) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
-    dD = P->d_D;
-  }
-  const bool host_out = !is_device_ptr(G);
-  if (!P->d_G) {
-    KLDI_TRY_CUDA(cudaMalloc(&P->d_G, sizeof(double) * 3 * std::max(P->natm, 1)));
-  }
-  double* dG = host_out ? P->d_G : G;
-  double* dE = host_out ? P->d_exc : Exc;
-  KLDI_TRY(ensure_tile_buffers(P, P->prec));
-  if (P->prec != KLDI_FP64 && !P->d_zscale) {
-    KLDI_TRY_CUDA(cudaMalloc(&P->d_zscale, sizeof(float) * std::max<int64_t>(P->npoints, 1)));
-  }
-  KLDI_TRY(internal_D(P, dD));
-  KLDI_TRY(prepare_D(P, dD));
-  KLDI_TRY_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * 3 * P->natm, P->stream));
-  for (const Batch& b : P->batches) {
-    KLDI_TRY(density_batch(P, b, dD, P->d_rho, P->d_grad));
-    KLDI_TRY(staged(P, KLDI_STAGE_XC, 1, [&] { return launch_xc(P, b, xc, P->d_rho, P->d_grad, P->stream); }));
-    if (P->prec == KLDI_FP64) {
-      KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x64(P, b, P->stream); }));
-      KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_grad64(P, b, dD, dG, P->stream); }));
-    } else {
-      // Z tiles (X stage), then the Q and R terms through the density-product kernel (V stage)
-      const bool gga_xc = xc != KLDI_XC_LDA_X;
-      KLDI_TRY(staged(P, KLDI_STAGE_V, gga_xc ? 3 : 2,
-                      [&] { return launch_grad_tc(P, b, gga_xc, dG, P->stream); }));
+  return kldi::guarded("kldi_exc_grad", [&]() -> kldi_status {
+    if (!P || !D || !G || !Exc) { set_error("kldi_exc_grad: null argument"); return KLDI_EINVAL; }
+    KLDI_TRY(check_xc(P, xc));
+    if (P->prec != KLDI_FP64 && !P->rec_fit_all) {
+      set_error("kldi_exc_grad: a basis block has more than 40 shells or 80 primitives (tensor-core gradient)");
+      return KLDI_EUNSUPPORTED;
     }
-  }
-  KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_finish(P, nullptr, dE, P->stream); }));
-  if (host_out) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(G, dG, sizeof(double) * 3 * P->natm, cudaMemcpyDeviceToHost, P->stream));
-    KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
-    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-    KLDI_TRY(check_device_error(P));
-  }
-  KLDI_TRY_CUDA(cudaGetLastError());
-  return KLDI_OK;
+    const size_t nbf2 = (size_t)P->nbf * P->nbf;
+    const double* dD = D;
+    if (!is_device_ptr(D)) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
+      dD = P->d_D;
+    }
+    const bool host_out = !is_device_ptr(G);
+    if (!P->d_G) {
+      KLDI_TRY_CUDA(cudaMalloc(&P->d_G, sizeof(double) * 3 * std::max(P->natm, 1)));
+    }
+    double* dG = host_out ? P->d_G : G;
+    double* dE = host_out ? P->d_exc : Exc;
+    KLDI_TRY(ensure_tile_buffers(P, P->prec));
+    if (P->prec != KLDI_FP64 && !P->d_zscale) {
+      KLDI_TRY_CUDA(cudaMalloc(&P->d_zscale, sizeof(float) * std::max<int64_t>(P->npoints, 1)));
+    }
+    KLDI_TRY(internal_D(P, dD));
+    KLDI_TRY(prepare_D(P, dD));
+    KLDI_TRY_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * 3 * P->natm, P->stream));
+    for (const Batch& b : P->batches) {
+      KLDI_TRY(density_batch(P, b, dD, P->d_rho, P->d_grad));
+      KLDI_TRY(staged(P, KLDI_STAGE_XC, 1, [&] { return launch_xc(P, b, xc, P->d_rho, P->d_grad, P->stream); }));
+      if (P->prec == KLDI_FP64) {
+        KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x64(P, b, P->stream); }));
+        KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_grad64(P, b, dD, dG, P->stream); }));
+      } else {
+        // Z tiles (X stage), then the Q and R terms through the density-product kernel (V stage)
+        const bool gga_xc = xc != KLDI_XC_LDA_X;
+        KLDI_TRY(staged(P, KLDI_STAGE_V, gga_xc ? 3 : 2,
+                        [&] { return launch_grad_tc(P, b, gga_xc, dG, P->stream); }));
+      }
+    }
+    KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_finish(P, nullptr, dE, P->stream); }));
+    if (host_out) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(G, dG, sizeof(double) * 3 * P->natm, cudaMemcpyDeviceToHost, P->stream));
+      KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
+      KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+      KLDI_TRY(check_device_error(P));
+    }
+    KLDI_TRY_CUDA(cudaGetLastError());
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
                                         double* const* V, double* Exc) {
-  if (!plans || nframes <= 0 || !D || !V || !Exc) { set_error("kldi_exc_batched: bad argument"); return KLDI_EINVAL; }
-  for (int k = 0; k < nframes; ++k) {
-    if (!plans[k] || !D[k] || !V[k]) { set_error("kldi_exc_batched: null entry %d", k); return KLDI_EINVAL; }
-    if (!is_device_ptr(D[k]) || !is_device_ptr(V[k])) {
-      set_error("kldi_exc_batched: device pointers only (entry %d)", k);
-      return KLDI_EINVAL;
+  return kldi::guarded("kldi_exc_batched", [&]() -> kldi_status {
+    if (!plans || nframes <= 0 || !D || !V || !Exc) { set_error("kldi_exc_batched: bad argument"); return KLDI_EINVAL; }
+    for (int k = 0; k < nframes; ++k) {
+      if (!plans[k] || !D[k] || !V[k]) { set_error("kldi_exc_batched: null entry %d", k); return KLDI_EINVAL; }
+      if (!is_device_ptr(D[k]) || !is_device_ptr(V[k])) {
+        set_error("kldi_exc_batched: device pointers only (entry %d)", k);
+        return KLDI_EINVAL;
+      }
+      KLDI_TRY(check_xc(plans[k], xc));
     }
-    KLDI_TRY(check_xc(plans[k], xc));
-  }
-  if (!is_device_ptr(Exc)) { set_error("kldi_exc_batched: Exc must be device memory"); return KLDI_EINVAL; }
-  // one graph of all frames, launched once on the first plan's stream
-  kldi_batch* B = nullptr;
-  KLDI_TRY(kldi_batch_create(plans, nframes, xc, D, V, Exc, plans[0]->stream, &B));
-  const kldi_status st = kldi_batch_launch(B);
-  const kldi_status st2 = kldi_batch_sync(B);
-  kldi_batch_free(B);
-  KLDI_TRY(st);
-  return st2;
+    if (!is_device_ptr(Exc)) { set_error("kldi_exc_batched: Exc must be device memory"); return KLDI_EINVAL; }
+    // one graph of all frames, launched once on the first plan's stream
+    kldi_batch* B = nullptr;
+    KLDI_TRY(kldi_batch_create(plans, nframes, xc, D, V, Exc, plans[0]->stream, &B));
+    const kldi_status st = kldi_batch_launch(B);
+    const kldi_status st2 = kldi_batch_sync(B);
+    kldi_batch_free(B);
+    KLDI_TRY(st);
+    return st2;
+  });
 }
 
 extern "C" kldi_status kldi_plan_profile(kldi_plan* P, int enable) {
-  if (!P) { set_error("kldi_plan_profile: null plan"); return KLDI_EINVAL; }
-  if (enable && P->prof_ev.empty()) {
-    P->prof_ev.resize(8192);
-    for (auto& e : P->prof_ev) KLDI_TRY_CUDA(cudaEventCreate(&e));
-  }
-  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-  P->prof_stage.clear();
-  P->prof_launches.clear();
-  P->prof = enable != 0;
-  return KLDI_OK;
+  return kldi::guarded("kldi_plan_profile", [&]() -> kldi_status {
+    if (!P) { set_error("kldi_plan_profile: null plan"); return KLDI_EINVAL; }
+    if (enable && P->prof_ev.empty()) {
+      P->prof_ev.resize(8192);
+      for (auto& e : P->prof_ev) KLDI_TRY_CUDA(cudaEventCreate(&e));
+    }
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    P->prof_stage.clear();
+    P->prof_launches.clear();
+    P->prof = enable != 0;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_plan_stage_times(kldi_plan* P, double* ms, int64_t* launches) {
-  if (!P) { set_error("kldi_plan_stage_times: null plan"); return KLDI_EINVAL; }
-  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-  double t[KLDI_NSTAGES] = {0};
-  int64_t n[KLDI_NSTAGES] = {0};
-  for (size_t k = 0; k < P->prof_stage.size(); ++k) {
-    float e = 0.f;
-    KLDI_TRY_CUDA(cudaEventElapsedTime(&e, P->prof_ev[2 * k], P->prof_ev[2 * k + 1]));
-    t[P->prof_stage[k]] += e;
-    n[P->prof_stage[k]] += P->prof_launches[k];
-  }
-  for (int s = 0; s < KLDI_NSTAGES; ++s) {
-    if (ms) ms[s] = t[s];
-    if (launches) launches[s] = n[s];
-  }
-  return KLDI_OK;
+  return kldi::guarded("kldi_plan_stage_times", [&]() -> kldi_status {
+    if (!P) { set_error("kldi_plan_stage_times: null plan"); return KLDI_EINVAL; }
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    double t[KLDI_NSTAGES] = {0};
+    int64_t n[KLDI_NSTAGES] = {0};
+    for (size_t k = 0; k < P->prof_stage.size(); ++k) {
+      float e = 0.f;
+      KLDI_TRY_CUDA(cudaEventElapsedTime(&e, P->prof_ev[2 * k], P->prof_ev[2 * k + 1]));
+      t[P->prof_stage[k]] += e;
+      n[P->prof_stage[k]] += P->prof_launches[k];
+    }
+    for (int s = 0; s < KLDI_NSTAGES; ++s) {
+      if (ms) ms[s] = t[s];
+      if (launches) launches[s] = n[s];
+    }
+    return KLDI_OK;
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -350,133 +364,141 @@ struct kldi_batch {
 
 extern "C" kldi_status kldi_plan_autotune(kldi_plan* P, int xc, const double* D, int reps, kldi_tuning* best,
                                           double* best_ms) {
-  if (!P || !D || reps < 1 || !is_device_ptr(D)) {
-    set_error("kldi_plan_autotune: bad argument (D must be device memory, reps >= 1)");
-    return KLDI_EINVAL;
-  }
-  KLDI_TRY(check_xc(P, xc));
-  const int cand[] = {0, 4, 8, 16, 32, 64, 128};
-  const kldi_tuning start = P->tune;
-  cudaEvent_t e0, e1;
-  KLDI_TRY_CUDA(cudaEventCreate(&e0));
-  KLDI_TRY_CUDA(cudaEventCreate(&e1));
-  double bms = 1e300;
-  kldi_tuning bt = start;
-  kldi_status st = KLDI_OK;
-  const int prof = P->prof;
-  P->prof = 0;
-  for (int c : cand) {
-    kldi_tuning t{c};
-    if ((st = kldi_plan_set_tuning(P, &t)) != KLDI_OK) break;
-    if ((st = exc_device(P, xc, D, P->d_V, P->d_exc)) != KLDI_OK) break;
-    cudaEventRecord(e0, P->stream);
-    for (int r = 0; r < reps && st == KLDI_OK; ++r) st = exc_device(P, xc, D, P->d_V, P->d_exc);
-    cudaEventRecord(e1, P->stream);
-    if (st != KLDI_OK) break;
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      set_error("kldi_plan_autotune: %s", cudaGetErrorString(cudaGetLastError()));
-      st = KLDI_ECUDA;
-      break;
+  return kldi::guarded("kldi_plan_autotune", [&]() -> kldi_status {
+    if (!P || !D || reps < 1 || !is_device_ptr(D)) {
+      set_error("kldi_plan_autotune: bad argument (D must be device memory, reps >= 1)");
+      return KLDI_EINVAL;
     }
-    if ((st = check_device_error(P)) != KLDI_OK) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms / reps < bms) {
-      bms = ms / reps;
-      bt = t;
+    KLDI_TRY(check_xc(P, xc));
+    const int cand[] = {0, 4, 8, 16, 32, 64, 128};
+    const kldi_tuning start = P->tune;
+    cudaEvent_t e0, e1;
+    KLDI_TRY_CUDA(cudaEventCreate(&e0));
+    KLDI_TRY_CUDA(cudaEventCreate(&e1));
+    double bms = 1e300;
+    kldi_tuning bt = start;
+    kldi_status st = KLDI_OK;
+    const int prof = P->prof;
+    P->prof = 0;
+    for (int c : cand) {
+      kldi_tuning t{c};
+      if ((st = kldi_plan_set_tuning(P, &t)) != KLDI_OK) break;
+      if ((st = exc_device(P, xc, D, P->d_V, P->d_exc)) != KLDI_OK) break;
+      cudaEventRecord(e0, P->stream);
+      for (int r = 0; r < reps && st == KLDI_OK; ++r) st = exc_device(P, xc, D, P->d_V, P->d_exc);
+      cudaEventRecord(e1, P->stream);
+      if (st != KLDI_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error("kldi_plan_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        st = KLDI_ECUDA;
+        break;
+      }
+      if ((st = check_device_error(P)) != KLDI_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / reps < bms) {
+        bms = ms / reps;
+        bt = t;
+      }
     }
-  }
-  P->prof = prof;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  KLDI_TRY(st);
-  KLDI_TRY(kldi_plan_set_tuning(P, &bt));
-  if (best) *best = bt;
-  if (best_ms) *best_ms = bms;
-  return KLDI_OK;
+    P->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    KLDI_TRY(st);
+    KLDI_TRY(kldi_plan_set_tuning(P, &bt));
+    if (best) *best = bt;
+    if (best_ms) *best_ms = bms;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_batch_create(kldi_plan* const* plans, int nframes, int xc, const double* const* D,
                                          double* const* V, double* Exc, void* stream, kldi_batch** out) {
-  if (!plans || nframes <= 0 || !D || !V || !Exc || !out) {
-    set_error("kldi_batch_create: bad argument");
-    return KLDI_EINVAL;
-  }
-  *out = nullptr;
-  if (!is_device_ptr(Exc)) { set_error("kldi_batch_create: Exc must be device memory"); return KLDI_EINVAL; }
-  for (int k = 0; k < nframes; ++k) {
-    if (!plans[k] || !D[k] || !V[k]) { set_error("kldi_batch_create: null entry %d", k); return KLDI_EINVAL; }
-    if (!is_device_ptr(D[k]) || !is_device_ptr(V[k])) {
-      set_error("kldi_batch_create: device pointers only (entry %d)", k);
+  return kldi::guarded("kldi_batch_create", [&]() -> kldi_status {
+    if (!plans || nframes <= 0 || !D || !V || !Exc || !out) {
+      set_error("kldi_batch_create: bad argument");
       return KLDI_EINVAL;
     }
-    if (plans[k]->device != plans[0]->device) {
-      set_error("kldi_batch_create: plans on different devices");
-      return KLDI_EINVAL;
+    *out = nullptr;
+    if (!is_device_ptr(Exc)) { set_error("kldi_batch_create: Exc must be device memory"); return KLDI_EINVAL; }
+    for (int k = 0; k < nframes; ++k) {
+      if (!plans[k] || !D[k] || !V[k]) { set_error("kldi_batch_create: null entry %d", k); return KLDI_EINVAL; }
+      if (!is_device_ptr(D[k]) || !is_device_ptr(V[k])) {
+        set_error("kldi_batch_create: device pointers only (entry %d)", k);
+        return KLDI_EINVAL;
+      }
+      if (plans[k]->device != plans[0]->device) {
+        set_error("kldi_batch_create: plans on different devices");
+        return KLDI_EINVAL;
+      }
+      KLDI_TRY(check_xc(plans[k], xc));
+      KLDI_TRY(ensure_tile_buffers(plans[k], plans[k]->prec));
     }
-    KLDI_TRY(check_xc(plans[k], xc));
-    KLDI_TRY(ensure_tile_buffers(plans[k], plans[k]->prec));
-  }
-  KLDI_TRY(prepare_tc_kernels());
-  kldi_batch* B = new kldi_batch;
-  B->plans.assign(plans, plans + nframes);
-  B->stream = static_cast<cudaStream_t>(stream);
-  if (!B->stream) {
-    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete B;
-      set_error("kldi_batch_create: stream creation failed");
+    KLDI_TRY(prepare_tc_kernels());
+    kldi_batch* B = new kldi_batch;
+    B->plans.assign(plans, plans + nframes);
+    B->stream = static_cast<cudaStream_t>(stream);
+    if (!B->stream) {
+      if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete B;
+        set_error("kldi_batch_create: stream creation failed");
+        return KLDI_ECUDA;
+      }
+      B->own_stream = true;
+    }
+    for (kldi_plan* P : B->plans) cudaStreamSynchronize(P->stream);
+    if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      set_error("kldi_batch_create: %s", cudaGetErrorString(cudaGetLastError()));
+      kldi_batch_free(B);
       return KLDI_ECUDA;
     }
-    B->own_stream = true;
-  }
-  for (kldi_plan* P : B->plans) cudaStreamSynchronize(P->stream);
-  if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    set_error("kldi_batch_create: %s", cudaGetErrorString(cudaGetLastError()));
-    kldi_batch_free(B);
-    return KLDI_ECUDA;
-  }
-  kldi_status st = KLDI_OK;
-  for (int k = 0; k < nframes && st == KLDI_OK; ++k) {
-    kldi_plan* P = plans[k];
-    const cudaStream_t keep = P->stream;
-    const int prof = P->prof;
-    P->stream = B->stream;
-    P->prof = 0;
-    st = exc_device(P, xc, D[k], V[k], Exc + k);
-    P->stream = keep;
-    P->prof = prof;
-  }
-  cudaGraph_t graph = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(B->stream, &graph);
-  if (st == KLDI_OK && (ec != cudaSuccess || !graph)) {
-    set_error("kldi_batch_create: capture failed: %s", cudaGetErrorString(ec));
-    st = KLDI_ECUDA;
-  }
-  if (st == KLDI_OK && cudaGraphInstantiate(&B->exec, graph, 0) != cudaSuccess) {
-    set_error("kldi_batch_create: graph instantiation failed: %s", cudaGetErrorString(cudaGetLastError()));
-    st = KLDI_ECUDA;
-  }
-  if (graph) cudaGraphDestroy(graph);
-  cudaGetLastError();
-  if (st != KLDI_OK) {
-    kldi_batch_free(B);
-    return st;
-  }
-  *out = B;
-  return KLDI_OK;
+    kldi_status st = KLDI_OK;
+    for (int k = 0; k < nframes && st == KLDI_OK; ++k) {
+      kldi_plan* P = plans[k];
+      const cudaStream_t keep = P->stream;
+      const int prof = P->prof;
+      P->stream = B->stream;
+      P->prof = 0;
+      st = exc_device(P, xc, D[k], V[k], Exc + k);
+      P->stream = keep;
+      P->prof = prof;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(B->stream, &graph);
+    if (st == KLDI_OK && (ec != cudaSuccess || !graph)) {
+      set_error("kldi_batch_create: capture failed: %s", cudaGetErrorString(ec));
+      st = KLDI_ECUDA;
+    }
+    if (st == KLDI_OK && cudaGraphInstantiate(&B->exec, graph, 0) != cudaSuccess) {
+      set_error("kldi_batch_create: graph instantiation failed: %s", cudaGetErrorString(cudaGetLastError()));
+      st = KLDI_ECUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != KLDI_OK) {
+      kldi_batch_free(B);
+      return st;
+    }
+    *out = B;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_batch_launch(kldi_batch* B) {
-  if (!B || !B->exec) { set_error("kldi_batch_launch: null batch"); return KLDI_EINVAL; }
-  KLDI_TRY_CUDA(cudaGraphLaunch(B->exec, B->stream));
-  return KLDI_OK;
+  return kldi::guarded("kldi_batch_launch", [&]() -> kldi_status {
+    if (!B || !B->exec) { set_error("kldi_batch_launch: null batch"); return KLDI_EINVAL; }
+    KLDI_TRY_CUDA(cudaGraphLaunch(B->exec, B->stream));
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_batch_sync(kldi_batch* B) {
-  if (!B) { set_error("kldi_batch_sync: null batch"); return KLDI_EINVAL; }
-  KLDI_TRY_CUDA(cudaStreamSynchronize(B->stream));
-  for (kldi_plan* P : B->plans) KLDI_TRY(check_device_error(P));
-  return KLDI_OK;
+  return kldi::guarded("kldi_batch_sync", [&]() -> kldi_status {
+    if (!B) { set_error("kldi_batch_sync: null batch"); return KLDI_EINVAL; }
+    KLDI_TRY_CUDA(cudaStreamSynchronize(B->stream));
+    for (kldi_plan* P : B->plans) KLDI_TRY(check_device_error(P));
+    return KLDI_OK;
+  });
 }
 
 extern "C" void kldi_batch_free(kldi_batch* B) {

@@ -94,195 +94,201 @@ static inline uint64_t morton60(uint64_t x, uint64_t y, uint64_t z) {
 extern "C" const char* kldi_last_error(void) { return kldi::last_error(); }
 
 extern "C" kldi_status kldi_make_grid(const kldi_molecule* mol, const kldi_grid_spec* spec, kldi_grid** out) {
-  using namespace kldi;
-  if (!mol || !spec || !out || mol->natm <= 0 || !mol->xyz || !mol->Z) {
-    set_error("kldi_make_grid: null argument or natm <= 0");
-    return KLDI_EINVAL;
-  }
-  if (spec->nrad <= 0 || spec->nregions <= 0 || !spec->ntheta) {
-    set_error("kldi_make_grid: bad grid spec");
-    return KLDI_EINVAL;
-  }
-  if (spec->block != kBlockPts) {
-    set_error("kldi_make_grid: only block = %d is supported", kBlockPts);
-    return KLDI_EUNSUPPORTED;
-  }
-  for (int r = 0; r < spec->nregions; ++r)
-    if (spec->ntheta[r] <= 0 || spec->ntheta[r] > 128) {
-      set_error("kldi_make_grid: ntheta out of range");
+  return kldi::guarded("kldi_make_grid", [&]() -> kldi_status {
+    using namespace kldi;
+    if (!mol || !spec || !out || mol->natm <= 0 || !mol->xyz || !mol->Z) {
+      set_error("kldi_make_grid: null argument or natm <= 0");
       return KLDI_EINVAL;
     }
-  const int natm = mol->natm;
-  const int nrad = spec->nrad;
-  // radial rule, increasing r
-  std::vector<double> rr(nrad), wr(nrad);
-  for (int i = 1; i <= nrad; ++i) {
-    const double th = i * M_PI / (nrad + 1);
-    const double x = std::cos(th);
-    const double wx = M_PI / (nrad + 1) * std::sin(th);
-    const double l2 = std::log(2.0);
-    const double r = 1.0 / l2 * std::pow(1.0 + x, 0.6) * std::log(2.0 / (1.0 - x));
-    const double dr = 1.0 / l2 * (0.6 * std::pow(1.0 + x, 0.6 - 1.0) * std::log(2.0 / (1.0 - x)) +
-                                  std::pow(1.0 + x, 0.6) / (1.0 - x));
-    rr[nrad - i] = r;
-    wr[nrad - i] = wx * dr * r * r;
-  }
-  // angular rules per region
-  struct Ang { std::vector<double> dx, dy, dz, w; };
-  std::vector<Ang> ang(spec->nregions);
-  for (int reg = 0; reg < spec->nregions; ++reg) {
-    const int nt = spec->ntheta[reg], np = 2 * nt;
-    std::vector<double> t, wt;
-    gauss_legendre(nt, t, wt);
-    Ang& a = ang[reg];
-    for (int j = 0; j < nt; ++j) {
-      const double st = std::sqrt(1.0 - t[j] * t[j]);
-      for (int k = 0; k < np; ++k) {
-        const double phi = 2.0 * M_PI * k / np;
-        a.dx.push_back(st * std::cos(phi));
-        a.dy.push_back(st * std::sin(phi));
-        a.dz.push_back(t[j]);
-        a.w.push_back(wt[j] * (2.0 * M_PI / np));
+    if (spec->nrad <= 0 || spec->nregions <= 0 || !spec->ntheta) {
+      set_error("kldi_make_grid: bad grid spec");
+      return KLDI_EINVAL;
+    }
+    if (spec->block != kBlockPts) {
+      set_error("kldi_make_grid: only block = %d is supported", kBlockPts);
+      return KLDI_EUNSUPPORTED;
+    }
+    for (int r = 0; r < spec->nregions; ++r)
+      if (spec->ntheta[r] <= 0 || spec->ntheta[r] > 128) {
+        set_error("kldi_make_grid: ntheta out of range");
+        return KLDI_EINVAL;
+      }
+    const int natm = mol->natm;
+    const int nrad = spec->nrad;
+    // radial rule, increasing r
+    std::vector<double> rr(nrad), wr(nrad);
+    for (int i = 1; i <= nrad; ++i) {
+      const double th = i * M_PI / (nrad + 1);
+      const double x = std::cos(th);
+      const double wx = M_PI / (nrad + 1) * std::sin(th);
+      const double l2 = std::log(2.0);
+      const double r = 1.0 / l2 * std::pow(1.0 + x, 0.6) * std::log(2.0 / (1.0 - x));
+      const double dr = 1.0 / l2 * (0.6 * std::pow(1.0 + x, 0.6 - 1.0) * std::log(2.0 / (1.0 - x)) +
+                                    std::pow(1.0 + x, 0.6) / (1.0 - x));
+      rr[nrad - i] = r;
+      wr[nrad - i] = wx * dr * r * r;
+    }
+    // angular rules per region
+    struct Ang { std::vector<double> dx, dy, dz, w; };
+    std::vector<Ang> ang(spec->nregions);
+    for (int reg = 0; reg < spec->nregions; ++reg) {
+      const int nt = spec->ntheta[reg], np = 2 * nt;
+      std::vector<double> t, wt;
+      gauss_legendre(nt, t, wt);
+      Ang& a = ang[reg];
+      for (int j = 0; j < nt; ++j) {
+        const double st = std::sqrt(1.0 - t[j] * t[j]);
+        for (int k = 0; k < np; ++k) {
+          const double phi = 2.0 * M_PI * k / np;
+          a.dx.push_back(st * std::cos(phi));
+          a.dy.push_back(st * std::sin(phi));
+          a.dz.push_back(t[j]);
+          a.w.push_back(wt[j] * (2.0 * M_PI / np));
+        }
       }
     }
-  }
-  int64_t per_atom = 0;
-  for (int ir = 0; ir < nrad; ++ir) {
-    const int reg = std::min(ir * spec->nregions / nrad, spec->nregions - 1);
-    per_atom += (int64_t)ang[reg].w.size();
-  }
-  const int64_t nreal = per_atom * natm;
-  const int64_t npoints = (nreal + kBlockPts - 1) / kBlockPts * kBlockPts;
-  kldi_grid* G = new (std::nothrow) kldi_grid;
-  if (!G) { set_error("kldi_make_grid: out of host memory"); return KLDI_ENOMEM; }
-  G->npoints = npoints;
-  G->nreal = nreal;
-  G->nblocks = npoints / kBlockPts;
-  G->xyz.resize(npoints * 3);
-  G->w.resize(npoints);
-  G->atom.resize(npoints);
-  std::vector<double> raw_w(npoints, 0.0);
-  const double* A = mol->xyz;
-
-  // points per atom, Morton-sorted within the atom
-#pragma omp parallel for schedule(dynamic)
-  for (int a = 0; a < natm; ++a) {
-    std::vector<double> px, py, pz, pw;
-    px.reserve(per_atom); py.reserve(per_atom); pz.reserve(per_atom); pw.reserve(per_atom);
+    int64_t per_atom = 0;
     for (int ir = 0; ir < nrad; ++ir) {
       const int reg = std::min(ir * spec->nregions / nrad, spec->nregions - 1);
-      const Ang& an = ang[reg];
-      for (size_t k = 0; k < an.w.size(); ++k) {
-        px.push_back(A[3 * a + 0] + rr[ir] * an.dx[k]);
-        py.push_back(A[3 * a + 1] + rr[ir] * an.dy[k]);
-        pz.push_back(A[3 * a + 2] + rr[ir] * an.dz[k]);
-        pw.push_back(wr[ir] * an.w[k]);
-      }
+      per_atom += (int64_t)ang[reg].w.size();
     }
-    const double lx = *std::min_element(px.begin(), px.end());
-    const double ly = *std::min_element(py.begin(), py.end());
-    const double lz = *std::min_element(pz.begin(), pz.end());
-    const int64_t n = (int64_t)px.size();
-    std::vector<uint64_t> key(n);
-    auto lat = [](double v) -> uint64_t {
-      double q = std::floor(v * 128.0);
-      if (q < 0) q = 0;
-      if (q > 1048575.0) q = 1048575.0;
-      return (uint64_t)q;
-    };
-    for (int64_t k = 0; k < n; ++k) key[k] = morton60(lat(px[k] - lx), lat(py[k] - ly), lat(pz[k] - lz));
-    std::vector<int64_t> ord(n);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int64_t i, int64_t j) { return key[i] < key[j]; });
-    const int64_t base = (int64_t)a * per_atom;
-    for (int64_t k = 0; k < n; ++k) {
-      const int64_t s = ord[k];
-      G->xyz[(base + k) * 3 + 0] = px[s];
-      G->xyz[(base + k) * 3 + 1] = py[s];
-      G->xyz[(base + k) * 3 + 2] = pz[s];
-      raw_w[base + k] = pw[s];
-      G->atom[base + k] = a;
-    }
-  }
-  for (int64_t k = nreal; k < npoints; ++k) {
-    for (int c = 0; c < 3; ++c) G->xyz[k * 3 + c] = G->xyz[(nreal - 1) * 3 + c];
-    G->atom[k] = G->atom[nreal - 1];
-  }
+    const int64_t nreal = per_atom * natm;
+    const int64_t npoints = (nreal + kBlockPts - 1) / kBlockPts * kBlockPts;
+    kldi_grid* G = new (std::nothrow) kldi_grid;
+    if (!G) { set_error("kldi_make_grid: out of host memory"); return KLDI_ENOMEM; }
+    G->npoints = npoints;
+    G->nreal = nreal;
+    G->nblocks = npoints / kBlockPts;
+    G->xyz.resize(npoints * 3);
+    G->w.resize(npoints);
+    G->atom.resize(npoints);
+    std::vector<double> raw_w(npoints, 0.0);
+    const double* A = mol->xyz;
 
-  // Becke weights
-  std::vector<double> R(natm * (int64_t)natm);
-  for (int b = 0; b < natm; ++b)
-    for (int c = 0; c < natm; ++c) {
-      const double dx = A[3 * b] - A[3 * c], dy = A[3 * b + 1] - A[3 * c + 1], dz = A[3 * b + 2] - A[3 * c + 2];
-      R[(int64_t)b * natm + c] = std::sqrt(dx * dx + dy * dy + dz * dz);
-    }
-  // neighbour order of every atom (by distance), used as the multiplication order
-  std::vector<int32_t> nbr(natm * (int64_t)natm);
-  for (int a = 0; a < natm; ++a) {
-    int32_t* o = &nbr[(int64_t)a * natm];
-    std::iota(o, o + natm, 0);
-    std::stable_sort(o, o + natm, [&](int32_t i, int32_t j) { return R[(int64_t)a * natm + i] < R[(int64_t)a * natm + j]; });
-  }
-  // on the current CUDA device when there is one (same arithmetic), else on the host cores
-  int ndev = 0;
-  const bool use_dev = natm > 1 && cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0;
-  cudaGetLastError();
-  if (use_dev) {
-    const kldi_status st = becke_weights_device(natm, A, R.data(), nbr.data(), G->xyz.data(), G->atom.data(),
-                                                raw_w.data(), nreal, G->w.data());
-    if (st != KLDI_OK) {
-      delete G;
-      return st;
-    }
-  } else
-#pragma omp parallel
-  {
-    std::vector<double> d(natm);
-#pragma omp for schedule(dynamic, 256)
-    for (int64_t k = 0; k < nreal; ++k) {
-      if (natm == 1) { G->w[k] = raw_w[k]; continue; }
-      const double x = G->xyz[k * 3], y = G->xyz[k * 3 + 1], z = G->xyz[k * 3 + 2];
-      const int own = G->atom[k];
-      for (int b = 0; b < natm; ++b) {
-        const double dx = x - A[3 * b], dy = y - A[3 * b + 1], dz = z - A[3 * b + 2];
-        d[b] = std::sqrt(dx * dx + dy * dy + dz * dz);
-      }
-      const int32_t* order = &nbr[(int64_t)own * natm];
-      double sum = 0.0, pown = 0.0;
-      for (int ib = 0; ib < natm; ++ib) {
-        const int b = order[ib];
-        double P = 1.0;
-        for (int ic = 0; ic < natm; ++ic) {
-          const int c = order[ic];
-          if (c == b) continue;
-          P *= becke_s((d[b] - d[c]) / R[(int64_t)b * natm + c]);
-          if (P < 1e-40) { P = 0.0; break; }
+    // points per atom, Morton-sorted within the atom
+  #pragma omp parallel for schedule(dynamic)
+    for (int a = 0; a < natm; ++a) {
+      std::vector<double> px, py, pz, pw;
+      px.reserve(per_atom); py.reserve(per_atom); pz.reserve(per_atom); pw.reserve(per_atom);
+      for (int ir = 0; ir < nrad; ++ir) {
+        const int reg = std::min(ir * spec->nregions / nrad, spec->nregions - 1);
+        const Ang& an = ang[reg];
+        for (size_t k = 0; k < an.w.size(); ++k) {
+          px.push_back(A[3 * a + 0] + rr[ir] * an.dx[k]);
+          py.push_back(A[3 * a + 1] + rr[ir] * an.dy[k]);
+          pz.push_back(A[3 * a + 2] + rr[ir] * an.dz[k]);
+          pw.push_back(wr[ir] * an.w[k]);
         }
-        sum += P;
-        if (b == own) pown = P;
       }
-      G->w[k] = raw_w[k] * (pown / sum);
+      const double lx = *std::min_element(px.begin(), px.end());
+      const double ly = *std::min_element(py.begin(), py.end());
+      const double lz = *std::min_element(pz.begin(), pz.end());
+      const int64_t n = (int64_t)px.size();
+      std::vector<uint64_t> key(n);
+      auto lat = [](double v) -> uint64_t {
+        double q = std::floor(v * 128.0);
+        if (q < 0) q = 0;
+        if (q > 1048575.0) q = 1048575.0;
+        return (uint64_t)q;
+      };
+      for (int64_t k = 0; k < n; ++k) key[k] = morton60(lat(px[k] - lx), lat(py[k] - ly), lat(pz[k] - lz));
+      std::vector<int64_t> ord(n);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::stable_sort(ord.begin(), ord.end(), [&](int64_t i, int64_t j) { return key[i] < key[j]; });
+      const int64_t base = (int64_t)a * per_atom;
+      for (int64_t k = 0; k < n; ++k) {
+        const int64_t s = ord[k];
+        G->xyz[(base + k) * 3 + 0] = px[s];
+        G->xyz[(base + k) * 3 + 1] = py[s];
+        G->xyz[(base + k) * 3 + 2] = pz[s];
+        raw_w[base + k] = pw[s];
+        G->atom[base + k] = a;
+      }
     }
-  }
-  for (int64_t k = nreal; k < npoints; ++k) G->w[k] = 0.0;
-  *out = G;
-  return KLDI_OK;
+    for (int64_t k = nreal; k < npoints; ++k) {
+      for (int c = 0; c < 3; ++c) G->xyz[k * 3 + c] = G->xyz[(nreal - 1) * 3 + c];
+      G->atom[k] = G->atom[nreal - 1];
+    }
+
+    // Becke weights
+    std::vector<double> R(natm * (int64_t)natm);
+    for (int b = 0; b < natm; ++b)
+      for (int c = 0; c < natm; ++c) {
+        const double dx = A[3 * b] - A[3 * c], dy = A[3 * b + 1] - A[3 * c + 1], dz = A[3 * b + 2] - A[3 * c + 2];
+        R[(int64_t)b * natm + c] = std::sqrt(dx * dx + dy * dy + dz * dz);
+      }
+    // neighbour order of every atom (by distance), used as the multiplication order
+    std::vector<int32_t> nbr(natm * (int64_t)natm);
+    for (int a = 0; a < natm; ++a) {
+      int32_t* o = &nbr[(int64_t)a * natm];
+      std::iota(o, o + natm, 0);
+      std::stable_sort(o, o + natm, [&](int32_t i, int32_t j) { return R[(int64_t)a * natm + i] < R[(int64_t)a * natm + j]; });
+    }
+    // on the current CUDA device when there is one (same arithmetic), else on the host cores
+    int ndev = 0;
+    const bool use_dev = natm > 1 && cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0;
+    cudaGetLastError();
+    if (use_dev) {
+      const kldi_status st = becke_weights_device(natm, A, R.data(), nbr.data(), G->xyz.data(), G->atom.data(),
+                                                  raw_w.data(), nreal, G->w.data());
+      if (st != KLDI_OK) {
+        delete G;
+        return st;
+      }
+    } else
+  #pragma omp parallel
+    {
+      std::vector<double> d(natm);
+  #pragma omp for schedule(dynamic, 256)
+      for (int64_t k = 0; k < nreal; ++k) {
+        if (natm == 1) { G->w[k] = raw_w[k]; continue; }
+        const double x = G->xyz[k * 3], y = G->xyz[k * 3 + 1], z = G->xyz[k * 3 + 2];
+        const int own = G->atom[k];
+        for (int b = 0; b < natm; ++b) {
+          const double dx = x - A[3 * b], dy = y - A[3 * b + 1], dz = z - A[3 * b + 2];
+          d[b] = std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        const int32_t* order = &nbr[(int64_t)own * natm];
+        double sum = 0.0, pown = 0.0;
+        for (int ib = 0; ib < natm; ++ib) {
+          const int b = order[ib];
+          double P = 1.0;
+          for (int ic = 0; ic < natm; ++ic) {
+            const int c = order[ic];
+            if (c == b) continue;
+            P *= becke_s((d[b] - d[c]) / R[(int64_t)b * natm + c]);
+            if (P < 1e-40) { P = 0.0; break; }
+          }
+          sum += P;
+          if (b == own) pown = P;
+        }
+        G->w[k] = raw_w[k] * (pown / sum);
+      }
+    }
+    for (int64_t k = nreal; k < npoints; ++k) G->w[k] = 0.0;
+    *out = G;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_grid_info(const kldi_grid* g, int64_t* npoints, int64_t* nreal, int64_t* nblocks) {
-  if (!g) { kldi::set_error("kldi_grid_info: null grid"); return KLDI_EINVAL; }
-  if (npoints) *npoints = g->npoints;
-  if (nreal) *nreal = g->nreal;
-  if (nblocks) *nblocks = g->nblocks;
-  return KLDI_OK;
+  return kldi::guarded("kldi_grid_info", [&]() -> kldi_status {
+    if (!g) { kldi::set_error("kldi_grid_info: null grid"); return KLDI_EINVAL; }
+    if (npoints) *npoints = g->npoints;
+    if (nreal) *nreal = g->nreal;
+    if (nblocks) *nblocks = g->nblocks;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_grid_export(const kldi_grid* g, double* xyz, double* w, int32_t* atom_of) {
-  if (!g) { kldi::set_error("kldi_grid_export: null grid"); return KLDI_EINVAL; }
-  if (xyz) std::memcpy(xyz, g->xyz.data(), sizeof(double) * g->xyz.size());
-  if (w) std::memcpy(w, g->w.data(), sizeof(double) * g->w.size());
-  if (atom_of) std::memcpy(atom_of, g->atom.data(), sizeof(int32_t) * g->atom.size());
-  return KLDI_OK;
+  return kldi::guarded("kldi_grid_export", [&]() -> kldi_status {
+    if (!g) { kldi::set_error("kldi_grid_export: null grid"); return KLDI_EINVAL; }
+    if (xyz) std::memcpy(xyz, g->xyz.data(), sizeof(double) * g->xyz.size());
+    if (w) std::memcpy(w, g->w.data(), sizeof(double) * g->w.size());
+    if (atom_of) std::memcpy(atom_of, g->atom.data(), sizeof(int32_t) * g->atom.size());
+    return KLDI_OK;
+  });
 }
 
 extern "C" void kldi_grid_free(kldi_grid* g) { delete g; }

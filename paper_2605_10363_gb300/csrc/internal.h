@@ -6,7 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <exception>
 #include <mutex>
+#include <new>
 #include <set>
 #include <string>
 #include <vector>
@@ -35,6 +37,25 @@ void set_error(const char* fmt, ...);
     kldi_status s_ = (expr);      \
     if (s_ != KLDI_OK) return s_; \
   } while (0)
+
+// Runs the body of a C-ABI call: host exceptions (allocation failures of the
+// standard containers and the like) become a status and a message instead of
+// unwinding through extern "C" into the caller.
+template <typename F>
+kldi_status guarded(const char* fn, F&& f) noexcept {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    set_error("%s: out of host memory", fn);
+    return KLDI_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error("%s: %s", fn, e.what());
+    return KLDI_EINVAL;
+  } catch (...) {
+    set_error("%s: unexpected host exception", fn);
+    return KLDI_EINVAL;
+  }
+}
 
 // Runs f() once per device for the call site (each lambda type has its own
 // state): kernel attributes such as the shared-memory opt-in belong to a

@@ -497,203 +497,217 @@ kldi_status launch_xc_mlp(const kldi_plan* P, const Batch& b, const double* rho,
 using namespace kldi;
 
 extern "C" kldi_status kldi_mlp_create(const float* params, const double* box, kldi_mlp** out) {
-  if (!params || !box || !out) {
-    set_error("kldi_mlp_create: null argument");
-    return KLDI_EINVAL;
-  }
-  *out = nullptr;
-  if (!(box[1] > box[0]) || !(box[3] > box[2]) || !std::isfinite(box[0]) || !std::isfinite(box[1]) ||
-      !std::isfinite(box[2]) || !std::isfinite(box[3])) {
-    set_error("kldi_mlp_create: the box needs lo < hi for both inputs");
-    return KLDI_EINVAL;
-  }
-  kldi_mlp* M = new kldi_mlp();
-  auto fail = [&](kldi_status st) {
-    kldi_mlp_free(M);
-    return st;
-  };
-  cudaGetDevice(&M->device);
-  std::memcpy(M->box, box, sizeof(M->box));
-  const size_t nb = sizeof(float) * kNP;
-  if (cudaMalloc(&M->d_param, nb) != cudaSuccess || cudaMalloc(&M->d_half, sizeof(__half) * kNP) != cudaSuccess ||
-      cudaMalloc(&M->d_m, nb) != cudaSuccess || cudaMalloc(&M->d_v, nb) != cudaSuccess ||
-      cudaMalloc(&M->d_grad, nb) != cudaSuccess || cudaMalloc(&M->d_loss, sizeof(float) * 2) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("kldi_mlp_create: device allocation failed");
-    return fail(KLDI_ENOMEM);
-  }
-  if (cudaMemcpy(M->d_param, params, nb, is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemset(M->d_m, 0, nb) != cudaSuccess || cudaMemset(M->d_v, 0, nb) != cudaSuccess) {
-    set_error("kldi_mlp_create: %s", cudaGetErrorString(cudaGetLastError()));
-    return fail(KLDI_ECUDA);
-  }
-  k_to_half<<<(kNP + 255) / 256, 256>>>(M->d_param, M->d_half);
-  if (cudaDeviceSynchronize() != cudaSuccess) {
-    set_error("kldi_mlp_create: %s", cudaGetErrorString(cudaGetLastError()));
-    return fail(KLDI_ECUDA);
-  }
-  *out = M;
-  return KLDI_OK;
+  return kldi::guarded("kldi_mlp_create", [&]() -> kldi_status {
+    if (!params || !box || !out) {
+      set_error("kldi_mlp_create: null argument");
+      return KLDI_EINVAL;
+    }
+    *out = nullptr;
+    if (!(box[1] > box[0]) || !(box[3] > box[2]) || !std::isfinite(box[0]) || !std::isfinite(box[1]) ||
+        !std::isfinite(box[2]) || !std::isfinite(box[3])) {
+      set_error("kldi_mlp_create: the box needs lo < hi for both inputs");
+      return KLDI_EINVAL;
+    }
+    kldi_mlp* M = new kldi_mlp();
+    auto fail = [&](kldi_status st) {
+      kldi_mlp_free(M);
+      return st;
+    };
+    cudaGetDevice(&M->device);
+    std::memcpy(M->box, box, sizeof(M->box));
+    const size_t nb = sizeof(float) * kNP;
+    if (cudaMalloc(&M->d_param, nb) != cudaSuccess || cudaMalloc(&M->d_half, sizeof(__half) * kNP) != cudaSuccess ||
+        cudaMalloc(&M->d_m, nb) != cudaSuccess || cudaMalloc(&M->d_v, nb) != cudaSuccess ||
+        cudaMalloc(&M->d_grad, nb) != cudaSuccess || cudaMalloc(&M->d_loss, sizeof(float) * 2) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("kldi_mlp_create: device allocation failed");
+      return fail(KLDI_ENOMEM);
+    }
+    if (cudaMemcpy(M->d_param, params, nb, is_device_ptr(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemset(M->d_m, 0, nb) != cudaSuccess || cudaMemset(M->d_v, 0, nb) != cudaSuccess) {
+      set_error("kldi_mlp_create: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(KLDI_ECUDA);
+    }
+    k_to_half<<<(kNP + 255) / 256, 256>>>(M->d_param, M->d_half);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      set_error("kldi_mlp_create: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(KLDI_ECUDA);
+    }
+    *out = M;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_mlp_get_params(const kldi_mlp* M, float* params) {
-  if (!M || !params) {
-    set_error("kldi_mlp_get_params: null argument");
-    return KLDI_EINVAL;
-  }
-  KLDI_TRY_CUDA(cudaDeviceSynchronize());
-  KLDI_TRY_CUDA(cudaMemcpy(params, M->d_param, sizeof(float) * kNP, cudaMemcpyDeviceToHost));
-  return KLDI_OK;
+  return kldi::guarded("kldi_mlp_get_params", [&]() -> kldi_status {
+    if (!M || !params) {
+      set_error("kldi_mlp_get_params: null argument");
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY_CUDA(cudaDeviceSynchronize());
+    KLDI_TRY_CUDA(cudaMemcpy(params, M->d_param, sizeof(float) * kNP, cudaMemcpyDeviceToHost));
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_mlp_loss_grad(kldi_mlp* M, const double* rho, const double* sigma, int64_t n,
                                           double rho_min, float* grad, float* loss) {
-  if (!M || !rho || !sigma || !grad || !loss || n <= 0 || n >= (int64_t(1) << 31)) {
-    set_error("kldi_mlp_loss_grad: null argument or n out of range");
-    return KLDI_EINVAL;
-  }
-  cudaStream_t s = nullptr;
-  DevBuf<double> tmp;
-  const double *drho, *dsig;
-  KLDI_TRY(device_inputs(rho, sigma, n, tmp, drho, dsig, s));
-  DevBuf<float4> data;
-  DevBuf<uint8_t> valid;
-  KLDI_TRY(data.alloc(n));
-  KLDI_TRY(valid.alloc(n));
-  k_mlp_prepare<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(map_of(M->box), drho, dsig, n, rho_min, data.p,
-                                                             valid.p);
-  KLDI_TRY_CUDA(cudaGetLastError());
-  KLDI_TRY(launch_partials(M, data.p, valid.p, n, 0, 0, 0, n, M->d_loss, s));
-  KLDI_TRY_CUDA(cudaMemcpyAsync(grad, M->d_grad, sizeof(float) * kNP, cudaMemcpyDeviceToHost, s));
-  KLDI_TRY_CUDA(cudaMemcpyAsync(loss, M->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
-  KLDI_TRY_CUDA(cudaStreamSynchronize(s));
-  return KLDI_OK;
+  return kldi::guarded("kldi_mlp_loss_grad", [&]() -> kldi_status {
+    if (!M || !rho || !sigma || !grad || !loss || n <= 0 || n >= (int64_t(1) << 31)) {
+      set_error("kldi_mlp_loss_grad: null argument or n out of range");
+      return KLDI_EINVAL;
+    }
+    cudaStream_t s = nullptr;
+    DevBuf<double> tmp;
+    const double *drho, *dsig;
+    KLDI_TRY(device_inputs(rho, sigma, n, tmp, drho, dsig, s));
+    DevBuf<float4> data;
+    DevBuf<uint8_t> valid;
+    KLDI_TRY(data.alloc(n));
+    KLDI_TRY(valid.alloc(n));
+    k_mlp_prepare<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(map_of(M->box), drho, dsig, n, rho_min, data.p,
+                                                               valid.p);
+    KLDI_TRY_CUDA(cudaGetLastError());
+    KLDI_TRY(launch_partials(M, data.p, valid.p, n, 0, 0, 0, n, M->d_loss, s));
+    KLDI_TRY_CUDA(cudaMemcpyAsync(grad, M->d_grad, sizeof(float) * kNP, cudaMemcpyDeviceToHost, s));
+    KLDI_TRY_CUDA(cudaMemcpyAsync(loss, M->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    KLDI_TRY_CUDA(cudaStreamSynchronize(s));
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_mlp_adam_step(kldi_mlp* M, const float* grad, double lr, double beta1, double beta2,
                                           double eps) {
-  if (!M || !grad || !(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
-      !(eps >= 0.0)) {
-    set_error("kldi_mlp_adam_step: invalid argument");
-    return KLDI_EINVAL;
-  }
-  const float* g = grad;
-  if (!is_device_ptr(grad)) {
-    KLDI_TRY_CUDA(cudaMemcpy(M->d_grad, grad, sizeof(float) * kNP, cudaMemcpyHostToDevice));
-    g = M->d_grad;
-  }
-  KLDI_TRY(launch_adam(M, g, lr, beta1, beta2, eps, nullptr));
-  KLDI_TRY_CUDA(cudaDeviceSynchronize());
-  return KLDI_OK;
+  return kldi::guarded("kldi_mlp_adam_step", [&]() -> kldi_status {
+    if (!M || !grad || !(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+        !(eps >= 0.0)) {
+      set_error("kldi_mlp_adam_step: invalid argument");
+      return KLDI_EINVAL;
+    }
+    const float* g = grad;
+    if (!is_device_ptr(grad)) {
+      KLDI_TRY_CUDA(cudaMemcpy(M->d_grad, grad, sizeof(float) * kNP, cudaMemcpyHostToDevice));
+      g = M->d_grad;
+    }
+    KLDI_TRY(launch_adam(M, g, lr, beta1, beta2, eps, nullptr));
+    KLDI_TRY_CUDA(cudaDeviceSynchronize());
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_mlp_train(kldi_mlp* M, const double* rho, const double* sigma, int64_t n,
                                       const kldi_train_options* opt, float* loss_per_epoch) {
-  if (!M || !rho || !sigma || !opt || n <= 0 || n >= (int64_t(1) << 31) || opt->epochs < 1 || opt->batch < 1 ||
-      opt->batch > 65536 || !(opt->lr0 >= 0.0) || !(opt->lr1 >= 0.0) || !(opt->beta1 >= 0.0 && opt->beta1 < 1.0) ||
-      !(opt->beta2 >= 0.0 && opt->beta2 < 1.0) || !(opt->eps >= 0.0)) {
-    set_error("kldi_mlp_train: invalid argument");
-    return KLDI_EINVAL;
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(opt->stream);
-  DevBuf<double> tmp;
-  const double *drho, *dsig;
-  KLDI_TRY(device_inputs(rho, sigma, n, tmp, drho, dsig, s));
-  DevBuf<float4> data;
-  DevBuf<uint8_t> valid;
-  KLDI_TRY(data.alloc(n));
-  KLDI_TRY(valid.alloc(n));
-  k_mlp_prepare<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(map_of(M->box), drho, dsig, n, opt->rho_min, data.p,
-                                                             valid.p);
-  KLDI_TRY_CUDA(cudaGetLastError());
-  const int64_t per_epoch = (n + opt->batch - 1) / opt->batch;
-  const int64_t total = per_epoch * opt->epochs;
-  DevBuf<float> hist;
-  KLDI_TRY(hist.alloc(total));
-  // multiplier of the affine permutation: coprime with n
-  uint64_t A = (0x9E3779B97F4A7C15ull % (uint64_t)n) | 1ull;
-  if (n == 1) A = 1;
-  while (gcd_u64(A, (uint64_t)n) != 1) A += 1;
-  const double kPi = 3.14159265358979323846;
-  int64_t step = 0;
-  for (int e = 0; e < opt->epochs; ++e) {
-    const uint64_t C = (uint64_t)(((unsigned __int128)(uint64_t)(e + 1) * 0xD1B54A32D192ED03ull) % (uint64_t)n);
-    for (int64_t b = 0; b < per_epoch; ++b, ++step) {
-      const int64_t j0 = b * opt->batch;
-      const int64_t cnt = std::min<int64_t>(opt->batch, n - j0);
-      KLDI_TRY(launch_partials(M, data.p, valid.p, n, (int64_t)A, (int64_t)C, j0, cnt, hist.p + step, s));
-      const double lr = total <= 1 ? opt->lr0
-                                   : opt->lr1 + 0.5 * (opt->lr0 - opt->lr1) *
-                                                    (1.0 + std::cos(kPi * (double)step / (double)(total - 1)));
-      KLDI_TRY(launch_adam(M, M->d_grad, lr, opt->beta1, opt->beta2, opt->eps, s));
+  return kldi::guarded("kldi_mlp_train", [&]() -> kldi_status {
+    if (!M || !rho || !sigma || !opt || n <= 0 || n >= (int64_t(1) << 31) || opt->epochs < 1 || opt->batch < 1 ||
+        opt->batch > 65536 || !(opt->lr0 >= 0.0) || !(opt->lr1 >= 0.0) || !(opt->beta1 >= 0.0 && opt->beta1 < 1.0) ||
+        !(opt->beta2 >= 0.0 && opt->beta2 < 1.0) || !(opt->eps >= 0.0)) {
+      set_error("kldi_mlp_train: invalid argument");
+      return KLDI_EINVAL;
     }
-  }
-  std::vector<float> h(total);
-  KLDI_TRY_CUDA(cudaMemcpyAsync(h.data(), hist.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
-  KLDI_TRY_CUDA(cudaStreamSynchronize(s));
-  if (loss_per_epoch)
+    cudaStream_t s = static_cast<cudaStream_t>(opt->stream);
+    DevBuf<double> tmp;
+    const double *drho, *dsig;
+    KLDI_TRY(device_inputs(rho, sigma, n, tmp, drho, dsig, s));
+    DevBuf<float4> data;
+    DevBuf<uint8_t> valid;
+    KLDI_TRY(data.alloc(n));
+    KLDI_TRY(valid.alloc(n));
+    k_mlp_prepare<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(map_of(M->box), drho, dsig, n, opt->rho_min, data.p,
+                                                               valid.p);
+    KLDI_TRY_CUDA(cudaGetLastError());
+    const int64_t per_epoch = (n + opt->batch - 1) / opt->batch;
+    const int64_t total = per_epoch * opt->epochs;
+    DevBuf<float> hist;
+    KLDI_TRY(hist.alloc(total));
+    // multiplier of the affine permutation: coprime with n
+    uint64_t A = (0x9E3779B97F4A7C15ull % (uint64_t)n) | 1ull;
+    if (n == 1) A = 1;
+    while (gcd_u64(A, (uint64_t)n) != 1) A += 1;
+    const double kPi = 3.14159265358979323846;
+    int64_t step = 0;
     for (int e = 0; e < opt->epochs; ++e) {
-      double acc = 0.0;
-      for (int64_t b = 0; b < per_epoch; ++b) acc += h[e * per_epoch + b];
-      loss_per_epoch[e] = (float)(acc / (double)per_epoch);
+      const uint64_t C = (uint64_t)(((unsigned __int128)(uint64_t)(e + 1) * 0xD1B54A32D192ED03ull) % (uint64_t)n);
+      for (int64_t b = 0; b < per_epoch; ++b, ++step) {
+        const int64_t j0 = b * opt->batch;
+        const int64_t cnt = std::min<int64_t>(opt->batch, n - j0);
+        KLDI_TRY(launch_partials(M, data.p, valid.p, n, (int64_t)A, (int64_t)C, j0, cnt, hist.p + step, s));
+        const double lr = total <= 1 ? opt->lr0
+                                     : opt->lr1 + 0.5 * (opt->lr0 - opt->lr1) *
+                                                      (1.0 + std::cos(kPi * (double)step / (double)(total - 1)));
+        KLDI_TRY(launch_adam(M, M->d_grad, lr, opt->beta1, opt->beta2, opt->eps, s));
+      }
     }
-  return KLDI_OK;
+    std::vector<float> h(total);
+    KLDI_TRY_CUDA(cudaMemcpyAsync(h.data(), hist.p, sizeof(float) * total, cudaMemcpyDeviceToHost, s));
+    KLDI_TRY_CUDA(cudaStreamSynchronize(s));
+    if (loss_per_epoch)
+      for (int e = 0; e < opt->epochs; ++e) {
+        double acc = 0.0;
+        for (int64_t b = 0; b < per_epoch; ++b) acc += h[e * per_epoch + b];
+        loss_per_epoch[e] = (float)(acc / (double)per_epoch);
+      }
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_mlp_eval(const kldi_mlp* M, const double* rho, const double* sigma, int64_t n,
                                      double rho_min, double* f, double* vrho, double* vsigma, int32_t* used) {
-  if (!M || !rho || !sigma || !f || !vrho || !vsigma || n <= 0) {
-    set_error("kldi_mlp_eval: null argument or n <= 0");
-    return KLDI_EINVAL;
-  }
-  cudaStream_t s = nullptr;
-  DevBuf<double> tmp;
-  const double *drho, *dsig;
-  KLDI_TRY(device_inputs(rho, sigma, n, tmp, drho, dsig, s));
-  const bool host_out = !is_device_ptr(f);
-  DevBuf<double> out;
-  DevBuf<int32_t> dused;
-  double *df = f, *dvr = vrho, *dvs = vsigma;
-  int32_t* du = used;
-  if (host_out) {
-    KLDI_TRY(out.alloc(3 * (size_t)n));
-    df = out.p;
-    dvr = out.p + n;
-    dvs = out.p + 2 * n;
-    if (used) {
-      KLDI_TRY(dused.alloc(n));
-      du = dused.p;
+  return kldi::guarded("kldi_mlp_eval", [&]() -> kldi_status {
+    if (!M || !rho || !sigma || !f || !vrho || !vsigma || n <= 0) {
+      set_error("kldi_mlp_eval: null argument or n <= 0");
+      return KLDI_EINVAL;
     }
-  }
-  k_mlp_eval<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(M->d_half, map_of(M->box), drho, dsig, n, rho_min, df,
-                                                          dvr, dvs, du);
-  KLDI_TRY_CUDA(cudaGetLastError());
-  if (host_out) {
-    KLDI_TRY_CUDA(cudaMemcpyAsync(f, df, 8 * n, cudaMemcpyDeviceToHost, s));
-    KLDI_TRY_CUDA(cudaMemcpyAsync(vrho, dvr, 8 * n, cudaMemcpyDeviceToHost, s));
-    KLDI_TRY_CUDA(cudaMemcpyAsync(vsigma, dvs, 8 * n, cudaMemcpyDeviceToHost, s));
-    if (used) KLDI_TRY_CUDA(cudaMemcpyAsync(used, du, 4 * n, cudaMemcpyDeviceToHost, s));
-    KLDI_TRY_CUDA(cudaStreamSynchronize(s));
-  }
-  return KLDI_OK;
+    cudaStream_t s = nullptr;
+    DevBuf<double> tmp;
+    const double *drho, *dsig;
+    KLDI_TRY(device_inputs(rho, sigma, n, tmp, drho, dsig, s));
+    const bool host_out = !is_device_ptr(f);
+    DevBuf<double> out;
+    DevBuf<int32_t> dused;
+    double *df = f, *dvr = vrho, *dvs = vsigma;
+    int32_t* du = used;
+    if (host_out) {
+      KLDI_TRY(out.alloc(3 * (size_t)n));
+      df = out.p;
+      dvr = out.p + n;
+      dvs = out.p + 2 * n;
+      if (used) {
+        KLDI_TRY(dused.alloc(n));
+        du = dused.p;
+      }
+    }
+    k_mlp_eval<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(M->d_half, map_of(M->box), drho, dsig, n, rho_min, df,
+                                                            dvr, dvs, du);
+    KLDI_TRY_CUDA(cudaGetLastError());
+    if (host_out) {
+      KLDI_TRY_CUDA(cudaMemcpyAsync(f, df, 8 * n, cudaMemcpyDeviceToHost, s));
+      KLDI_TRY_CUDA(cudaMemcpyAsync(vrho, dvr, 8 * n, cudaMemcpyDeviceToHost, s));
+      KLDI_TRY_CUDA(cudaMemcpyAsync(vsigma, dvs, 8 * n, cudaMemcpyDeviceToHost, s));
+      if (used) KLDI_TRY_CUDA(cudaMemcpyAsync(used, du, 4 * n, cudaMemcpyDeviceToHost, s));
+      KLDI_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_plan_set_mlp(kldi_plan* P, const kldi_mlp* M) {
-  if (!P) {
-    set_error("kldi_plan_set_mlp: null plan");
-    return KLDI_EINVAL;
-  }
-  if (M && !P->gga) {
-    set_error("kldi_plan_set_mlp: the learned functional is a GGA; screen the plan with KLDI_XC_PBE");
-    return KLDI_EINVAL;
-  }
-  if (M && M->device != P->device) {
-    set_error("kldi_plan_set_mlp: network and plan live on different devices");
-    return KLDI_EINVAL;
-  }
-  P->mlp = M;
-  return KLDI_OK;
+  return kldi::guarded("kldi_plan_set_mlp", [&]() -> kldi_status {
+    if (!P) {
+      set_error("kldi_plan_set_mlp: null plan");
+      return KLDI_EINVAL;
+    }
+    if (M && !P->gga) {
+      set_error("kldi_plan_set_mlp: the learned functional is a GGA; screen the plan with KLDI_XC_PBE");
+      return KLDI_EINVAL;
+    }
+    if (M && M->device != P->device) {
+      set_error("kldi_plan_set_mlp: network and plan live on different devices");
+      return KLDI_EINVAL;
+    }
+    P->mlp = M;
+    return KLDI_OK;
+  });
 }
 
 extern "C" void kldi_mlp_free(kldi_mlp* M) {

@@ -95,46 +95,48 @@ bool on_device(const void* p) {
 
 extern "C" kldi_status kldi_exc_energy_noalloc(int xc, int64_t npoints, const double* rho, const double* grad,
                                                const double* w, double rho_min, double* Exc, void* stream) {
-  using namespace kldi;
-  if (xc != KLDI_XC_LDA_X && xc != KLDI_XC_PBE) {
-    set_error("kldi_exc_energy_noalloc: functional must be KLDI_XC_LDA_X or KLDI_XC_PBE");
-    return KLDI_EINVAL;
-  }
-  if (npoints <= 0 || !rho || !w || !Exc || (xc == KLDI_XC_PBE && !grad)) {
-    set_error("kldi_exc_energy_noalloc: null pointer or npoints <= 0");
-    return KLDI_EINVAL;
-  }
-  const int64_t nb = (npoints + kBlockPts - 1) / kBlockPts;
-  if (nb > kMaxPartials) {
-    set_error("kldi_exc_energy_noalloc: %lld points exceed the fixed maximum of %lld (%d blocks of %d)",
-              (long long)npoints, (long long)kMaxPartials * kBlockPts, kMaxPartials, kBlockPts);
-    return KLDI_EINVAL;
-  }
-  if (!on_device(rho) || !on_device(w) || !on_device(Exc) || (grad && !on_device(grad))) {
-    set_error("kldi_exc_energy_noalloc: rho, grad, w and Exc must be device memory (host data would need a staging allocation)");
-    return KLDI_EINVAL;
-  }
-  int dev = 0;
-  KLDI_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("kldi_exc_energy_noalloc: device ordinal %d out of range", dev);
-    return KLDI_EUNSUPPORTED;
-  }
-  double* part = g_partials_addr[dev];
-  if (!part) {
-    // first call on this device: resolve the device address of the array
-    std::lock_guard<std::mutex> lk(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
-      void* p = nullptr;
-      KLDI_TRY_CUDA(cudaGetSymbolAddress(&p, g_partials));
-      g_partials_addr[dev] = static_cast<double*>(p);
+  return kldi::guarded("kldi_exc_energy_noalloc", [&]() -> kldi_status {
+    using namespace kldi;
+    if (xc != KLDI_XC_LDA_X && xc != KLDI_XC_PBE) {
+      set_error("kldi_exc_energy_noalloc: functional must be KLDI_XC_LDA_X or KLDI_XC_PBE");
+      return KLDI_EINVAL;
     }
-    part = g_partials_addr[dev];
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_energy_partials<<<(unsigned)nb, kBlockPts, 0, s>>>(rho, grad, w, npoints, xc, rho_min, part);
-  KLDI_TRY_CUDA(cudaGetLastError());
-  k_energy_sum<<<1, 1024, 0, s>>>(part, nb, Exc);
-  KLDI_TRY_CUDA(cudaGetLastError());
-  return KLDI_OK;
+    if (npoints <= 0 || !rho || !w || !Exc || (xc == KLDI_XC_PBE && !grad)) {
+      set_error("kldi_exc_energy_noalloc: null pointer or npoints <= 0");
+      return KLDI_EINVAL;
+    }
+    const int64_t nb = (npoints + kBlockPts - 1) / kBlockPts;
+    if (nb > kMaxPartials) {
+      set_error("kldi_exc_energy_noalloc: %lld points exceed the fixed maximum of %lld (%d blocks of %d)",
+                (long long)npoints, (long long)kMaxPartials * kBlockPts, kMaxPartials, kBlockPts);
+      return KLDI_EINVAL;
+    }
+    if (!on_device(rho) || !on_device(w) || !on_device(Exc) || (grad && !on_device(grad))) {
+      set_error("kldi_exc_energy_noalloc: rho, grad, w and Exc must be device memory (host data would need a staging allocation)");
+      return KLDI_EINVAL;
+    }
+    int dev = 0;
+    KLDI_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+      set_error("kldi_exc_energy_noalloc: device ordinal %d out of range", dev);
+      return KLDI_EUNSUPPORTED;
+    }
+    double* part = g_partials_addr[dev];
+    if (!part) {
+      // first call on this device: resolve the device address of the array
+      std::lock_guard<std::mutex> lk(g_setup_mutex);
+      if (!g_partials_addr[dev]) {
+        void* p = nullptr;
+        KLDI_TRY_CUDA(cudaGetSymbolAddress(&p, g_partials));
+        g_partials_addr[dev] = static_cast<double*>(p);
+      }
+      part = g_partials_addr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_energy_partials<<<(unsigned)nb, kBlockPts, 0, s>>>(rho, grad, w, npoints, xc, rho_min, part);
+    KLDI_TRY_CUDA(cudaGetLastError());
+    k_energy_sum<<<1, 1024, 0, s>>>(part, nb, Exc);
+    KLDI_TRY_CUDA(cudaGetLastError());
+    return KLDI_OK;
+  });
 }

@@ -275,380 +275,386 @@ kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
 
 extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* mol, const kldi_basis* basis,
                                    const kldi_options* opt, kldi_plan** out) {
-  if (!grid || !mol || !basis || !opt || !out) {
-    set_error("kldi_screen: null argument");
-    return KLDI_EINVAL;
-  }
-  if (basis->nshell <= 0 || !basis->atom || !basis->l || !basis->nprim || !basis->exps || !basis->coefs) {
-    set_error("kldi_screen: empty or incomplete basis");
-    return KLDI_EINVAL;
-  }
-  if (opt->prec < KLDI_FP64 || opt->prec > KLDI_BF16X6 || opt->xc < KLDI_XC_LDA_X || opt->xc > KLDI_XC_MLP) {
-    set_error("kldi_screen: bad precision or functional");
-    return KLDI_EINVAL;
-  }
-  if (!(opt->t_b >= 0.0) || !(opt->t_d >= 0.0) || !(opt->rho_min >= 0.0)) {
-    set_error("kldi_screen: thresholds must be >= 0");
-    return KLDI_EINVAL;
-  }
-  if (opt->prec == KLDI_TF32X3) {
-    set_error("KLDI_TF32X3 is not provided: 11-bit slices cannot keep the tensor-core sums exact");
-    return KLDI_EUNSUPPORTED;
-  }
-  // optional shell order: the plan works on the permuted basis; fnperm maps an
-  // internal function index to the caller's
-  std::vector<int32_t> p_atom, p_l, p_nprim, fnperm;
-  std::vector<double> p_exps, p_coefs;
-  kldi_basis permuted;
-  if (opt->shell_order) {
-    const int ns0 = basis->nshell;
-    std::vector<char> seen(ns0, 0);
-    std::vector<int64_t> poff(ns0 + 1, 0), foff(ns0 + 1, 0);
-    for (int s = 0; s < ns0; ++s) {
-      const int l = basis->l[s];
-      if (l < 0 || l > 2 || basis->nprim[s] <= 0) {
-        set_error("kldi_screen: shell %d has l=%d nprim=%d (supported: l <= 2)", s, l, basis->nprim[s]);
-        return l > 2 ? KLDI_EUNSUPPORTED : KLDI_EINVAL;
-      }
-      poff[s + 1] = poff[s] + basis->nprim[s];
-      foff[s + 1] = foff[s] + (l + 1) * (l + 2) / 2;
+  return kldi::guarded("kldi_screen", [&]() -> kldi_status {
+    if (!grid || !mol || !basis || !opt || !out) {
+      set_error("kldi_screen: null argument");
+      return KLDI_EINVAL;
     }
-    for (int k = 0; k < ns0; ++k) {
-      const int s = opt->shell_order[k];
-      if (s < 0 || s >= ns0 || seen[s]) {
-        set_error("kldi_screen: shell_order is not a permutation of 0 .. %d", ns0 - 1);
-        return KLDI_EINVAL;
-      }
-      seen[s] = 1;
-      p_atom.push_back(basis->atom[s]);
-      p_l.push_back(basis->l[s]);
-      p_nprim.push_back(basis->nprim[s]);
-      for (int64_t i = poff[s]; i < poff[s + 1]; ++i) {
-        p_exps.push_back(basis->exps[i]);
-        p_coefs.push_back(basis->coefs[i]);
-      }
-      for (int64_t f = foff[s]; f < foff[s + 1]; ++f) fnperm.push_back((int32_t)f);
+    if (basis->nshell <= 0 || !basis->atom || !basis->l || !basis->nprim || !basis->exps || !basis->coefs) {
+      set_error("kldi_screen: empty or incomplete basis");
+      return KLDI_EINVAL;
     }
-    permuted = kldi_basis{ns0, p_atom.data(), p_l.data(), p_nprim.data(), p_exps.data(), p_coefs.data()};
-    basis = &permuted;
-  }
-  kldi_plan* P = new (std::nothrow) kldi_plan;
-  if (!P) { set_error("kldi_screen: out of host memory"); return KLDI_ENOMEM; }
-  P->opt = *opt;
-  P->opt.shell_order = nullptr;   // read here only
-  P->gga = opt->xc != KLDI_XC_LDA_X;
-  P->prec = opt->prec;
-  P->stream = (cudaStream_t)opt->stream;
-  cudaGetDevice(&P->device);
-  cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
-  auto fail = [&](kldi_status s) {
-    free_plan_buffers(P);
-    delete P;
-    return s;
-  };
+    if (opt->prec < KLDI_FP64 || opt->prec > KLDI_BF16X6 || opt->xc < KLDI_XC_LDA_X || opt->xc > KLDI_XC_MLP) {
+      set_error("kldi_screen: bad precision or functional");
+      return KLDI_EINVAL;
+    }
+    if (!(opt->t_b >= 0.0) || !(opt->t_d >= 0.0) || !(opt->rho_min >= 0.0)) {
+      set_error("kldi_screen: thresholds must be >= 0");
+      return KLDI_EINVAL;
+    }
+    if (opt->prec == KLDI_TF32X3) {
+      set_error("KLDI_TF32X3 is not provided: 11-bit slices cannot keep the tensor-core sums exact");
+      return KLDI_EUNSUPPORTED;
+    }
+    // optional shell order: the plan works on the permuted basis; fnperm maps an
+    // internal function index to the caller's
+    std::vector<int32_t> p_atom, p_l, p_nprim, fnperm;
+    std::vector<double> p_exps, p_coefs;
+    kldi_basis permuted;
+    if (opt->shell_order) {
+      const int ns0 = basis->nshell;
+      std::vector<char> seen(ns0, 0);
+      std::vector<int64_t> poff(ns0 + 1, 0), foff(ns0 + 1, 0);
+      for (int s = 0; s < ns0; ++s) {
+        const int l = basis->l[s];
+        if (l < 0 || l > 2 || basis->nprim[s] <= 0) {
+          set_error("kldi_screen: shell %d has l=%d nprim=%d (supported: l <= 2)", s, l, basis->nprim[s]);
+          return l > 2 ? KLDI_EUNSUPPORTED : KLDI_EINVAL;
+        }
+        poff[s + 1] = poff[s] + basis->nprim[s];
+        foff[s + 1] = foff[s] + (l + 1) * (l + 2) / 2;
+      }
+      for (int k = 0; k < ns0; ++k) {
+        const int s = opt->shell_order[k];
+        if (s < 0 || s >= ns0 || seen[s]) {
+          set_error("kldi_screen: shell_order is not a permutation of 0 .. %d", ns0 - 1);
+          return KLDI_EINVAL;
+        }
+        seen[s] = 1;
+        p_atom.push_back(basis->atom[s]);
+        p_l.push_back(basis->l[s]);
+        p_nprim.push_back(basis->nprim[s]);
+        for (int64_t i = poff[s]; i < poff[s + 1]; ++i) {
+          p_exps.push_back(basis->exps[i]);
+          p_coefs.push_back(basis->coefs[i]);
+        }
+        for (int64_t f = foff[s]; f < foff[s + 1]; ++f) fnperm.push_back((int32_t)f);
+      }
+      permuted = kldi_basis{ns0, p_atom.data(), p_l.data(), p_nprim.data(), p_exps.data(), p_coefs.data()};
+      basis = &permuted;
+    }
+    kldi_plan* P = new (std::nothrow) kldi_plan;
+    if (!P) { set_error("kldi_screen: out of host memory"); return KLDI_ENOMEM; }
+    P->opt = *opt;
+    P->opt.shell_order = nullptr;   // read here only
+    P->gga = opt->xc != KLDI_XC_LDA_X;
+    P->prec = opt->prec;
+    P->stream = (cudaStream_t)opt->stream;
+    cudaGetDevice(&P->device);
+    cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    auto fail = [&](kldi_status s) {
+      free_plan_buffers(P);
+      delete P;
+      return s;
+    };
 
-  // ---- basis: normalised coefficients, function offsets, block -> shell ranges
-  const int ns = basis->nshell;
-  std::vector<DevShell> shells(ns);
-  std::vector<double> alpha, coef;
-  int fn = 0, off = 0;
-  for (int s = 0; s < ns; ++s) {
-    const int l = basis->l[s], np = basis->nprim[s], a = basis->atom[s];
-    if (l < 0 || l > 2 || np <= 0 || a < 0 || a >= mol->natm) {
-      set_error("kldi_screen: shell %d has l=%d nprim=%d atom=%d (supported: l <= 2)", s, l, np, a);
-      return fail(l > 2 ? KLDI_EUNSUPPORTED : KLDI_EINVAL);
+    // ---- basis: normalised coefficients, function offsets, block -> shell ranges
+    const int ns = basis->nshell;
+    std::vector<DevShell> shells(ns);
+    std::vector<double> alpha, coef;
+    int fn = 0, off = 0;
+    for (int s = 0; s < ns; ++s) {
+      const int l = basis->l[s], np = basis->nprim[s], a = basis->atom[s];
+      if (l < 0 || l > 2 || np <= 0 || a < 0 || a >= mol->natm) {
+        set_error("kldi_screen: shell %d has l=%d nprim=%d atom=%d (supported: l <= 2)", s, l, np, a);
+        return fail(l > 2 ? KLDI_EUNSUPPORTED : KLDI_EINVAL);
+      }
+      const double* ex = basis->exps + off;
+      const double* cc = basis->coefs + off;
+      double so = 0.0;
+      for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j)
+          so += cc[i] * cc[j] * std::pow(2.0 * std::sqrt(ex[i] * ex[j]) / (ex[i] + ex[j]), l + 1.5);
+      if (!(so > 0.0)) {
+        set_error("kldi_screen: shell %d has zero norm", s);
+        return fail(KLDI_EINVAL);
+      }
+      const double rescale = 1.0 / std::sqrt(so);
+      for (int i = 0; i < np; ++i) {
+        if (!(ex[i] > 0.0)) { set_error("kldi_screen: non-positive exponent"); return fail(KLDI_EINVAL); }
+        alpha.push_back(ex[i]);
+        coef.push_back(cc[i] * std::pow(2.0 * ex[i] / M_PI, 0.75) * std::pow(4.0 * ex[i], 0.5 * l) * rescale);
+      }
+      shells[s] = DevShell{mol->xyz[3 * a], mol->xyz[3 * a + 1], mol->xyz[3 * a + 2], l, np, off, fn, a, 0};
+      fn += (l + 1) * (l + 2) / 2;
+      off += np;
     }
-    const double* ex = basis->exps + off;
-    const double* cc = basis->coefs + off;
-    double so = 0.0;
-    for (int i = 0; i < np; ++i)
-      for (int j = 0; j < np; ++j)
-        so += cc[i] * cc[j] * std::pow(2.0 * std::sqrt(ex[i] * ex[j]) / (ex[i] + ex[j]), l + 1.5);
-    if (!(so > 0.0)) {
-      set_error("kldi_screen: shell %d has zero norm", s);
-      return fail(KLDI_EINVAL);
-    }
-    const double rescale = 1.0 / std::sqrt(so);
-    for (int i = 0; i < np; ++i) {
-      if (!(ex[i] > 0.0)) { set_error("kldi_screen: non-positive exponent"); return fail(KLDI_EINVAL); }
-      alpha.push_back(ex[i]);
-      coef.push_back(cc[i] * std::pow(2.0 * ex[i] / M_PI, 0.75) * std::pow(4.0 * ex[i], 0.5 * l) * rescale);
-    }
-    shells[s] = DevShell{mol->xyz[3 * a], mol->xyz[3 * a + 1], mol->xyz[3 * a + 2], l, np, off, fn, a, 0};
-    fn += (l + 1) * (l + 2) / 2;
-    off += np;
-  }
-  P->nbf = fn;
-  P->nshell = ns;
-  P->nbb = (fn + kBasisBlk - 1) / kBasisBlk;
-  P->nbf_pad = P->nbb * kBasisBlk;
-  P->nvt = (P->nbb + 3) / 4;
-  P->npoints = grid->npoints;
-  P->nblocks = grid->nblocks;
-  const int64_t nbb = P->nbb, nblk = P->nblocks;
-  std::vector<int32_t> bb_begin(nbb, ns), bb_end(nbb, 0);
-  for (int s = 0; s < ns; ++s) {
-    const int f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
-    for (int p = f0 / kBasisBlk; p <= (f1 - 1) / kBasisBlk; ++p) {
-      bb_begin[p] = std::min(bb_begin[p], s);
-      bb_end[p] = std::max(bb_end[p], s + 1);
-    }
-  }
-  for (int64_t p = 0; p < nbb; ++p) {
-    int npr_blk = 0;
-    for (int s = bb_begin[p]; s < bb_end[p]; ++s) {
-      npr_blk += shells[s].nprim;
-      if (shells[s].nprim > 255) npr_blk += 1 << 20;
-    }
-    if (bb_end[p] - bb_begin[p] > 40 || npr_blk > 80) P->rec_fit_all = false;
-  }
-  // FP32 hi/lo pairs: hi = fp32(v), lo = fp32(v - hi)
-  const size_t npr = alpha.size();
-  P->nprim_total = (int64_t)npr;
-  std::vector<float> alpha_f(4 * npr), coef_f(2 * npr);
-  for (size_t k = 0; k < npr; ++k) {
-    const double ac = alpha[k] * coef[k];
-    alpha_f[k] = (float)alpha[k];
-    alpha_f[npr + k] = (float)(alpha[k] - (double)alpha_f[k]);
-    alpha_f[2 * npr + k] = (float)coef[k];
-    alpha_f[3 * npr + k] = (float)(coef[k] - (double)alpha_f[2 * npr + k]);
-    coef_f[k] = (float)ac;
-    coef_f[npr + k] = (float)(ac - (double)coef_f[k]);
-  }
-  kldi_status st;
-  if ((st = upload(P, &P->d_xyz, grid->xyz.data(), grid->xyz.size())) != KLDI_OK) return fail(st);
-  {
-    // anchors and relative FP32 coordinates for the FP32 basis kernels
-    const int natm = mol->natm;
-    P->natm = natm;
-    std::vector<int32_t> anchor(grid->nblocks);
-    std::vector<float4> prel(grid->npoints);
-    for (int64_t g = 0; g < grid->nblocks; ++g) {
-      const int a = grid->atom[g * kBlockPts];
-      anchor[g] = a;
-      for (int i = 0; i < kBlockPts; ++i) {
-        const int64_t k = g * kBlockPts + i;
-        prel[k] = make_float4((float)(grid->xyz[k * 3] - mol->xyz[3 * a]), (float)(grid->xyz[k * 3 + 1] - mol->xyz[3 * a + 1]),
-                              (float)(grid->xyz[k * 3 + 2] - mol->xyz[3 * a + 2]), 0.f);
+    P->nbf = fn;
+    P->nshell = ns;
+    P->nbb = (fn + kBasisBlk - 1) / kBasisBlk;
+    P->nbf_pad = P->nbb * kBasisBlk;
+    P->nvt = (P->nbb + 3) / 4;
+    P->npoints = grid->npoints;
+    P->nblocks = grid->nblocks;
+    const int64_t nbb = P->nbb, nblk = P->nblocks;
+    std::vector<int32_t> bb_begin(nbb, ns), bb_end(nbb, 0);
+    for (int s = 0; s < ns; ++s) {
+      const int f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
+      for (int p = f0 / kBasisBlk; p <= (f1 - 1) / kBasisBlk; ++p) {
+        bb_begin[p] = std::min(bb_begin[p], s);
+        bb_end[p] = std::max(bb_end[p], s + 1);
       }
     }
-    std::vector<float> rel((size_t)natm * natm * 8, 0.f);
-    for (int a = 0; a < natm; ++a)
-      for (int b = 0; b < natm; ++b) {
-        float* r = &rel[((size_t)a * natm + b) * 8];
-        for (int c = 0; c < 3; ++c) {
-          const double d = mol->xyz[3 * b + c] - mol->xyz[3 * a + c];
-          r[c] = (float)d;
-          r[3 + c] = (float)(d - (double)r[c]);
+    for (int64_t p = 0; p < nbb; ++p) {
+      int npr_blk = 0;
+      for (int s = bb_begin[p]; s < bb_end[p]; ++s) {
+        npr_blk += shells[s].nprim;
+        if (shells[s].nprim > 255) npr_blk += 1 << 20;
+      }
+      if (bb_end[p] - bb_begin[p] > 40 || npr_blk > 80) P->rec_fit_all = false;
+    }
+    // FP32 hi/lo pairs: hi = fp32(v), lo = fp32(v - hi)
+    const size_t npr = alpha.size();
+    P->nprim_total = (int64_t)npr;
+    std::vector<float> alpha_f(4 * npr), coef_f(2 * npr);
+    for (size_t k = 0; k < npr; ++k) {
+      const double ac = alpha[k] * coef[k];
+      alpha_f[k] = (float)alpha[k];
+      alpha_f[npr + k] = (float)(alpha[k] - (double)alpha_f[k]);
+      alpha_f[2 * npr + k] = (float)coef[k];
+      alpha_f[3 * npr + k] = (float)(coef[k] - (double)alpha_f[2 * npr + k]);
+      coef_f[k] = (float)ac;
+      coef_f[npr + k] = (float)(ac - (double)coef_f[k]);
+    }
+    kldi_status st;
+    if ((st = upload(P, &P->d_xyz, grid->xyz.data(), grid->xyz.size())) != KLDI_OK) return fail(st);
+    {
+      // anchors and relative FP32 coordinates for the FP32 basis kernels
+      const int natm = mol->natm;
+      P->natm = natm;
+      std::vector<int32_t> anchor(grid->nblocks);
+      std::vector<float4> prel(grid->npoints);
+      for (int64_t g = 0; g < grid->nblocks; ++g) {
+        const int a = grid->atom[g * kBlockPts];
+        anchor[g] = a;
+        for (int i = 0; i < kBlockPts; ++i) {
+          const int64_t k = g * kBlockPts + i;
+          prel[k] = make_float4((float)(grid->xyz[k * 3] - mol->xyz[3 * a]), (float)(grid->xyz[k * 3 + 1] - mol->xyz[3 * a + 1]),
+                                (float)(grid->xyz[k * 3 + 2] - mol->xyz[3 * a + 2]), 0.f);
         }
       }
-    if ((st = upload(P, &P->d_anchor, anchor.data(), anchor.size())) != KLDI_OK) return fail(st);
-    if ((st = upload(P, &P->d_prel, prel.data(), prel.size())) != KLDI_OK) return fail(st);
-    if ((st = upload(P, &P->d_relatom, rel.data(), rel.size())) != KLDI_OK) return fail(st);
-  }
-  if ((st = upload(P, &P->d_w, grid->w.data(), grid->w.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_shells, shells.data(), shells.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_alpha, alpha.data(), alpha.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_coef, coef.data(), coef.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_alpha_f, alpha_f.data(), alpha_f.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_coef_f, coef_f.data(), coef_f.size())) != KLDI_OK) return fail(st);
-  {
-    // packed copies for the FP32 kernels (one vector load per shell / primitive)
-    std::vector<int4> shf(ns);
-    for (int s2 = 0; s2 < ns; ++s2)
-      shf[s2] = make_int4(shells[s2].l | (shells[s2].nprim << 8), shells[s2].prim_off, shells[s2].fn_off,
-                          shells[s2].atom);
-    std::vector<float4> prf(npr);
-    std::vector<float2> pac(npr);
-    for (size_t k = 0; k < (size_t)npr; ++k) {
-      prf[k] = make_float4(alpha_f[k], alpha_f[npr + k], alpha_f[2 * npr + k], alpha_f[3 * npr + k]);
-      pac[k] = make_float2(coef_f[k], coef_f[npr + k]);
+      std::vector<float> rel((size_t)natm * natm * 8, 0.f);
+      for (int a = 0; a < natm; ++a)
+        for (int b = 0; b < natm; ++b) {
+          float* r = &rel[((size_t)a * natm + b) * 8];
+          for (int c = 0; c < 3; ++c) {
+            const double d = mol->xyz[3 * b + c] - mol->xyz[3 * a + c];
+            r[c] = (float)d;
+            r[3 + c] = (float)(d - (double)r[c]);
+          }
+        }
+      if ((st = upload(P, &P->d_anchor, anchor.data(), anchor.size())) != KLDI_OK) return fail(st);
+      if ((st = upload(P, &P->d_prel, prel.data(), prel.size())) != KLDI_OK) return fail(st);
+      if ((st = upload(P, &P->d_relatom, rel.data(), rel.size())) != KLDI_OK) return fail(st);
     }
-    if ((st = upload(P, &P->d_shell_f, shf.data(), shf.size())) != KLDI_OK) return fail(st);
-    if ((st = upload(P, &P->d_prim_f, prf.data(), prf.size())) != KLDI_OK) return fail(st);
-    if ((st = upload(P, &P->d_prim_ac, pac.data(), pac.size())) != KLDI_OK) return fail(st);
-  }
-  if ((st = upload(P, &P->d_bb_begin, bb_begin.data(), bb_begin.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_bb_end, bb_end.data(), bb_end.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_w, grid->w.data(), grid->w.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_shells, shells.data(), shells.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_alpha, alpha.data(), alpha.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_coef, coef.data(), coef.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_alpha_f, alpha_f.data(), alpha_f.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_coef_f, coef_f.data(), coef_f.size())) != KLDI_OK) return fail(st);
+    {
+      // packed copies for the FP32 kernels (one vector load per shell / primitive)
+      std::vector<int4> shf(ns);
+      for (int s2 = 0; s2 < ns; ++s2)
+        shf[s2] = make_int4(shells[s2].l | (shells[s2].nprim << 8), shells[s2].prim_off, shells[s2].fn_off,
+                            shells[s2].atom);
+      std::vector<float4> prf(npr);
+      std::vector<float2> pac(npr);
+      for (size_t k = 0; k < (size_t)npr; ++k) {
+        prf[k] = make_float4(alpha_f[k], alpha_f[npr + k], alpha_f[2 * npr + k], alpha_f[3 * npr + k]);
+        pac[k] = make_float2(coef_f[k], coef_f[npr + k]);
+      }
+      if ((st = upload(P, &P->d_shell_f, shf.data(), shf.size())) != KLDI_OK) return fail(st);
+      if ((st = upload(P, &P->d_prim_f, prf.data(), prf.size())) != KLDI_OK) return fail(st);
+      if ((st = upload(P, &P->d_prim_ac, pac.data(), pac.size())) != KLDI_OK) return fail(st);
+    }
+    if ((st = upload(P, &P->d_bb_begin, bb_begin.data(), bb_begin.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_bb_end, bb_end.data(), bb_end.size())) != KLDI_OK) return fail(st);
 
-  // ---- geometric candidates: shell extent R_s beyond which the value (and
-  // gradient) bound r^l sum|c| e^{-a r^2} (+ l r^(l-1) .. + 2 a r^(l+1) ..) < t_b/2.
-  const double tb = opt->t_b;
-  std::vector<double> ext(ns, 0.0);
-  for (int s = 0; s < ns; ++s) {
-    const int l = shells[s].l, np = shells[s].nprim, o = shells[s].prim_off;
-    double Rs = 0.0;
-    for (double r = 60.0; r >= 0.0; r -= 0.01) {
-      double v = 0.0, gd = 0.0;
-      for (int k = 0; k < np; ++k) {
-        const double e = std::fabs(coef[o + k]) * std::exp(-alpha[o + k] * r * r);
-        v += e;
-        gd += 2.0 * alpha[o + k] * e;
-      }
-      double b = std::pow(r, l) * v;
-      if (P->gga) b = std::max(b, (l > 0 ? l * std::pow(r, l - 1) * v : 0.0) + std::pow(r, l + 1) * gd);
-      if (b >= 0.5 * tb) { Rs = r + 0.05; break; }
-    }
-    ext[s] = tb > 0.0 ? Rs : 1e300;
-  }
-  std::vector<double> gc(nblk * 4);
-  for (int64_t g = 0; g < nblk; ++g) {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int i = 0; i < kBlockPts; ++i)
-      for (int c = 0; c < 3; ++c) {
-        const double v = grid->xyz[(g * kBlockPts + i) * 3 + c];
-        lo[c] = std::min(lo[c], v);
-        hi[c] = std::max(hi[c], v);
-      }
-    double rad = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      gc[g * 4 + c] = 0.5 * (lo[c] + hi[c]);
-      rad += 0.25 * (hi[c] - lo[c]) * (hi[c] - lo[c]);
-    }
-    gc[g * 4 + 3] = std::sqrt(rad);
-  }
-  std::vector<std::vector<int32_t>> cand(nblk);
-#pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t g = 0; g < nblk; ++g) {
-    std::vector<char> mark(nbb, 0);
+    // ---- geometric candidates: shell extent R_s beyond which the value (and
+    // gradient) bound r^l sum|c| e^{-a r^2} (+ l r^(l-1) .. + 2 a r^(l+1) ..) < t_b/2.
+    const double tb = opt->t_b;
+    std::vector<double> ext(ns, 0.0);
     for (int s = 0; s < ns; ++s) {
-      const double dx = shells[s].cx - gc[g * 4], dy = shells[s].cy - gc[g * 4 + 1], dz = shells[s].cz - gc[g * 4 + 2];
-      const double d = std::sqrt(dx * dx + dy * dy + dz * dz) - gc[g * 4 + 3];
-      if (d <= ext[s]) {
-        const int f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
-        for (int p = f0 / kBasisBlk; p <= (f1 - 1) / kBasisBlk; ++p) mark[p] = 1;
+      const int l = shells[s].l, np = shells[s].nprim, o = shells[s].prim_off;
+      double Rs = 0.0;
+      for (double r = 60.0; r >= 0.0; r -= 0.01) {
+        double v = 0.0, gd = 0.0;
+        for (int k = 0; k < np; ++k) {
+          const double e = std::fabs(coef[o + k]) * std::exp(-alpha[o + k] * r * r);
+          v += e;
+          gd += 2.0 * alpha[o + k] * e;
+        }
+        double b = std::pow(r, l) * v;
+        if (P->gga) b = std::max(b, (l > 0 ? l * std::pow(r, l - 1) * v : 0.0) + std::pow(r, l + 1) * gd);
+        if (b >= 0.5 * tb) { Rs = r + 0.05; break; }
       }
+      ext[s] = tb > 0.0 ? Rs : 1e300;
     }
-    for (int p = 0; p < nbb; ++p)
-      if (mark[p]) cand[g].push_back(p);
-  }
-  std::vector<int64_t> cptr(nblk + 1, 0);
-  for (int64_t g = 0; g < nblk; ++g) cptr[g + 1] = cptr[g] + (int64_t)cand[g].size();
-  const int64_t ncand = cptr[nblk];
-  std::vector<int32_t> cg(ncand), cp(ncand);
-  for (int64_t g = 0; g < nblk; ++g)
-    for (size_t k = 0; k < cand[g].size(); ++k) {
-      cg[cptr[g] + k] = (int32_t)g;
-      cp[cptr[g] + k] = cand[g][k];
-    }
-  int32_t *d_cg = nullptr, *d_cp = nullptr;
-  double* d_cb = nullptr;
-  std::vector<double> cb(ncand);
-  if (ncand) {
-    if (cudaMalloc(&d_cg, ncand * 4) != cudaSuccess || cudaMalloc(&d_cp, ncand * 4) != cudaSuccess ||
-        cudaMalloc(&d_cb, ncand * 8) != cudaSuccess) {
-      cudaFree(d_cg); cudaFree(d_cp); cudaFree(d_cb);
-      set_error("kldi_screen: cudaMalloc of the candidate list failed");
-      return fail(KLDI_ENOMEM);
-    }
-    cudaMemcpy(d_cg, cg.data(), ncand * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(d_cp, cp.data(), ncand * 4, cudaMemcpyHostToDevice);
-    st = launch_block_max(P, d_cg, d_cp, ncand, d_cb, 0);
-    cudaError_t e = cudaMemcpy(cb.data(), d_cb, ncand * 8, cudaMemcpyDeviceToHost);
-    cudaFree(d_cg); cudaFree(d_cp); cudaFree(d_cb);
-    if (st != KLDI_OK) return fail(st);
-    if (e != cudaSuccess) {
-      set_error("kldi_screen: block summary kernel failed: %s", cudaGetErrorString(e));
-      return fail(KLDI_ECUDA);
-    }
-  }
-  // ---- retained lists S_g = {p : b_gp >= t_b}
-  P->blk_ptr.assign(nblk + 1, 0);
-  for (int64_t g = 0; g < nblk; ++g) {
-    for (int64_t k = cptr[g]; k < cptr[g + 1]; ++k)
-      if (cb[k] >= tb) {
-        P->blk_idx.push_back(cp[k]);
-        P->bmax.push_back(cb[k]);
+    std::vector<double> gc(nblk * 4);
+    for (int64_t g = 0; g < nblk; ++g) {
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int i = 0; i < kBlockPts; ++i)
+        for (int c = 0; c < 3; ++c) {
+          const double v = grid->xyz[(g * kBlockPts + i) * 3 + c];
+          lo[c] = std::min(lo[c], v);
+          hi[c] = std::max(hi[c], v);
+        }
+      double rad = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        gc[g * 4 + c] = 0.5 * (lo[c] + hi[c]);
+        rad += 0.25 * (hi[c] - lo[c]) * (hi[c] - lo[c]);
       }
-    if ((int64_t)P->blk_idx.size() > INT32_MAX) {
-      set_error("kldi_screen: more than 2^31 retained tiles");
-      return fail(KLDI_EUNSUPPORTED);
+      gc[g * 4 + 3] = std::sqrt(rad);
     }
-    P->blk_ptr[g + 1] = (int32_t)P->blk_idx.size();
-  }
-  P->ntiles = (int64_t)P->blk_idx.size();
-  std::vector<int32_t> tile_of(nblk * nbb, -1);
-  for (int64_t g = 0; g < nblk; ++g)
-    for (int32_t t = P->blk_ptr[g]; t < P->blk_ptr[g + 1]; ++t) tile_of[g * nbb + P->blk_idx[t]] = t;
-  if ((st = upload(P, &P->d_blk_ptr, P->blk_ptr.data(), P->blk_ptr.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_blk_idx, P->blk_idx.data(), P->blk_idx.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_bmax, P->bmax.data(), P->bmax.size())) != KLDI_OK) return fail(st);
-  if ((st = upload(P, &P->d_tile_of, tile_of.data(), tile_of.size())) != KLDI_OK) return fail(st);
-  {
-    std::vector<int32_t> tile_g(std::max<int64_t>(P->ntiles, 1), 0);
+    std::vector<std::vector<int32_t>> cand(nblk);
+  #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t g = 0; g < nblk; ++g) {
+      std::vector<char> mark(nbb, 0);
+      for (int s = 0; s < ns; ++s) {
+        const double dx = shells[s].cx - gc[g * 4], dy = shells[s].cy - gc[g * 4 + 1], dz = shells[s].cz - gc[g * 4 + 2];
+        const double d = std::sqrt(dx * dx + dy * dy + dz * dz) - gc[g * 4 + 3];
+        if (d <= ext[s]) {
+          const int f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
+          for (int p = f0 / kBasisBlk; p <= (f1 - 1) / kBasisBlk; ++p) mark[p] = 1;
+        }
+      }
+      for (int p = 0; p < nbb; ++p)
+        if (mark[p]) cand[g].push_back(p);
+    }
+    std::vector<int64_t> cptr(nblk + 1, 0);
+    for (int64_t g = 0; g < nblk; ++g) cptr[g + 1] = cptr[g] + (int64_t)cand[g].size();
+    const int64_t ncand = cptr[nblk];
+    std::vector<int32_t> cg(ncand), cp(ncand);
     for (int64_t g = 0; g < nblk; ++g)
-      for (int32_t t = P->blk_ptr[g]; t < P->blk_ptr[g + 1]; ++t) tile_g[t] = (int32_t)g;
-    if ((st = upload(P, &P->d_tile_g, tile_g.data(), tile_g.size())) != KLDI_OK) return fail(st);
-  }
+      for (size_t k = 0; k < cand[g].size(); ++k) {
+        cg[cptr[g] + k] = (int32_t)g;
+        cp[cptr[g] + k] = cand[g][k];
+      }
+    int32_t *d_cg = nullptr, *d_cp = nullptr;
+    double* d_cb = nullptr;
+    std::vector<double> cb(ncand);
+    if (ncand) {
+      if (cudaMalloc(&d_cg, ncand * 4) != cudaSuccess || cudaMalloc(&d_cp, ncand * 4) != cudaSuccess ||
+          cudaMalloc(&d_cb, ncand * 8) != cudaSuccess) {
+        cudaFree(d_cg); cudaFree(d_cp); cudaFree(d_cb);
+        set_error("kldi_screen: cudaMalloc of the candidate list failed");
+        return fail(KLDI_ENOMEM);
+      }
+      cudaMemcpy(d_cg, cg.data(), ncand * 4, cudaMemcpyHostToDevice);
+      cudaMemcpy(d_cp, cp.data(), ncand * 4, cudaMemcpyHostToDevice);
+      st = launch_block_max(P, d_cg, d_cp, ncand, d_cb, 0);
+      cudaError_t e = cudaMemcpy(cb.data(), d_cb, ncand * 8, cudaMemcpyDeviceToHost);
+      cudaFree(d_cg); cudaFree(d_cp); cudaFree(d_cb);
+      if (st != KLDI_OK) return fail(st);
+      if (e != cudaSuccess) {
+        set_error("kldi_screen: block summary kernel failed: %s", cudaGetErrorString(e));
+        return fail(KLDI_ECUDA);
+      }
+    }
+    // ---- retained lists S_g = {p : b_gp >= t_b}
+    P->blk_ptr.assign(nblk + 1, 0);
+    for (int64_t g = 0; g < nblk; ++g) {
+      for (int64_t k = cptr[g]; k < cptr[g + 1]; ++k)
+        if (cb[k] >= tb) {
+          P->blk_idx.push_back(cp[k]);
+          P->bmax.push_back(cb[k]);
+        }
+      if ((int64_t)P->blk_idx.size() > INT32_MAX) {
+        set_error("kldi_screen: more than 2^31 retained tiles");
+        return fail(KLDI_EUNSUPPORTED);
+      }
+      P->blk_ptr[g + 1] = (int32_t)P->blk_idx.size();
+    }
+    P->ntiles = (int64_t)P->blk_idx.size();
+    std::vector<int32_t> tile_of(nblk * nbb, -1);
+    for (int64_t g = 0; g < nblk; ++g)
+      for (int32_t t = P->blk_ptr[g]; t < P->blk_ptr[g + 1]; ++t) tile_of[g * nbb + P->blk_idx[t]] = t;
+    if ((st = upload(P, &P->d_blk_ptr, P->blk_ptr.data(), P->blk_ptr.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_blk_idx, P->blk_idx.data(), P->blk_idx.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_bmax, P->bmax.data(), P->bmax.size())) != KLDI_OK) return fail(st);
+    if ((st = upload(P, &P->d_tile_of, tile_of.data(), tile_of.size())) != KLDI_OK) return fail(st);
+    {
+      std::vector<int32_t> tile_g(std::max<int64_t>(P->ntiles, 1), 0);
+      for (int64_t g = 0; g < nblk; ++g)
+        for (int32_t t = P->blk_ptr[g]; t < P->blk_ptr[g + 1]; ++t) tile_g[t] = (int32_t)g;
+      if ((st = upload(P, &P->d_tile_g, tile_g.data(), tile_g.size())) != KLDI_OK) return fail(st);
+    }
 
-  // ---- batches and V work lists (tile buffers are allocated at first use)
-  {
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    int64_t cap = (int64_t)(0.35 * (double)free_b) / tile_bytes_max();
-    if (const char* env = getenv("KLDI_TILE_CAP")) cap = std::max<int64_t>(1, atoll(env));
-    if ((st = build_work(P, cap)) != KLDI_OK) return fail(st);
-  }
+    // ---- batches and V work lists (tile buffers are allocated at first use)
+    {
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      int64_t cap = (int64_t)(0.35 * (double)free_b) / tile_bytes_max();
+      if (const char* env = getenv("KLDI_TILE_CAP")) cap = std::max<int64_t>(1, atoll(env));
+      if ((st = build_work(P, cap)) != KLDI_OK) return fail(st);
+    }
 
-  // ---- per-evaluation buffers
-  const size_t nbf2 = (size_t)P->nbf * P->nbf;
-  if ((st = dalloc(P, &P->d_D, nbf2)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_V, nbf2)) != KLDI_OK) return fail(st);
-  if (!fnperm.empty()) {
-    if ((st = upload(P, &P->d_fnperm, fnperm.data(), fnperm.size())) != KLDI_OK) return fail(st);
-    if ((st = dalloc(P, &P->d_Dint, nbf2)) != KLDI_OK) return fail(st);
-    if ((st = dalloc(P, &P->d_Vint, nbf2)) != KLDI_OK) return fail(st);
-  }
-  if ((st = dalloc(P, &P->d_dmax, (size_t)nbb * nbb)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_rho, (size_t)P->npoints)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_grad, (size_t)P->npoints * 3)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_xcoef, (size_t)P->npoints * 4)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_xmax, (size_t)std::max<int64_t>(P->ntiles, 1))) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_eblk, (size_t)nblk)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_exc, 1)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_err, 1)) != KLDI_OK) return fail(st);
-  if ((st = dalloc(P, &P->d_vnext, 1)) != KLDI_OK) return fail(st);
-  if (cudaMemset(P->d_err, 0, sizeof(int)) != cudaSuccess) { set_error("kldi_screen: memset failed"); return fail(KLDI_ECUDA); }
-  *out = P;
-  return KLDI_OK;
+    // ---- per-evaluation buffers
+    const size_t nbf2 = (size_t)P->nbf * P->nbf;
+    if ((st = dalloc(P, &P->d_D, nbf2)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_V, nbf2)) != KLDI_OK) return fail(st);
+    if (!fnperm.empty()) {
+      if ((st = upload(P, &P->d_fnperm, fnperm.data(), fnperm.size())) != KLDI_OK) return fail(st);
+      if ((st = dalloc(P, &P->d_Dint, nbf2)) != KLDI_OK) return fail(st);
+      if ((st = dalloc(P, &P->d_Vint, nbf2)) != KLDI_OK) return fail(st);
+    }
+    if ((st = dalloc(P, &P->d_dmax, (size_t)nbb * nbb)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_rho, (size_t)P->npoints)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_grad, (size_t)P->npoints * 3)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_xcoef, (size_t)P->npoints * 4)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_xmax, (size_t)std::max<int64_t>(P->ntiles, 1))) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_eblk, (size_t)nblk)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_exc, 1)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_err, 1)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_vnext, 1)) != KLDI_OK) return fail(st);
+    if (cudaMemset(P->d_err, 0, sizeof(int)) != cudaSuccess) { set_error("kldi_screen: memset failed"); return fail(KLDI_ECUDA); }
+    *out = P;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_plan_set_precision(kldi_plan* P, int prec) {
-  if (!P || prec < KLDI_FP64 || prec > KLDI_BF16X6) {
-    set_error("kldi_plan_set_precision: bad argument");
-    return KLDI_EINVAL;
-  }
-  KLDI_TRY(ensure_tile_buffers(P, prec));
-  P->prec = prec;
-  // the V work lists differ between the FP64 and the tensor-core products
-  if ((prec == KLDI_FP64) != P->work_fp64) {
-    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-    KLDI_TRY(build_work(P, P->tile_cap));
-  }
-  return KLDI_OK;
+  return kldi::guarded("kldi_plan_set_precision", [&]() -> kldi_status {
+    if (!P || prec < KLDI_FP64 || prec > KLDI_BF16X6) {
+      set_error("kldi_plan_set_precision: bad argument");
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY(ensure_tile_buffers(P, prec));
+    P->prec = prec;
+    // the V work lists differ between the FP64 and the tensor-core products
+    if ((prec == KLDI_FP64) != P->work_fp64) {
+      KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+      KLDI_TRY(build_work(P, P->tile_cap));
+    }
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_workspace_create(int64_t bytes, kldi_workspace** out) {
-  if (!out || bytes <= 0) {
-    set_error("kldi_workspace_create: bad argument");
-    return KLDI_EINVAL;
-  }
-  *out = nullptr;
-  kldi_workspace* ws = new (std::nothrow) kldi_workspace;
-  if (!ws) {
-    set_error("kldi_workspace_create: out of host memory");
-    return KLDI_ENOMEM;
-  }
-  cudaGetDevice(&ws->device);
-  if (cudaMalloc(&ws->base, (size_t)bytes) != cudaSuccess) {
-    cudaGetLastError();
-    delete ws;
-    set_error("kldi_workspace_create: cudaMalloc of %lld bytes failed", (long long)bytes);
-    return KLDI_ENOMEM;
-  }
-  ws->bytes = bytes;
-  *out = ws;
-  return KLDI_OK;
+  return kldi::guarded("kldi_workspace_create", [&]() -> kldi_status {
+    if (!out || bytes <= 0) {
+      set_error("kldi_workspace_create: bad argument");
+      return KLDI_EINVAL;
+    }
+    *out = nullptr;
+    kldi_workspace* ws = new (std::nothrow) kldi_workspace;
+    if (!ws) {
+      set_error("kldi_workspace_create: out of host memory");
+      return KLDI_ENOMEM;
+    }
+    cudaGetDevice(&ws->device);
+    if (cudaMalloc(&ws->base, (size_t)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      delete ws;
+      set_error("kldi_workspace_create: cudaMalloc of %lld bytes failed", (long long)bytes);
+      return KLDI_ENOMEM;
+    }
+    ws->bytes = bytes;
+    *out = ws;
+    return KLDI_OK;
+  });
 }
 
 extern "C" void kldi_workspace_free(kldi_workspace* ws) {
@@ -658,94 +664,106 @@ extern "C" void kldi_workspace_free(kldi_workspace* ws) {
 }
 
 extern "C" kldi_status kldi_plan_set_workspace(kldi_plan* P, const kldi_workspace* ws) {
-  if (!P) {
-    set_error("kldi_plan_set_workspace: null plan");
-    return KLDI_EINVAL;
-  }
-  int64_t cap;
-  if (ws) {
-    if (ws->device != P->device) {
-      set_error("kldi_plan_set_workspace: workspace and plan live on different devices");
+  return kldi::guarded("kldi_plan_set_workspace", [&]() -> kldi_status {
+    if (!P) {
+      set_error("kldi_plan_set_workspace: null plan");
       return KLDI_EINVAL;
     }
-    cap = ws->bytes / tile_bytes_max();
-    int64_t maxblk = 0;
-    for (int64_t g = 0; g < P->nblocks; ++g) maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
-    if (cap < maxblk) {
-      set_error("kldi_plan_set_workspace: %lld bytes hold %lld tiles, a grid block needs %lld", (long long)ws->bytes,
-                (long long)cap, (long long)maxblk);
-      return KLDI_EINVAL;
+    int64_t cap;
+    if (ws) {
+      if (ws->device != P->device) {
+        set_error("kldi_plan_set_workspace: workspace and plan live on different devices");
+        return KLDI_EINVAL;
+      }
+      cap = ws->bytes / tile_bytes_max();
+      int64_t maxblk = 0;
+      for (int64_t g = 0; g < P->nblocks; ++g) maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
+      if (cap < maxblk) {
+        set_error("kldi_plan_set_workspace: %lld bytes hold %lld tiles, a grid block needs %lld", (long long)ws->bytes,
+                  (long long)cap, (long long)maxblk);
+        return KLDI_EINVAL;
+      }
+    } else {
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      cap = (int64_t)(0.35 * (double)free_b) / tile_bytes_max();
     }
-  } else {
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    cap = (int64_t)(0.35 * (double)free_b) / tile_bytes_max();
-  }
-  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-  free_own_tile_buffers(P);
-  P->ws = ws;
-  KLDI_TRY(build_work(P, cap));
-  if (ws) KLDI_TRY(ensure_tile_buffers(P, P->prec));
-  return KLDI_OK;
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    free_own_tile_buffers(P);
+    P->ws = ws;
+    KLDI_TRY(build_work(P, cap));
+    if (ws) KLDI_TRY(ensure_tile_buffers(P, P->prec));
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_plan_set_block_range(kldi_plan* P, int64_t g0, int64_t g1) {
-  if (!P || g0 < 0 || g1 < g0 || g1 > P->nblocks) {
-    set_error("kldi_plan_set_block_range: need 0 <= g0 <= g1 <= nblocks");
-    return KLDI_EINVAL;
-  }
-  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-  // blocks outside the range contribute nothing to E_xc
-  KLDI_TRY_CUDA(cudaMemset(P->d_eblk, 0, sizeof(double) * P->nblocks));
-  P->range_g0 = g0;
-  P->range_g1 = g1;
-  return build_work(P, P->tile_cap);
+  return kldi::guarded("kldi_plan_set_block_range", [&]() -> kldi_status {
+    if (!P || g0 < 0 || g1 < g0 || g1 > P->nblocks) {
+      set_error("kldi_plan_set_block_range: need 0 <= g0 <= g1 <= nblocks");
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    // blocks outside the range contribute nothing to E_xc
+    KLDI_TRY_CUDA(cudaMemset(P->d_eblk, 0, sizeof(double) * P->nblocks));
+    P->range_g0 = g0;
+    P->range_g1 = g1;
+    return build_work(P, P->tile_cap);
+  });
 }
 
 extern "C" kldi_status kldi_plan_set_tuning(kldi_plan* P, const kldi_tuning* t) {
-  if (!P || !t || t->v_seg < 0) {
-    set_error("kldi_plan_set_tuning: bad argument");
-    return KLDI_EINVAL;
-  }
-  if (t->v_seg == P->tune.v_seg) return KLDI_OK;
-  KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-  P->tune = *t;
-  return build_work(P, P->tile_cap);
+  return kldi::guarded("kldi_plan_set_tuning", [&]() -> kldi_status {
+    if (!P || !t || t->v_seg < 0) {
+      set_error("kldi_plan_set_tuning: bad argument");
+      return KLDI_EINVAL;
+    }
+    if (t->v_seg == P->tune.v_seg) return KLDI_OK;
+    KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    P->tune = *t;
+    return build_work(P, P->tile_cap);
+  });
 }
 
 extern "C" kldi_status kldi_plan_get_tuning(const kldi_plan* P, kldi_tuning* t) {
-  if (!P || !t) {
-    set_error("kldi_plan_get_tuning: null argument");
-    return KLDI_EINVAL;
-  }
-  *t = P->tune;
-  return KLDI_OK;
+  return kldi::guarded("kldi_plan_get_tuning", [&]() -> kldi_status {
+    if (!P || !t) {
+      set_error("kldi_plan_get_tuning: null argument");
+      return KLDI_EINVAL;
+    }
+    *t = P->tune;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_plan_info(const kldi_plan* P, kldi_plan_stats* s) {
-  if (!P || !s) { set_error("kldi_plan_info: null argument"); return KLDI_EINVAL; }
-  s->nbf = P->nbf;
-  s->nbasis_blocks = P->nbb;
-  s->npoints = P->npoints;
-  s->nblocks = P->nblocks;
-  s->retained = P->ntiles;
-  int64_t ps = 0;
-  for (int64_t g = 0; g < P->nblocks; ++g) {
-    const int64_t n = P->blk_ptr[g + 1] - P->blk_ptr[g];
-    ps += n * n;
-  }
-  s->pair_slots = ps;
-  s->vtile_work = P->vtile_work;
-  s->workspace_bytes = P->workspace_bytes;
-  return KLDI_OK;
+  return kldi::guarded("kldi_plan_info", [&]() -> kldi_status {
+    if (!P || !s) { set_error("kldi_plan_info: null argument"); return KLDI_EINVAL; }
+    s->nbf = P->nbf;
+    s->nbasis_blocks = P->nbb;
+    s->npoints = P->npoints;
+    s->nblocks = P->nblocks;
+    s->retained = P->ntiles;
+    int64_t ps = 0;
+    for (int64_t g = 0; g < P->nblocks; ++g) {
+      const int64_t n = P->blk_ptr[g + 1] - P->blk_ptr[g];
+      ps += n * n;
+    }
+    s->pair_slots = ps;
+    s->vtile_work = P->vtile_work;
+    s->workspace_bytes = P->workspace_bytes;
+    return KLDI_OK;
+  });
 }
 
 extern "C" kldi_status kldi_plan_export_lists(const kldi_plan* P, int32_t* blk_ptr, int32_t* blk_idx, double* bmax) {
-  if (!P) { set_error("kldi_plan_export_lists: null plan"); return KLDI_EINVAL; }
-  if (blk_ptr) std::memcpy(blk_ptr, P->blk_ptr.data(), P->blk_ptr.size() * 4);
-  if (blk_idx) std::memcpy(blk_idx, P->blk_idx.data(), P->blk_idx.size() * 4);
-  if (bmax) std::memcpy(bmax, P->bmax.data(), P->bmax.size() * 8);
-  return KLDI_OK;
+  return kldi::guarded("kldi_plan_export_lists", [&]() -> kldi_status {
+    if (!P) { set_error("kldi_plan_export_lists: null plan"); return KLDI_EINVAL; }
+    if (blk_ptr) std::memcpy(blk_ptr, P->blk_ptr.data(), P->blk_ptr.size() * 4);
+    if (blk_idx) std::memcpy(blk_idx, P->blk_idx.data(), P->blk_idx.size() * 4);
+    if (bmax) std::memcpy(bmax, P->bmax.data(), P->bmax.size() * 8);
+    return KLDI_OK;
+  });
 }
 
 extern "C" void kldi_plan_free(kldi_plan* P) {
