@@ -51,3 +51,35 @@ def test_screened_gradient_at_zero_thresholds_is_dense():
     Gd = og_.exc_gradient(s, grid, screened=False, xc_kind="pbe")
     Gs = og_.exc_gradient(s, grid, screened=True, xc_kind="pbe", t_b=0.0, t_d=0.0)
     assert np.allclose(Gs, Gd, rtol=1e-12, atol=1e-14)
+
+
+def test_gradient_with_learned_functional_matches_finite_differences():
+    """The gradient is formed from the functional's (f, v_rho, v_sigma); the
+    surrogate's v_rho is a separate network output (trained towards the
+    analytic one), so the formula is the derivative of E only when that output
+    is df/drho.  A network with zero weights and equal output biases c is
+    exactly that (f = c e0, v_rho = c v0 = df/drho, v_sigma = 0): the oracle's
+    gradient through the network path must then match finite differences."""
+    import math
+
+    from oracle import mlp as om
+    s = synth.make_system(1)
+    grid = og.build_grid(s.Z, s.xyz, s.grid)
+    p = np.zeros(om.NP)
+    p[om.O_B3:] = 1.3
+    box = om.Box(math.log(1e-14) - 1.0, math.log(1e6), math.log(1e-30) - 1.0, math.log(1e12))
+    mlp = (p, box)
+    G = og_.exc_gradient(s, grid, screened=False, xc_kind="mlp", mlp=mlp)
+    Gx = og_.exc_gradient(s, grid, screened=False, xc_kind="lda_x")
+    assert np.allclose(G, 1.3 * Gx, rtol=1e-12, atol=1e-15)      # the network is 1.3 x Slater exchange
+
+    def energy(atom, axis, delta):
+        xyz = s.xyz.copy()
+        xyz[atom, axis] += delta
+        return oe.evaluate(s, grid, ob.build_shells(xyz, s.basis), screened=False, want_v=False, xc_kind="mlp",
+                           mlp=mlp).E
+
+    h = 1e-4
+    for atom, axis in ((0, 1), (4, 0)):
+        fd = (energy(atom, axis, h) - energy(atom, axis, -h)) / (2 * h)
+        assert abs(fd - G[atom, axis]) <= 1e-7 + 1e-5 * abs(fd), (atom, axis, fd, G[atom, axis])
