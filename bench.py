@@ -315,7 +315,7 @@ def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analyt
 
 # ---------------------------------------------------------------------------- batched frames
 def run_large(args, dev, stream):
-    """The 1000-atom C/N/O/H cluster (9000 functions, 11.55M points): one
+    """The 1000-atom C/N/O/H cluster (9000 functions, 11.65M points): one
     evaluation per precision mode (BF16x6, BF16x3, the FP64 block form; the
     tensor modes after one untimed evaluation), with the plan statistics.  The overlap matrix
     (for the shell order) is the Kohn-Sham setup's input; building it in numpy
@@ -365,7 +365,7 @@ def run_large(args, dev, stream):
         "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "cnoh1000_pbe: 1000 atoms (240 C, 80 N, 80 O, 600 H, 0.1 atoms/A^3), 9000 "
-                               "Cartesian s/p/d functions, 11.55M points, PBE-form, t_b = t_d = 1e-10",
+                               "Cartesian s/p/d functions, 11.65M points, PBE-form, t_b = t_d = 1e-10",
                    "precision": "bf16x6", "system_seconds": round(t_sys, 1), "order_seconds": round(t_order, 1),
                    "basis_order": "overlap-signature clustering" if order is not None else "atom order"},
         "speedup_vs_fp64": modes["fp64"]["ms_per_step"] / main["ms_per_step"],
