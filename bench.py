@@ -575,6 +575,9 @@ def main():
             m = {"ms_per_step": ms, "value": npts_real / (ms * 1e-3)}
             if "dExc_vs_oracle" in out_extra:
                 m["dExc_vs_oracle"] = float(E.item()) - gold["E_screened"]
+                Vm = V.cpu().numpy()
+                m["max_dV_sampled_vs_oracle"] = float(np.abs(Vm[vs[:, 0].astype(int), vs[:, 1].astype(int)]
+                                                             - vs[:, 2]).max())
             modes[pm] = m
             del p2
         out_extra["speedup_vs_fp64"] = modes["fp64"]["ms_per_step"] / ms_step
