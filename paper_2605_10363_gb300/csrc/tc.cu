@@ -21,15 +21,17 @@
 //               [32 n][32 k] = D[32p + k][32q + n] / f_n in NS BF16 planes,
 //               64-byte swizzle.
 //  k_phi_split  per grid block: point scales e_i >= max_mu |phi_mu(r_i)| from the
-//               shell bound r^l sum_k |c_k| exp(-a_k r^2); then per retained
-//               tile (g, p) two slicings of Phi (Eq. phi_def): by point (the
-//               A operand of the density product) and by function with the
-//               tile's column maxima (the A operand of the V product).
+//               shell bound r^l sum_k |c_k| exp(-a_k r^2); then every retained
+//               tile (g, p) of Phi (Eq. phi_def) sliced by point: the A operand
+//               of the density product.
 //  k_rho_tc     density product R = Phi_g D over the executed pairs of grid
 //               block g (Eq. executed_block_output), warp-ballot pair screen
 //               (Eq. block_pair_filter), bulk-copy pipeline, tcgen05.mma
 //               M = 128 N = 128 per level, drains every <= 8 executed chunks
-//               (256 K), fused row-dot rho = sum Phi . R, grad rho.
+//               (256 K), fused row-dot rho = sum Phi . R, grad rho; with the
+//               gradient epilogues, the Q = Z D and R = Phi D terms of the
+//               nuclear gradient contracted with basis derivatives per atom.
+//  k_z_split    the gradient's Z = 2 a phi + b . grad phi tiles, sliced by point.
 //  k_x_split    X tile = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi);
 //               Phi~ = c phi and X~ = X / c (per-point balance c), sliced per
 //               function with one shared column scale; x_gq = max |X|.
