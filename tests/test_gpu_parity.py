@@ -156,16 +156,20 @@ def test_unsupported_and_invalid_requests(sys_cache):
     assert e.value.status == kldi.EINVAL
 
 
-@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
-def test_full_size_water33(prec):
-    """33 waters (1.15M points, 825 functions) in the launch configuration the
-    benchmark times, against stored oracle values: E_xc, tr(D V), sampled V
-    elements and rho / grad rho on sampled grid blocks."""
+@pytest.mark.parametrize("prec,order", [("bf16x6", "overlap"), ("bf16x6", "atom"), ("bf16x3", "atom")])
+def test_full_size_water33(prec, order):
+    """33 waters (1.15M points, 825 functions) against stored oracle values:
+    E_xc, tr(D V), sampled V elements and rho / grad rho on sampled grid blocks.
+    The benchmark's launch configuration is BF16x6 in the overlap-signature
+    shell order; the stored values come from the oracle in the generated (atom)
+    order, whose screened block partition differs by the screening error
+    (dense - screened = 1.2e-9 Ha on this system)."""
     path = os.path.join(HERE, "golden", "water33_pbe.json")
     gold = json.load(open(path))
     from paper_2605_10363_gb300 import kldi
-    s = synth.make_system(2)
-    plan = kldi.plan_for_system(s, prec=prec, xc="pbe")
+    s = synth.make_system(2, keep_overlap=True)
+    perm = kldi.order_shells(s.meta["S"], synth.shell_sizes(s.basis)) if order == "overlap" else None
+    plan = kldi.plan_for_system(s, prec=prec, xc="pbe", shell_order=perm)
     assert plan.npoints == gold["npoints"]
     V = np.zeros((s.nbf, s.nbf))
     E = np.zeros(1)
