@@ -27,9 +27,14 @@ formula to get wrong).
 
 Pins (tests): the Slater constant through the closed-form exchange energy of
 a single s-Gaussian density; PBE exchange at sigma = 0 equals Slater; F(s)
-limits 1 + mu s^2 and 1 + kappa; the PW92 high-density log coefficient equals
-A; H -> beta t^2 for small t and eps + H -> 0 for large t; complex-step
-derivatives against central finite differences.
+limits 1 + mu s^2 and 1 + kappa; H -> beta t^2 for small t and eps + H -> 0
+for large t; complex-step derivatives against central finite differences.
+The PW92 fit constants through the published expansions of the uniform gas:
+high density c0 = (1 - ln 2) / pi^2, c1 = 0.046644, no rs^(1/2) term,
+c2 = 0.00664 (A, b1, b2, a1); low density d0 = 0.4335, d1 = 1.4408 (a1, b3,
+b4).  The reduced gradients s^2, t^2 and beta, mu through the second-order
+gradient coefficient of correlation (Ma-Brueckner, 0.004235 in Hartree units),
+which PBE correlation reproduces and PBE exchange cancels at every density.
 """
 from __future__ import annotations
 

@@ -20,6 +20,7 @@
 // (for example on two streams) race on it and must be ordered by the caller.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "internal.h"
@@ -34,8 +35,10 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) double g_partials[kMaxPartials];
 
 // Device address of g_partials, looked up once per device with that device
-// current.  In host code the symbol name is only a host-side stand-in.
-double* g_partials_addr[kMaxDevices] = {nullptr};
+// current.  In host code the symbol name is only a host-side stand-in.  The
+// slots are atomics: a call may read a slot while another thread's first call
+// on the same device writes it (under g_setup_mutex).
+std::atomic<double*> g_partials_addr[kMaxDevices] = {};
 std::mutex g_setup_mutex;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -121,16 +124,17 @@ extern "C" kldi_status kldi_exc_energy_noalloc(int xc, int64_t npoints, const do
       set_error("kldi_exc_energy_noalloc: device ordinal %d out of range", dev);
       return KLDI_EUNSUPPORTED;
     }
-    double* part = g_partials_addr[dev];
+    double* part = g_partials_addr[dev].load(std::memory_order_acquire);
     if (!part) {
       // first call on this device: resolve the device address of the array
       std::lock_guard<std::mutex> lk(g_setup_mutex);
-      if (!g_partials_addr[dev]) {
+      part = g_partials_addr[dev].load(std::memory_order_relaxed);
+      if (!part) {
         void* p = nullptr;
         KLDI_TRY_CUDA(cudaGetSymbolAddress(&p, g_partials));
-        g_partials_addr[dev] = static_cast<double*>(p);
+        part = static_cast<double*>(p);
+        g_partials_addr[dev].store(part, std::memory_order_release);
       }
-      part = g_partials_addr[dev];
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_energy_partials<<<(unsigned)nb, kBlockPts, 0, s>>>(rho, grad, w, npoints, xc, rho_min, part);

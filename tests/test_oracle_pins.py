@@ -276,3 +276,54 @@ def test_executed_pairs_brute_force():
             dm = max(abs(D[m, n]) for m in range(32 * p, min(nbf, 32 * p + 32))
                      for n in range(32 * q, min(nbf, 32 * q + 32)))
             assert E1[i, j] == (dm >= t_b and b[p] * dm * b[q] >= t_d)
+
+
+# ---------------------------------------------------------------- PW92 / PBE constants
+# Published coefficients of the spin-unpolarised uniform gas (Perdew & Wang,
+# Phys. Rev. B 45, 13244 (1992)): high density eps_c = c0 ln rs - c1 + c2 rs ln rs
+# - c3 rs + ..., with no rs^(1/2) term; low density eps_c = -d0 / rs + d1 / rs^(3/2) + ...
+PW92_C1, PW92_C2 = 0.046644, 0.00664
+PW92_D0, PW92_D1 = 0.4335, 1.4408
+# Second-order gradient coefficient of correlation in the high-density limit
+# (Ma & Brueckner; the Rasolt-Geldart form 0.001667 + 0.002568 at rs = 0),
+# E_c^(2) = C_c int |grad rho|^2 / rho^(4/3), Hartree units.  PBE (Perdew, Burke,
+# Ernzerhof, Phys. Rev. Lett. 77, 3865 (1996)) fixes beta so that H -> beta t^2
+# reproduces it, and mu = beta pi^2 / 3 so that exchange cancels it.
+MA_BRUECKNER_CC = 0.004235
+
+
+def test_pw92_high_density_expansion():
+    """The oracle's eps_PW92 fitted on rs in [1e-10, 1e-6]: log coefficient
+    c0 = (1 - ln 2) / pi^2 (exact), constant -c1, no rs^(1/2) term, c2 rs ln rs.
+    A typo in A, b1, b2 or a1 moves one of these."""
+    rs = np.geomspace(1e-10, 1e-6, 40)
+    M = np.stack([np.log(rs), np.ones_like(rs), np.sqrt(rs), rs * np.log(rs), rs], 1)
+    c0, cst, half, c2, _ = np.linalg.lstsq(M, ox.eps_pw92(rs), rcond=None)[0]
+    assert abs(c0 - (1.0 - math.log(2.0)) / math.pi ** 2) < 1e-6
+    assert abs(-cst - PW92_C1) < 2e-6
+    assert abs(half) < 2e-6
+    assert abs(c2 - PW92_C2) < 1e-5
+
+
+def test_pw92_low_density_expansion():
+    """rs eps_PW92 fitted as a polynomial in u = rs^(-1/2) on rs in [1.1e3, 2.5e5]:
+    intercept -d0 and slope d1 (pins a1 / b4 and a1 b3 / b4^2)."""
+    u = np.linspace(0.002, 0.03, 40)
+    c = np.polynomial.polynomial.polyfit(u, ox.eps_pw92(u ** -2) * u ** -2, 5)
+    assert abs(-c[0] - PW92_D0) < 1e-4
+    assert abs(c[1] - PW92_D1) < 5e-4
+
+
+@pytest.mark.parametrize("rho", [1e-4, 1e-2, 1.0, 1e2, 1e4])
+def test_pbe_gradient_coefficients(rho):
+    """d f / d sigma at sigma = 0 (complex step) times rho^(4/3): correlation
+    gives the Ma-Brueckner coefficient at every density and exchange its
+    negative.  A factor in s^2 or t^2 (k_F, k_s, the 4 or 2 of the reduced
+    gradients), or a wrong beta or mu, moves them."""
+    r = np.array([rho], dtype=complex)
+    h = 1e-30 * rho ** (8.0 / 3.0)
+    s = np.array([1j * h])
+    cc = np.imag(ox.f_pbe_c(r, s))[0] / h * rho ** (4.0 / 3.0)
+    cx = np.imag(ox.f_pbe_x(r, s))[0] / h * rho ** (4.0 / 3.0)
+    assert abs(cc - MA_BRUECKNER_CC) < 1e-6
+    assert abs(cx + MA_BRUECKNER_CC) < 1e-6
