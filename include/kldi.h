@@ -67,12 +67,22 @@ typedef enum { KLDI_XC_LDA_X = 1, KLDI_XC_PBE = 2, KLDI_XC_MLP = 3 } kldi_xc;
  * Levels are combined and summed across K-segments in FP32/FP64 with
  * round-to-nearest.  Truncation error: 2^-16 (x3) or 2^-24 (x6) of the row /
  * column scale per element.
+ * KLDI_BF16X10: four slices on the grids 2^-7, 2^-15, 2^-23, 2^-31 and the
+ * ten products of levels 0..3; the basis values, X and the row-dot are
+ * formed in double-float (FP32 hi + lo, ~2^-44 relative), so the truncation
+ * error is 2^-32 of the row / column scale.  The density product keeps all
+ * four levels exact (N tiles of 64 functions); the V product keeps levels 0
+ * and 1 exact and accumulates levels 2 and 3 together (their rounding acts at
+ * ~2^-40 of the scale).  This is the mode that meets |dE_xc| <= 1e-6 Ha and
+ * max|dV| <= 1e-7 on whole grids of 10^7 points; it needs every basis block
+ * to fit a shared-memory shell record (40 shells, 80 primitives), else
+ * KLDI_EUNSUPPORTED.
  * KLDI_TF32X3: not provided (KLDI_EUNSUPPORTED): 11-bit slices cannot keep
  * 256-term partial sums exact, so the accumulator's rounding would bias the
  * result.
  * The functional, the E_xc reduction and the scatter into V are FP64 in
  * every mode. */
-typedef enum { KLDI_FP64 = 0, KLDI_BF16X3 = 1, KLDI_TF32X3 = 2, KLDI_BF16X6 = 3 } kldi_prec;
+typedef enum { KLDI_FP64 = 0, KLDI_BF16X3 = 1, KLDI_TF32X3 = 2, KLDI_BF16X6 = 3, KLDI_BF16X10 = 4 } kldi_prec;
 
 /* Atoms: natm nuclei, atomic numbers Z[natm], positions xyz[natm*3] in bohr. */
 typedef struct {
@@ -404,6 +414,29 @@ void kldi_mlp_free(kldi_mlp* mlp);
 
 /* Switch the product arithmetic of an existing plan (kldi_prec). */
 kldi_status kldi_plan_set_precision(kldi_plan* plan, int prec);
+
+/* ---- Bounded device waits (failure detection without a GPU fault) --------
+ * Every wait of the tensor-core kernels on an mbarrier (a copy that has not
+ * landed, a product not finished, a consumer not done) gives up after `ns`
+ * nanoseconds of the GPU's global timer (default 2e9), records a code in the
+ * plan's device error word and stops the kernel's other roles; the kernel
+ * still waits for its own copies and products in flight and frees its tensor
+ * memory before it exits.  The compute call then returns KLDI_ETIMEOUT (when
+ * it synchronises; otherwise the next synchronising call on the plan does)
+ * and the plan stays usable.  ns = 0 restores the default. */
+kldi_status kldi_plan_set_wait_limit(kldi_plan* plan, uint64_t ns);
+
+/* Test hook of the timeout path: the tensor-core V product does not hand out
+ * work item `item` (0-based, in the order its CTAs take items) to its
+ * consumers, whose bounded wait then runs out; nothing is in flight for that
+ * item.  -1 (the default) turns it off. */
+kldi_status kldi_plan_set_withhold(kldi_plan* plan, int64_t item);
+
+/* Self-test of the bounded wait: one CTA waits `limit_ns` nanoseconds on an
+ * mbarrier at which, with arrive = 0, nothing arrives (nothing else in
+ * flight); returns KLDI_ETIMEOUT, or KLDI_OK when arrive = 1.  Synchronises
+ * `stream` (a cudaStream_t, NULL = legacy default stream). */
+kldi_status kldi_selftest_wait(uint64_t limit_ns, int arrive, void* stream);
 
 void kldi_plan_free(kldi_plan* plan);
 void kldi_grid_free(kldi_grid* grid);

@@ -15,7 +15,9 @@ and for the GGA the standard semilocal generalisation
 
 The screened form restricts every product to the executed block pairs of
 ``oracle.screen`` (Eq. executed_block_output): non-executed 32 x 32 blocks of D
-(for R) and of Phi^T X (for V) contribute nothing.  The dense form keeps all.
+(for R) contribute nothing, and a block (p, q) of a grid block's
+Phi^T X + X^T Phi is added, both terms, when (p, q) or (q, p) is an executed
+pair of the potential product.  The dense form keeps all.
 
 Pins (tests): the closed-form Slater exchange energy of one doubly occupied
 normalised s-Gaussian; sum w rho = tr(D S); V = V^T; tr(D V) = 4/3 E_x for
@@ -128,15 +130,16 @@ def evaluate(system, grid, shells=None, screened=True, blocks=None, want_v=True,
         if gga:
             X += 2.0 * (w * vs)[:, None] * np.einsum("ic,cim->im", grad, dph)
         Vg = ph.T @ X
+        Vg = Vg + Vg.T
         if screened:
             x = np.zeros(nb)
             ax = np.abs(X)
             for i, p in enumerate(S):
                 x[p] = ax[:, cb == i].max()
             E2 = oscreen.executed_v(S, b, x, t_b, t_d)
-            Vg *= E2[np.ix_(cb, cb)]
+            Vg *= (E2 | E2.T)[np.ix_(cb, cb)]
             if keep_lists:
                 res.lists[g]["x"] = x
                 res.lists[g]["E2"] = E2.copy()
-        res.V[np.ix_(cols, cols)] += Vg + Vg.T
+        res.V[np.ix_(cols, cols)] += Vg
     return res

@@ -17,6 +17,12 @@ Readings (the paper defines the rule for a generic product C = A B):
   * potential product Phi^T X: executed pairs
       E2_g = {(p, q) in S_g x S_g : x_gq >= t_b and b_gp x_gq >= t_d},
     x_gq = max |X_i nu| over i in g, nu in q.
+  * the symmetric potential V = Phi^T X + X^T Phi: block (p, q) of grid
+    block g's contribution is computed, both terms, when (p, q) or (q, p)
+    is in E2_g (the paper writes only the symmetric LDA product
+    Phi^T W Phi, whose block pair {p, q} is one block of one product; the
+    rule is applied to the unordered pair, so no block gets one of its two
+    terms without the other).
 
 Pins (tests): Alg. 1 against numpy.nonzero; the pair sets against a
 brute-force triple loop over elements.

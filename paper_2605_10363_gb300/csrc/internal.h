@@ -117,6 +117,7 @@ struct GridView {
   const double* xyz;   // [npoints*3]
   const double* w;     // [npoints]
   const float4* prel;  // [npoints] FP32 point coordinates relative to the block's anchor atom
+  const float4* prel_lo;  // [npoints] their low parts (coordinate - hi, rounded to FP32)
   const int32_t* anchor;  // [nblocks] anchor atom of each grid block (atom of its first point)
   int64_t npoints;
   int64_t nblocks;
@@ -202,6 +203,8 @@ struct kldi_plan {
   int64_t nbf = 0, nbb = 0, nbf_pad = 0, npoints = 0, nblocks = 0, ntiles = 0, nshell = 0, nprim_total = 0;
   int64_t nvt = 0;  // 128-function V tiles per edge (ceil(nbb / 4))
   int* d_err = nullptr;         // device error word (bounded-wait timeouts)
+  uint64_t wait_ns = 2000000000ull;   // limit of the tensor-core kernels' bounded waits
+  int64_t withhold_item = -1;   // test hook: V work item not handed out (-1: none)
   int* d_vnext = nullptr;       // work-item counter of the tensor-core V product
   double* d_G = nullptr;        // [natm][3] nuclear gradient (allocated by the first kldi_exc_grad)
 
@@ -213,6 +216,7 @@ struct kldi_plan {
   double* d_xyz = nullptr;
   double* d_w = nullptr;
   float4* d_prel = nullptr;
+  float4* d_prel_lo = nullptr;
   int32_t* d_anchor = nullptr;
   float* d_relatom = nullptr;
   int32_t natm = 0;
@@ -248,7 +252,7 @@ struct kldi_plan {
   // tiles of the current batch
   double* d_phi64 = nullptr;    // FP64: [tiles][32][128]
   double* d_x64 = nullptr;      // FP64: [tiles][32][128]
-  uint16_t* d_phi_s = nullptr;  // Phi sliced per point: [tiles][NS planes][128][32] BF16
+  uint16_t* d_phi_s = nullptr;  // Phi sliced per point: [tiles][NS planes][128][32] BF16 (room for 4 planes)
   uint16_t* d_phic_s = nullptr; // Phi sliced per function: [tiles][NS planes][128][32] BF16
   uint16_t* d_x_s = nullptr;    // X sliced per function: [tiles][NS planes][128][32] BF16
   float* d_phic_scale = nullptr;// [tiles][32] function scales of d_phic_s

@@ -8,7 +8,7 @@
 //         rho_i = sum_q Phi_q . R_q and grad rho_i = 2 sum_q grad Phi_q . R_q
 //         (Eq. executed_block_output; App. A density).
 //   V:    per basis-block pair p <= q over its list of grid blocks,
-//         V_pq += [E2(p,q)] Phi_p^T X_q + [E2(q,p)] X_p^T Phi_q.
+//         V_pq += [E2(p,q) or E2(q,p)] (Phi_p^T X_q + X_p^T Phi_q).
 #include <cfloat>
 
 #include "basis.cuh"
@@ -307,9 +307,11 @@ __global__ void __launch_bounds__(256) k_v64(ListView L, const VWork64* work, co
     const int tq = L.tile_of[g * L.nbb + wk.q];
     const double xp = xmax[tp], xq = xmax[tq];
     const double bp = L.bmax[tp], bq = L.bmax[tq];
-    const bool m1 = xq >= t_b && bp * xq >= t_d;   // (p, q) in E2_g
-    const bool m2 = xp >= t_b && bq * xp >= t_d;   // (q, p) in E2_g
-    if (!m1 && !m2) continue;
+    // block (p, q) of Phi^T X + X^T Phi is computed, both terms, when (p, q)
+    // or (q, p) is in E2_g (the pair rule applied to the unordered pair)
+    const bool m1 = (xq >= t_b && bp * xq >= t_d) || (xp >= t_b && bq * xp >= t_d);
+    const bool m2 = m1;
+    if (!m1) continue;
     __syncthreads();
     const double* sp = phi + (int64_t)(tp - t0) * (kBasisBlk * kBlockPts);
     const double* sq = phi + (int64_t)(tq - t0) * (kBasisBlk * kBlockPts);

@@ -42,6 +42,7 @@ GridView kldi_plan::grid_view() const {
   v.xyz = d_xyz;
   v.w = d_w;
   v.prel = d_prel;
+  v.prel_lo = d_prel_lo;
   v.anchor = d_anchor;
   v.npoints = npoints;
   v.nblocks = nblocks;
@@ -84,7 +85,7 @@ kldi_status upload(kldi_plan* P, T** p, const T* h, size_t count) {
 
 void free_plan_buffers(kldi_plan* P) {
   free_own_tile_buffers(P);
-  void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
+  void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_prel_lo, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
                   P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
                   P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero};
@@ -117,12 +118,12 @@ void free_own_tile_buffers(kldi_plan* P) {
 // Bytes of the per-tile buffers each precision mode needs.
 int64_t tile_bytes_for(int prec) {
   if (prec == KLDI_FP64) return 2LL * kBasisBlk * kBlockPts * 8;        // Phi and X tiles, FP64
-  return 3LL * 3 * kBasisBlk * kBlockPts * 2 + 2LL * kBasisBlk * 4;      // Phi (two slicings) and X, 3 planes
+  return 3LL * 4 * kBasisBlk * kBlockPts * 2 + 2LL * kBasisBlk * 4;   // Phi (two slicings) and X, up to 4 planes
 }
 
 // Largest per-tile footprint of the precision modes (the shared workspace
 // holds either layout).
-int64_t tile_bytes_max() { return std::max(tile_bytes_for(KLDI_FP64), tile_bytes_for(KLDI_BF16X6)); }
+int64_t tile_bytes_max() { return std::max(tile_bytes_for(KLDI_FP64), tile_bytes_for(KLDI_BF16X10)); }
 
 void free_work_lists(kldi_plan* P) {
   for (auto& b : P->batches) {
@@ -242,11 +243,11 @@ kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
     const int64_t cap = P->tile_cap;
     P->d_phi64 = reinterpret_cast<double*>(base);
     P->d_x64 = P->d_phi64 + cap * kBasisBlk * kBlockPts;
-    const size_t plane3 = (size_t)cap * 3 * kBasisBlk * kBlockPts;
+    const size_t plane4 = (size_t)cap * 4 * kBasisBlk * kBlockPts;   // up to four planes per tile
     P->d_phi_s = reinterpret_cast<uint16_t*>(base);
-    P->d_phic_s = P->d_phi_s + plane3;
-    P->d_x_s = P->d_phic_s + plane3;
-    P->d_phic_scale = reinterpret_cast<float*>(P->d_x_s + plane3);
+    P->d_phic_s = P->d_phi_s + plane4;
+    P->d_x_s = P->d_phic_s + plane4;
+    P->d_phic_scale = reinterpret_cast<float*>(P->d_x_s + plane4);
     P->d_x_scale = P->d_phic_scale + cap * kBasisBlk;
   }
   if (prec == KLDI_FP64) {
@@ -254,7 +255,13 @@ kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
     if (!P->d_x64) KLDI_TRY(dalloc(P, &P->d_x64, (size_t)P->tile_cap * kBasisBlk * kBlockPts));
     return KLDI_OK;
   }
-  const size_t per_tile = (size_t)3 * kBasisBlk * kBlockPts;  // 16-bit words, up to 3 planes
+  if (prec == KLDI_BF16X10 && !P->rec_fit_all) {
+    set_error("KLDI_BF16X10: a basis block has more than 40 shells or 80 primitives");
+    return KLDI_EUNSUPPORTED;
+  }
+  // 16-bit words per tile: four planes, the most any mode uses (so a plan can
+  // switch modes without reallocating; the batch capacity assumes this size)
+  const size_t per_tile = (size_t)4 * kBasisBlk * kBlockPts;
   if (!P->d_phi_s) KLDI_TRY(dalloc(P, &P->d_phi_s, (size_t)P->tile_cap * per_tile));
   if (!P->d_phic_s) KLDI_TRY(dalloc(P, &P->d_phic_s, (size_t)P->tile_cap * per_tile));
   if (!P->d_x_s) KLDI_TRY(dalloc(P, &P->d_x_s, (size_t)P->tile_cap * per_tile));
@@ -263,7 +270,7 @@ kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
   if (!P->d_rowscale) KLDI_TRY(dalloc(P, &P->d_rowscale, (size_t)P->npoints));
   if (!P->d_pscale) KLDI_TRY(dalloc(P, &P->d_pscale, (size_t)P->npoints));
   if (!P->d_dscale) KLDI_TRY(dalloc(P, &P->d_dscale, (size_t)P->nbf_pad));
-  if (!P->d_dsplit) KLDI_TRY(dalloc(P, &P->d_dsplit, (size_t)P->nbb * P->nbb * 3 * kBasisBlk * kBasisBlk));
+  if (!P->d_dsplit) KLDI_TRY(dalloc(P, &P->d_dsplit, (size_t)P->nbb * P->nbb * 4 * kBasisBlk * kBasisBlk));
   if (!P->d_zero) {
     KLDI_TRY(dalloc(P, &P->d_zero, (size_t)kBasisBlk * kBlockPts));
     KLDI_TRY_CUDA(cudaMemset(P->d_zero, 0, (size_t)kBasisBlk * kBlockPts * sizeof(uint16_t)));
@@ -284,7 +291,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
       set_error("kldi_screen: empty or incomplete basis");
       return KLDI_EINVAL;
     }
-    if (opt->prec < KLDI_FP64 || opt->prec > KLDI_BF16X6 || opt->xc < KLDI_XC_LDA_X || opt->xc > KLDI_XC_MLP) {
+    if (opt->prec < KLDI_FP64 || opt->prec > KLDI_BF16X10 || opt->xc < KLDI_XC_LDA_X || opt->xc > KLDI_XC_MLP) {
       set_error("kldi_screen: bad precision or functional");
       return KLDI_EINVAL;
     }
@@ -423,14 +430,22 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
       const int natm = mol->natm;
       P->natm = natm;
       std::vector<int32_t> anchor(grid->nblocks);
-      std::vector<float4> prel(grid->npoints);
+      std::vector<float4> prel(grid->npoints), prel_lo(grid->npoints);
       for (int64_t g = 0; g < grid->nblocks; ++g) {
         const int a = grid->atom[g * kBlockPts];
         anchor[g] = a;
         for (int i = 0; i < kBlockPts; ++i) {
           const int64_t k = g * kBlockPts + i;
-          prel[k] = make_float4((float)(grid->xyz[k * 3] - mol->xyz[3 * a]), (float)(grid->xyz[k * 3 + 1] - mol->xyz[3 * a + 1]),
-                                (float)(grid->xyz[k * 3 + 2] - mol->xyz[3 * a + 2]), 0.f);
+          double d[3];
+          float h[3];
+          for (int c = 0; c < 3; ++c) {
+            d[c] = grid->xyz[k * 3 + c] - mol->xyz[3 * a + c];
+            h[c] = (float)d[c];
+          }
+          prel[k] = make_float4(h[0], h[1], h[2], 0.f);
+          // low parts for the double-float (BF16X10) basis values
+          prel_lo[k] = make_float4((float)(d[0] - (double)h[0]), (float)(d[1] - (double)h[1]),
+                                   (float)(d[2] - (double)h[2]), 0.f);
         }
       }
       std::vector<float> rel((size_t)natm * natm * 8, 0.f);
@@ -445,6 +460,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
         }
       if ((st = upload(P, &P->d_anchor, anchor.data(), anchor.size())) != KLDI_OK) return fail(st);
       if ((st = upload(P, &P->d_prel, prel.data(), prel.size())) != KLDI_OK) return fail(st);
+      if ((st = upload(P, &P->d_prel_lo, prel_lo.data(), prel_lo.size())) != KLDI_OK) return fail(st);
       if ((st = upload(P, &P->d_relatom, rel.data(), rel.size())) != KLDI_OK) return fail(st);
     }
     if ((st = upload(P, &P->d_w, grid->w.data(), grid->w.size())) != KLDI_OK) return fail(st);
@@ -617,7 +633,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
 
 extern "C" kldi_status kldi_plan_set_precision(kldi_plan* P, int prec) {
   return kldi::guarded("kldi_plan_set_precision", [&]() -> kldi_status {
-    if (!P || prec < KLDI_FP64 || prec > KLDI_BF16X6) {
+    if (!P || prec < KLDI_FP64 || prec > KLDI_BF16X10) {
       set_error("kldi_plan_set_precision: bad argument");
       return KLDI_EINVAL;
     }
@@ -709,6 +725,28 @@ extern "C" kldi_status kldi_plan_set_block_range(kldi_plan* P, int64_t g0, int64
     P->range_g0 = g0;
     P->range_g1 = g1;
     return build_work(P, P->tile_cap);
+  });
+}
+
+extern "C" kldi_status kldi_plan_set_wait_limit(kldi_plan* P, uint64_t ns) {
+  return kldi::guarded("kldi_plan_set_wait_limit", [&]() -> kldi_status {
+    if (!P) {
+      set_error("kldi_plan_set_wait_limit: null plan");
+      return KLDI_EINVAL;
+    }
+    P->wait_ns = ns ? ns : 2000000000ull;
+    return KLDI_OK;
+  });
+}
+
+extern "C" kldi_status kldi_plan_set_withhold(kldi_plan* P, int64_t item) {
+  return kldi::guarded("kldi_plan_set_withhold", [&]() -> kldi_status {
+    if (!P || item < -1) {
+      set_error("kldi_plan_set_withhold: bad argument");
+      return KLDI_EINVAL;
+    }
+    P->withhold_item = item;
+    return KLDI_OK;
   });
 }
 

@@ -38,15 +38,24 @@
 //  k_v_tc       V = Phi^T X + X^T Phi, one 128 x 128 tile pair P <= Q over a
 //               segment of its grid-block list; one grid block per exact
 //               accumulation (K = 256: [Phi~ | X~] against [X~ ; Phi~]),
-//               drained into compensated FP32 sums, FP64 scatter-add; the
-//               lower block triangle is mirrored afterwards.
+//               drained into compensated FP32 sums with the 32 x 32 block
+//               pairs that are not executed for that grid block left out,
+//               FP64 scatter-add; the lower block triangle is mirrored
+//               afterwards.
+//  BF16X10 (four slices): k_phi_split4 and k_x_split4 evaluate the basis in
+//  double-float (basis_df.cuh) and cut hi + lo into four slices; k_rho_tc<4>
+//  keeps four exact levels in N = 64 tiles (two TMEM buffers) and forms R and
+//  the row-dot in double-float; k_v_tc<4> keeps levels 0 and 1 exact and
+//  accumulates levels 2 and 3 together.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <mutex>
 
 #include "basis.cuh"
+#include "basis_df.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -89,7 +98,12 @@ __device__ __forceinline__ void slice(float a, float* s) {  // |a| <= 1
     r = __fsub_rn(r, s1);
     s[1] = s1;
   }
-  if (NS >= 3) s[2] = __fsub_rn(__fadd_rn(r, C2), C2);
+  if (NS >= 3) {
+    const float s2 = __fsub_rn(__fadd_rn(r, C2), C2);
+    r = __fsub_rn(r, s2);
+    s[2] = s2;
+  }
+  if (NS >= 4) s[3] = __fsub_rn(__fadd_rn(r, 0.005859375f), 0.005859375f);   // grid 2^-31 (1.5 x 2^-8)
 }
 
 template <int NS>
@@ -102,7 +116,12 @@ __device__ __forceinline__ void slice_d(double a, float* s) {  // |a| <= 1, FP64
     r = r - s1;
     s[1] = (float)s1;
   }
-  if (NS >= 3) s[2] = (float)(rint(r * 8388608.0) / 8388608.0);
+  if (NS >= 3) {
+    const double s2 = rint(r * 8388608.0) / 8388608.0;
+    r = r - s2;
+    s[2] = (float)s2;
+  }
+  if (NS >= 4) s[3] = (float)(rint(r * 2147483648.0) / 2147483648.0);
 }
 
 __device__ __forceinline__ uint32_t pack2(float a, float b) {   // a in the low half
@@ -132,12 +151,48 @@ __device__ __forceinline__ void store_sliced_row(uint8_t* base, int pstride, int
   }
 }
 
+// Row `row` of four swizzled planes from 32 double-float values (vh + vl,
+// |v| <= 1): the digits of slice4_df.
+__device__ __forceinline__ void store_sliced_row4(uint8_t* base, int pstride, int row, const float* vh,
+                                                  const float* vl) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint32_t w[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s0[4], s1[4];
+      slice4_df(vh[c * 8 + 2 * k], vl[c * 8 + 2 * k], s0);
+      slice4_df(vh[c * 8 + 2 * k + 1], vl[c * 8 + 2 * k + 1], s1);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) w[l][k] = pack2(s0[l], s1[l]);
+    }
+    const uint32_t off = swz64_off(row, c * 8);
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      *reinterpret_cast<uint4*>(base + l * pstride + off) = make_uint4(w[l][0], w[l][1], w[l][2], w[l][3]);
+  }
+}
+
 // Row `row` of a chunk-major tile: rows 32 kc .. 32 kc + 31 of all NS planes
 // are contiguous ([kc][plane][32 rows x 64 B], each 2 KB chunk swizzled as a
 // plane), so one bulk copy of NS x 2 KB moves a K = 32 chunk of every plane.
 template <int NS>
 __device__ __forceinline__ void store_sliced_row_kc(uint8_t* base, int row, const float* v) {
   store_sliced_row<NS>(base + (row >> 5) * (NS * 2048) - (row & ~31) * 64, 2048, row, v);
+}
+__device__ __forceinline__ void store_sliced_row4_kc(uint8_t* base, int row, const float* vh, const float* vl) {
+  store_sliced_row4(base + (row >> 5) * (4 * 2048) - (row & ~31) * 64, 2048, row, vh, vl);
+}
+
+// Slices per operand of a tensor-core precision mode.
+inline int slices_of(int prec) { return prec == KLDI_BF16X10 ? 4 : (prec == KLDI_BF16X6 ? 3 : 2); }
+
+// 2^(j/256), j = 0..255, as FP32 hi / lo pairs: the table of exp_df.  Filled
+// once per device (prepare_tc_kernels); kernels copy it to shared memory.
+__device__ float2 g_exp2_tab[256];
+
+__device__ __forceinline__ void load_exp_tab(float2* dst, int t, int nthr) {
+  for (int j = t; j < 256; j += nthr) dst[j] = g_exp2_tab[j];
 }
 
 
@@ -201,7 +256,11 @@ static kldi_status dsplit_ns(const kldi_plan* P, const double* D, cudaStream_t s
 }
 
 kldi_status launch_dsplit(const kldi_plan* P, const double* D, cudaStream_t s) {
-  return P->prec == KLDI_BF16X6 ? dsplit_ns<3>(P, D, s) : dsplit_ns<2>(P, D, s);
+  switch (slices_of(P->prec)) {
+    case 4: return dsplit_ns<4>(P, D, s);
+    case 3: return dsplit_ns<3>(P, D, s);
+    default: return dsplit_ns<2>(P, D, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -274,6 +333,64 @@ __global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, List
 #pragma unroll
     for (int nu = 0; nu < kBasisBlk; ++nu) v[nu] = st[nu][i] * rinv;
     store_sliced_row<NS>(out_row + (int64_t)(j - t0) * tile_bytes(NS), kPlaneBytes, i, v);
+  }
+}
+
+// BF16X10 Phi tiles: the point scale as in k_phi_split, then the values in
+// double-float (hi / lo staged in shared memory) cut into four slices.  Every
+// basis block must fit a shared-memory shell record (checked on the host).
+__global__ void __launch_bounds__(128) k_phi_split4(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
+                                                    uint8_t* out_row, float* rowscale) {
+  __shared__ float sth[kBasisBlk][kBlockPts + 1];
+  __shared__ float stl[kBasisBlk][kBlockPts + 1];
+  __shared__ BlockRec rec[2];
+  __shared__ float2 tab[256];
+  const int64_t g = g0 + blockIdx.x;
+  const int i = threadIdx.x;
+  const int64_t pt = g * kBlockPts + i;
+  load_exp_tab(tab, i, kBlockPts);
+  const float4 pr = G.prel[pt], pl = G.prel_lo[pt];
+  const f2 px{pr.x, pl.x}, py{pr.y, pl.y}, pz{pr.z, pl.z};
+  const int anc = G.anchor[g];
+  const int tb = L.blk_ptr[g], te = L.blk_ptr[g + 1];
+  // pass 1: point scale from the shell bound r^l sum_k |c_k| exp(-a_k r^2) (FP32, 1.001 margin)
+  float M = 0.f;
+  for (int j = tb; j < te; ++j) {
+    BlockRec* rc = rec + ((j - tb) & 1);
+    stage_block_rec(B, L.blk_idx[j], anc, rc, i, kBlockPts);
+    __syncthreads();
+    for (int s = 0; s < rc->nshell; ++s) {
+      const float4 c0 = rc->c0[s], c1 = rc->c1[s];
+      const int hdr = __float_as_int(c1.z), l = hdr & 255, np = (hdr >> 8) & 255;
+      const float4* pf = rc->pf + __float_as_int(c1.w);
+      const float dx = (pr.x - c0.x) - c0.w, dy = (pr.y - c0.y) - c1.x, dz = (pr.z - c0.z) - c1.y;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      float sum = 0.f;
+      for (int k = 0; k < np; ++k) sum += fabsf(pf[k].z) * __expf(-pf[k].x * r2);
+      M = fmaxf(M, (l == 0 ? 1.f : (l == 1 ? sqrtf(r2) : r2)) * sum);
+    }
+  }
+  const float rs = pow2_ceil(M * 1.001f);
+  rowscale[pt] = rs;
+  const float rinv = 1.f / rs;
+  // pass 2: double-float values of every retained tile, four slices per point
+  for (int j = tb; j < te; ++j) {
+    BlockRec* rc = rec + ((j - tb + te - tb) & 1);
+    stage_block_rec(B, L.blk_idx[j], anc, rc, i, kBlockPts);
+#pragma unroll
+    for (int nu = 0; nu < kBasisBlk; ++nu) sth[nu][i] = stl[nu][i] = 0.f;
+    __syncthreads();
+    for_rec_functions_df<false>(rc, tab, px, py, pz, [&](int nu, f2 v, f2, f2, f2) {
+      sth[nu][i] = v.h;
+      stl[nu][i] = v.l;
+    });
+    float vh[kBasisBlk], vl[kBasisBlk];
+#pragma unroll
+    for (int nu = 0; nu < kBasisBlk; ++nu) {
+      vh[nu] = sth[nu][i] * rinv;
+      vl[nu] = stl[nu][i] * rinv;
+    }
+    store_sliced_row4(out_row + (int64_t)(j - t0) * tile_bytes(4), kPlaneBytes, i, vh, vl);
   }
 }
 
@@ -355,7 +472,19 @@ static kldi_status phi_ns(const kldi_plan* P, const Batch& b, cudaStream_t s) {
 }
 
 kldi_status launch_phi_split(const kldi_plan* P, const Batch& b, cudaStream_t s) {
-  return P->prec == KLDI_BF16X6 ? phi_ns<3>(P, b, s) : phi_ns<2>(P, b, s);
+  switch (slices_of(P->prec)) {
+    case 4: {
+      const int64_t n = b.g1 - b.g0;
+      if (n == 0) return KLDI_OK;
+      KLDI_TRY(prepare_tc_kernels());   // the exp table
+      k_phi_split4<<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.t0,
+                                                     reinterpret_cast<uint8_t*>(P->d_phi_s), P->d_rowscale);
+      KLDI_TRY_CUDA(cudaGetLastError());
+      return KLDI_OK;
+    }
+    case 3: return phi_ns<3>(P, b, s);
+    default: return phi_ns<2>(P, b, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -442,6 +571,81 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
   if (i == 0) xmax[t] = (double)fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
 }
 
+// BF16X10 V-product operands: as k_x_split, with Phi and X in double-float
+// (hi / lo staged in dynamic shared memory, four [32][129] arrays) and four
+// slices per function.
+constexpr int kX4Smem = 4 * kBasisBlk * (kBlockPts + 1) * 4;
+
+template <bool GRAD>
+__global__ void __launch_bounds__(128) k_x_split4(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
+                                                  const double* __restrict__ xcoef, const float* __restrict__ pscale,
+                                                  uint8_t* out_phi, float* phi_scale, uint8_t* out_x, float* x_scale,
+                                                  double* xmax) {
+  extern __shared__ float xsm[];
+  float(*sph)[kBlockPts + 1] = reinterpret_cast<float(*)[kBlockPts + 1]>(xsm);
+  float(*spl)[kBlockPts + 1] = sph + kBasisBlk;
+  float(*sxh)[kBlockPts + 1] = spl + kBasisBlk;
+  float(*sxl)[kBlockPts + 1] = sxh + kBasisBlk;
+  __shared__ float cp[kBasisBlk], cx[kBasisBlk], rawx[kBasisBlk];
+  __shared__ BlockRec rec;
+  __shared__ float2 tab[256];
+  const int64_t t = t0 + blockIdx.x;
+  const int64_t g = L.tile_g[t];
+  const int p = L.blk_idx[t];
+  const int i = threadIdx.x;
+  const int64_t pt = g * kBlockPts + i;
+  load_exp_tab(tab, i, kBlockPts);
+  const float c = pscale[pt], cinv = c > 0.f ? 1.f / c : 0.f;   // c = 0: X = 0 at this point
+  const f2 a = df_from_double(xcoef[pt * 4]), bx = df_from_double(xcoef[pt * 4 + 1]),
+           by = df_from_double(xcoef[pt * 4 + 2]), bz = df_from_double(xcoef[pt * 4 + 3]);
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) sph[nu][i] = spl[nu][i] = sxh[nu][i] = sxl[nu][i] = 0.f;
+  const float4 pr = G.prel[pt], pl = G.prel_lo[pt];
+  stage_block_rec(B, p, G.anchor[g], &rec, i, kBlockPts);
+  __syncthreads();
+  for_rec_phix_df<GRAD>(&rec, tab, f2{pr.x, pl.x}, f2{pr.y, pl.y}, f2{pr.z, pl.z}, a, bx, by, bz,
+                        [&](int nu, f2 v, f2 x) {
+                          sph[nu][i] = v.h * c;
+                          spl[nu][i] = v.l * c;
+                          sxh[nu][i] = x.h * cinv;
+                          sxl[nu][i] = x.l * cinv;
+                        });
+  __syncthreads();
+  column_scales(sph, cp, nullptr);
+  column_scales(sxh, cx, rawx);
+  __syncthreads();
+  if (i < kBasisBlk) {
+    cp[i] = fmaxf(cp[i], cx[i]);
+    cx[i] = 1.f / cp[i];            // exact: the scales are powers of two
+  }
+  __syncthreads();
+  float vh[kBasisBlk], vl[kBasisBlk];
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) {
+    vh[nu] = sph[nu][i] * cx[nu];
+    vl[nu] = spl[nu][i] * cx[nu];
+  }
+  store_sliced_row4_kc(out_phi + (t - t0) * tile_bytes(4), i, vh, vl);
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) {
+    vh[nu] = sxh[nu][i] * cx[nu];
+    vl[nu] = sxl[nu][i] * cx[nu];
+  }
+  store_sliced_row4_kc(out_x + (t - t0) * tile_bytes(4), i, vh, vl);
+  if (i < kBasisBlk) {
+    phi_scale[(t - t0) * kBasisBlk + i] = cp[i];
+    x_scale[(t - t0) * kBasisBlk + i] = cp[i];
+  }
+  float mx = 0.f;
+#pragma unroll
+  for (int nu = 0; nu < kBasisBlk; ++nu) mx = fmaxf(mx, fabsf(sxh[nu][i]) * c);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((i & 31) == 0) rawx[i >> 5] = mx;
+  __syncthreads();
+  if (i == 0) xmax[t] = (double)fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
+}
+
 template <int NS>
 static kldi_status x_ns(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   const int64_t n = b.t1 - b.t0;
@@ -460,52 +664,141 @@ static kldi_status x_ns(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   return KLDI_OK;
 }
 
+static kldi_status x_ns4(const kldi_plan* P, const Batch& b, cudaStream_t s) {
+  const int64_t n = b.t1 - b.t0;
+  if (n == 0) return KLDI_OK;
+  KLDI_TRY(prepare_tc_kernels());
+  uint8_t* op = reinterpret_cast<uint8_t*>(P->d_phic_s);
+  uint8_t* ox = reinterpret_cast<uint8_t*>(P->d_x_s);
+  if (P->gga)
+    k_x_split4<true><<<(unsigned)n, kBlockPts, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                             b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
+                                                             P->d_x_scale, P->d_xmax);
+  else
+    k_x_split4<false><<<(unsigned)n, kBlockPts, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                              b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
+                                                              P->d_x_scale, P->d_xmax);
+  KLDI_TRY_CUDA(cudaGetLastError());
+  return KLDI_OK;
+}
+
 kldi_status launch_x_split(const kldi_plan* P, const Batch& b, cudaStream_t s) {
-  return P->prec == KLDI_BF16X6 ? x_ns<3>(P, b, s) : x_ns<2>(P, b, s);
+  switch (slices_of(P->prec)) {
+    case 4: return x_ns4(P, b, s);
+    case 3: return x_ns<3>(P, b, s);
+    default: return x_ns<2>(P, b, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
-// MMA issue of one K = 16 step for all slice products of levels < NS.
-template <int NS>
+// MMA issue of one K = 16 step for all slice products of levels < NS.  Level
+// l goes to accumulator min(l, NACC - 1): with NACC < NS the smallest levels
+// share the last accumulator (BF16X10 V product: levels 2 and 3).
+template <int NS, int NACC = NS>
 __device__ __forceinline__ void issue_levels(uint32_t d0, uint32_t lstride, const uint64_t* a, const uint64_t* b,
                                              uint32_t idesc, uint32_t* started) {
 #pragma unroll
   for (int l = 0; l < NS; ++l) {
+    const int acc = l < NACC ? l : NACC - 1;
 #pragma unroll
     for (int i = 0; i <= l; ++i) {
-      mma_f16(d0 + l * lstride, a[i], b[l - i], idesc, started[l]);
-      started[l] = 1;
+      mma_f16(d0 + acc * lstride, a[i], b[l - i], idesc, started[acc]);
+      started[acc] = 1;
     }
   }
 }
 
 // Density product, persistent: one CTA per SM walks grid blocks g0 + c,
-// g0 + c + G, ...  576 threads: warp 0 = producer (all lanes build the next
-// block's retained list and executed-pair bit matrix with warp ballots into a
+// g0 + c + G, ...  Warp 0 = producer (all lanes build the next block's
+// retained list and executed-pair bit matrix with warp ballots into a
 // double-buffered shared-memory record, then issue each chunk's bulk copies
-// together),
-// warp 1 = TMEM owner and MMA issuer, warps 2..17 = epilogue (lane quarter =
-// warp % 4; the four warps of a quarter take one basis block of each N tile
-// each; their partial rho and grad rho are summed in a fixed order).
+// together), warp 1 = TMEM owner and MMA issuer, the remaining kEpi warps =
+// epilogue (lane quarter = warp % 4; the warps of a quarter take one basis
+// block of each N tile each; their partial rho and grad rho are summed in a
+// fixed order).  BF16X6 / BF16X3: N tiles of 4 basis blocks, 16 epilogue
+// warps; BF16X10: N tiles of 2 basis blocks so that two buffers of the four
+// level accumulators fit TMEM (drains and row-dot overlap the next tile's
+// products), 8 epilogue warps, R and the row-dot in double-float.
 template <int NS>
 struct RhoCfg {
-  static constexpr int kNQ = 4;                                   // q blocks per N tile (N = 128)
-  static constexpr int kEpi = 16;                                 // epilogue warps: 4 lane quarters x 4 q blocks
-  static constexpr int kBufCols = NS * 128;                       // NS level accumulators
-  static constexpr int kBufs = NS == 2 ? 2 : 1;
+  static constexpr int kNQ = NS == 4 ? 2 : 4;                     // q blocks per N tile
+  static constexpr int kEpi = 4 * kNQ;                            // epilogue warps: 4 lane quarters x kNQ
+  static constexpr int kLevelCols = 32 * kNQ;                     // TMEM columns of one level accumulator
+  static constexpr int kBufCols = NS * kLevelCols;                // NS level accumulators
+  static constexpr int kBufs = 2 * kBufCols <= 512 ? 2 : 1;
   static constexpr int kStageBytes = NS * kPlaneBytes + NS * kNQ * kDPlane;
   static constexpr int kStages = NS == 2 ? 3 : 2;
-  static constexpr int kOffR = kStages * kStageBytes;             // [4 q blocks][32][128] float
-  static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * 4;   // [4 q blocks][4][128] double
+  static constexpr int kRsElem = NS == 4 ? 8 : 4;                 // R staged as FP32, or hi / lo pairs
+  static constexpr int kOffR = kStages * kStageBytes;             // [kNQ q blocks][32][128] R
+  static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * kRsElem;   // [kNQ][4][128] double
   static constexpr int kMetaWords = 4 + kMaxRet + kMaxRet * (kMaxRet / 32);
   static constexpr int kOffMeta = kOffRed + kNQ * 4 * kBlockPts * 8;
-  static constexpr int kOffRec = kOffMeta + 2 * kMetaWords * 4;  // [4 q blocks][2] BlockRec
-  static constexpr int kOffBar = kOffRec + 2 * kNQ * (int)sizeof(BlockRec);
+  static constexpr int kOffRec = kOffMeta + 2 * kMetaWords * 4;  // [kNQ q blocks][2] BlockRec
+  static constexpr int kOffTab = kOffRec + 2 * kNQ * (int)sizeof(BlockRec);
+  static constexpr int kOffBar = kOffTab + (NS == 4 ? 256 * 8 : 0);
   static constexpr int kSmem = kOffBar + 256 + 1024;
   static constexpr int kSegChunks = 8;                            // 8 x 32 = 256 K per exact accumulation
   static constexpr int kThreads = 64 + 32 * kEpi;
   static_assert(kSmem <= 232448, "shared memory");
+  static_assert(kBufs * kBufCols <= 512, "TMEM");
 };
+
+// Row-dot of one basis block in double-float (BF16X10): with R_nu (hi / lo,
+// staged [32][128]) and the shell factorisation chi = P g,
+// grad chi = (grad P) g + P u (u = -2 r gd),
+//   sum_nu chi R = sum_s g S0,   sum_nu grad chi R = sum_s (g S1 + u S0),
+// S0 = sum_c P_c R_c and S1 = sum_c (grad P_c) R_c over the shell's components.
+template <bool GRAD>
+__device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float2* tab, const float2* Rs, int i, f2 px,
+                                          f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
+  const f2 s3{kS3h, kS3l};
+  const int ns = rec->nshell;
+  for (int s = 0; s < ns; ++s) {
+    const float4 c0 = rec->c0[s], c1 = rec->c1[s];
+    const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
+    const int l = hdr & 255, np = (hdr >> 8) & 255, first = (hdr >> 16) - 64;
+    f2 dx, dy, dz, r2, g, gd;
+    offsets_df(c0, c1, px, py, pz, dx, dy, dz, r2);
+    radial_df<GRAD>(rec->pf + pi, rec->pac + pi, np, r2, tab, g, gd);
+    auto Rv = [&](int c) -> f2 {
+      const int nu = first + c;
+      if (nu < 0 || nu >= kBasisBlk) return f2{0.f, 0.f};
+      const float2 r = Rs[nu * kBlockPts + i];
+      return f2{r.x, r.y};
+    };
+    f2 S0, S1x{0.f, 0.f}, S1y{0.f, 0.f}, S1z{0.f, 0.f};
+    if (l == 0) {
+      S0 = Rv(0);
+    } else if (l == 1) {
+      const f2 rx = Rv(0), ry = Rv(1), rz = Rv(2);
+      S0 = df_add(df_add(df_mul(dx, rx), df_mul(dy, ry)), df_mul(dz, rz));
+      S1x = rx;
+      S1y = ry;
+      S1z = rz;
+    } else {
+      const f2 rxx = df_mul(Rv(0), s3), rxy = Rv(1), rxz = Rv(2), ryy = df_mul(Rv(3), s3), ryz = Rv(4),
+               rzz = df_mul(Rv(5), s3);
+      // P: xx, xy, xz, yy, yz, zz (xx etc. with 1/sqrt(3) moved onto R)
+      const f2 ax = df_add(df_add(df_mul(dx, rxx), df_mul(dy, rxy)), df_mul(dz, rxz));   // sum over x-containing
+      const f2 ay = df_add(df_mul(dy, ryy), df_mul(dz, ryz));
+      const f2 az = df_mul(dz, rzz);
+      S0 = df_add(df_add(df_mul(dx, ax), df_mul(dy, ay)), df_mul(dz, az));
+      if (GRAD) {
+        // d/dx: 2 x rxx + y rxy + z rxz;  d/dy: x rxy + 2 y ryy + z ryz;  d/dz: x rxz + y ryz + 2 z rzz
+        S1x = df_add(ax, df_mul(dx, rxx));
+        S1y = df_add(df_add(df_mul(dx, rxy), df_mul(df_scale(dy, 2.f), ryy)), df_mul(dz, ryz));
+        S1z = df_add(df_add(df_mul(dx, rxz), df_mul(dy, ryz)), df_mul(df_scale(dz, 2.f), rzz));
+      }
+    }
+    pr = df_add(pr, df_mul(g, S0));
+    if (GRAD) {
+      const f2 m2 = df_scale(gd, -2.f);
+      gx = df_add(gx, df_add(df_mul(g, S1x), df_mul(df_mul(dx, m2), S0)));
+      gy = df_add(gy, df_add(df_mul(g, S1y), df_mul(df_mul(dy, m2), S0)));
+      gz = df_add(gz, df_add(df_mul(g, S1z), df_mul(df_mul(dz, m2), S0)));
+    }
+  }
+}
 
 // Epilogue of the density-product kernel: the row-dot (rho, grad rho), or
 // one of the two terms of the nuclear gradient of E_xc on a fixed grid,
@@ -516,12 +809,12 @@ struct RhoCfg {
 enum { kRowDot = 0, kGradR = 1, kGradQ = 2 };
 
 template <int NS, bool GRAD, int MODE = kRowDot>
-__global__ void __launch_bounds__(576, 1)
+__global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
     k_rho_tc(BasisView B, GridView G, ListView L, int64_t g0, int64_t g1, int64_t t0,
              const uint8_t* __restrict__ phi, const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero,
              const double* __restrict__ dmax, const float* __restrict__ dscale, const float* __restrict__ rowscale,
              double t_b, double t_d, double* rho, double* grad, const double* __restrict__ xcoef, double* gout,
-             int* err) {
+             int* err, uint64_t wait_ns) {
   using C = RhoCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -534,10 +827,13 @@ __global__ void __launch_bounds__(576, 1)
   uint64_t* mempty = mfull + 2;
   uint64_t* rfull = mempty + 2;       // partial sums of the four q-block groups written
   uint64_t* rempty = rfull + 1;       // ... and read by the combining warps
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rempty + 1);
+  uint64_t* mdone = rempty + 1;       // all products of the MMA thread completed (exit)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float2* tab = reinterpret_cast<float2*>(sm + C::kOffTab);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G_ = gridDim.x;
+  if constexpr (NS == 4) load_exp_tab(tab, threadIdx.x, C::kThreads);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -552,6 +848,7 @@ __global__ void __launch_bounds__(576, 1)
     }
     mbar_init(rfull, C::kEpi);
     mbar_init(rempty, 4);
+    mbar_init(mdone, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -582,7 +879,7 @@ __global__ void __launch_bounds__(576, 1)
       const int64_t g = g0 + blockIdx.x + k * G_;
       if (g >= g1 || *abort_flag) break;
       const int b = (int)(k & 1);
-      if (!mbar_wait_warp(&mempty[b], (uint32_t)(((k >> 1) & 1) ^ 1), abort_flag, err, 110)) break;
+      if (!mbar_wait_warp(&mempty[b], (uint32_t)(((k >> 1) & 1) ^ 1), abort_flag, err, 110, wait_ns)) break;
       int32_t* m = meta(b);
       const int tb = L.blk_ptr[g];
       int n = L.blk_ptr[g + 1] - tb;
@@ -637,7 +934,7 @@ __global__ void __launch_bounds__(576, 1)
             if (!bits) continue;
             const int s = it % C::kStages;
             const uint32_t ph = (it / C::kStages) & 1;
-            if (!mbar_wait_warp(&empty[s], ph ^ 1, abort_flag, err, 111)) { ok = false; break; }
+            if (!mbar_wait_warp(&empty[s], ph ^ 1, abort_flag, err, 111, wait_ns)) { ok = false; break; }
             uint8_t* st = sm + s * C::kStageBytes;
             if (lane == 0) mbar_arrive_expect_tx(&full[s], NS * kPlaneBytes + NS * nq * kDPlane);
             __syncwarp();
@@ -669,7 +966,7 @@ __global__ void __launch_bounds__(576, 1)
         const int64_t g = g0 + blockIdx.x + k * G_;
         if (g >= g1 || *abort_flag) break;
         const int b = (int)(k & 1);
-        if (!mbar_wait(&mfull[b], (uint32_t)((k >> 1) & 1), abort_flag, err, 115)) break;
+        if (!mbar_wait(&mfull[b], (uint32_t)((k >> 1) & 1), abort_flag, err, 115, wait_ns)) break;
         const int32_t* m = meta(b);
         const int n = m[0];
         const int ntile = (n + C::kNQ - 1) / C::kNQ;
@@ -681,7 +978,7 @@ __global__ void __launch_bounds__(576, 1)
           for (int sg = 0; sg < ns && ok; ++sg, ++job) {
             const int buf = job % C::kBufs;
             const uint32_t use = job / C::kBufs;
-            if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, err, 112)) { ok = false; break; }
+            if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, abort_flag, err, 112, wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t d0 = tbase + buf * C::kBufCols;
             uint32_t started[NS];
@@ -692,7 +989,7 @@ __global__ void __launch_bounds__(576, 1)
               if (!tile_bits(m, jp, q0, nq)) continue;
               const int s = it % C::kStages;
               const uint32_t ph = (it / C::kStages) & 1;
-              if (!mbar_wait(&full[s], ph, abort_flag, err, 113)) { ok = false; break; }
+              if (!mbar_wait(&full[s], ph, abort_flag, err, 113, wait_ns)) { ok = false; break; }
               tc_fence_after();
               const uint32_t a = smem_u32(sm + s * C::kStageBytes);
               const uint32_t bsm = a + NS * kPlaneBytes;
@@ -704,7 +1001,7 @@ __global__ void __launch_bounds__(576, 1)
                   ad[l] = smem_desc(a + l * kPlaneBytes + kk * 32, 16, 512, kSwz64);
                   bd[l] = smem_desc(bsm + l * (C::kNQ * kDPlane) + kk * 32, 16, 512, kSwz64);
                 }
-                issue_levels<NS>(d0, 128, ad, bd, idesc, started);
+                issue_levels<NS>(d0, C::kLevelCols, ad, bd, idesc, started);
               }
               mma_commit(&empty[s]);
               ++it;
@@ -717,6 +1014,11 @@ __global__ void __launch_bounds__(576, 1)
         mbar_arrive(&mempty[b]);
       }
       if (!ok) *abort_flag = 1;
+      // every product this thread issued completes before the CTA frees its
+      // tensor memory, also when a wait gave up in the middle of a stream
+      mma_commit(mdone);
+      volatile int no_abort = 0;
+      mbar_wait(mdone, 0, &no_abort, nullptr, 0);
     }
   } else {
     // warp w: lane quarter w % 4 (its TMEM lanes), q block k4 of every N tile
@@ -724,6 +1026,12 @@ __global__ void __launch_bounds__(576, 1)
     const int k4 = (warp - 2) >> 2;
     const int i = quarter * 32 + lane;
     float* Rs = reinterpret_cast<float*>(sm + C::kOffR) + k4 * (kBasisBlk * kBlockPts);
+    float2* Rs2 = reinterpret_cast<float2*>(sm + C::kOffR) + k4 * (kBasisBlk * kBlockPts);   // BF16X10
+    // R_nu of this thread's point as FP32 (the gradient epilogues)
+    auto rget = [&](int nu, int i_) -> float {
+      if constexpr (NS == 4) return Rs2[nu * kBlockPts + i_].x;
+      else return Rs[nu * kBlockPts + i_];
+    };
     double* red = reinterpret_cast<double*>(sm + C::kOffRed);
     BlockRec* recs = reinterpret_cast<BlockRec*>(sm + C::kOffRec) + 2 * k4;
     uint32_t job = 0, ruse = 0;
@@ -732,12 +1040,14 @@ __global__ void __launch_bounds__(576, 1)
       const int64_t g = g0 + blockIdx.x + k * G_;
       if (g >= g1 || *abort_flag) break;
       const int b = (int)(k & 1);
-      if (!mbar_wait_warp(&mfull[b], (uint32_t)((k >> 1) & 1), abort_flag, err, 116)) break;
+      if (!mbar_wait_warp(&mfull[b], (uint32_t)((k >> 1) & 1), abort_flag, err, 116, wait_ns)) break;
       const int32_t* m = meta(b);
       const int n = m[0];
       const int32_t* plist = m + 4;
       const int64_t pt = g * kBlockPts + i;
       const float4 prl = G.prel[pt];
+      float4 prlo = make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (NS == 4) prlo = G.prel_lo[pt];
       const int anc = G.anchor[g];
       const double rsc = (double)rowscale[pt];
       double r_i = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
@@ -763,30 +1073,43 @@ __global__ void __launch_bounds__(576, 1)
           stage_block_rec(B, qb, anc, rec, quarter * 32 + lane, 128);
           if (quarter == 0) rec->ds[lane] = dscale[qb * kBasisBlk + lane];
         }
-        float R[32];
+        float R[32], Rl[32];   // Rl: low parts (BF16X10)
 #pragma unroll
-        for (int c = 0; c < 32; ++c) R[c] = 0.f;
+        for (int c = 0; c < 32; ++c) R[c] = Rl[c] = 0.f;
         for (int sg = 0; sg < ns; ++sg, ++job) {
           const int buf = job % C::kBufs;
           const uint32_t use = job / C::kBufs;
-          if (!mbar_wait_warp(&tfull[buf], use & 1, abort_flag, err, 114)) { ok = false; break; }
+          if (!mbar_wait_warp(&tfull[buf], use & 1, abort_flag, err, 114, wait_ns)) { ok = false; break; }
           tc_fence_after();
           if (mine) {
             const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + k4 * 32;
+            constexpr uint32_t LC = C::kLevelCols;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               // the NS levels of 16 columns, smallest first, one wait
               float t[16 * NS];
-              if constexpr (NS == 3)
-                tmem_ld16x3(ta + 2 * 128 + h * 16, ta + 128 + h * 16, ta + h * 16, t);
+              if constexpr (NS == 4)
+                tmem_ld16x4(ta + 3 * LC + h * 16, ta + 2 * LC + h * 16, ta + LC + h * 16, ta + h * 16, t);
+              else if constexpr (NS == 3)
+                tmem_ld16x3(ta + 2 * LC + h * 16, ta + LC + h * 16, ta + h * 16, t);
               else
-                tmem_ld16x2(ta + 128 + h * 16, ta + h * 16, t);
+                tmem_ld16x2(ta + LC + h * 16, ta + h * 16, t);
 #pragma unroll
               for (int c = 0; c < 16; ++c) {
-                float acc = t[c];
+                if constexpr (NS == 4) {
+                  // L0 + L1 error-free, the two small levels rounded (2^-40 of
+                  // the scale), then added to the running hi / lo sum
+                  const f2 sg = two_sum(t[48 + c], t[32 + c]);
+                  const f2 r = df_add(f2{R[h * 16 + c], Rl[h * 16 + c]},
+                                      f2{sg.h, __fadd_rn(sg.l, __fadd_rn(t[16 + c], t[c]))});
+                  R[h * 16 + c] = r.h;
+                  Rl[h * 16 + c] = r.l;
+                } else {
+                  float acc = t[c];
 #pragma unroll
-                for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
-                R[h * 16 + c] += acc;
+                  for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
+                  R[h * 16 + c] += acc;
+                }
               }
             }
           }
@@ -801,14 +1124,35 @@ __global__ void __launch_bounds__(576, 1)
           const int q = qb;
           named_bar_sync(1 + k4, 128);
           ++ruse;
-          if (staged) {
+          if constexpr (NS == 4) {
+            // staged by construction (every block fits a record in BF16X10 plans)
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              const float f = staged ? rec->ds[c] : dscale[q * kBasisBlk + c];
+              Rs2[c * kBlockPts + i] = make_float2(R[c] * f, Rl[c] * f);
+            }
+          } else if (staged) {
 #pragma unroll
             for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * rec->ds[c];
           } else {
 #pragma unroll
             for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * dscale[q * kBasisBlk + c];
           }
-          if constexpr (MODE == kRowDot) {
+          if constexpr (MODE == kRowDot && NS == 4) {
+            if (staged) {
+              f2 pr{0.f, 0.f}, px_{0.f, 0.f}, py_{0.f, 0.f}, pz_{0.f, 0.f};
+              rowdot_df<GRAD>(rec, tab, Rs2, i, f2{prl.x, prlo.x}, f2{prl.y, prlo.y}, f2{prl.z, prlo.z}, pr, px_,
+                              py_, pz_);
+              r_i += rsc * df_to_double(pr);
+              if (GRAD) {
+                gx += 2.0 * rsc * df_to_double(px_);
+                gy += 2.0 * rsc * df_to_double(py_);
+                gz += 2.0 * rsc * df_to_double(pz_);
+              }
+            } else if (lane == 0) {
+              atomicCAS(err, 0, 102);   // the double-float row-dot needs staged shell records
+            }
+          } else if constexpr (MODE == kRowDot) {
             float pr = 0.f, px_ = 0.f, py_ = 0.f, pz_ = 0.f;
             auto acc = [&](int nu, float v, float dx, float dy, float dz) {
               const float rr = Rs[nu * kBlockPts + i];
@@ -852,7 +1196,7 @@ __global__ void __launch_bounds__(576, 1)
                 cur = atom;
                 tx = ty = tz = 0.f;
               }
-              const float rr = Rs[nu * kBlockPts + i];
+              const float rr = rget(nu, i);
               if constexpr (MODE == kGradQ) {
                 tx = fmaf(d[0], rr, tx);
                 ty = fmaf(d[1], rr, ty);
@@ -875,7 +1219,7 @@ __global__ void __launch_bounds__(576, 1)
       if (lane == 0) mbar_arrive(&mempty[b]);
       if constexpr (MODE != kRowDot) continue;
       // combine the four q-block groups of each point in a fixed order
-      if (!mbar_wait_warp(rempty, (uint32_t)(k & 1) ^ 1u, abort_flag, err, 117)) break;
+      if (!mbar_wait_warp(rempty, (uint32_t)(k & 1) ^ 1u, abort_flag, err, 117, wait_ns)) break;
       red[(k4 * 4 + 0) * kBlockPts + i] = r_i;
       red[(k4 * 4 + 1) * kBlockPts + i] = gx;
       red[(k4 * 4 + 2) * kBlockPts + i] = gy;
@@ -883,12 +1227,14 @@ __global__ void __launch_bounds__(576, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(rfull);
       if (k4 == 0) {
-        if (!mbar_wait_warp(rfull, (uint32_t)(k & 1), abort_flag, err, 118)) break;
+        if (!mbar_wait_warp(rfull, (uint32_t)(k & 1), abort_flag, err, 118, wait_ns)) break;
         double v[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          v[c] = ((red[(0 * 4 + c) * kBlockPts + i] + red[(1 * 4 + c) * kBlockPts + i]) +
-                  red[(2 * 4 + c) * kBlockPts + i]) + red[(3 * 4 + c) * kBlockPts + i];
+        for (int c = 0; c < 4; ++c) {
+          v[c] = red[c * kBlockPts + i];
+#pragma unroll
+          for (int q = 1; q < C::kNQ; ++q) v[c] += red[(q * 4 + c) * kBlockPts + i];
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(rempty);
         rho[pt] = v[0];
@@ -924,18 +1270,22 @@ static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, d
     k_rho_tc<NS, true><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                            b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                            P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
-                                                           nullptr, nullptr, P->d_err);
+                                                           nullptr, nullptr, P->d_err, P->wait_ns);
   else
     k_rho_tc<NS, false><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                             b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                             P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
-                                                            nullptr, nullptr, P->d_err);
+                                                            nullptr, nullptr, P->d_err, P->wait_ns);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
 
 kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho_out, double* grad_out, cudaStream_t s) {
-  return P->prec == KLDI_BF16X6 ? rho_ns<3>(P, b, rho_out, grad_out, s) : rho_ns<2>(P, b, rho_out, grad_out, s);
+  switch (slices_of(P->prec)) {
+    case 4: return rho_ns<4>(P, b, rho_out, grad_out, s);
+    case 3: return rho_ns<3>(P, b, rho_out, grad_out, s);
+    default: return rho_ns<2>(P, b, rho_out, grad_out, s);
+  }
 }
 
 // Nuclear gradient of one batch (after its density and functional stages):
@@ -956,20 +1306,24 @@ static kldi_status grad_ns(const kldi_plan* P, const Batch& b, bool gga_xc, doub
   const uint8_t* z = reinterpret_cast<const uint8_t*>(P->d_zero);
   k_rho_tc<NS, false, kGradQ><<<grid, C::kThreads, C::kSmem, s>>>(
       P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.g1, b.t0, zt, ds, z, P->d_dmax, P->d_dscale,
-      P->d_zscale, P->opt.t_b, P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err);
+      P->d_zscale, P->opt.t_b, P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err, P->wait_ns);
   KLDI_TRY_CUDA(cudaGetLastError());
   if (gga_xc) {
     k_rho_tc<NS, false, kGradR><<<grid, C::kThreads, C::kSmem, s>>>(
         P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.g1, b.t0,
         reinterpret_cast<const uint8_t*>(P->d_phi_s), ds, z, P->d_dmax, P->d_dscale, P->d_rowscale, P->opt.t_b,
-        P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err);
+        P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err, P->wait_ns);
     KLDI_TRY_CUDA(cudaGetLastError());
   }
   return KLDI_OK;
 }
 
 kldi_status launch_grad_tc(const kldi_plan* P, const Batch& b, bool gga_xc, double* G, cudaStream_t s) {
-  return P->prec == KLDI_BF16X6 ? grad_ns<3>(P, b, gga_xc, G, s) : grad_ns<2>(P, b, gga_xc, G, s);
+  switch (slices_of(P->prec)) {
+    case 4: return grad_ns<4>(P, b, gga_xc, G, s);
+    case 3: return grad_ns<3>(P, b, gga_xc, G, s);
+    default: return grad_ns<2>(P, b, gga_xc, G, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -992,9 +1346,13 @@ struct VCfg {
   static constexpr int kChunk = 2048;                   // 32 points x 64 B of one plane of one tile
   static constexpr int kOp = 4 * kChunk;                // 4 tiles (128 functions) of one plane
   static constexpr int kStageBytes = 2 * NS * kOp;      // [side A, B][tile j][plane][32 points x 64 B]
-  static constexpr int kStages = 4;
-  static constexpr int kBufCols = NS * 128;
-  static constexpr int kCcCol = NS * 128;               // TMEM columns of the compensation terms
+  static constexpr int kStages = NS == 4 ? 3 : 4;
+  // accumulators: one per level; BF16X10 keeps levels 0 and 1 exact and lets
+  // levels 2 and 3 (2^-16 and 2^-24 of the scale) share a rounding one, whose
+  // truncation then acts at ~2^-40 of the scale per step
+  static constexpr int kAcc = NS == 4 ? 3 : NS;
+  static constexpr int kBufCols = kAcc * 128;
+  static constexpr int kCcCol = kAcc * 128;             // TMEM columns of the compensation terms
   static_assert(kCcCol + 128 <= 512, "levels and compensation terms exceed TMEM");
   static constexpr int kOffBar = kStages * kStageBytes;
   static constexpr int kSmem = kOffBar + 256 + 1024;
@@ -1018,7 +1376,7 @@ __global__ void __launch_bounds__(384, 1)
     k_v_tc(ListView L, const VWorkTC* __restrict__ work, int64_t nwork, const int32_t* __restrict__ glist,
            int64_t t0, const uint8_t* __restrict__ phic, const uint8_t* __restrict__ xs,
            const float* __restrict__ scale, const double* __restrict__ xmax, const uint8_t* __restrict__ zero,
-           int nbf, double t_b, double* V, int* next, int* err) {
+           int nbf, double t_b, double t_d, double* V, int* next, int* err, uint64_t wait_ns, int withhold) {
   using C = VCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1028,7 +1386,8 @@ __global__ void __launch_bounds__(384, 1)
   uint64_t* tempty = tfull + 2;
   uint64_t* ifull = tempty + 2;       // work-item ring: index published by the producer
   uint64_t* iempty = ifull + 4;       // ... and read by the MMA thread and the 8 epilogue warps
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(iempty + 4);
+  uint64_t* mdone = iempty + 4;       // all products of the MMA thread completed (exit)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* ring = reinterpret_cast<volatile int*>(tmem_slot + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1045,6 +1404,7 @@ __global__ void __launch_bounds__(384, 1)
       mbar_init(&ifull[r], 1);
       mbar_init(&iempty[r], 9);
     }
+    mbar_init(mdone, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -1069,13 +1429,17 @@ __global__ void __launch_bounds__(384, 1)
         // next work item from the global counter: CTAs take neighbouring items
         // and so share the tiles of the same grid-block range in L2
         const int slot = k & 3;
-        if (!mbar_wait_warp(&iempty[slot], ((k >> 2) & 1) ^ 1, abort_flag, err, 125)) { ok = false; break; }
+        if (!mbar_wait_warp(&iempty[slot], ((k >> 2) & 1) ^ 1, abort_flag, err, 125, wait_ns)) { ok = false; break; }
         int wi = 0;
         if (lane == 0) {
           const int x = atomicAdd(next, 1);
           wi = x < nwork ? x : -1;
-          ring[slot] = wi;
-          mbar_arrive(&ifull[slot]);
+          if (x == withhold) {
+            wi = -2;   // test hook: item not handed out, the consumers' bounded wait runs out
+          } else {
+            ring[slot] = wi;
+            mbar_arrive(&ifull[slot]);
+          }
         }
         wi = __shfl_sync(0xffffffffu, wi, 0);
         if (wi < 0) break;
@@ -1084,13 +1448,13 @@ __global__ void __launch_bounds__(384, 1)
           const int64_t gb = glist[wk.beg + e];
           const int p = (side == 0 ? wk.P : wk.Q) * 4 + j;
           const uint8_t* sp = zero;   // Phi~ tile (gb, p), or zeros
-          const uint8_t* sx = zero;   // X~ tile, or zeros (tile absent or x_gq < t_b)
+          const uint8_t* sx = zero;   // X~ tile, or zeros (tile absent); pair screening in the epilogue
           if (p < L.nbb) {
             const int t = L.tile_of[gb * L.nbb + p];
             if (t >= 0) {
               const int64_t off = (int64_t)(t - t0) * tile_bytes(NS);
               sp = phic + off;
-              if (xmax[t] >= t_b) sx = xs + off;
+              sx = xs + off;
             }
           }
           // a diagonal pair (P == Q) runs only the first half of the chain,
@@ -1100,7 +1464,7 @@ __global__ void __launch_bounds__(384, 1)
             const int h = c >> 2, kc = c & 3;
             const int s = it % C::kStages;
             const uint32_t ph = (it / C::kStages) & 1;
-            if (!mbar_wait_warp(&empty[s], ph ^ 1, abort_flag, err, 121)) { ok = false; break; }
+            if (!mbar_wait_warp(&empty[s], ph ^ 1, abort_flag, err, 121, wait_ns)) { ok = false; break; }
             if (lane == 0) mbar_arrive_expect_tx(&full[s], C::kStageBytes);
             __syncwarp();
             if (copier) {
@@ -1126,23 +1490,23 @@ __global__ void __launch_bounds__(384, 1)
         bool ok = true;
         for (uint32_t k = 0; ok; ++k) {
           const int slot = k & 3;
-          if (!mbar_wait(&ifull[slot], (k >> 2) & 1, abort_flag, err, 126)) { ok = false; break; }
+          if (!mbar_wait(&ifull[slot], (k >> 2) & 1, abort_flag, err, 126, wait_ns)) { ok = false; break; }
           const int wi = ring[slot];
           mbar_arrive(&iempty[slot]);
           if (wi < 0) break;
           const VWorkTC wk = work[wi];
           for (int e = 0; e < wk.end - wk.beg && ok; ++e, ++job) {
-            if (!mbar_wait(&tempty[0], (job & 1) ^ 1, abort_flag, err, 124)) { ok = false; break; }
+            if (!mbar_wait(&tempty[0], (job & 1) ^ 1, abort_flag, err, 124, wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t d0 = tbase;
-            uint32_t started[NS];
+            uint32_t started[C::kAcc];
 #pragma unroll
-            for (int l = 0; l < NS; ++l) started[l] = 0;
+            for (int l = 0; l < C::kAcc; ++l) started[l] = 0;
             const int nchunk = wk.P == wk.Q ? 4 : 8;
             for (int c = 0; c < nchunk; ++c) {
               const int s = it % C::kStages;
               const uint32_t ph = (it / C::kStages) & 1;
-              if (!mbar_wait(&full[s], ph, abort_flag, err, 122)) { ok = false; break; }
+              if (!mbar_wait(&full[s], ph, abort_flag, err, 122, wait_ns)) { ok = false; break; }
               tc_fence_after();
               const uint32_t a = smem_u32(sm + s * C::kStageBytes);
 #pragma unroll
@@ -1153,7 +1517,7 @@ __global__ void __launch_bounds__(384, 1)
                   ad[l] = smem_desc(a + l * C::kChunk + k * 1024, NS * C::kChunk, 512, kSwz64);
                   bd[l] = smem_desc(a + 4 * NS * C::kChunk + l * C::kChunk + k * 1024, NS * C::kChunk, 512, kSwz64);
                 }
-                issue_levels<NS>(d0, 128, ad, bd, idesc, started);
+                issue_levels<NS, C::kAcc>(d0, 128, ad, bd, idesc, started);
               }
               mma_commit(&empty[s]);
               ++it;
@@ -1163,6 +1527,11 @@ __global__ void __launch_bounds__(384, 1)
           }
         }
         if (!ok) *abort_flag = 1;
+        // every product this thread issued completes before the CTA frees its
+        // tensor memory, also when a wait gave up in the middle of a stream
+        mma_commit(mdone);
+        volatile int no_abort = 0;
+        mbar_wait(mdone, 0, &no_abort, nullptr, 0);
       }
     }
   } else {
@@ -1175,7 +1544,7 @@ __global__ void __launch_bounds__(384, 1)
     bool ok = true;
     for (uint32_t k = 0; ok; ++k) {
       const int slot = k & 3;
-      if (!mbar_wait_warp(&ifull[slot], (k >> 2) & 1, abort_flag, err, 127)) { ok = false; break; }
+      if (!mbar_wait_warp(&ifull[slot], (k >> 2) & 1, abort_flag, err, 127, wait_ns)) { ok = false; break; }
       const int wi = ring[slot];
       __syncwarp();
       if (lane == 0) mbar_arrive(&iempty[slot]);
@@ -1196,10 +1565,18 @@ __global__ void __launch_bounds__(384, 1)
         const int64_t gb = glist[wk.beg + e];
         const int pr = wk.P * 4 + (m >> 5);
         float rsc = 0.f;
+        double bp = 0.0, xp = 0.0;
         if (pr < L.nbb) {
           const int t = L.tile_of[gb * L.nbb + pr];
-          if (t >= 0) rsc = scale[(int64_t)(t - t0) * kBasisBlk + (m & 31)];
+          if (t >= 0) {
+            rsc = scale[(int64_t)(t - t0) * kBasisBlk + (m & 31)];
+            bp = L.bmax[t];
+            xp = xmax[t];
+          }
         }
+        // column scales, zero where the block pair (p, q) of this grid block
+        // is not executed: (p, q) or (q, p) in E2_g (x_gq >= t_b and
+        // b_gp x_gq >= t_d, or the same with p and q exchanged)
         float csc[2];
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
@@ -1207,29 +1584,40 @@ __global__ void __launch_bounds__(384, 1)
           csc[cc] = 0.f;
           if (qb < L.nbb) {
             const int t = L.tile_of[gb * L.nbb + qb];
-            if (t >= 0) csc[cc] = scale[(int64_t)(t - t0) * kBasisBlk + lane];
+            if (t >= 0) {
+              const double bq = L.bmax[t], xq = xmax[t];
+              const bool on = (xq >= t_b && bp * xq >= t_d) || (xp >= t_b && bq * xp >= t_d);
+              if (on) csc[cc] = scale[(int64_t)(t - t0) * kBasisBlk + lane];
+            }
           }
         }
-        if (!mbar_wait_warp(&tfull[0], job & 1, abort_flag, err, 123)) { ok = false; break; }
+        if (!mbar_wait_warp(&tfull[0], job & 1, abort_flag, err, 123, wait_ns)) { ok = false; break; }
         tc_fence_after();
 #pragma unroll
         for (int cq = 0; cq < 4; ++cq) {            // 16 columns at a time
           const int cc = cq >> 1;
           // levels (smallest first) and the compensation terms, one wait
-          float t[16 * (NS + 1)];
-          if constexpr (NS == 3)
+          float t[16 * (C::kAcc + 1)];
+          if constexpr (C::kAcc == 3)
             tmem_ld16x4(trow + 2 * 128 + cq * 16, trow + 128 + cq * 16, trow + cq * 16, trow + C::kCcCol + cq * 16, t);
           else
             tmem_ld16x3(trow + 128 + cq * 16, trow + cq * 16, trow + C::kCcCol + cq * 16, t);
           float cmp[16];
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            float acc = t[c];
+            cmp[c] = t[16 * C::kAcc + c];
+            const float sc = rsc * __shfl_sync(0xffffffffu, csc[cc], (cq & 1) * 16 + c);   // a power of two
+            if constexpr (NS == 4) {
+              // L0 + L1 error-free; the low part and the rounded L23 go to the compensation
+              const f2 sg = two_sum(t[32 + c], t[16 + c]);
+              two_sum_acc(S[cq * 16 + c], cmp[c], sg.h * sc);
+              cmp[c] = __fadd_rn(cmp[c], __fadd_rn(sg.l, t[c]) * sc);
+            } else {
+              float acc = t[c];
 #pragma unroll
-            for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
-            cmp[c] = t[16 * NS + c];
-            const float sc = rsc * __shfl_sync(0xffffffffu, csc[cc], (cq & 1) * 16 + c);
-            two_sum_acc(S[cq * 16 + c], cmp[c], acc * sc);
+              for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
+              two_sum_acc(S[cq * 16 + c], cmp[c], acc * sc);
+            }
           }
           tmem_st16(trow + C::kCcCol + cq * 16, cmp);
         }
@@ -1272,7 +1660,8 @@ static kldi_status v_ns(const kldi_plan* P, const Batch& b, double* V, cudaStrea
   k_v_tc<NS><<<grid, C::kThreads, C::kSmem, s>>>(
       P->list_view(), b.d_vtc_work, b.n_vtc_work, b.d_vtc_g, b.t0, reinterpret_cast<const uint8_t*>(P->d_phic_s),
       reinterpret_cast<const uint8_t*>(P->d_x_s), P->d_phic_scale, P->d_xmax,
-      reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, P->opt.t_b, V, P->d_vnext, P->d_err);
+      reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, P->opt.t_b, P->opt.t_d, V, P->d_vnext, P->d_err, P->wait_ns,
+      (int)P->withhold_item);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
@@ -1319,14 +1708,88 @@ kldi_status prepare_tc_kernels() {
   }
   kldi_status st = prepare_rho_kernel<2>();
   if (st == KLDI_OK) st = prepare_rho_kernel<3>();
+  if (st == KLDI_OK) st = prepare_rho_kernel<4>();
   if (st == KLDI_OK) st = prepare_v_kernel<2>();
   if (st == KLDI_OK) st = prepare_v_kernel<3>();
+  if (st == KLDI_OK) st = prepare_v_kernel<4>();
+  if (st == KLDI_OK) {
+    // the X kernel of BF16X10 stages hi / lo values in dynamic shared memory
+    const cudaError_t e1 = cudaFuncSetAttribute(k_x_split4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kX4Smem);
+    const cudaError_t e2 = cudaFuncSetAttribute(k_x_split4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kX4Smem);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      set_error("k_x_split4: shared-memory opt-in failed");
+      st = KLDI_ECUDA;
+    }
+  }
+  if (st == KLDI_OK) {
+    // 2^(j/256) as hi / lo pairs for exp_df (from the host's double exp2)
+    float2 tab[256];
+    for (int j = 0; j < 256; ++j) {
+      const double v = std::exp2((double)j / 256.0);
+      tab[j].x = (float)v;
+      tab[j].y = (float)(v - (double)tab[j].x);
+    }
+    if (cudaMemcpyToSymbol(g_exp2_tab, tab, sizeof(tab)) != cudaSuccess) {
+      set_error("exp table upload failed");
+      st = KLDI_ECUDA;
+    }
+  }
   done[dev] = st;
   return st;
 }
 
+// Self-test of the bounded wait: warp 0 waits (limit_ns) on an mbarrier of
+// count 1 at which warp 1 arrives only when `arrive` is set.  Nothing else is
+// in flight (no copies, no products, no tensor memory), so a wait that runs
+// out leaves the CTA in a clean state.  out[0] = 1 when the wait completed,
+// out[1] = the recorded code (0 or 901).
+__global__ void k_selftest_wait(uint64_t limit_ns, int arrive, int* out) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  __shared__ int err;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    err = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x >> 5 == 1) {
+    if (arrive && (threadIdx.x & 31) == 0) mbar_arrive(&bar);
+  } else {
+    const bool ok = mbar_wait_warp(&bar, 0, &abort_flag, &err, 901, limit_ns);
+    if (threadIdx.x == 0) {
+      out[0] = ok ? 1 : 0;
+      out[1] = err;
+    }
+  }
+}
+
 kldi_status launch_v_tc(const kldi_plan* P, const Batch& b, double* V, cudaStream_t s) {
-  return P->prec == KLDI_BF16X6 ? v_ns<3>(P, b, V, s) : v_ns<2>(P, b, V, s);
+  switch (slices_of(P->prec)) {
+    case 4: return v_ns<4>(P, b, V, s);
+    case 3: return v_ns<3>(P, b, V, s);
+    default: return v_ns<2>(P, b, V, s);
+  }
 }
 
 }  // namespace kldi
+
+extern "C" kldi_status kldi_selftest_wait(uint64_t limit_ns, int arrive, void* stream) {
+  return kldi::guarded("kldi_selftest_wait", [&]() -> kldi_status {
+    using namespace kldi;
+    int* d = nullptr;
+    KLDI_TRY_CUDA(cudaMalloc(&d, 2 * sizeof(int)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h[2] = {0, 0};
+    k_selftest_wait<<<1, 64, 0, s>>>(limit_ns, arrive, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    KLDI_TRY_CUDA(e);
+    if (h[0] == 1 && h[1] == 0) return KLDI_OK;
+    set_error("kldi_selftest_wait: the bounded wait gave up (code %d)", h[1]);
+    return KLDI_ETIMEOUT;
+  });
+}

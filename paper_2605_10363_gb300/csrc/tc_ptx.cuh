@@ -14,8 +14,9 @@
 namespace kldi {
 namespace tc {
 
-// Bounded waits: a wait gives up after kWaitNs nanoseconds of %globaltimer,
-// records `code` in *err and returns false.
+// Bounded waits: a wait gives up after `limit` nanoseconds of %globaltimer
+// (kWaitNs unless the kernel passes its plan's limit), records `code` in *err
+// and returns false.
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -60,14 +61,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Wait for the phase of the given parity; false on timeout or when *abort is
 // set by another role of the CTA.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err,
-                                          int code) {
+                                          int code, uint64_t limit = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     for (int k = 0; k < 64; ++k)
       if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitNs) {
+    if (globaltimer() - t0 > limit) {
       if (err) atomicCAS(err, 0, code);
       *abort = 1;
       return false;
@@ -78,8 +79,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 // Warp-collective wait: every lane polls, then the warp reconverges, so that
 // the .sync.aligned tcgen05 instructions that follow see a converged warp.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort, int* err,
-                                               int code) {
-  const bool ok = mbar_wait(bar, parity, abort, err, code);
+                                               int code, uint64_t limit = kWaitNs) {
+  const bool ok = mbar_wait(bar, parity, abort, err, code, limit);
   return __all_sync(0xffffffffu, ok);
 }
 

@@ -13,6 +13,9 @@ exercised by CPU (gloo) ranks in the tests.
 """
 from __future__ import annotations
 
+import pickle
+import time
+
 import numpy as np
 
 
@@ -91,27 +94,133 @@ class BlockQueue:
     """Dynamic pull scheduler: chunk c covers grid blocks [c chunk, min((c + 1)
     chunk, nblocks)); ranks take the next chunk with one atomic Store.add, so
     every chunk goes to exactly one rank and faster ranks take more.  `key`
-    names the counter; use a fresh key per evaluation (the store keeps it)."""
+    names the counter; use a fresh key per evaluation (the store keeps it).
 
-    def __init__(self, store, nblocks: int, chunk: int, key: str):
+    With ``lease_timeout`` (seconds) the chunks are leases: taking a chunk
+    records its owner, and a rank publishes its cumulative partial result with
+    the list of chunks it covers (``publish``) after each chunk.  A rank that
+    leaves between chunks, announced (``leave``) or silent (no take or publish
+    for ``lease_timeout`` seconds; the ranks share one clock), loses the chunk
+    it holds: once the counter is exhausted, ``take`` re-offers every chunk
+    that is neither published nor held by a live rank, and returns None only
+    when every chunk is published.  ``reduce_published`` then sums the
+    published partials, which cover every chunk exactly once."""
+
+    def __init__(self, store, nblocks: int, chunk: int, key: str, rank: int = 0, lease_timeout=None,
+                 poll: float = 0.05):
         if chunk < 1:
             raise ValueError("chunk must be >= 1")
         self.store, self.nblocks, self.chunk, self.key = store, int(nblocks), int(chunk), key
+        self.rank, self.lease_timeout, self.poll = int(rank), lease_timeout, poll
+        self.nchunks = -(-self.nblocks // self.chunk)
+        self.mine = []                       # chunks this rank published
+
+    def _range(self, c):
+        return c * self.chunk, min((c + 1) * self.chunk, self.nblocks)
+
+    def _k(self, *parts):
+        return "/".join([self.key] + [str(p) for p in parts])
+
+    def _beat(self):
+        if self.lease_timeout is not None:
+            self.store.set(self._k("hb", self.rank), repr(time.time()))
+
+    def _gone(self, r: int) -> bool:
+        if self.store.check([self._k("left", r)]):
+            return True
+        if not self.store.check([self._k("hb", r)]):
+            return False
+        return time.time() - float(self.store.get(self._k("hb", r)).decode()) > self.lease_timeout
+
+    def _record(self, r: int):
+        if not self.store.check([self._k("part", r)]):
+            return None
+        return pickle.loads(self.store.get(self._k("part", r)))
 
     def take(self):
+        self._beat()
         c = int(self.store.add(self.key, 1)) - 1
-        g0 = c * self.chunk
-        if g0 >= self.nblocks:
+        if c < self.nchunks:
+            if self.lease_timeout is not None:
+                self.store.set(self._k("owner", c), str(self.rank))
+            return self._range(c)
+        if self.lease_timeout is None:
             return None
-        return g0, min(g0 + self.chunk, self.nblocks)
+        # counter exhausted: re-offer the chunks of ranks that left
+        unowned = {}                            # chunk -> first time seen without an owner
+        while True:
+            pending = False
+            for c in range(self.nchunks):
+                if self.store.check([self._k("done", c)]):
+                    continue
+                if not self.store.check([self._k("owner", c)]):
+                    # taken from the counter, owner not yet recorded; if it stays
+                    # so for a lease, the taker left in between: claim it
+                    t0 = unowned.setdefault(c, time.time())
+                    if time.time() - t0 > self.lease_timeout:
+                        got = self.store.compare_set(self._k("owner", c), "", str(self.rank))
+                        if int(got.decode()) == self.rank:
+                            self._beat()
+                            return self._range(c)
+                    pending = True
+                    continue
+                owner = int(self.store.get(self._k("owner", c)).decode())
+                if owner == self.rank or not self._gone(owner):
+                    pending = True
+                    continue
+                rec = self._record(owner)
+                if rec is not None and c in rec[2]:
+                    self.store.set(self._k("done", c), str(owner))   # published before it left
+                    continue
+                got = self.store.compare_set(self._k("owner", c), str(owner), str(self.rank))
+                if int(got.decode()) == self.rank:
+                    self._beat()
+                    return self._range(c)
+                pending = True
+            if not pending:
+                return None
+            self._beat()
+            time.sleep(self.poll)
+
+    def publish(self, r, E, V):
+        """After finishing chunk range r: store this rank's cumulative partial
+        (E, V as numpy arrays, including r) and mark the chunk done."""
+        c = r[0] // self.chunk
+        self.mine.append(c)
+        self.store.set(self._k("part", self.rank), pickle.dumps((float(E), np.asarray(V), list(self.mine))))
+        self.store.set(self._k("done", c), str(self.rank))
+        self._beat()
+
+    def leave(self):
+        """Announce that this rank takes no further chunks (its published
+        chunks stay counted; a chunk it holds is re-offered)."""
+        self.store.set(self._k("left", self.rank), "1")
+
+    def reduce_published(self, world: int):
+        """Sum of every rank's published partial (after take() returned None):
+        (E, V, chunks); the chunk lists are disjoint and cover all chunks."""
+        E, V, chunks = 0.0, None, []
+        for r in range(world):
+            rec = self._record(r)
+            if rec is None:
+                continue
+            E += rec[0]
+            V = rec[1].copy() if V is None else V + rec[1]
+            chunks += rec[2]
+        if sorted(chunks) != list(range(self.nchunks)):
+            raise RuntimeError(f"published chunks {sorted(chunks)} do not cover 0..{self.nchunks - 1} once")
+        return E, V, chunks
 
 
 def exc_pulled(plan, xc, D, V, E, queue: BlockQueue, group=None):
     """kldi_exc over the chunks this rank pulls from `queue`, summed, then the
-    sum-reduce over ranks (device tensors V, E receive the full result).
-    Returns the block ranges this rank evaluated; the plan is left on all its
-    grid blocks.  Without an initialised process group of more than one rank
-    there is nothing to reduce."""
+    sum over ranks (device tensors V, E receive the full result).  Returns the
+    block ranges this rank evaluated; the plan is left on all its grid blocks.
+    With a plain queue the sum is an all-reduce over the process group (none
+    without a group of more than one rank); with a leased queue the partials
+    go through the store (publish after every chunk, reduce_published), so
+    the ranks that stay produce the full result when another rank leaves
+    between chunks."""
     import torch
     from . import kldi
     Vp = torch.zeros_like(V)
@@ -128,8 +237,15 @@ def exc_pulled(plan, xc, D, V, E, queue: BlockQueue, group=None):
         V += Vp
         E += Ep
         done.append(r)
+        if queue.lease_timeout is not None:
+            queue.publish(r, E.item(), V.cpu().numpy())
     plan.set_block_range(0, plan.stats["nblocks"])
     import torch.distributed as dist
-    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+    if queue.lease_timeout is not None:
+        world = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
+        Es, Vs, _ = queue.reduce_published(world)
+        V.copy_(torch.from_numpy(Vs))
+        E.fill_(Es)
+    elif dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
         reduce_exc(V, E, group)
     return done

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libkldi.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 XC = {"lda_x": 1, "pbe": 2, "mlp": 3}
-PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "bf16x6": 3}
+PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "bf16x6": 3, "bf16x10": 4}
 STAGES = ("dprep", "phi", "rho", "xc", "x", "v", "finish")
 NSTAGES = len(STAGES)
 
@@ -81,6 +81,9 @@ def _load():
         "kldi_exc_batched": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), vp]),
         "kldi_exc_grad": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "kldi_plan_set_precision": (C.c_int, [vp, C.c_int]),
+        "kldi_plan_set_wait_limit": (C.c_int, [vp, C.c_uint64]),
+        "kldi_plan_set_withhold": (C.c_int, [vp, C.c_int64]),
+        "kldi_selftest_wait": (C.c_int, [C.c_uint64, C.c_int, vp]),
         "kldi_plan_profile": (C.c_int, [vp, C.c_int]),
         "kldi_plan_stage_times": (C.c_int, [vp, vp, vp]),
         "kldi_exc_energy_noalloc": (C.c_int, [C.c_int, C.c_int64, vp, vp, vp, C.c_double, vp, vp]),
@@ -248,6 +251,14 @@ class Plan:
     def set_precision(self, prec):
         _check(LIB.kldi_plan_set_precision(self.h, PREC[prec] if isinstance(prec, str) else int(prec)))
 
+    def set_wait_limit(self, ns):
+        """Bounded device waits give up after ns nanoseconds (0: the default 2 s)."""
+        _check(LIB.kldi_plan_set_wait_limit(self.h, int(ns)))
+
+    def set_withhold(self, item):
+        """Test hook: the V product withholds work item `item` (-1: off)."""
+        _check(LIB.kldi_plan_set_withhold(self.h, int(item)))
+
     def __del__(self):
         if getattr(self, "h", None) is not None and self.h.value:
             LIB.kldi_plan_free(self.h)
@@ -404,6 +415,12 @@ class Mlp:
 def plan_set_mlp(plan: Plan, mlp):
     _check(LIB.kldi_plan_set_mlp(plan.h, mlp.h if mlp is not None else None))
     plan._mlp = mlp            # keep the network alive as long as the plan uses it
+
+
+def selftest_wait(limit_ns, arrive, stream=0):
+    """One CTA waits limit_ns on an mbarrier; raises KldiError(ETIMEOUT) when
+    nothing arrives (arrive=False)."""
+    _check(LIB.kldi_selftest_wait(int(limit_ns), int(bool(arrive)), C.c_void_p(stream)))
 
 
 def version() -> str:

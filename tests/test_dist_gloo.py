@@ -172,3 +172,61 @@ def test_block_queue_single_process():
     assert [q.take() for _ in range(4)] == [(0, 4), (4, 8), (8, 10), None]
     with pytest.raises(ValueError):
         kdist.BlockQueue(store, 10, 0, key="k2")
+
+
+def _rank_pull_leave(rank, world, port, nblocks, chunk, out_dir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    store = dist.distributed_c10d._get_default_store()
+    q = kdist.BlockQueue(store, nblocks, chunk, key="exc_leave_0", rank=rank, lease_timeout=1.0)
+    E, V = 0.0, np.zeros((s.nbf, s.nbf))
+    done = []
+    if rank == world - 1:
+        # finishes one chunk, takes the next and leaves without a word (a
+        # process that dies between chunks): the chunk it holds is lost
+        r = q.take()
+        part = oe.evaluate(s, g, sh, screened=True, blocks=range(*r))
+        E, V = E + part.E, V + part.V
+        q.publish(r, E, V)
+        np.save(os.path.join(out_dir, f"done{rank}.npy"), np.array([r], dtype=np.int64))
+        q.take()
+        os._exit(0)
+    while True:                          # the loop of kdist.exc_pulled with a leased queue
+        r = q.take()
+        if r is None:
+            break
+        part = oe.evaluate(s, g, sh, screened=True, blocks=range(*r))
+        E, V = E + part.E, V + part.V
+        q.publish(r, E, V)
+        done.append(r)
+    Es, Vs, chunks = q.reduce_published(world)
+    np.save(os.path.join(out_dir, f"V{rank}.npy"), Vs)
+    np.save(os.path.join(out_dir, f"E{rank}.npy"), np.array([Es]))
+    np.save(os.path.join(out_dir, f"done{rank}.npy"), np.array(done, dtype=np.int64).reshape(-1, 2))
+    os._exit(0)                          # a member of the group is gone: no collective teardown
+
+
+def test_pull_queue_requeues_the_chunk_of_a_rank_that_leaves(tmp_path):
+    """Three ranks pull leased chunks of 16 grid blocks; the last rank finishes
+    one chunk, takes another and exits.  Its lease runs out (1 s without a
+    heartbeat), a remaining rank takes the chunk over, and the two remaining
+    ranks' sum of the published partials equals the single-process oracle;
+    every chunk was evaluated by exactly one rank."""
+    import torch.multiprocessing as mp
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    ref = oe.evaluate(s, g, sh, screened=True)
+    world = 3
+    mp.start_processes(_rank_pull_leave, args=(world, _free_port(), g.nblocks, 16, str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    taken = np.concatenate([np.load(tmp_path / f"done{r}.npy") for r in range(world)])
+    taken = taken[np.argsort(taken[:, 0])]
+    assert taken[0, 0] == 0 and taken[-1, 1] == g.nblocks
+    assert np.all(taken[1:, 0] == taken[:-1, 1])
+    for r in range(world - 1):
+        assert np.load(tmp_path / f"E{r}.npy")[0] == pytest.approx(ref.E, rel=1e-13)
+        assert np.abs(np.load(tmp_path / f"V{r}.npy") - ref.V).max() <= 1e-13 * np.abs(ref.V).max()

@@ -61,10 +61,12 @@ def test_gradient_device_buffers():
         assert float(Ed[0]) == pytest.approx(float(Eh[0]), rel=1e-14)
 
 
-TC_TOL = {"bf16x6": 2.0 ** -21, "bf16x3": 2.0 ** -13}
+# BF16X10 plans run the gradient through the same FP32 derivative epilogues
+# (R and Q rounded to FP32), so they share BF16X6's bound
+TC_TOL = {"bf16x10": 2.0 ** -21, "bf16x6": 2.0 ** -21, "bf16x3": 2.0 ** -13}
 
 
-@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16x10", "bf16x6", "bf16x3"])
 @pytest.mark.parametrize("name,xc", [("w1", "lda_x"), ("w1", "pbe"), ("w4", "pbe"), ("w6", "pbe")])
 def test_tensor_core_gradient_matches_oracle(name, xc, prec):
     from paper_2605_10363_gb300 import kldi
@@ -82,7 +84,7 @@ def test_tensor_core_gradient_matches_oracle(name, xc, prec):
     # translational invariance is not exact on a fixed grid, so no sum rule is
     # asserted; the energy of the call is the plan's energy
     Eref = oe.evaluate(s, g, sh, screened=True, want_v=False, xc_kind=xc).E
-    assert abs(E[0] - Eref) <= (1e-6 if prec == "bf16x6" else 1e-3)
+    assert abs(E[0] - Eref) <= (1e-3 if prec == "bf16x3" else 1e-6)
 
 
 def _wide_block_system():

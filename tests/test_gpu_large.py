@@ -2,17 +2,19 @@
 grid blocks in the launch configuration the benchmark uses, and the grid's
 Becke weights computed on the GPU.
 
-The 1000-atom C/N/O/H cluster (9000 functions, 11.65M points): the library
-evaluates the whole grid; on seeded contiguous ranges of grid blocks the
-plan restricted to the range (kldi_plan_set_block_range) gives the range's
-partial E_xc and V, which the screened FP64 oracle evaluates exactly.
-Tolerances are those of BF16x6: |dE| <= 1e-6 Ha per range (the partial sums
-are far smaller than the whole), max|dV| <= 3e-7.  rho at a point follows the
-error model of the sliced product: every element of Phi is exact to 2^-24 of
-its point's scale (>= max_m |phi_m|) and every element of D to 2^-24 of its
-column scale (max_m |D_mn|), so
-  |d rho_i| <= 2^-22 sum_n |phi_n| (2 max_m |phi_m| sum_m |D_mn| + max_m |D_mn| sum_m |phi_m|)
-(a factor 4 over the slicing bound for the FP32 drains)."""
+The 1000-atom C/N/O/H cluster (9000 functions, 11.65M points) in BF16X10 (the
+mode held to the stated target):
+  * whole grid: E_xc within 1e-6 Ha and every element of V within 1e-7 of the
+    FP64 block form on the same plan;
+  * the FP64 block form and BF16X10 on seeded contiguous ranges of grid
+    blocks (kldi_plan_set_block_range: the range's partial E_xc and V) against
+    the screened FP64 oracle: FP64 to 1e-10, BF16X10 to 1e-6 Ha / 1e-7;
+  * rho at a point follows the error model of the sliced product: every
+    element of Phi is exact to 2^-32 of its point's scale (>= max_m |phi_m|)
+    and every element of D to 2^-32 of its column scale (max_m |D_mn|), so
+      |d rho_i| <= 2^-30 sum_n |phi_n| (2 max_m |phi_m| sum_m |D_mn| + max_m |D_mn| sum_m |phi_m|)
+    (a factor 4 over the slicing bound for the double-float drains).
+BF16X6 on the whole grid is measured and stated (it misses 1e-6 Ha here)."""
 import numpy as np
 import pytest
 
@@ -46,26 +48,41 @@ def cnoh():
     return synth.make_system(3)
 
 
-def test_cnoh1000_full_grid_sampled_ranges(cnoh):
+def test_cnoh1000_whole_grid_and_sampled_ranges(cnoh):
     import torch
     kldi = _kldi()
     s = cnoh
-    plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe")
+    plan = kldi.plan_for_system(s, prec="bf16x10", xc="pbe")
     nb = plan.stats["nblocks"]
     D = torch.from_numpy(s.D).cuda()
-    V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda")
-    E = torch.zeros(1, dtype=torch.float64, device="cuda")
-    kldi.exc(plan, "pbe", D, V, E)                       # the whole grid
-    torch.cuda.synchronize()
-    Vw = V.cpu().numpy()
-    assert np.isfinite(E.item()) and E.item() < 0.0
-    assert np.array_equal(Vw, Vw.T)
+
+    def whole(prec):
+        plan.set_precision(prec)
+        V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda")
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        kldi.exc(plan, "pbe", D, V, E)
+        torch.cuda.synchronize()
+        return E.item(), V
+
+    E10, V10 = whole("bf16x10")
+    E6, V6 = whole("bf16x6")
+    E64, V64 = whole("fp64")
+    dV10 = (V10 - V64).abs().max().item()
+    dV6 = (V6 - V64).abs().max().item()
+    print(f"cnoh1000 whole grid: E_xc {E64:.9f} Ha (fp64); bf16x10 dE {E10 - E64:+.2e} max|dV| {dV10:.2e}; "
+          f"bf16x6 dE {E6 - E64:+.2e} max|dV| {dV6:.2e}; max|V| {V64.abs().max().item():.3f}")
+    assert np.isfinite(E64) and E64 < 0.0
+    assert abs(E10 - E64) <= 1e-6
+    assert dV10 <= 1e-7
+    assert abs(E6 - E64) <= 5e-5            # BF16X6: its measured error, stated
+    assert torch.equal(V10, V10.T)
+    del V6
     # retained fraction of basis-block pairs (the workload's stated 5-15 % band)
     ptr, idx, _ = plan.lists()
     n = np.diff(ptr).astype(np.float64)
     frac = float(np.sum(n * n)) / (nb * plan.stats["nbasis_blocks"] ** 2)
-    print(f"cnoh1000: E_xc {E.item():.6f} Ha, mean retained blocks {n.mean():.1f} of "
-          f"{plan.stats['nbasis_blocks']}, retained pair fraction {frac:.3f}")
+    print(f"cnoh1000: mean retained blocks {n.mean():.1f} of {plan.stats['nbasis_blocks']}, "
+          f"retained pair fraction {frac:.3f}")
     # sampled ranges against the oracle
     rng = np.random.default_rng(23)
     starts = sorted(rng.choice(nb - 6, size=3, replace=False).tolist())
@@ -75,25 +92,29 @@ def test_cnoh1000_full_grid_sampled_ranges(cnoh):
     sh = ob.build_shells(s.xyz, s.basis)
     rho_full = torch.zeros(plan.npoints, dtype=torch.float64, device="cuda")
     grad_full = torch.zeros((plan.npoints, 3), dtype=torch.float64, device="cuda")
+    aD = np.abs(s.D)
     for g0, g1 in ranges:
         ref = oe.evaluate(s, go, sh, screened=True, blocks=range(g0, g1))
-        plan.set_block_range(g0, g1)
-        Vr = torch.zeros_like(V)
-        Er = torch.zeros_like(E)
-        kldi.exc(plan, "pbe", D, Vr, Er)
-        kldi.density(plan, D, rho_full, grad_full)
-        torch.cuda.synchronize()
         pts = slice(g0 * 128, g1 * 128)
-        r_gpu = rho_full[pts].cpu().numpy()
         ap = np.abs(ob.eval_basis(go.points[pts], sh, deriv=False)[0])
-        aD = np.abs(s.D)
-        bound = 2.0 ** -22 * (2.0 * ap.max(axis=1) * (ap @ aD.sum(axis=0)) + ap.sum(axis=1) * (ap @ aD.max(axis=0)))
-        ratio = np.abs(r_gpu - ref.rho[pts]) / (bound + 1e-300)
-        print(f"range {g0}: dE {Er.item() - ref.E:.2e}, max|dV| {np.abs(Vr.cpu().numpy() - ref.V).max():.2e}, "
-              f"max rho error / bound {ratio.max():.3f}")
-        assert abs(Er.item() - ref.E) <= 1e-6, (g0, Er.item(), ref.E)
-        assert np.abs(Vr.cpu().numpy() - ref.V).max() <= 3e-7, g0
-        assert np.all(ratio <= 1.0), g0
+        bound = 2.0 ** -30 * (2.0 * ap.max(axis=1) * (ap @ aD.sum(axis=0)) + ap.sum(axis=1) * (ap @ aD.max(axis=0)))
+        plan.set_block_range(g0, g1)        # work lists of the range only (cheap to switch precision)
+        for prec, tE, tV in (("fp64", 1e-10, 1e-10), ("bf16x10", 1e-6, 1e-7)):
+            plan.set_precision(prec)
+            Vr = torch.zeros_like(V10)
+            Er = torch.zeros(1, dtype=torch.float64, device="cuda")
+            kldi.exc(plan, "pbe", D, Vr, Er)
+            kldi.density(plan, D, rho_full, grad_full)
+            torch.cuda.synchronize()
+            r_gpu = rho_full[pts].cpu().numpy()
+            dV = np.abs(Vr.cpu().numpy() - ref.V).max()
+            ratio = np.abs(r_gpu - ref.rho[pts]) / (bound + 1e-300)
+            print(f"range {g0} {prec}: dE {Er.item() - ref.E:.2e}, max|dV| {dV:.2e}, "
+                  f"max rho error / bound {ratio.max():.3f}")
+            assert abs(Er.item() - ref.E) <= tE, (g0, prec, Er.item(), ref.E)
+            assert dV <= tV, (g0, prec, dV)
+            if prec == "bf16x10":
+                assert np.all(ratio <= 1.0), g0
 
 
 def _density_points(system):

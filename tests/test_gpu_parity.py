@@ -2,15 +2,17 @@
 same seeded inputs, element by element.
 
 Tolerances (written per mode, derived from the arithmetic):
-  fp64    FP64 block form: |dE| <= 1e-10 Ha, max|dV| <= 1e-10, rho to 1e-12.
-  bf16x6  three 8-bit slices per operand, exact tensor-core accumulation:
-          |dE| <= 1e-6 Ha (the stated target); max|dV| <= 3e-7 (the stated
-          target is 1e-7; the FP32 basis values leave ~1e-7 of noise on the
-          largest V elements, see the design notes); rho to 4e-5 of |rho| +
-          1e-9 (fixed-point slices are relative to the point's largest
-          function value).
-  bf16x3  two 8-bit slices: element error 2^-16 of the row / column scale,
-          so |dE| <= 3e-5 |E| and max|dV| <= 2e-4.
+  fp64     FP64 block form: |dE| <= 1e-10 Ha, max|dV| <= 1e-10, rho to 1e-12.
+  bf16x10  four 8-bit slices per operand (2^-32 of the row / column scale),
+           exact tensor-core levels, double-float basis values, X and
+           row-dot: the stated target |dE| <= 1e-6 Ha and max|dV| <= 1e-7;
+           rho to 1e-7 of |rho| + 1e-12.
+  bf16x6   three 8-bit slices, FP32 basis values: the fast mode, held to its
+           measured error, not to the target: |dE| <= 1e-6 Ha on these small
+           systems, max|dV| <= 3e-7 (the largest V elements, ~5 Ha, carry the
+           2^-24 relative error of FP32 operands); rho to 4e-5 of |rho| + 1e-9.
+  bf16x3   two 8-bit slices: element error 2^-16 of the row / column scale,
+           so |dE| <= 3e-5 |E| and max|dV| <= 2e-4.
 Index work (the retained lists) is compared exactly; summaries to 1e-12.
 """
 import json
@@ -29,6 +31,7 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 TOL = {
     "fp64": dict(E_abs=1e-10, V=1e-10, rho_rel=1e-12, rho_abs=1e-14),
+    "bf16x10": dict(E_abs=1e-6, V=1e-7, rho_rel=1e-7, rho_abs=1e-12),
     "bf16x6": dict(E_abs=1e-6, V=3e-7, rho_rel=4e-5, rho_abs=1e-9),
     "bf16x3": dict(E_rel=3e-5, V=2e-4, rho_rel=2e-2, rho_abs=1e-7),
 }
@@ -81,18 +84,21 @@ def check(prec, E, V, rho, ref):
     assert np.all(np.abs(rho - ref.rho) <= t["rho_rel"] * np.abs(ref.rho) + t["rho_abs"])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x6", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x10", "bf16x6", "bf16x3"])
 @pytest.mark.parametrize("name,xc", [("w1", "lda_x"), ("w1", "pbe"), ("w4", "pbe")])
 def test_exc_matches_oracle(sys_cache, prec, name, xc):
     s = sys_cache[name]
     ref, g = oracle_run((name, xc), s, xc)
     plan, E, V, rho, grad = run_lib(s, prec, xc)
+    print(f"{name} {xc} {prec}: dE {E - ref.E:+.2e} max|dV| {np.abs(V - ref.V).max():.2e}")
     check(prec, E, V, rho, ref)
     if grad is not None and prec == "fp64":
         assert np.allclose(grad, ref.grad, rtol=1e-11, atol=1e-13)
+    if grad is not None and prec == "bf16x10":
+        assert np.all(np.abs(grad - ref.grad) <= 1e-7 * np.abs(ref.grad) + 1e-11)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6", "bf16x10"])
 def test_device_pointers_equal_host_pointers(sys_cache, prec):
     s = sys_cache["w1"]
     _, E1, V1, _, _ = run_lib(s, prec, "lda_x", device=False)
@@ -122,7 +128,7 @@ def test_vxc_from_oracle_density(sys_cache):
     from paper_2605_10363_gb300 import kldi
     s = sys_cache["w4"]
     ref, g = oracle_run(("w4", "pbe"), s, "pbe")
-    for prec, tV in (("fp64", 1e-10), ("bf16x6", 3e-7)):
+    for prec, tV in (("fp64", 1e-10), ("bf16x10", 1e-7), ("bf16x6", 3e-7)):
         plan = kldi.plan_for_system(s, prec=prec, xc="pbe")
         V = np.zeros((s.nbf, s.nbf))
         E = np.zeros(1)
@@ -156,14 +162,16 @@ def test_unsupported_and_invalid_requests(sys_cache):
     assert e.value.status == kldi.EINVAL
 
 
-@pytest.mark.parametrize("prec,order", [("bf16x6", "overlap"), ("bf16x6", "atom"), ("bf16x3", "atom")])
+@pytest.mark.parametrize("prec,order", [("bf16x10", "overlap"), ("bf16x10", "atom"), ("bf16x6", "overlap"),
+                                        ("bf16x6", "atom"), ("bf16x3", "atom")])
 def test_full_size_water33(prec, order):
     """33 waters (1.15M points, 825 functions) against stored oracle values:
     E_xc, tr(D V), sampled V elements and rho / grad rho on sampled grid blocks.
-    The benchmark's launch configuration is BF16x6 in the overlap-signature
+    The benchmark's launch configuration is BF16x10 in the overlap-signature
     shell order; the stored values come from the oracle in the generated (atom)
     order, whose screened block partition differs by the screening error
-    (dense - screened = 1.2e-9 Ha on this system)."""
+    (dense - screened = 1.2e-9 Ha on this system; sampled V elements of the two
+    partitions differ by up to ~3e-8)."""
     path = os.path.join(HERE, "golden", "water33_pbe.json")
     gold = json.load(open(path))
     from paper_2605_10363_gb300 import kldi
