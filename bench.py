@@ -5,9 +5,11 @@ Metric: grid points per second of the rho + V_xc build (one kldi_exc call:
 D -> rho, grad rho -> PBE-form functional -> E_xc and V), on the 33-water
 cluster (99 atoms, 825 Cartesian functions, 1,153,350 grid points in 9,011
 blocks of 128, t_b = t_d = 1e-10), synthetic seeded inputs.  The headline
-mode is BF16x6 (three exact fixed-point BF16 slices per operand), the mode
-whose E_xc stays within 1e-6 Ha of the FP64 oracle; BF16x3 and the FP64 block
-form (the speedup denominator) are timed beside it.
+mode is BF16x10 (four exact fixed-point BF16 slices per operand, double-float
+basis values), the mode held to |dE_xc| <= 1e-6 Ha and max|dV| <= 1e-7 against
+the FP64 oracle; the FP64 block form (the speedup denominator), BF16x6 and
+BF16x3 are timed beside it with their errors, and the 1000-atom cluster and
+the learned functional on the 167-water cluster run as side modes.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -44,8 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x6")
-    ap.add_argument("--no-side-modes", action="store_true", help="skip the FP64 / BF16x3 side measurements")
+    ap.add_argument("--prec", default="bf16x10")
+    ap.add_argument("--no-side-modes", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 1000-atom and 167-water side modes (a few minutes of host preprocessing)")
     ap.add_argument("--nwaters", type=int, default=0,
                     help="profiling case: a smaller water cluster of the same recipe (not a bench line)")
     ap.add_argument("--workload", default="water33", choices=["water33", "frames", "cnoh1000"],
@@ -119,11 +123,18 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- work counts
-def work_counts(plan, system, splits, counts=None):
+SPLITS = {"bf16x3": 3, "bf16x6": 6, "bf16x10": 10, "fp64": 1}
+NTILE = {"bf16x10": 2}     # basis blocks per N tile of the density product (4 otherwise)
+
+
+def work_counts(plan, system, splits, counts=None, nq=4):
     """Tensor-pipe FLOPs of one evaluation per product (algorithmic: executed
     block pairs x 2 x 128 x d_p d_q x slice products), from the retained lists
     and the D block maxima; `counts` (a dict) also receives the executed tensor
-    FLOPs including the padding of the 128-wide tiles."""
+    FLOPs including the padding of the tiles (density product: N tiles of nq
+    retained blocks), and the V product's algorithmic count over the executed
+    pairs p <= q of the symmetric product (v_pairs_pq) beside the S_g^2 count
+    that the returned value uses."""
     counts = {} if counts is None else counts
     ptr, idx, b = plan.lists()
     D = system.D
@@ -135,6 +146,7 @@ def work_counts(plan, system, splits, counts=None):
     dmax = pad.reshape(nbb, 32, nbb, 32).max(axis=(1, 3))
     f_rho = 0.0
     f_v = 0.0
+    f_v_pq = 0.0
     x_rho = 0.0
     x_v = 0.0
     for g in range(len(ptr) - 1):
@@ -147,14 +159,16 @@ def work_counts(plan, system, splits, counts=None):
         dd = np.outer(dsz[S], dsz[S])
         f_rho += 2.0 * 128 * float((dd * e1).sum())
         f_v += 2.0 * 128 * float(dd.sum())
+        f_v_pq += 2.0 * 128 * float(np.triu(dd).sum())
         # executed tensor work (tile padding included): density chunks of
-        # 128 x 128 x 32 per (N tile of 4 retained blocks, p with any executed
-        # pair); V jobs of 128 x 128 x 256 per tile pair P < Q, x 128 for P = Q
-        for q0 in range(0, S.size, 4):
-            x_rho += 2.0 * 128 * 128 * 32 * float(np.any(e1[:, q0:q0 + 4], axis=1).sum())
+        # 128 x (32 nq) x 32 per (N tile of nq retained blocks, p with any
+        # executed pair); V jobs of 128 x 128 x 256 per tile pair P < Q, x 128
+        # for P = Q
+        for q0 in range(0, S.size, nq):
+            x_rho += 2.0 * 128 * (32 * nq) * 32 * float(np.any(e1[:, q0:q0 + nq], axis=1).sum())
         nvt = len(set((S // 4).tolist()))
         x_v += 2.0 * 128 * 128 * (256 * nvt * (nvt - 1) / 2 + 128 * nvt)
-    counts.update(executed_rho=splits * x_rho, executed_v=splits * x_v)
+    counts.update(executed_rho=splits * x_rho, executed_v=splits * x_v, v_pairs_pq=splits * f_v_pq)
     return splits * f_rho, splits * f_v
 
 
@@ -209,16 +223,16 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
-# DRAM bytes per tensor FLOP of the two product kernels, from the ncu capture
-# summarised in profiles/ncu_full_water12_bf16x6.md (12-water case of the same
-# recipe; dram__bytes_read.sum + dram__bytes_write.sum over the launch's tensor
-# FLOPs).  The benchmark scales them by the launch's FLOPs.  Set an entry to
-# None when its kernel changes until it is captured again.
-DRAM_BYTES_PER_FLOP = {"k_v_tc": (1.586324e9 + 0.003784e9) / 4.159e11,
-                       "k_rho_tc": None}   # changed since the capture (packed basis records)
+# DRAM bytes per tensor FLOP of the product kernels, from an ncu capture of
+# the same kernel on a smaller case of the same recipe
+# (dram__bytes_read.sum + dram__bytes_write.sum over the launch's tensor
+# FLOPs); the benchmark scales them by the launch's FLOPs.  An entry is
+# removed when its kernel changes, until it is captured again.
+DRAM_BYTES_PER_FLOP = {}
+DRAM_SOURCE = None
 
 
-# ---------------------------------------------------------------------------- learned functional mode
+# ---------------------------------------------------------------------------- other shell order
 def order_mode(kldi, s, plan, order, stream, dev, args, E_main):
     """The same workload with the other shell order inside the plan (atom
     order if the main line uses the overlap-signature order, and conversely):
@@ -254,126 +268,7 @@ def order_mode(kldi, s, plan, order, stream, dev, args, E_main):
     return out
 
 
-def mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, xc_ms_analytic, E_analytic):
-    """Train the surrogate on the GPU on ~50M grid points of the two-water and
-    33-water systems (their densities from the library; the 33-water grid under
-    44 density matrices of its recipe), then time the same evaluation with the
-    network fused between the products."""
-    import torch
-
-    import synth
-
-    def points(system, p=None):
-        p = p or kldi.plan_for_system(system, prec="fp64", xc="pbe")
-        rho = np.zeros(p.npoints)
-        grad = np.zeros((p.npoints, 3))
-        kldi.density(p, system.D, rho, grad)
-        return rho, np.einsum("ic,ic->i", grad, grad)
-
-    # ~50M training points: the two-water system and the 33-water system under
-    # its own density and 43 further densities of the same recipe
-    r1, s1 = points(synth.make_system(1))
-    rs, ss = [r1], [s1]
-    Dv = [s.D] + synth.density_variants(s, 43)
-    for Dk in Dv:
-        rho_k = np.zeros(plan.npoints)
-        grad_k = np.zeros((plan.npoints, 3))
-        kldi.density(plan, Dk, rho_k, grad_k)
-        rs.append(rho_k)
-        ss.append(np.einsum("ic,ic->i", grad_k, grad_k))
-    rho = np.concatenate(rs)
-    sig = np.concatenate(ss)
-    del rs, ss
-    box = synth.mlp_box(rho, sig)
-    net = kldi.Mlp(synth.mlp_init(42), box)
-    epochs = 6
-    t0 = time.perf_counter()
-    hist = net.train(rho, sig, epochs=epochs, batch=8192, lr0=3e-3, lr1=1e-5)
-    t_train = time.perf_counter() - t0
-    kldi.plan_set_mlp(plan, net)
-    kldi.exc(plan, "mlp", D, V, E)
-    torch.cuda.synchronize(dev)
-    plan.profile(True)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    steps = max(3, args.steps // 2)
-    a.record(stream)
-    for _ in range(steps):
-        kldi.exc(plan, "mlp", D, V, E)
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_stage, _ = plan.stage_times()
-    plan.profile(False)
-    kldi.plan_set_mlp(plan, None)
-    ms = a.elapsed_time(b) / steps
-    return {"ms_per_step": ms, "value": plan.grid.nreal / (ms * 1e-3),
-            "dExc_vs_analytic": float(E.item()) - E_analytic,
-            "functional_stage_ms": {"mlp": ms_stage[3] / steps, "analytic": xc_ms_analytic},
-            "training": {"points": int(rho.size), "epochs": epochs, "batch": 8192, "seconds": round(t_train, 2),
-                         "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1])}}
-
-
 # ---------------------------------------------------------------------------- batched frames
-def run_large(args, dev, stream):
-    """The 1000-atom C/N/O/H cluster (9000 functions, 11.65M points): one
-    evaluation per precision mode (BF16x6, BF16x3, the FP64 block form; the
-    tensor modes after one untimed evaluation), with the plan statistics.  The overlap matrix
-    (for the shell order) is the Kohn-Sham setup's input; building it in numpy
-    and the plans are preprocessing, reported separately."""
-    import torch
-
-    import synth
-    from paper_2605_10363_gb300 import kldi
-    t0 = time.perf_counter()
-    s = synth.make_system(3, keep_overlap=True)
-    t_sys = time.perf_counter() - t0
-    order = None
-    t_order = 0.0
-    if args.basis_order == "overlap":
-        t1 = time.perf_counter()
-        order = kldi.order_shells(s.meta["S"], synth.shell_sizes(s.basis))
-        t_order = time.perf_counter() - t1
-    s.meta.pop("S")
-    D = torch.from_numpy(s.D).to(dev)
-    V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device=dev)
-    E = torch.zeros(1, dtype=torch.float64, device=dev)
-    modes = {}
-    npts = 0
-    for prec in ("bf16x6", "bf16x3", "fp64"):
-        t1 = time.perf_counter()
-        plan = kldi.plan_for_system(s, prec=prec, xc="pbe", stream=stream.cuda_stream, shell_order=order)
-        t_plan = time.perf_counter() - t1
-        npts = plan.grid.nreal
-        if prec != "fp64":                 # the FP64 form takes tens of seconds: one evaluation
-            kldi.exc(plan, "pbe", D, V, E)
-        torch.cuda.synchronize(dev)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        kldi.exc(plan, "pbe", D, V, E)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = a.elapsed_time(b)
-        st = plan.stats
-        modes[prec] = {"ms_per_step": ms, "value": npts / (ms * 1e-3), "E_xc": float(E.item()),
-                       "plan_seconds": round(t_plan, 1),
-                       "retained_fraction": st["pair_slots"] / (st["nblocks"] * st["nbasis_blocks"] ** 2)}
-        del plan
-    main = modes["bf16x6"]
-    print(json.dumps({
-        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-        "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "cnoh1000_pbe: 1000 atoms (240 C, 80 N, 80 O, 600 H, 0.1 atoms/A^3), 9000 "
-                               "Cartesian s/p/d functions, 11.65M points, PBE-form, t_b = t_d = 1e-10",
-                   "precision": "bf16x6", "system_seconds": round(t_sys, 1), "order_seconds": round(t_order, 1),
-                   "basis_order": "overlap-signature clustering" if order is not None else "atom order"},
-        "speedup_vs_fp64": modes["fp64"]["ms_per_step"] / main["ms_per_step"],
-        "dE_bf16x6_vs_fp64": modes["bf16x6"]["E_xc"] - modes["fp64"]["E_xc"],
-        "dE_bf16x3_vs_fp64": modes["bf16x3"]["E_xc"] - modes["fp64"]["E_xc"],
-        "modes": modes}), flush=True)
-
-
 def run_frames(args, dev, stream):
     """Frames of uneven size (20-130 waters, own D each) through one CUDA-graph
     batch with a shared tile workspace and the tuned V decomposition."""
@@ -424,6 +319,161 @@ def run_frames(args, dev, stream):
         "E_xc": E.cpu().numpy().tolist()}), flush=True)
 
 
+# ---------------------------------------------------------------------------- side modes
+def timed(kldi, plan, xc, D, V, E, stream, dev, steps, warm=1):
+    import torch
+    for _ in range(warm):
+        kldi.exc(plan, xc, D, V, E)
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        kldi.exc(plan, xc, D, V, E)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / steps
+
+
+def precision_modes(kldi, s, order, D, V_main, E_main, stream, dev, args, gold):
+    """The FP64 block form (speedup denominator), BF16x6 and BF16x3 on the
+    main workload, one plan switched between them: time, E_xc against the
+    stored oracle value and against the FP64 block form, and max|dV| over the
+    whole matrix against the FP64 block form (the main line's V too)."""
+    import torch
+    p2 = kldi.plan_for_system(s, prec="fp64", xc="pbe", stream=stream.cuda_stream, shell_order=order)
+    nbf = s.nbf
+    V = torch.zeros((nbf, nbf), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    modes = {}
+    ms = timed(kldi, p2, "pbe", D, V, E, stream, dev, 2)
+    V64, E64 = V.clone(), float(E.item())
+    modes["fp64"] = {"ms_per_step": ms, "value": p2.grid.nreal / (ms * 1e-3), "E_xc": E64}
+    for pm in ("bf16x6", "bf16x3"):
+        p2.set_precision(pm)
+        ms = timed(kldi, p2, "pbe", D, V, E, stream, dev, max(3, args.steps // 2))
+        modes[pm] = {"ms_per_step": ms, "value": p2.grid.nreal / (ms * 1e-3), "E_xc": float(E.item()),
+                     "dExc_vs_fp64": float(E.item()) - E64, "max_dV_vs_fp64": float((V - V64).abs().max().item())}
+    for pm, m in modes.items():
+        if gold is not None:
+            m["dExc_vs_oracle"] = m["E_xc"] - gold["E_screened"]
+    main = {"dExc_vs_fp64": E_main - E64, "max_dV_vs_fp64": float((V_main - V64).abs().max().item()),
+            "max_abs_V": float(V64.abs().max().item())}
+    del p2
+    return modes, main
+
+
+def large_mode(kldi, dev, stream, args):
+    """The 1000-atom C/N/O/H cluster (9000 functions, 11.65M points) on one
+    plan switched between the precision modes: time per evaluation, points/s,
+    E_xc and max|dV| against the FP64 block form, and the density product's
+    tensor rate.  Building the system (numpy) and the plan is preprocessing,
+    reported separately."""
+    import torch
+
+    import synth
+    t0 = time.perf_counter()
+    s = synth.make_system(3, keep_overlap=True)
+    t_sys = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    order = kldi.order_shells(s.meta.pop("S"), synth.shell_sizes(s.basis))
+    t_order = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    plan = kldi.plan_for_system(s, prec="bf16x10", xc="pbe", stream=stream.cuda_stream, shell_order=order)
+    t_plan = time.perf_counter() - t1
+    D = torch.from_numpy(s.D).to(dev)
+    V = torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    res, Vs, Es = {}, {}, {}
+    npts = plan.grid.nreal
+    for pm in ("bf16x10", "bf16x6", "bf16x3", "fp64"):
+        plan.set_precision(pm)
+        ms = timed(kldi, plan, "pbe", D, V, E, stream, dev, 1, warm=0 if pm == "fp64" else 1)
+        res[pm] = {"ms_per_step": ms, "value": npts / (ms * 1e-3), "E_xc": float(E.item())}
+        if pm in ("bf16x10", "bf16x6"):
+            Vs[pm] = V.clone()
+        Es[pm] = float(E.item())
+    for pm in ("bf16x10", "bf16x6"):
+        res[pm]["dExc_vs_fp64"] = Es[pm] - Es["fp64"]
+        res[pm]["max_dV_vs_fp64"] = float((Vs[pm] - V).abs().max().item())
+        res[pm]["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res[pm]["ms_per_step"]
+    res["bf16x3"]["dExc_vs_fp64"] = Es["bf16x3"] - Es["fp64"]
+    st = plan.stats
+    out = {"workload": "cnoh1000_pbe: 1000 atoms (240 C, 80 N, 80 O, 600 H, 0.1 atoms/A^3), 9000 Cartesian "
+                       "s/p/d functions, 11.65M points, PBE-form, t_b = t_d = 1e-10, overlap-signature order",
+           "points": int(npts), "modes": res,
+           "retained_pair_fraction": st["pair_slots"] / (st["nblocks"] * st["nbasis_blocks"] ** 2),
+           "host_seconds": {"system": round(t_sys, 1), "order": round(t_order, 1), "plan": round(t_plan, 1)}}
+    del plan, Vs
+    return out
+
+
+def learned_mode(kldi, s2, plan2, dev, stream, args):
+    """The learned functional: the surrogate trained on the GPU on ~50M grid
+    points of the two-water and 33-water systems (their densities from the
+    library; the 33-water grid under 44 density matrices of its recipe), then
+    fused between the products on the 167-water cluster (501 atoms, 4175
+    functions, 5.84M points, BF16x10) against the analytic PBE-form functional
+    on the same plan: time, functional-stage time and the E_xc difference."""
+    import torch
+
+    import synth
+
+    def points(system, p=None):
+        p = p or kldi.plan_for_system(system, prec="fp64", xc="pbe")
+        rho = np.zeros(p.npoints)
+        grad = np.zeros((p.npoints, 3))
+        kldi.density(p, system.D, rho, grad)
+        return rho, np.einsum("ic,ic->i", grad, grad)
+
+    r1, s1 = points(synth.make_system(1))
+    rs, ss = [r1], [s1]
+    for Dk in [s2.D] + synth.density_variants(s2, 43):
+        rho_k = np.zeros(plan2.npoints)
+        grad_k = np.zeros((plan2.npoints, 3))
+        kldi.density(plan2, Dk, rho_k, grad_k)
+        rs.append(rho_k)
+        ss.append(np.einsum("ic,ic->i", grad_k, grad_k))
+    rho = np.concatenate(rs)
+    sig = np.concatenate(ss)
+    del rs, ss
+    box = synth.mlp_box(rho, sig)
+    net = kldi.Mlp(synth.mlp_init(42), box)
+    epochs = 6
+    t0 = time.perf_counter()
+    hist = net.train(rho, sig, epochs=epochs, batch=8192, lr0=3e-3, lr1=1e-5)
+    t_train = time.perf_counter() - t0
+    npts_train = int(rho.size)
+    del rho, sig
+    t0 = time.perf_counter()
+    s5 = synth.make_system(5)
+    plan = kldi.plan_for_system(s5, prec="bf16x10", xc="pbe", stream=stream.cuda_stream)
+    t_plan = time.perf_counter() - t0
+    D = torch.from_numpy(s5.D).to(dev)
+    V = torch.zeros((s5.nbf, s5.nbf), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = {}
+    for xc in ("pbe", "mlp"):
+        if xc == "mlp":
+            kldi.plan_set_mlp(plan, net)
+        ms = timed(kldi, plan, xc, D, V, E, stream, dev, 3)
+        plan.profile(True)
+        kldi.exc(plan, xc, D, V, E)
+        st, _ = plan.stage_times()
+        plan.profile(False)
+        out[xc] = {"ms_per_step": ms, "value": plan.grid.nreal / (ms * 1e-3), "E_xc": float(E.item()),
+                   "functional_stage_ms": float(st[3])}
+    kldi.plan_set_mlp(plan, None)
+    return {"workload": "water167_pbe: 167 waters (501 atoms), 4175 functions, 5.84M points, BF16x10",
+            "analytic": out["pbe"], "learned": out["mlp"],
+            "dExc_learned_vs_analytic": out["mlp"]["E_xc"] - out["pbe"]["E_xc"],
+            "speedup_learned_vs_analytic": out["pbe"]["ms_per_step"] / out["mlp"]["ms_per_step"],
+            "training": {"points": npts_train, "epochs": epochs, "batch": 8192,
+                         "seconds": round(t_train, 2), "loss_first_epoch": float(hist[0]),
+                         "loss_last_epoch": float(hist[-1])},
+            "plan_seconds": round(t_plan, 1)}
+
+
 # ---------------------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -433,9 +483,10 @@ def main():
         return
     if args.workload == "cnoh1000":
         import torch
+        from paper_2605_10363_gb300 import kldi
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
-        run_large(args, dev, torch.cuda.current_stream(dev))
+        print(json.dumps(large_mode(kldi, dev, torch.cuda.current_stream(dev), args)), flush=True)
         return
     if args.workload == "frames":
         import torch
@@ -493,6 +544,7 @@ def main():
     ms_step = ms_total / args.steps
     value = npts_real * args.steps * world / (ms_total * 1e-3)
     E_ours = float(E.item())
+    V_main = V.clone()
 
     # end to end through the public API with pinned host buffers
     Dh = torch.from_numpy(s.D).pin_memory()
@@ -509,22 +561,24 @@ def main():
            "d2h_bytes_per_step": nbf * nbf * 8 + 8}
 
     out_extra = {}
+    gold = None
     # accuracy against the stored oracle values of this workload
     gold_path = os.path.join(ROOT, "tests", "golden", "water33_pbe.json")
     if os.path.exists(gold_path) and not args.nwaters:
         gold = json.load(open(gold_path))
         out_extra["dExc_vs_oracle"] = E_ours - gold["E_screened"]
-        Vn = V.cpu().numpy()
+        Vn = V_main.cpu().numpy()
         vs = np.array(gold["V_samples"])
         out_extra["max_dV_sampled_vs_oracle"] = float(np.abs(Vn[vs[:, 0].astype(int), vs[:, 1].astype(int)]
                                                              - vs[:, 2]).max())
         out_extra["oracle_values"] = ("screened FP64 oracle in the atom order (tests/golden); a plan in another "
                                       "shell order screens other 32-function blocks, a difference of the order of "
-                                      "this workload's screening error (dense - screened = 1.2e-9 Ha)")
+                                      "this workload's screening error (dense - screened = 1.2e-9 Ha); the "
+                                      "whole-matrix max|dV| is taken against the FP64 block form on the same plan")
 
-    splits = {"bf16x3": 3, "bf16x6": 6, "fp64": 1}[args.prec]
+    splits = SPLITS[args.prec]
     executed = {}
-    f_rho, f_v = work_counts(plan, s_int, splits, executed)
+    f_rho, f_v = work_counts(plan, s_int, splits, executed, nq=NTILE.get(args.prec, 4))
     names = kldi.STAGES
     per_stage = {names[k]: round(stage_ms[k] / args.steps, 4) for k in range(len(names))}
     dom = "rho" if stage_ms[2] >= stage_ms[5] else "v"
@@ -533,55 +587,40 @@ def main():
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
         pk = json.load(open(peaks_path))
-        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        peak_src = "measured (bf16 sustained)"
+        peak = pk.get("bf16_tflops", pk.get("bf16_tflops_sustained"))
+        peak_src = "measured (bf16 burst; the step is well under a second)"
     else:
-        peak, peak_src = 1700.0, "fallback (bf16 sustained)"
+        peak, peak_src = 1900.0, "fallback (bf16 burst)"
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     oth = 5 if dom == "rho" else 2
     oth_ms = stage_ms[oth] / max(1, stage_n[oth])
     dom_kernel = "k_rho_tc" if dom == "rho" else "k_v_tc"
-    bpf = DRAM_BYTES_PER_FLOP.get(dom_kernel) if args.prec == "bf16x6" else None
+    bpf = DRAM_BYTES_PER_FLOP.get((dom_kernel, args.prec))
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": bpf * dom_flops if bpf else None,
-            "traffic_source": "ncu 12-water capture scaled by FLOPs (profiles/ncu_full_water12_bf16x6.md)"
-            if bpf else None,
+            "traffic_source": DRAM_SOURCE if bpf else None,
             "kernel": dom_kernel, "peak_source": peak_src,
             "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
+            "flops_note": ("tensor-pipe FLOPs = slice products x 2 x 128 x sum d_p d_q over the density "
+                           "product's executed pairs E1_g, and over S_g^2 for the V product (its two terms "
+                           "Phi^T X + X^T Phi cover every ordered pair); V over p <= q only: v_flops_pq"),
+            "v_flops_pq": executed["v_pairs_pq"],
             "executed_flops_per_launch": executed["executed_rho" if dom == "rho" else "executed_v"],
             "executed_tflops": executed["executed_rho" if dom == "rho" else "executed_v"] / (dom_ms * 1e-3) / 1e12,
             "other_kernel": {"kernel": "k_v_tc" if dom == "rho" else "k_rho_tc",
                              "ms_per_launch": oth_ms,
                              "achieved": (f_v if dom == "rho" else f_rho) / (oth_ms * 1e-3) / 1e12,
+                             "frac": (f_v if dom == "rho" else f_rho) / (oth_ms * 1e-3) / 1e12 / peak,
                              "executed_flops_per_launch": executed["executed_v" if dom == "rho" else "executed_rho"],
                              "executed_tflops": executed["executed_v" if dom == "rho" else "executed_rho"]
                              / (oth_ms * 1e-3) / 1e12}}
 
-    # side modes: the FP64 block form (speedup denominator) and BF16x3
     modes = {}
     if not args.no_side_modes and rank == 0:
-        for pm, steps in (("fp64", 2), ("bf16x3", max(3, args.steps // 2))):
-            p2 = kldi.plan_for_system(s, prec=pm, xc="pbe", stream=stream.cuda_stream, shell_order=order)
-            kldi.exc(p2, "pbe", D, V, E)
-            torch.cuda.synchronize(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            bb = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(steps):
-                kldi.exc(p2, "pbe", D, V, E)
-            bb.record(stream)
-            torch.cuda.synchronize(dev)
-            ms = a.elapsed_time(bb) / steps
-            m = {"ms_per_step": ms, "value": npts_real / (ms * 1e-3)}
-            if "dExc_vs_oracle" in out_extra:
-                m["dExc_vs_oracle"] = float(E.item()) - gold["E_screened"]
-                Vm = V.cpu().numpy()
-                m["max_dV_sampled_vs_oracle"] = float(np.abs(Vm[vs[:, 0].astype(int), vs[:, 1].astype(int)]
-                                                             - vs[:, 2]).max())
-            modes[pm] = m
-            del p2
+        modes, acc = precision_modes(kldi, s, order, D, V_main, E_ours, stream, dev, args, gold)
+        out_extra.update(acc)
         out_extra["speedup_vs_fp64"] = modes["fp64"]["ms_per_step"] / ms_step
-        # nuclear gradient of E_xc (FP64 block form)
+        # nuclear gradient of E_xc: FP64 block form and the tensor-core form
         pg = kldi.plan_for_system(s, prec="fp64", xc="pbe", stream=stream.cuda_stream, shell_order=order)
         Gd = torch.zeros((len(s.Z), 3), dtype=torch.float64, device=dev)
         kldi.exc_grad(pg, "pbe", D, Gd, E)
@@ -597,24 +636,23 @@ def main():
         modes["gradient_fp64"] = {"ms_per_step": ms, "value": npts_real / (ms * 1e-3),
                                   "max_abs_gradient": float(Gd.abs().max().item())}
         del pg
-        # the same gradient through the tensor-core density product (BF16x6)
-        pt = kldi.plan_for_system(s, prec=args.prec, xc="pbe", stream=stream.cuda_stream, shell_order=order)
         Gt = torch.zeros((len(s.Z), 3), dtype=torch.float64, device=dev)
         for _ in range(2):
-            kldi.exc_grad(pt, "pbe", D, Gt, E)
+            kldi.exc_grad(plan, "pbe", D, Gt, E)
         torch.cuda.synchronize(dev)
         a.record(stream)
         for _ in range(5):
-            kldi.exc_grad(pt, "pbe", D, Gt, E)
+            kldi.exc_grad(plan, "pbe", D, Gt, E)
         bb.record(stream)
         torch.cuda.synchronize(dev)
         mt = a.elapsed_time(bb) / 5
         modes["gradient_" + args.prec] = {"ms_per_step": mt, "value": npts_real / (mt * 1e-3),
                                           "max_abs_diff_vs_fp64": float((Gt - Gd).abs().max().item()),
                                           "speedup_vs_fp64": ms / mt}
-        del pt
-        modes["mlp"] = mlp_mode(kldi, s, plan, D, V, E, stream, dev, args, stage_ms[3] / args.steps, E_ours)
         modes["other_basis_order"] = order_mode(kldi, s, plan, order, stream, dev, args, E_ours)
+        if not args.no_large and not args.nwaters:
+            modes["cnoh1000"] = large_mode(kldi, dev, stream, args)
+            modes["learned_water167"] = learned_mode(kldi, s, plan, dev, stream, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.nwaters:
