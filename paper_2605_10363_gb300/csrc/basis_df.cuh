@@ -195,11 +195,14 @@ __device__ __forceinline__ void for_rec_functions_df(const BlockRec* rec, const 
 
 // Calls f(nu, chi, X) (hi / lo) for every function of a staged basis block,
 // with X = a chi + b . grad chi (the V product's operand; a, b per point).
-// Per shell, b . grad chi = g (b . grad P) + P (b . u) with u = -2 r gd, so the
-// gradient is never formed component by component.
+// Per shell, with chi = P g and grad chi = (grad P) g + P u (u = -2 r gd):
+//   X = a chi + (g b) . grad P + P (b . u),
+// where grad P has one or two non-zero components, so each function costs a
+// few double-float products.
 template <bool GRAD, typename F>
 __device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float2* tab, f2 px, f2 py, f2 pz, f2 a,
                                                 f2 bx, f2 by, f2 bz, F&& f) {
+  const f2 s3{kS3h, kS3l};
   const int ns = rec->nshell;
   for (int s = 0; s < ns; ++s) {
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
@@ -208,21 +211,36 @@ __device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float
     f2 dx, dy, dz, r2, g, gd;
     offsets_df(c0, c1, px, py, pz, dx, dy, dz, r2);
     radial_df<GRAD>(rec->pf + pi, rec->pac + pi, np, r2, tab, g, gd);
-    f2 w{0.f, 0.f};   // b . u = -2 gd (b . r)
-    if (GRAD) w = df_mul(df_scale(gd, -2.f), df_add(df_add(df_mul(bx, dx), df_mul(by, dy)), df_mul(bz, dz)));
-    const int ncomp = (l + 1) * (l + 2) / 2;
-    for (int c = 0; c < ncomp; ++c) {
+    f2 w{0.f, 0.f}, gbx{0.f, 0.f}, gby{0.f, 0.f}, gbz{0.f, 0.f};
+    if (GRAD) {
+      w = df_mul(df_scale(gd, -2.f), df_add(df_add(df_mul(bx, dx), df_mul(by, dy)), df_mul(bz, dz)));
+      gbx = df_mul(g, bx);
+      gby = df_mul(g, by);
+      gbz = df_mul(g, bz);
+    }
+    auto emit = [&](int c, f2 P, f2 bdP) {   // bdP = (g b) . grad P
       const int nu = first + c;
-      if (nu < 0 || nu >= kBasisBlk) continue;
-      f2 P, Px, Py, Pz;
-      cart_df(l, c, dx, dy, dz, P, Px, Py, Pz);
+      if (nu < 0 || nu >= kBasisBlk) return;
       const f2 v = df_mul(P, g);
-      if (GRAD) {
-        const f2 t = df_add(df_add(df_mul(a, P), df_mul(bx, Px)), df_add(df_mul(by, Py), df_mul(bz, Pz)));
-        f(nu, v, df_add(df_mul(g, t), df_mul(P, w)));
-      } else {
-        f(nu, v, df_mul(a, v));
-      }
+      f2 x = df_mul(a, v);
+      if (GRAD) x = df_add(x, df_add(bdP, df_mul(P, w)));
+      f(nu, v, x);
+    };
+    const f2 z{0.f, 0.f};
+    if (l == 0) {
+      emit(0, f2{1.f, 0.f}, z);
+    } else if (l == 1) {
+      emit(0, dx, gbx);
+      emit(1, dy, gby);
+      emit(2, dz, gbz);
+    } else {
+      const f2 sx = df_mul(dx, s3), sy = df_mul(dy, s3), sz = df_mul(dz, s3);
+      emit(0, df_mul(dx, sx), GRAD ? df_scale(df_mul(gbx, sx), 2.f) : z);
+      emit(1, df_mul(dx, dy), GRAD ? df_add(df_mul(gbx, dy), df_mul(gby, dx)) : z);
+      emit(2, df_mul(dx, dz), GRAD ? df_add(df_mul(gbx, dz), df_mul(gbz, dx)) : z);
+      emit(3, df_mul(dy, sy), GRAD ? df_scale(df_mul(gby, sy), 2.f) : z);
+      emit(4, df_mul(dy, dz), GRAD ? df_add(df_mul(gby, dz), df_mul(gbz, dy)) : z);
+      emit(5, df_mul(dz, sz), GRAD ? df_scale(df_mul(gbz, sz), 2.f) : z);
     }
   }
 }

@@ -718,11 +718,16 @@ __device__ __forceinline__ void issue_levels(uint32_t d0, uint32_t lstride, cons
 // fixed order).  BF16X6 / BF16X3: N tiles of 4 basis blocks, 16 epilogue
 // warps; BF16X10: N tiles of 2 basis blocks so that two buffers of the four
 // level accumulators fit TMEM (drains and row-dot overlap the next tile's
-// products), 8 epilogue warps, R and the row-dot in double-float.
+// products), 16 epilogue warps, two per (lane quarter, q block) draining half
+// the columns each and sharing the row-dot's shells, R and the row-dot in
+// double-float.
 template <int NS>
 struct RhoCfg {
   static constexpr int kNQ = NS == 4 ? 2 : 4;                     // q blocks per N tile
-  static constexpr int kEpi = 4 * kNQ;                            // epilogue warps: 4 lane quarters x kNQ
+  static constexpr int kHalves = NS == 4 ? 2 : 1;                 // warps per (lane quarter, q block)
+  static constexpr int kEpi = 4 * kNQ * kHalves;                  // epilogue warps
+  static constexpr int kGroups = kNQ * kHalves;                   // epilogue groups of 4 warps (one per quarter)
+  static constexpr int kColsPerWarp = 32 / kHalves;               // TMEM columns a warp drains
   static constexpr int kLevelCols = 32 * kNQ;                     // TMEM columns of one level accumulator
   static constexpr int kBufCols = NS * kLevelCols;                // NS level accumulators
   static constexpr int kBufs = 2 * kBufCols <= 512 ? 2 : 1;
@@ -730,9 +735,9 @@ struct RhoCfg {
   static constexpr int kStages = NS == 2 ? 3 : 2;
   static constexpr int kRsElem = NS == 4 ? 8 : 4;                 // R staged as FP32, or hi / lo pairs
   static constexpr int kOffR = kStages * kStageBytes;             // [kNQ q blocks][32][128] R
-  static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * kRsElem;   // [kNQ][4][128] double
+  static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * kRsElem;   // [kGroups][4][128] double
   static constexpr int kMetaWords = 4 + kMaxRet + kMaxRet * (kMaxRet / 32);
-  static constexpr int kOffMeta = kOffRed + kNQ * 4 * kBlockPts * 8;
+  static constexpr int kOffMeta = kOffRed + kGroups * 4 * kBlockPts * 8;
   static constexpr int kOffRec = kOffMeta + 2 * kMetaWords * 4;  // [kNQ q blocks][2] BlockRec
   static constexpr int kOffTab = kOffRec + 2 * kNQ * (int)sizeof(BlockRec);
   static constexpr int kOffBar = kOffTab + (NS == 4 ? 256 * 8 : 0);
@@ -743,17 +748,18 @@ struct RhoCfg {
   static_assert(kBufs * kBufCols <= 512, "TMEM");
 };
 
-// Row-dot of one basis block in double-float (BF16X10): with R_nu (hi / lo,
-// staged [32][128]) and the shell factorisation chi = P g,
+// Row-dot of one basis block in double-float (BF16X10), over the shells
+// s0, s0 + sstep, ...: with R_nu (hi / lo, staged [32][128]) and the shell
+// factorisation chi = P g,
 // grad chi = (grad P) g + P u (u = -2 r gd),
 //   sum_nu chi R = sum_s g S0,   sum_nu grad chi R = sum_s (g S1 + u S0),
 // S0 = sum_c P_c R_c and S1 = sum_c (grad P_c) R_c over the shell's components.
 template <bool GRAD>
-__device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float2* tab, const float2* Rs, int i, f2 px,
-                                          f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
+__device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float2* tab, const float2* Rs, int i, int s0,
+                                          int sstep, f2 px, f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
   const f2 s3{kS3h, kS3l};
   const int ns = rec->nshell;
-  for (int s = 0; s < ns; ++s) {
+  for (int s = s0; s < ns; s += sstep) {
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
     const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
     const int l = hdr & 255, np = (hdr >> 8) & 255, first = (hdr >> 16) - 64;
@@ -1021,9 +1027,13 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
       mbar_wait(mdone, 0, &no_abort, nullptr, 0);
     }
   } else {
-    // warp w: lane quarter w % 4 (its TMEM lanes), q block k4 of every N tile
+    // warp w: lane quarter w % 4 (its TMEM lanes), group grp = q block k4 of
+    // every N tile and, for BF16X10, half: the half of the q block's columns it
+    // drains and the parity of the shells whose row-dot terms it forms
     const int quarter = warp & 3;
-    const int k4 = (warp - 2) >> 2;
+    const int grp = (warp - 2) >> 2;
+    const int k4 = grp % C::kNQ;
+    const int half = grp / C::kNQ;
     const int i = quarter * 32 + lane;
     float* Rs = reinterpret_cast<float*>(sm + C::kOffR) + k4 * (kBasisBlk * kBlockPts);
     float2* Rs2 = reinterpret_cast<float2*>(sm + C::kOffR) + k4 * (kBasisBlk * kBlockPts);   // BF16X10
@@ -1070,8 +1080,8 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
         const int qb = mine ? plist[q0 + k4] : 0;
         const bool staged = mine && block_rec_fits(B, qb);
         if (staged) {
-          stage_block_rec(B, qb, anc, rec, quarter * 32 + lane, 128);
-          if (quarter == 0) rec->ds[lane] = dscale[qb * kBasisBlk + lane];
+          stage_block_rec(B, qb, anc, rec, half * 128 + quarter * 32 + lane, 128 * C::kHalves);
+          if (quarter == 0 && half == 0) rec->ds[lane] = dscale[qb * kBasisBlk + lane];
         }
         float R[32], Rl[32];   // Rl: low parts (BF16X10)
 #pragma unroll
@@ -1082,34 +1092,40 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
           if (!mbar_wait_warp(&tfull[buf], use & 1, abort_flag, err, 114, wait_ns)) { ok = false; break; }
           tc_fence_after();
           if (mine) {
-            const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + k4 * 32;
+            const uint32_t ta = tbase + ((uint32_t)(quarter * 32) << 16) + buf * C::kBufCols + k4 * 32 +
+                                half * C::kColsPerWarp;
             constexpr uint32_t LC = C::kLevelCols;
+            if constexpr (NS == 4) {
+              // 8 columns of the four levels at a time (registers)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+              for (int h = 0; h < C::kColsPerWarp / 8; ++h) {
+                float t[32];
+                tmem_ld8x4(ta + 3 * LC + h * 8, ta + 2 * LC + h * 8, ta + LC + h * 8, ta + h * 8, t);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                  // hi: the running sum plus L0, error-free; lo: its error plus
+                  // L1 and the two small levels (rounded at ~2^-32 of the scale)
+                  const f2 sg = two_sum(R[h * 8 + c], t[24 + c]);
+                  R[h * 8 + c] = sg.h;
+                  Rl[h * 8 + c] = __fadd_rn(Rl[h * 8 + c],
+                                            __fadd_rn(__fadd_rn(sg.l, t[16 + c]), __fadd_rn(t[8 + c], t[c])));
+                }
+              }
+            }
+#pragma unroll
+            for (int h = 0; h < (NS == 4 ? 0 : C::kColsPerWarp / 16); ++h) {
               // the NS levels of 16 columns, smallest first, one wait
               float t[16 * NS];
-              if constexpr (NS == 4)
-                tmem_ld16x4(ta + 3 * LC + h * 16, ta + 2 * LC + h * 16, ta + LC + h * 16, ta + h * 16, t);
-              else if constexpr (NS == 3)
+              if constexpr (NS == 3)
                 tmem_ld16x3(ta + 2 * LC + h * 16, ta + LC + h * 16, ta + h * 16, t);
-              else
+              else if constexpr (NS == 2)
                 tmem_ld16x2(ta + LC + h * 16, ta + h * 16, t);
 #pragma unroll
               for (int c = 0; c < 16; ++c) {
-                if constexpr (NS == 4) {
-                  // L0 + L1 error-free, the two small levels rounded (2^-40 of
-                  // the scale), then added to the running hi / lo sum
-                  const f2 sg = two_sum(t[48 + c], t[32 + c]);
-                  const f2 r = df_add(f2{R[h * 16 + c], Rl[h * 16 + c]},
-                                      f2{sg.h, __fadd_rn(sg.l, __fadd_rn(t[16 + c], t[c]))});
-                  R[h * 16 + c] = r.h;
-                  Rl[h * 16 + c] = r.l;
-                } else {
-                  float acc = t[c];
+                float acc = t[c];
 #pragma unroll
-                  for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
-                  R[h * 16 + c] += acc;
-                }
+                for (int l = 1; l < NS; ++l) acc += t[16 * l + c];
+                R[h * 16 + c] += acc;
               }
             }
           }
@@ -1122,15 +1138,17 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
         // (a tile without executed pairs has R = 0 and adds nothing)
         if (mine) {
           const int q = qb;
-          named_bar_sync(1 + k4, 128);
+          named_bar_sync(1 + k4, 128 * C::kHalves);
           ++ruse;
           if constexpr (NS == 4) {
-            // staged by construction (every block fits a record in BF16X10 plans)
+            // this warp's columns; the row-dot reads both halves' columns
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-              const float f = staged ? rec->ds[c] : dscale[q * kBasisBlk + c];
-              Rs2[c * kBlockPts + i] = make_float2(R[c] * f, Rl[c] * f);
+            for (int c = 0; c < C::kColsPerWarp; ++c) {
+              const int col = half * C::kColsPerWarp + c;
+              const float f = staged ? rec->ds[col] : dscale[q * kBasisBlk + col];
+              Rs2[col * kBlockPts + i] = make_float2(R[c] * f, Rl[c] * f);
             }
+            named_bar_sync(1 + k4, 128 * C::kHalves);
           } else if (staged) {
 #pragma unroll
             for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * rec->ds[c];
@@ -1141,8 +1159,8 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
           if constexpr (MODE == kRowDot && NS == 4) {
             if (staged) {
               f2 pr{0.f, 0.f}, px_{0.f, 0.f}, py_{0.f, 0.f}, pz_{0.f, 0.f};
-              rowdot_df<GRAD>(rec, tab, Rs2, i, f2{prl.x, prlo.x}, f2{prl.y, prlo.y}, f2{prl.z, prlo.z}, pr, px_,
-                              py_, pz_);
+              rowdot_df<GRAD>(rec, tab, Rs2, i, half, C::kHalves, f2{prl.x, prlo.x}, f2{prl.y, prlo.y},
+                              f2{prl.z, prlo.z}, pr, px_, py_, pz_);
               r_i += rsc * df_to_double(pr);
               if (GRAD) {
                 gx += 2.0 * rsc * df_to_double(px_);
@@ -1173,9 +1191,10 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
               gy += 2.0 * rsc * (double)py_;
               gz += 2.0 * rsc * (double)pz_;
             }
-          } else if (staged) {
+          } else if (staged && half == 0) {
             // per atom of the block's shells: the warp's sum over its 32
-            // points, one FP64 atomic per atom and component
+            // points, one FP64 atomic per atom and component (BF16X10: the
+            // first half of the warps)
             const float rscf = (float)rsc;
             int cur = -1;
             float tx = 0.f, ty = 0.f, tz = 0.f;
@@ -1209,7 +1228,7 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
               }
             });
             if (cur >= 0) flush();
-          } else if (lane == 0) {
+          } else if (!staged && lane == 0) {
             atomicCAS(err, 0, 102);   // the gradient epilogue needs staged shell records
           }
         }
@@ -1220,20 +1239,20 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
       if constexpr (MODE != kRowDot) continue;
       // combine the four q-block groups of each point in a fixed order
       if (!mbar_wait_warp(rempty, (uint32_t)(k & 1) ^ 1u, abort_flag, err, 117, wait_ns)) break;
-      red[(k4 * 4 + 0) * kBlockPts + i] = r_i;
-      red[(k4 * 4 + 1) * kBlockPts + i] = gx;
-      red[(k4 * 4 + 2) * kBlockPts + i] = gy;
-      red[(k4 * 4 + 3) * kBlockPts + i] = gz;
+      red[(grp * 4 + 0) * kBlockPts + i] = r_i;
+      red[(grp * 4 + 1) * kBlockPts + i] = gx;
+      red[(grp * 4 + 2) * kBlockPts + i] = gy;
+      red[(grp * 4 + 3) * kBlockPts + i] = gz;
       __syncwarp();
       if (lane == 0) mbar_arrive(rfull);
-      if (k4 == 0) {
+      if (grp == 0) {
         if (!mbar_wait_warp(rfull, (uint32_t)(k & 1), abort_flag, err, 118, wait_ns)) break;
         double v[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           v[c] = red[c * kBlockPts + i];
 #pragma unroll
-          for (int q = 1; q < C::kNQ; ++q) v[c] += red[(q * 4 + c) * kBlockPts + i];
+          for (int q = 1; q < C::kGroups; ++q) v[c] += red[(q * 4 + c) * kBlockPts + i];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(rempty);

@@ -174,3 +174,42 @@ def test_pulled_chunks_equal_one_evaluation():
     kldi.exc(plan, "pbe", D, V, E)
     torch.cuda.synchronize()
     assert E.item() == pytest.approx(E1.item(), rel=1e-14)
+
+
+def test_trajectory_frames_at_target_tolerance():
+    """Frames of the 256-frame trajectory recipe at their stated sizes (the
+    smallest, the largest and a middle one of the first 32 frames, 24-128
+    waters) in BF16X10 through one CUDA-graph batch over a shared workspace,
+    each plan restricted to a seeded 6-block range: every frame's partial
+    E_xc and V against the screened FP64 oracle on the same blocks at the
+    stated target (|dE| <= 1e-6 Ha, max|dV| <= 1e-7)."""
+    import torch
+    kldi = _kldi()
+    sizes = synth.frame_sizes(32)
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes)), int(np.argsort(sizes)[len(sizes) // 2])]
+    systems = [synth.make_system(4, frame=k) for k in pick]
+    ws = kldi.Workspace(20000 * 98560)
+    plans, ranges = [], []
+    rng = np.random.default_rng(31)
+    for s in systems:
+        p = kldi.plan_for_system(s, prec="bf16x10", xc="pbe")
+        p.set_workspace(ws)
+        g0 = int(rng.integers(0, p.stats["nblocks"] - 6))
+        p.set_block_range(g0, g0 + 6)
+        plans.append(p)
+        ranges.append((g0, g0 + 6))
+    Ds = [torch.from_numpy(s.D).cuda() for s in systems]
+    Vs = [torch.zeros((s.nbf, s.nbf), dtype=torch.float64, device="cuda") for s in systems]
+    E = torch.zeros(len(systems), dtype=torch.float64, device="cuda")
+    batch = kldi.Batch(plans, "pbe", Ds, Vs, E)
+    batch.launch()
+    batch.sync()
+    for k, (s, (g0, g1)) in enumerate(zip(systems, ranges)):
+        go = og.build_grid(s.Z, s.xyz, s.grid, weight_blocks=list(range(g0, g1)))
+        ref = oe.evaluate(s, go, ob.build_shells(s.xyz, s.basis), screened=True, blocks=range(g0, g1))
+        dE = E[k].item() - ref.E
+        dV = np.abs(Vs[k].cpu().numpy() - ref.V).max()
+        print(f"frame {pick[k]} ({sizes[pick[k]]} waters), blocks {g0}..{g1}: dE {dE:+.2e}, max|dV| {dV:.2e}")
+        assert abs(dE) <= 1e-6
+        assert dV <= 1e-7
+    del batch
