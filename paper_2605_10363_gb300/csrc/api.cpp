@@ -69,7 +69,10 @@ kldi_status potential_batch(kldi_plan* P, const Batch& b, int xc, const double* 
     KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x64(P, b, P->stream); }));
     KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_v64(P, b, V, P->stream); }));
   } else {
-    // the V product's operands come from the X kernel; the per-point Phi slices are not needed
+    // the V product's operands come from the X kernel; the per-point Phi slices are not
+    // needed, but BF16X10's X kernel reads the radial factors the Phi kernel writes
+    if (!phi_ready && P->prec == KLDI_BF16X10)
+      KLDI_TRY(staged(P, KLDI_STAGE_PHI, 1, [&] { return launch_phi_split(P, b, P->stream); }));
     KLDI_TRY(staged(P, KLDI_STAGE_X, 1, [&] { return launch_x_split(P, b, P->stream); }));
     KLDI_TRY(staged(P, KLDI_STAGE_V, 1, [&] { return launch_v_tc(P, b, V, P->stream); }));
   }

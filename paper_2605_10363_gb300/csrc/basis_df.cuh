@@ -133,6 +133,14 @@ __device__ __forceinline__ void offsets_df(const float4& c0, const float4& c1, f
   r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
 }
 
+// Offsets of a point from a staged shell centre, hi / lo (no r^2).
+__device__ __forceinline__ void offsets3_df(const float4& c0, const float4& c1, f2 px, f2 py, f2 pz, f2& dx, f2& dy,
+                                            f2& dz) {
+  dx = df_sub(px, f2{c0.x, c0.w});
+  dy = df_sub(py, f2{c0.y, c1.x});
+  dz = df_sub(pz, f2{c0.z, c1.y});
+}
+
 // Cartesian component c of a shell of angular momentum l: P and dP/dr_a
 // (normalisation 1/sqrt(3) on xx, yy, zz), hi / lo.
 __device__ __forceinline__ void cart_df(int l, int c, f2 dx, f2 dy, f2 dz, f2& P, f2& Px, f2& Py, f2& Pz) {
@@ -199,18 +207,21 @@ __device__ __forceinline__ void for_rec_functions_df(const BlockRec* rec, const 
 //   X = a chi + (g b) . grad P + P (b . u),
 // where grad P has one or two non-zero components, so each function costs a
 // few double-float products.
+// The radial factors come from the Phi kernel: rad[s * 128] = (g hi, g lo,
+// gd hi, gd lo) of shell s of the block at this point.
 template <bool GRAD, typename F>
-__device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float2* tab, f2 px, f2 py, f2 pz, f2 a,
+__device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float4* rad, f2 px, f2 py, f2 pz, f2 a,
                                                 f2 bx, f2 by, f2 bz, F&& f) {
   const f2 s3{kS3h, kS3l};
   const int ns = rec->nshell;
   for (int s = 0; s < ns; ++s) {
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
-    const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
-    const int l = hdr & 255, np = (hdr >> 8) & 255, first = (hdr >> 16) - 64;
-    f2 dx, dy, dz, r2, g, gd;
-    offsets_df(c0, c1, px, py, pz, dx, dy, dz, r2);
-    radial_df<GRAD>(rec->pf + pi, rec->pac + pi, np, r2, tab, g, gd);
+    const int hdr = __float_as_int(c1.z);
+    const int l = hdr & 255, first = (hdr >> 16) - 64;
+    const float4 q = rad[s * kBlockPts];
+    const f2 g{q.x, q.y}, gd{q.z, q.w};
+    f2 dx, dy, dz;
+    offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
     f2 w{0.f, 0.f}, gbx{0.f, 0.f}, gby{0.f, 0.f}, gbz{0.f, 0.f};
     if (GRAD) {
       w = df_mul(df_scale(gd, -2.f), df_add(df_add(df_mul(bx, dx), df_mul(by, dy)), df_mul(bz, dz)));

@@ -261,6 +261,13 @@ struct kldi_plan {
   float* d_pscale = nullptr;    // [npoints] per-point balance c_i: Phi c and X / c in the V product
   float* d_zscale = nullptr;    // [npoints] point scales of the gradient's Z tiles (first tensor-core gradient)
   bool rec_fit_all = true;      // every basis block fits a shared-memory shell record (40 shells, 80 primitives)
+  // BF16X10: radial factors (g, gd) of every (tile, shell of its basis block, point) in hi / lo, written
+  // by the Phi kernel and read by the density product's row-dot and the X kernel
+  std::vector<int32_t> bb_nshell;   // [nbb] shells with a function in basis block p
+  std::vector<int64_t> rad_ptr;     // [ntiles + 1] prefix of bb_nshell over the tiles
+  int64_t* d_rad_ptr = nullptr;
+  float4* d_rad = nullptr;          // [shells of the batch][128]: g hi, g lo, gd hi, gd lo
+  int64_t rad_cap = 0;              // shell rows d_rad holds
   float* d_dscale = nullptr;    // [nbf_pad] column scales of d_dsplit
   uint16_t* d_dsplit = nullptr; // sliced D block pairs [nbb*nbb][NS planes][32][32]
   uint16_t* d_zero = nullptr;   // zero block (bulk-copy source for masked / absent blocks)

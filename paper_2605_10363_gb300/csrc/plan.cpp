@@ -88,7 +88,7 @@ void free_plan_buffers(kldi_plan* P) {
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_prel_lo, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
                   P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
-                  P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero};
+                  P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero, P->d_rad_ptr, P->d_rad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& b : P->batches) {
@@ -258,6 +258,18 @@ kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
   if (prec == KLDI_BF16X10 && !P->rec_fit_all) {
     set_error("KLDI_BF16X10: a basis block has more than 40 shells or 80 primitives");
     return KLDI_EUNSUPPORTED;
+  }
+  if (prec == KLDI_BF16X10) {
+    // radial factors of the largest batch (the batches change with the block range and tuning)
+    int64_t need = 1;
+    for (const Batch& b : P->batches) need = std::max(need, P->rad_ptr[b.t1] - P->rad_ptr[b.t0]);
+    if (need > P->rad_cap) {
+      if (P->d_rad) cudaFree(P->d_rad);
+      P->d_rad = nullptr;
+      P->rad_cap = 0;
+      KLDI_TRY(dalloc(P, &P->d_rad, (size_t)need * kBlockPts));
+      P->rad_cap = need;
+    }
   }
   // 16-bit words per tile: four planes, the most any mode uses (so a plan can
   // switch modes without reallocating; the batch capacity assumes this size)
@@ -487,6 +499,8 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     }
     if ((st = upload(P, &P->d_bb_begin, bb_begin.data(), bb_begin.size())) != KLDI_OK) return fail(st);
     if ((st = upload(P, &P->d_bb_end, bb_end.data(), bb_end.size())) != KLDI_OK) return fail(st);
+    P->bb_nshell.resize(nbb);
+    for (int64_t p = 0; p < nbb; ++p) P->bb_nshell[p] = std::max(0, bb_end[p] - bb_begin[p]);
 
     // ---- geometric candidates: shell extent R_s beyond which the value (and
     // gradient) bound r^l sum|c| e^{-a r^2} (+ l r^(l-1) .. + 2 a r^(l+1) ..) < t_b/2.
@@ -584,6 +598,9 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
       P->blk_ptr[g + 1] = (int32_t)P->blk_idx.size();
     }
     P->ntiles = (int64_t)P->blk_idx.size();
+    P->rad_ptr.assign(P->ntiles + 1, 0);
+    for (int64_t t = 0; t < P->ntiles; ++t) P->rad_ptr[t + 1] = P->rad_ptr[t] + P->bb_nshell[P->blk_idx[t]];
+    if ((st = upload(P, &P->d_rad_ptr, P->rad_ptr.data(), P->rad_ptr.size())) != KLDI_OK) return fail(st);
     std::vector<int32_t> tile_of(nblk * nbb, -1);
     for (int64_t g = 0; g < nblk; ++g)
       for (int32_t t = P->blk_ptr[g]; t < P->blk_ptr[g + 1]; ++t) tile_of[g * nbb + P->blk_idx[t]] = t;

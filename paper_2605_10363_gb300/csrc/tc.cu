@@ -339,8 +339,10 @@ __global__ void __launch_bounds__(128) k_phi_split(BasisView B, GridView G, List
 // BF16X10 Phi tiles: the point scale as in k_phi_split, then the values in
 // double-float (hi / lo staged in shared memory) cut into four slices.  Every
 // basis block must fit a shared-memory shell record (checked on the host).
+template <bool GRAD>
 __global__ void __launch_bounds__(128) k_phi_split4(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
-                                                    uint8_t* out_row, float* rowscale) {
+                                                    uint8_t* out_row, float* rowscale, float4* __restrict__ rad,
+                                                    const int64_t* __restrict__ rad_ptr) {
   __shared__ float sth[kBasisBlk][kBlockPts + 1];
   __shared__ float stl[kBasisBlk][kBlockPts + 1];
   __shared__ BlockRec rec[2];
@@ -380,10 +382,28 @@ __global__ void __launch_bounds__(128) k_phi_split4(BasisView B, GridView G, Lis
 #pragma unroll
     for (int nu = 0; nu < kBasisBlk; ++nu) sth[nu][i] = stl[nu][i] = 0.f;
     __syncthreads();
-    for_rec_functions_df<false>(rc, tab, px, py, pz, [&](int nu, f2 v, f2, f2, f2) {
-      sth[nu][i] = v.h;
-      stl[nu][i] = v.l;
-    });
+    // per shell: the radial factors g (and gd) go to the radial buffer for the
+    // row-dot and the X kernel, the values P g to the staging array
+    float4* rtile = rad + (rad_ptr[j] - rad_ptr[t0]) * kBlockPts;
+    for (int s = 0; s < rc->nshell; ++s) {
+      const float4 c0 = rc->c0[s], c1 = rc->c1[s];
+      const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
+      const int l = hdr & 255, np = (hdr >> 8) & 255, first = (hdr >> 16) - 64;
+      f2 dx, dy, dz, r2, g, gd;
+      offsets_df(c0, c1, px, py, pz, dx, dy, dz, r2);
+      radial_df<GRAD>(rc->pf + pi, rc->pac + pi, np, r2, tab, g, gd);
+      rtile[s * kBlockPts + i] = make_float4(g.h, g.l, gd.h, gd.l);
+      const int ncomp = (l + 1) * (l + 2) / 2;
+      for (int c = 0; c < ncomp; ++c) {
+        const int nu = first + c;
+        if (nu < 0 || nu >= kBasisBlk) continue;
+        f2 P, Px, Py, Pz;
+        cart_df(l, c, dx, dy, dz, P, Px, Py, Pz);
+        const f2 v = df_mul(P, g);
+        sth[nu][i] = v.h;
+        stl[nu][i] = v.l;
+      }
+    }
     float vh[kBasisBlk], vl[kBasisBlk];
 #pragma unroll
     for (int nu = 0; nu < kBasisBlk; ++nu) {
@@ -477,8 +497,14 @@ kldi_status launch_phi_split(const kldi_plan* P, const Batch& b, cudaStream_t s)
       const int64_t n = b.g1 - b.g0;
       if (n == 0) return KLDI_OK;
       KLDI_TRY(prepare_tc_kernels());   // the exp table
-      k_phi_split4<<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.t0,
-                                                     reinterpret_cast<uint8_t*>(P->d_phi_s), P->d_rowscale);
+      if (P->gga)
+        k_phi_split4<true><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                             b.t0, reinterpret_cast<uint8_t*>(P->d_phi_s),
+                                                             P->d_rowscale, P->d_rad, P->d_rad_ptr);
+      else
+        k_phi_split4<false><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+                                                              b.t0, reinterpret_cast<uint8_t*>(P->d_phi_s),
+                                                              P->d_rowscale, P->d_rad, P->d_rad_ptr);
       KLDI_TRY_CUDA(cudaGetLastError());
       return KLDI_OK;
     }
@@ -580,7 +606,8 @@ template <bool GRAD>
 __global__ void __launch_bounds__(128) k_x_split4(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
                                                   const double* __restrict__ xcoef, const float* __restrict__ pscale,
                                                   uint8_t* out_phi, float* phi_scale, uint8_t* out_x, float* x_scale,
-                                                  double* xmax) {
+                                                  double* xmax, const float4* __restrict__ rad,
+                                                  const int64_t* __restrict__ rad_ptr) {
   extern __shared__ float xsm[];
   float(*sph)[kBlockPts + 1] = reinterpret_cast<float(*)[kBlockPts + 1]>(xsm);
   float(*spl)[kBlockPts + 1] = sph + kBasisBlk;
@@ -588,13 +615,11 @@ __global__ void __launch_bounds__(128) k_x_split4(BasisView B, GridView G, ListV
   float(*sxl)[kBlockPts + 1] = sxh + kBasisBlk;
   __shared__ float cp[kBasisBlk], cx[kBasisBlk], rawx[kBasisBlk];
   __shared__ BlockRec rec;
-  __shared__ float2 tab[256];
   const int64_t t = t0 + blockIdx.x;
   const int64_t g = L.tile_g[t];
   const int p = L.blk_idx[t];
   const int i = threadIdx.x;
   const int64_t pt = g * kBlockPts + i;
-  load_exp_tab(tab, i, kBlockPts);
   const float c = pscale[pt], cinv = c > 0.f ? 1.f / c : 0.f;   // c = 0: X = 0 at this point
   const f2 a = df_from_double(xcoef[pt * 4]), bx = df_from_double(xcoef[pt * 4 + 1]),
            by = df_from_double(xcoef[pt * 4 + 2]), bz = df_from_double(xcoef[pt * 4 + 3]);
@@ -603,7 +628,8 @@ __global__ void __launch_bounds__(128) k_x_split4(BasisView B, GridView G, ListV
   const float4 pr = G.prel[pt], pl = G.prel_lo[pt];
   stage_block_rec(B, p, G.anchor[g], &rec, i, kBlockPts);
   __syncthreads();
-  for_rec_phix_df<GRAD>(&rec, tab, f2{pr.x, pl.x}, f2{pr.y, pl.y}, f2{pr.z, pl.z}, a, bx, by, bz,
+  for_rec_phix_df<GRAD>(&rec, rad + (rad_ptr[t] - rad_ptr[t0]) * kBlockPts + i, f2{pr.x, pl.x}, f2{pr.y, pl.y},
+                        f2{pr.z, pl.z}, a, bx, by, bz,
                         [&](int nu, f2 v, f2 x) {
                           sph[nu][i] = v.h * c;
                           spl[nu][i] = v.l * c;
@@ -673,11 +699,11 @@ static kldi_status x_ns4(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   if (P->gga)
     k_x_split4<true><<<(unsigned)n, kBlockPts, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                              b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
-                                                             P->d_x_scale, P->d_xmax);
+                                                             P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr);
   else
     k_x_split4<false><<<(unsigned)n, kBlockPts, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                               b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
-                                                              P->d_x_scale, P->d_xmax);
+                                                              P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
@@ -740,7 +766,7 @@ struct RhoCfg {
   static constexpr int kOffMeta = kOffRed + kGroups * 4 * kBlockPts * 8;
   static constexpr int kOffRec = kOffMeta + 2 * kMetaWords * 4;  // [kNQ q blocks][2] BlockRec
   static constexpr int kOffTab = kOffRec + 2 * kNQ * (int)sizeof(BlockRec);
-  static constexpr int kOffBar = kOffTab + (NS == 4 ? 256 * 8 : 0);
+  static constexpr int kOffBar = kOffTab;
   static constexpr int kSmem = kOffBar + 256 + 1024;
   static constexpr int kSegChunks = 8;                            // 8 x 32 = 256 K per exact accumulation
   static constexpr int kThreads = 64 + 32 * kEpi;
@@ -754,18 +780,21 @@ struct RhoCfg {
 // grad chi = (grad P) g + P u (u = -2 r gd),
 //   sum_nu chi R = sum_s g S0,   sum_nu grad chi R = sum_s (g S1 + u S0),
 // S0 = sum_c P_c R_c and S1 = sum_c (grad P_c) R_c over the shell's components.
+// The radial factors g, gd of each shell at this point come from the Phi
+// kernel (rad[s * 128]).
 template <bool GRAD>
-__device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float2* tab, const float2* Rs, int i, int s0,
+__device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad, const float2* Rs, int i, int s0,
                                           int sstep, f2 px, f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
   const f2 s3{kS3h, kS3l};
   const int ns = rec->nshell;
   for (int s = s0; s < ns; s += sstep) {
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
-    const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
-    const int l = hdr & 255, np = (hdr >> 8) & 255, first = (hdr >> 16) - 64;
-    f2 dx, dy, dz, r2, g, gd;
-    offsets_df(c0, c1, px, py, pz, dx, dy, dz, r2);
-    radial_df<GRAD>(rec->pf + pi, rec->pac + pi, np, r2, tab, g, gd);
+    const int hdr = __float_as_int(c1.z);
+    const int l = hdr & 255, first = (hdr >> 16) - 64;
+    const float4 q = rad[s * kBlockPts];
+    const f2 g{q.x, q.y}, gd{q.z, q.w};
+    f2 dx, dy, dz;
+    offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
     auto Rv = [&](int c) -> f2 {
       const int nu = first + c;
       if (nu < 0 || nu >= kBasisBlk) return f2{0.f, 0.f};
@@ -820,7 +849,7 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
              const uint8_t* __restrict__ phi, const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero,
              const double* __restrict__ dmax, const float* __restrict__ dscale, const float* __restrict__ rowscale,
              double t_b, double t_d, double* rho, double* grad, const double* __restrict__ xcoef, double* gout,
-             int* err, uint64_t wait_ns) {
+             int* err, uint64_t wait_ns, const float4* __restrict__ rad, const int64_t* __restrict__ rad_ptr) {
   using C = RhoCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -836,10 +865,8 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
   uint64_t* mdone = rempty + 1;       // all products of the MMA thread completed (exit)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float2* tab = reinterpret_cast<float2*>(sm + C::kOffTab);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G_ = gridDim.x;
-  if constexpr (NS == 4) load_exp_tab(tab, threadIdx.x, C::kThreads);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -1159,8 +1186,9 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
           if constexpr (MODE == kRowDot && NS == 4) {
             if (staged) {
               f2 pr{0.f, 0.f}, px_{0.f, 0.f}, py_{0.f, 0.f}, pz_{0.f, 0.f};
-              rowdot_df<GRAD>(rec, tab, Rs2, i, half, C::kHalves, f2{prl.x, prlo.x}, f2{prl.y, prlo.y},
-                              f2{prl.z, prlo.z}, pr, px_, py_, pz_);
+              const int64_t tq = m[1] + q0 + k4;   // tile (g, q block)
+              rowdot_df<GRAD>(rec, rad + (rad_ptr[tq] - rad_ptr[t0]) * kBlockPts + i, Rs2, i, half, C::kHalves,
+                              f2{prl.x, prlo.x}, f2{prl.y, prlo.y}, f2{prl.z, prlo.z}, pr, px_, py_, pz_);
               r_i += rsc * df_to_double(pr);
               if (GRAD) {
                 gx += 2.0 * rsc * df_to_double(px_);
@@ -1289,12 +1317,12 @@ static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, d
     k_rho_tc<NS, true><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                            b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                            P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
-                                                           nullptr, nullptr, P->d_err, P->wait_ns);
+                                                           nullptr, nullptr, P->d_err, P->wait_ns, P->d_rad, P->d_rad_ptr);
   else
     k_rho_tc<NS, false><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                             b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                             P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
-                                                            nullptr, nullptr, P->d_err, P->wait_ns);
+                                                            nullptr, nullptr, P->d_err, P->wait_ns, P->d_rad, P->d_rad_ptr);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
@@ -1325,13 +1353,13 @@ static kldi_status grad_ns(const kldi_plan* P, const Batch& b, bool gga_xc, doub
   const uint8_t* z = reinterpret_cast<const uint8_t*>(P->d_zero);
   k_rho_tc<NS, false, kGradQ><<<grid, C::kThreads, C::kSmem, s>>>(
       P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.g1, b.t0, zt, ds, z, P->d_dmax, P->d_dscale,
-      P->d_zscale, P->opt.t_b, P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err, P->wait_ns);
+      P->d_zscale, P->opt.t_b, P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err, P->wait_ns, P->d_rad, P->d_rad_ptr);
   KLDI_TRY_CUDA(cudaGetLastError());
   if (gga_xc) {
     k_rho_tc<NS, false, kGradR><<<grid, C::kThreads, C::kSmem, s>>>(
         P->basis_view(), P->grid_view(), P->list_view(), b.g0, b.g1, b.t0,
         reinterpret_cast<const uint8_t*>(P->d_phi_s), ds, z, P->d_dmax, P->d_dscale, P->d_rowscale, P->opt.t_b,
-        P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err, P->wait_ns);
+        P->opt.t_d, nullptr, nullptr, P->d_xcoef, G, P->d_err, P->wait_ns, P->d_rad, P->d_rad_ptr);
     KLDI_TRY_CUDA(cudaGetLastError());
   }
   return KLDI_OK;
