@@ -209,16 +209,23 @@ __device__ __forceinline__ void for_rec_functions_df(const BlockRec* rec, const 
 // few double-float products.
 // The radial factors come from the Phi kernel: rad[s * 128] = (g hi, g lo,
 // gd hi, gd lo) of shell s of the block at this point.
+// Shells s0, s0 + sstep, ... of the block.
 template <bool GRAD, typename F>
-__device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float4* rad, f2 px, f2 py, f2 pz, f2 a,
-                                                f2 bx, f2 by, f2 bz, F&& f) {
+__device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float4* rad, int s0, int sstep, f2 px,
+                                                f2 py, f2 pz, f2 a, f2 bx, f2 by, f2 bz, F&& f) {
   const f2 s3{kS3h, kS3l};
   const int ns = rec->nshell;
-  for (int s = 0; s < ns; ++s) {
+  // radial factors loaded two shells ahead (the loads come from HBM / L2)
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 qa = s0 < ns ? rad[s0 * kBlockPts] : z4;
+  float4 qb = s0 + sstep < ns ? rad[(s0 + sstep) * kBlockPts] : z4;
+  for (int s = s0; s < ns; s += sstep) {
+    const float4 q = qa;
+    qa = qb;
+    qb = s + 2 * sstep < ns ? rad[(s + 2 * sstep) * kBlockPts] : z4;
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
     const int hdr = __float_as_int(c1.z);
     const int l = hdr & 255, first = (hdr >> 16) - 64;
-    const float4 q = rad[s * kBlockPts];
     const f2 g{q.x, q.y}, gd{q.z, q.w};
     f2 dx, dy, dz;
     offsets3_df(c0, c1, px, py, pz, dx, dy, dz);

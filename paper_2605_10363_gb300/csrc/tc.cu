@@ -153,10 +153,11 @@ __device__ __forceinline__ void store_sliced_row(uint8_t* base, int pstride, int
 
 // Row `row` of four swizzled planes from 32 double-float values (vh + vl,
 // |v| <= 1): the digits of slice4_df.
+template <int C0 = 0, int C1 = 4>   // the 16-byte chunks [C0, C1) of the row
 __device__ __forceinline__ void store_sliced_row4(uint8_t* base, int pstride, int row, const float* vh,
                                                   const float* vl) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = C0; c < C1; ++c) {
     uint32_t w[4][4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -180,8 +181,9 @@ template <int NS>
 __device__ __forceinline__ void store_sliced_row_kc(uint8_t* base, int row, const float* v) {
   store_sliced_row<NS>(base + (row >> 5) * (NS * 2048) - (row & ~31) * 64, 2048, row, v);
 }
+template <int C0 = 0, int C1 = 4>
 __device__ __forceinline__ void store_sliced_row4_kc(uint8_t* base, int row, const float* vh, const float* vl) {
-  store_sliced_row4(base + (row >> 5) * (4 * 2048) - (row & ~31) * 64, 2048, row, vh, vl);
+  store_sliced_row4<C0, C1>(base + (row >> 5) * (4 * 2048) - (row & ~31) * 64, 2048, row, vh, vl);
 }
 
 // Slices per operand of a tensor-core precision mode.
@@ -599,15 +601,20 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
 
 // BF16X10 V-product operands: as k_x_split, with Phi and X in double-float
 // (hi / lo staged in dynamic shared memory, four [32][129] arrays) and four
-// slices per function.
+// slices per function.  256 threads: point i = t % 128, and the shells of the
+// block split between the two halves t / 128 (even, odd), which also split
+// each row's 16-byte chunks when slicing.  The radial factors come from the
+// Phi kernel.
 constexpr int kX4Smem = 4 * kBasisBlk * (kBlockPts + 1) * 4;
+constexpr int kX4Threads = 256;
 
 template <bool GRAD>
-__global__ void __launch_bounds__(128) k_x_split4(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
-                                                  const double* __restrict__ xcoef, const float* __restrict__ pscale,
-                                                  uint8_t* out_phi, float* phi_scale, uint8_t* out_x, float* x_scale,
-                                                  double* xmax, const float4* __restrict__ rad,
-                                                  const int64_t* __restrict__ rad_ptr) {
+__global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridView G, ListView L, int64_t g0,
+                                                         int64_t t0, const double* __restrict__ xcoef,
+                                                         const float* __restrict__ pscale, uint8_t* out_phi,
+                                                         float* phi_scale, uint8_t* out_x, float* x_scale,
+                                                         double* xmax, const float4* __restrict__ rad,
+                                                         const int64_t* __restrict__ rad_ptr) {
   extern __shared__ float xsm[];
   float(*sph)[kBlockPts + 1] = reinterpret_cast<float(*)[kBlockPts + 1]>(xsm);
   float(*spl)[kBlockPts + 1] = sph + kBasisBlk;
@@ -618,31 +625,35 @@ __global__ void __launch_bounds__(128) k_x_split4(BasisView B, GridView G, ListV
   const int64_t t = t0 + blockIdx.x;
   const int64_t g = L.tile_g[t];
   const int p = L.blk_idx[t];
-  const int i = threadIdx.x;
+  const int i = threadIdx.x & (kBlockPts - 1), half = threadIdx.x >> 7;
   const int64_t pt = g * kBlockPts + i;
   const float c = pscale[pt], cinv = c > 0.f ? 1.f / c : 0.f;   // c = 0: X = 0 at this point
   const f2 a = df_from_double(xcoef[pt * 4]), bx = df_from_double(xcoef[pt * 4 + 1]),
            by = df_from_double(xcoef[pt * 4 + 2]), bz = df_from_double(xcoef[pt * 4 + 3]);
 #pragma unroll
-  for (int nu = 0; nu < kBasisBlk; ++nu) sph[nu][i] = spl[nu][i] = sxh[nu][i] = sxl[nu][i] = 0.f;
+  for (int k = 0; k < kBasisBlk / 2; ++k) {
+    const int nu = half * (kBasisBlk / 2) + k;
+    sph[nu][i] = spl[nu][i] = sxh[nu][i] = sxl[nu][i] = 0.f;
+  }
   const float4 pr = G.prel[pt], pl = G.prel_lo[pt];
-  stage_block_rec(B, p, G.anchor[g], &rec, i, kBlockPts);
+  stage_block_rec(B, p, G.anchor[g], &rec, threadIdx.x, kX4Threads);
   __syncthreads();
-  for_rec_phix_df<GRAD>(&rec, rad + (rad_ptr[t] - rad_ptr[t0]) * kBlockPts + i, f2{pr.x, pl.x}, f2{pr.y, pl.y},
-                        f2{pr.z, pl.z}, a, bx, by, bz,
-                        [&](int nu, f2 v, f2 x) {
+  for_rec_phix_df<GRAD>(&rec, rad + (rad_ptr[t] - rad_ptr[t0]) * kBlockPts + i, half, 2, f2{pr.x, pl.x},
+                        f2{pr.y, pl.y}, f2{pr.z, pl.z}, a, bx, by, bz, [&](int nu, f2 v, f2 x) {
                           sph[nu][i] = v.h * c;
                           spl[nu][i] = v.l * c;
                           sxh[nu][i] = x.h * cinv;
                           sxl[nu][i] = x.l * cinv;
                         });
   __syncthreads();
-  column_scales(sph, cp, nullptr);
-  column_scales(sxh, cx, rawx);
+  if (threadIdx.x < kBlockPts) {
+    column_scales(sph, cp, nullptr);
+    column_scales(sxh, cx, rawx);
+  }
   __syncthreads();
-  if (i < kBasisBlk) {
-    cp[i] = fmaxf(cp[i], cx[i]);
-    cx[i] = 1.f / cp[i];            // exact: the scales are powers of two
+  if (threadIdx.x < kBasisBlk) {
+    cp[threadIdx.x] = fmaxf(cp[threadIdx.x], cx[threadIdx.x]);
+    cx[threadIdx.x] = 1.f / cp[threadIdx.x];   // exact: the scales are powers of two
   }
   __syncthreads();
   float vh[kBasisBlk], vl[kBasisBlk];
@@ -651,25 +662,33 @@ __global__ void __launch_bounds__(128) k_x_split4(BasisView B, GridView G, ListV
     vh[nu] = sph[nu][i] * cx[nu];
     vl[nu] = spl[nu][i] * cx[nu];
   }
-  store_sliced_row4_kc(out_phi + (t - t0) * tile_bytes(4), i, vh, vl);
+  if (half == 0)
+    store_sliced_row4_kc<0, 2>(out_phi + (t - t0) * tile_bytes(4), i, vh, vl);
+  else
+    store_sliced_row4_kc<2, 4>(out_phi + (t - t0) * tile_bytes(4), i, vh, vl);
 #pragma unroll
   for (int nu = 0; nu < kBasisBlk; ++nu) {
     vh[nu] = sxh[nu][i] * cx[nu];
     vl[nu] = sxl[nu][i] * cx[nu];
   }
-  store_sliced_row4_kc(out_x + (t - t0) * tile_bytes(4), i, vh, vl);
-  if (i < kBasisBlk) {
-    phi_scale[(t - t0) * kBasisBlk + i] = cp[i];
-    x_scale[(t - t0) * kBasisBlk + i] = cp[i];
+  if (half == 0)
+    store_sliced_row4_kc<0, 2>(out_x + (t - t0) * tile_bytes(4), i, vh, vl);
+  else
+    store_sliced_row4_kc<2, 4>(out_x + (t - t0) * tile_bytes(4), i, vh, vl);
+  if (threadIdx.x < kBasisBlk) {
+    phi_scale[(t - t0) * kBasisBlk + threadIdx.x] = cp[threadIdx.x];
+    x_scale[(t - t0) * kBasisBlk + threadIdx.x] = cp[threadIdx.x];
   }
+  // x_gq = max |X| over the tile, with X = X~ c_i
   float mx = 0.f;
+  if (half == 0) {
 #pragma unroll
-  for (int nu = 0; nu < kBasisBlk; ++nu) mx = fmaxf(mx, fabsf(sxh[nu][i]) * c);
+    for (int nu = 0; nu < kBasisBlk; ++nu) mx = fmaxf(mx, fabsf(sxh[nu][i]) * c);
+  }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (half == 0 && (i & 31) == 0) rawx[i >> 5] = mx;
   __syncthreads();
-  if ((i & 31) == 0) rawx[i >> 5] = mx;
-  __syncthreads();
-  if (i == 0) xmax[t] = (double)fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
+  if (threadIdx.x == 0) xmax[t] = (double)fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
 }
 
 template <int NS>
@@ -697,11 +716,11 @@ static kldi_status x_ns4(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   uint8_t* op = reinterpret_cast<uint8_t*>(P->d_phic_s);
   uint8_t* ox = reinterpret_cast<uint8_t*>(P->d_x_s);
   if (P->gga)
-    k_x_split4<true><<<(unsigned)n, kBlockPts, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+    k_x_split4<true><<<(unsigned)n, kX4Threads, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                              b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
                                                              P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr);
   else
-    k_x_split4<false><<<(unsigned)n, kBlockPts, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+    k_x_split4<false><<<(unsigned)n, kX4Threads, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                               b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
                                                               P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr);
   KLDI_TRY_CUDA(cudaGetLastError());
@@ -787,11 +806,17 @@ __device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad
                                           int sstep, f2 px, f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
   const f2 s3{kS3h, kS3l};
   const int ns = rec->nshell;
+  // radial factors loaded two shells ahead (the loads come from HBM / L2)
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 qa = s0 < ns ? rad[s0 * kBlockPts] : z4;
+  float4 qb = s0 + sstep < ns ? rad[(s0 + sstep) * kBlockPts] : z4;
   for (int s = s0; s < ns; s += sstep) {
+    const float4 q = qa;
+    qa = qb;
+    qb = s + 2 * sstep < ns ? rad[(s + 2 * sstep) * kBlockPts] : z4;
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
     const int hdr = __float_as_int(c1.z);
     const int l = hdr & 255, first = (hdr >> 16) - 64;
-    const float4 q = rad[s * kBlockPts];
     const f2 g{q.x, q.y}, gd{q.z, q.w};
     f2 dx, dy, dz;
     offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
@@ -1173,7 +1198,8 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
             for (int c = 0; c < C::kColsPerWarp; ++c) {
               const int col = half * C::kColsPerWarp + c;
               const float f = staged ? rec->ds[col] : dscale[q * kBasisBlk + col];
-              Rs2[col * kBlockPts + i] = make_float2(R[c] * f, Rl[c] * f);
+              const f2 r = two_sum(R[c], Rl[c]);   // normalised: hi is R to FP32 (the gradient epilogues read hi)
+              Rs2[col * kBlockPts + i] = make_float2(r.h * f, r.l * f);
             }
             named_bar_sync(1 + k4, 128 * C::kHalves);
           } else if (staged) {
