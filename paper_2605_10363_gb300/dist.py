@@ -196,6 +196,20 @@ class BlockQueue:
         chunks stay counted; a chunk it holds is re-offered)."""
         self.store.set(self._k("left", self.rank), "1")
 
+    def finish(self, world: int, host_rank: int = 0):
+        """Mark this rank done; the rank whose process hosts the store (rank 0
+        with the default TCP store) then waits until every other rank is done
+        or gone, so the store outlives their last use of it."""
+        self.store.set(self._k("fin", self.rank), "1")
+        if self.rank != host_rank:
+            return
+        while True:
+            waiting = [r for r in range(world) if r != self.rank and not self.store.check([self._k("fin", r)])
+                       and not self._gone(r)]
+            if not waiting:
+                return
+            time.sleep(self.poll)
+
     def reduce_published(self, world: int):
         """Sum of every rank's published partial (after take() returned None):
         (E, V, chunks); the chunk lists are disjoint and cover all chunks."""
@@ -244,6 +258,7 @@ def exc_pulled(plan, xc, D, V, E, queue: BlockQueue, group=None):
     if queue.lease_timeout is not None:
         world = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
         Es, Vs, _ = queue.reduce_published(world)
+        queue.finish(world)
         V.copy_(torch.from_numpy(Vs))
         E.fill_(Es)
     elif dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:

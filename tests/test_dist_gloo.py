@@ -203,6 +203,7 @@ def _rank_pull_leave(rank, world, port, nblocks, chunk, out_dir):
         q.publish(r, E, V)
         done.append(r)
     Es, Vs, chunks = q.reduce_published(world)
+    q.finish(world)                      # rank 0 hosts the store: it leaves last
     np.save(os.path.join(out_dir, f"V{rank}.npy"), Vs)
     np.save(os.path.join(out_dir, f"E{rank}.npy"), np.array([Es]))
     np.save(os.path.join(out_dir, f"done{rank}.npy"), np.array(done, dtype=np.int64).reshape(-1, 2))
