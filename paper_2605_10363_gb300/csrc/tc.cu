@@ -806,14 +806,12 @@ __device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad
                                           int sstep, f2 px, f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
   const f2 s3{kS3h, kS3l};
   const int ns = rec->nshell;
-  // radial factors loaded two shells ahead (the loads come from HBM / L2)
+  // radial factors loaded one shell ahead (the loads come from HBM / L2)
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 qa = s0 < ns ? rad[s0 * kBlockPts] : z4;
-  float4 qb = s0 + sstep < ns ? rad[(s0 + sstep) * kBlockPts] : z4;
   for (int s = s0; s < ns; s += sstep) {
     const float4 q = qa;
-    qa = qb;
-    qb = s + 2 * sstep < ns ? rad[(s + 2 * sstep) * kBlockPts] : z4;
+    qa = s + sstep < ns ? rad[(s + sstep) * kBlockPts] : z4;
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
     const int hdr = __float_as_int(c1.z);
     const int l = hdr & 255, first = (hdr >> 16) - 64;
@@ -826,28 +824,54 @@ __device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad
       const float2 r = Rs[nu * kBlockPts + i];
       return f2{r.x, r.y};
     };
-    f2 S0, S1x{0.f, 0.f}, S1y{0.f, 0.f}, S1z{0.f, 0.f};
+    // S0 = sum_c P_c R_c and S1 = sum_c (grad P_c) R_c, one component at a
+    // time (few values live at once)
+    f2 S0{0.f, 0.f}, S1x{0.f, 0.f}, S1y{0.f, 0.f}, S1z{0.f, 0.f};
     if (l == 0) {
       S0 = Rv(0);
     } else if (l == 1) {
-      const f2 rx = Rv(0), ry = Rv(1), rz = Rv(2);
-      S0 = df_add(df_add(df_mul(dx, rx), df_mul(dy, ry)), df_mul(dz, rz));
-      S1x = rx;
-      S1y = ry;
-      S1z = rz;
+      S1x = Rv(0);
+      S1y = Rv(1);
+      S1z = Rv(2);
+      S0 = df_add(df_add(df_mul(dx, S1x), df_mul(dy, S1y)), df_mul(dz, S1z));
     } else {
-      const f2 rxx = df_mul(Rv(0), s3), rxy = Rv(1), rxz = Rv(2), ryy = df_mul(Rv(3), s3), ryz = Rv(4),
-               rzz = df_mul(Rv(5), s3);
-      // P: xx, xy, xz, yy, yz, zz (xx etc. with 1/sqrt(3) moved onto R)
-      const f2 ax = df_add(df_add(df_mul(dx, rxx), df_mul(dy, rxy)), df_mul(dz, rxz));   // sum over x-containing
-      const f2 ay = df_add(df_mul(dy, ryy), df_mul(dz, ryz));
-      const f2 az = df_mul(dz, rzz);
-      S0 = df_add(df_add(df_mul(dx, ax), df_mul(dy, ay)), df_mul(dz, az));
-      if (GRAD) {
-        // d/dx: 2 x rxx + y rxy + z rxz;  d/dy: x rxy + 2 y ryy + z ryz;  d/dz: x rxz + y ryz + 2 z rzz
-        S1x = df_add(ax, df_mul(dx, rxx));
-        S1y = df_add(df_add(df_mul(dx, rxy), df_mul(df_scale(dy, 2.f), ryy)), df_mul(dz, ryz));
-        S1z = df_add(df_add(df_mul(dx, rxz), df_mul(dy, ryz)), df_mul(df_scale(dz, 2.f), rzz));
+      // xx, yy, zz (with 1/sqrt(3)): P = r_a^2 s3, d_a P = 2 r_a s3
+      // xy, xz, yz: P = r_a r_b, d_a P = r_b, d_b P = r_a
+      {
+        const f2 t = df_mul(dx, df_mul(Rv(0), s3));
+        S0 = df_mul(dx, t);
+        S1x = df_scale(t, 2.f);
+      }
+      {
+        const f2 r = Rv(1);
+        const f2 t = df_mul(dy, r);
+        S0 = df_add(S0, df_mul(dx, t));
+        S1x = df_add(S1x, t);
+        S1y = df_mul(dx, r);
+      }
+      {
+        const f2 r = Rv(2);
+        const f2 t = df_mul(dz, r);
+        S0 = df_add(S0, df_mul(dx, t));
+        S1x = df_add(S1x, t);
+        S1z = df_mul(dx, r);
+      }
+      {
+        const f2 t = df_mul(dy, df_mul(Rv(3), s3));
+        S0 = df_add(S0, df_mul(dy, t));
+        S1y = df_add(S1y, df_scale(t, 2.f));
+      }
+      {
+        const f2 r = Rv(4);
+        const f2 t = df_mul(dz, r);
+        S0 = df_add(S0, df_mul(dy, t));
+        S1y = df_add(S1y, t);
+        S1z = df_add(S1z, df_mul(dy, r));
+      }
+      {
+        const f2 t = df_mul(dz, df_mul(Rv(5), s3));
+        S0 = df_add(S0, df_mul(dz, t));
+        S1z = df_add(S1z, df_scale(t, 2.f));
       }
     }
     pr = df_add(pr, df_mul(g, S0));
@@ -1113,6 +1137,9 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
       const int anc = G.anchor[g];
       const double rsc = (double)rowscale[pt];
       double r_i = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+      // the point's sums over its tiles in double-float (FP64 arithmetic is
+      // slow on this GPU), scaled and converted once per grid block
+      f2 ar{0.f, 0.f}, agx{0.f, 0.f}, agy{0.f, 0.f}, agz{0.f, 0.f};
       float bx = 0.f, by = 0.f, bz = 0.f;   // b_i of the gradient's Hessian term
       if constexpr (MODE == kGradR) {
         bx = (float)xcoef[pt * 4 + 1];
@@ -1215,11 +1242,11 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
               const int64_t tq = m[1] + q0 + k4;   // tile (g, q block)
               rowdot_df<GRAD>(rec, rad + (rad_ptr[tq] - rad_ptr[t0]) * kBlockPts + i, Rs2, i, half, C::kHalves,
                               f2{prl.x, prlo.x}, f2{prl.y, prlo.y}, f2{prl.z, prlo.z}, pr, px_, py_, pz_);
-              r_i += rsc * df_to_double(pr);
+              ar = df_add(ar, pr);
               if (GRAD) {
-                gx += 2.0 * rsc * df_to_double(px_);
-                gy += 2.0 * rsc * df_to_double(py_);
-                gz += 2.0 * rsc * df_to_double(pz_);
+                agx = df_add(agx, px_);
+                agy = df_add(agy, py_);
+                agz = df_add(agz, pz_);
               }
             } else if (lane == 0) {
               atomicCAS(err, 0, 102);   // the double-float row-dot needs staged shell records
@@ -1239,11 +1266,11 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
               for_rec_functions<GRAD>(rec, prl.x, prl.y, prl.z, acc);
             else
               for_block_functions<float, GRAD>(B, q, prl.x, prl.y, prl.z, acc, anc);
-            r_i += rsc * (double)pr;
+            ar = df_add(ar, f2{pr, 0.f});
             if (GRAD) {
-              gx += 2.0 * rsc * (double)px_;
-              gy += 2.0 * rsc * (double)py_;
-              gz += 2.0 * rsc * (double)pz_;
+              agx = df_add(agx, f2{px_, 0.f});
+              agy = df_add(agy, f2{py_, 0.f});
+              agz = df_add(agz, f2{pz_, 0.f});
             }
           } else if (staged && half == 0) {
             // per atom of the block's shells: the warp's sum over its 32
@@ -1291,6 +1318,10 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&mempty[b]);
       if constexpr (MODE != kRowDot) continue;
+      r_i = rsc * df_to_double(ar);                  // rsc: a power of two
+      gx = 2.0 * rsc * df_to_double(agx);
+      gy = 2.0 * rsc * df_to_double(agy);
+      gz = 2.0 * rsc * df_to_double(agz);
       // combine the four q-block groups of each point in a fixed order
       if (!mbar_wait_warp(rempty, (uint32_t)(k & 1) ^ 1u, abort_flag, err, 117, wait_ns)) break;
       red[(grp * 4 + 0) * kBlockPts + i] = r_i;
