@@ -59,6 +59,21 @@ __device__ __forceinline__ f2 df_mulf(f2 a, float b) {   // b an FP32 number
   return fast_two_sum(p.h, fmaf(a.l, b, p.l));
 }
 __device__ __forceinline__ f2 df_scale(f2 a, float s) { return {a.h * s, a.l * s}; }   // s a power of two
+// Unnormalised forms for short chains (a product or sum feeding the next):
+// the low part may exceed half an ulp of the high part, which the products
+// below still take into account; dropped terms are ~2^-44 of the result.
+__device__ __forceinline__ f2 df_mul_u(f2 a, f2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  return {p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
+}
+__device__ __forceinline__ f2 df_add_u(f2 a, f2 b) {
+  const f2 s = two_sum(a.h, b.h);
+  return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ f2 df_sub_u(f2 a, f2 b) {
+  const f2 s = two_sum(a.h, -b.h);
+  return {s.h, __fadd_rn(s.l, __fsub_rn(a.l, b.l))};
+}
 __device__ __forceinline__ f2 df_neg(f2 a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ double df_to_double(f2 a) { return (double)a.h + (double)a.l; }
 __device__ __forceinline__ f2 df_from_double(double v) {
@@ -136,9 +151,9 @@ __device__ __forceinline__ void offsets_df(const float4& c0, const float4& c1, f
 // Offsets of a point from a staged shell centre, hi / lo (no r^2).
 __device__ __forceinline__ void offsets3_df(const float4& c0, const float4& c1, f2 px, f2 py, f2 pz, f2& dx, f2& dy,
                                             f2& dz) {
-  dx = df_sub(px, f2{c0.x, c0.w});
-  dy = df_sub(py, f2{c0.y, c1.x});
-  dz = df_sub(pz, f2{c0.z, c1.y});
+  dx = df_sub_u(px, f2{c0.x, c0.w});
+  dy = df_sub_u(py, f2{c0.y, c1.x});
+  dz = df_sub_u(pz, f2{c0.z, c1.y});
 }
 
 // Cartesian component c of a shell of angular momentum l: P and dP/dr_a
@@ -231,18 +246,19 @@ __device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float
     offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
     f2 w{0.f, 0.f}, gbx{0.f, 0.f}, gby{0.f, 0.f}, gbz{0.f, 0.f};
     if (GRAD) {
-      w = df_mul(df_scale(gd, -2.f), df_add(df_add(df_mul(bx, dx), df_mul(by, dy)), df_mul(bz, dz)));
-      gbx = df_mul(g, bx);
-      gby = df_mul(g, by);
-      gbz = df_mul(g, bz);
+      w = df_mul_u(df_scale(gd, -2.f), df_add_u(df_add_u(df_mul_u(bx, dx), df_mul_u(by, dy)), df_mul_u(bz, dz)));
+      gbx = df_mul_u(g, bx);
+      gby = df_mul_u(g, by);
+      gbz = df_mul_u(g, bz);
     }
     auto emit = [&](int c, f2 P, f2 bdP) {   // bdP = (g b) . grad P
       const int nu = first + c;
       if (nu < 0 || nu >= kBasisBlk) return;
-      const f2 v = df_mul(P, g);
-      f2 x = df_mul(a, v);
-      if (GRAD) x = df_add(x, df_add(bdP, df_mul(P, w)));
-      f(nu, v, x);
+      const f2 v = df_mul_u(P, g);
+      f2 x = df_mul_u(a, v);
+      if (GRAD) x = df_add_u(x, df_add_u(bdP, df_mul_u(P, w)));
+      // normalised for the slicing (which takes the top digits from hi alone)
+      f(nu, two_sum(v.h, v.l), two_sum(x.h, x.l));
     };
     const f2 z{0.f, 0.f};
     if (l == 0) {
@@ -252,13 +268,13 @@ __device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float
       emit(1, dy, gby);
       emit(2, dz, gbz);
     } else {
-      const f2 sx = df_mul(dx, s3), sy = df_mul(dy, s3), sz = df_mul(dz, s3);
-      emit(0, df_mul(dx, sx), GRAD ? df_scale(df_mul(gbx, sx), 2.f) : z);
-      emit(1, df_mul(dx, dy), GRAD ? df_add(df_mul(gbx, dy), df_mul(gby, dx)) : z);
-      emit(2, df_mul(dx, dz), GRAD ? df_add(df_mul(gbx, dz), df_mul(gbz, dx)) : z);
-      emit(3, df_mul(dy, sy), GRAD ? df_scale(df_mul(gby, sy), 2.f) : z);
-      emit(4, df_mul(dy, dz), GRAD ? df_add(df_mul(gby, dz), df_mul(gbz, dy)) : z);
-      emit(5, df_mul(dz, sz), GRAD ? df_scale(df_mul(gbz, sz), 2.f) : z);
+      const f2 sx = df_mul_u(dx, s3), sy = df_mul_u(dy, s3), sz = df_mul_u(dz, s3);
+      emit(0, df_mul_u(dx, sx), GRAD ? df_scale(df_mul_u(gbx, sx), 2.f) : z);
+      emit(1, df_mul_u(dx, dy), GRAD ? df_add_u(df_mul_u(gbx, dy), df_mul_u(gby, dx)) : z);
+      emit(2, df_mul_u(dx, dz), GRAD ? df_add_u(df_mul_u(gbx, dz), df_mul_u(gbz, dx)) : z);
+      emit(3, df_mul_u(dy, sy), GRAD ? df_scale(df_mul_u(gby, sy), 2.f) : z);
+      emit(4, df_mul_u(dy, dz), GRAD ? df_add_u(df_mul_u(gby, dz), df_mul_u(gbz, dy)) : z);
+      emit(5, df_mul_u(dz, sz), GRAD ? df_scale(df_mul_u(gbz, sz), 2.f) : z);
     }
   }
 }

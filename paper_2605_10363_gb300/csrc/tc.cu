@@ -833,53 +833,53 @@ __device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad
       S1x = Rv(0);
       S1y = Rv(1);
       S1z = Rv(2);
-      S0 = df_add(df_add(df_mul(dx, S1x), df_mul(dy, S1y)), df_mul(dz, S1z));
+      S0 = df_add_u(df_add_u(df_mul_u(dx, S1x), df_mul_u(dy, S1y)), df_mul_u(dz, S1z));
     } else {
       // xx, yy, zz (with 1/sqrt(3)): P = r_a^2 s3, d_a P = 2 r_a s3
       // xy, xz, yz: P = r_a r_b, d_a P = r_b, d_b P = r_a
       {
-        const f2 t = df_mul(dx, df_mul(Rv(0), s3));
-        S0 = df_mul(dx, t);
+        const f2 t = df_mul_u(dx, df_mul_u(Rv(0), s3));
+        S0 = df_mul_u(dx, t);
         S1x = df_scale(t, 2.f);
       }
       {
         const f2 r = Rv(1);
-        const f2 t = df_mul(dy, r);
-        S0 = df_add(S0, df_mul(dx, t));
-        S1x = df_add(S1x, t);
-        S1y = df_mul(dx, r);
+        const f2 t = df_mul_u(dy, r);
+        S0 = df_add_u(S0, df_mul_u(dx, t));
+        S1x = df_add_u(S1x, t);
+        S1y = df_mul_u(dx, r);
       }
       {
         const f2 r = Rv(2);
-        const f2 t = df_mul(dz, r);
-        S0 = df_add(S0, df_mul(dx, t));
-        S1x = df_add(S1x, t);
-        S1z = df_mul(dx, r);
+        const f2 t = df_mul_u(dz, r);
+        S0 = df_add_u(S0, df_mul_u(dx, t));
+        S1x = df_add_u(S1x, t);
+        S1z = df_mul_u(dx, r);
       }
       {
-        const f2 t = df_mul(dy, df_mul(Rv(3), s3));
-        S0 = df_add(S0, df_mul(dy, t));
-        S1y = df_add(S1y, df_scale(t, 2.f));
+        const f2 t = df_mul_u(dy, df_mul_u(Rv(3), s3));
+        S0 = df_add_u(S0, df_mul_u(dy, t));
+        S1y = df_add_u(S1y, df_scale(t, 2.f));
       }
       {
         const f2 r = Rv(4);
-        const f2 t = df_mul(dz, r);
-        S0 = df_add(S0, df_mul(dy, t));
-        S1y = df_add(S1y, t);
-        S1z = df_add(S1z, df_mul(dy, r));
+        const f2 t = df_mul_u(dz, r);
+        S0 = df_add_u(S0, df_mul_u(dy, t));
+        S1y = df_add_u(S1y, t);
+        S1z = df_add_u(S1z, df_mul_u(dy, r));
       }
       {
-        const f2 t = df_mul(dz, df_mul(Rv(5), s3));
-        S0 = df_add(S0, df_mul(dz, t));
-        S1z = df_add(S1z, df_scale(t, 2.f));
+        const f2 t = df_mul_u(dz, df_mul_u(Rv(5), s3));
+        S0 = df_add_u(S0, df_mul_u(dz, t));
+        S1z = df_add_u(S1z, df_scale(t, 2.f));
       }
     }
-    pr = df_add(pr, df_mul(g, S0));
+    pr = df_add_u(pr, df_mul_u(g, S0));
     if (GRAD) {
       const f2 m2 = df_scale(gd, -2.f);
-      gx = df_add(gx, df_add(df_mul(g, S1x), df_mul(df_mul(dx, m2), S0)));
-      gy = df_add(gy, df_add(df_mul(g, S1y), df_mul(df_mul(dy, m2), S0)));
-      gz = df_add(gz, df_add(df_mul(g, S1z), df_mul(df_mul(dz, m2), S0)));
+      gx = df_add_u(gx, df_add_u(df_mul_u(g, S1x), df_mul_u(df_mul_u(dx, m2), S0)));
+      gy = df_add_u(gy, df_add_u(df_mul_u(g, S1y), df_mul_u(df_mul_u(dy, m2), S0)));
+      gz = df_add_u(gz, df_add_u(df_mul_u(g, S1z), df_mul_u(df_mul_u(dz, m2), S0)));
     }
   }
 }
