@@ -293,7 +293,7 @@ def run_frames(args, dev, stream):
     big = int(np.argmax([p.npoints for p in plans]))
     tuning, _ = plans[big].autotune("pbe", Ds[big], reps=2)
     for p in plans:
-        p.set_tuning(tuning["v_seg"])
+        p.set_tuning(tuning["v_seg"], tuning["rho_ntile"])
     batch = kldi.Batch(plans, "pbe", Ds, Vs, E, stream=stream.cuda_stream)
     for _ in range(max(1, args.warmup)):
         batch.launch()
@@ -314,7 +314,7 @@ def run_frames(args, dev, stream):
         "config": {"workload": f"frames: the first {args.frames} frames of the trajectory recipe "
                                f"(waters {[int(x) for x in synth.frame_sizes(args.frames)]}), PBE-form, one CUDA-graph "
                                f"launch per step", "precision": args.prec, "points": int(npts),
-                   "tuned_v_seg": tuning["v_seg"], "plan_seconds": round(t_plan, 1),
+                   "tuning": tuning, "plan_seconds": round(t_plan, 1),
                    "basis_order": "overlap-signature clustering" if args.basis_order == "overlap" else "atom order"},
         "E_xc": E.cpu().numpy().tolist()}), flush=True)
 

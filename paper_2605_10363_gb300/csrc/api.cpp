@@ -365,6 +365,22 @@ struct kldi_batch {
   std::vector<kldi_plan*> plans;
 };
 
+// Times `reps` evaluations with tuning t (after one untimed one); ms per evaluation.
+static kldi_status time_tuning(kldi_plan* P, int xc, const double* D, int reps, const kldi_tuning& t,
+                               cudaEvent_t e0, cudaEvent_t e1, double* ms_out) {
+  KLDI_TRY(kldi_plan_set_tuning(P, &t));
+  KLDI_TRY(exc_device(P, xc, D, P->d_V, P->d_exc));
+  KLDI_TRY_CUDA(cudaEventRecord(e0, P->stream));
+  for (int r = 0; r < reps; ++r) KLDI_TRY(exc_device(P, xc, D, P->d_V, P->d_exc));
+  KLDI_TRY_CUDA(cudaEventRecord(e1, P->stream));
+  KLDI_TRY_CUDA(cudaEventSynchronize(e1));
+  KLDI_TRY(check_device_error(P));
+  float ms = 0.f;
+  KLDI_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  *ms_out = ms / reps;
+  return KLDI_OK;
+}
+
 extern "C" kldi_status kldi_plan_autotune(kldi_plan* P, int xc, const double* D, int reps, kldi_tuning* best,
                                           double* best_ms) {
   return kldi::guarded("kldi_plan_autotune", [&]() -> kldi_status {
@@ -373,36 +389,30 @@ extern "C" kldi_status kldi_plan_autotune(kldi_plan* P, int xc, const double* D,
       return KLDI_EINVAL;
     }
     KLDI_TRY(check_xc(P, xc));
-    const int cand[] = {0, 4, 8, 16, 32, 64, 128};
-    const kldi_tuning start = P->tune;
     cudaEvent_t e0, e1;
     KLDI_TRY_CUDA(cudaEventCreate(&e0));
     KLDI_TRY_CUDA(cudaEventCreate(&e1));
-    double bms = 1e300;
-    kldi_tuning bt = start;
-    kldi_status st = KLDI_OK;
     const int prof = P->prof;
     P->prof = 0;
-    for (int c : cand) {
-      kldi_tuning t{c};
-      if ((st = kldi_plan_set_tuning(P, &t)) != KLDI_OK) break;
-      if ((st = exc_device(P, xc, D, P->d_V, P->d_exc)) != KLDI_OK) break;
-      cudaEventRecord(e0, P->stream);
-      for (int r = 0; r < reps && st == KLDI_OK; ++r) st = exc_device(P, xc, D, P->d_V, P->d_exc);
-      cudaEventRecord(e1, P->stream);
-      if (st != KLDI_OK) break;
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        set_error("kldi_plan_autotune: %s", cudaGetErrorString(cudaGetLastError()));
-        st = KLDI_ECUDA;
-        break;
-      }
-      if ((st = check_device_error(P)) != KLDI_OK) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms / reps < bms) {
-        bms = ms / reps;
-        bt = t;
-      }
+    // coordinate search: the density product's N tile at the default V
+    // decomposition, then the V work-item span with the chosen tile
+    kldi_tuning bt{0, 0};
+    double bms = 1e300;
+    kldi_status st = KLDI_OK;
+    std::vector<int> tiles = {0};
+    if (P->prec == KLDI_BF16X3 || P->prec == KLDI_BF16X6) tiles = {128, 64};
+    for (int nt : tiles) {
+      double ms = 0.0;
+      const kldi_tuning t{0, nt};
+      if ((st = time_tuning(P, xc, D, reps, t, e0, e1, &ms)) != KLDI_OK) break;
+      if (ms < bms) { bms = ms; bt = t; }
+    }
+    const int segs[] = {4, 8, 32, 64, 128};
+    for (int k = 0; k < 5 && st == KLDI_OK && P->prec != KLDI_FP64; ++k) {
+      double ms = 0.0;
+      const kldi_tuning t{segs[k], bt.rho_ntile};
+      if ((st = time_tuning(P, xc, D, reps, t, e0, e1, &ms)) != KLDI_OK) break;
+      if (ms < bms) { bms = ms; bt = t; }
     }
     P->prof = prof;
     cudaEventDestroy(e0);

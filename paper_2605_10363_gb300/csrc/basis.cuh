@@ -188,10 +188,12 @@ __device__ __forceinline__ void stage_block_rec(const BasisView& B, int p, int a
 }
 
 // for_block_functions<float> from a staged record (same arithmetic, same bits).
+// Shells s0, s0 + sstep, ... (all by default).
 template <bool GRAD, typename F>
-__device__ __forceinline__ void for_rec_functions(const BlockRec* rec, float px, float py, float pz, F&& f) {
+__device__ __forceinline__ void for_rec_functions(const BlockRec* rec, float px, float py, float pz, F&& f,
+                                                  int s0 = 0, int sstep = 1) {
   const int ns = rec->nshell;
-  for (int s = 0; s < ns; ++s) {
+  for (int s = s0; s < ns; s += sstep) {
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
     const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
     const float dx = (px - c0.x) - c0.w, dy = (py - c0.y) - c1.x, dz = (pz - c0.z) - c1.y;

@@ -191,7 +191,7 @@ struct kldi_workspace {
 struct kldi_plan {
   kldi_options opt{};
   const kldi_workspace* ws = nullptr;   // shared per-tile buffers (not owned), or NULL
-  kldi_tuning tune{0};
+  kldi_tuning tune{0, 0};
   bool work_fp64 = false;               // which V work lists the batches hold
   int64_t range_g0 = 0, range_g1 = -1;  // grid blocks evaluated: [range_g0, range_g1), -1 = all
   int gga = 0;

@@ -769,14 +769,18 @@ extern "C" kldi_status kldi_plan_set_withhold(kldi_plan* P, int64_t item) {
 
 extern "C" kldi_status kldi_plan_set_tuning(kldi_plan* P, const kldi_tuning* t) {
   return kldi::guarded("kldi_plan_set_tuning", [&]() -> kldi_status {
-    if (!P || !t || t->v_seg < 0) {
-      set_error("kldi_plan_set_tuning: bad argument");
+    if (!P || !t || t->v_seg < 0 || (t->rho_ntile != 0 && t->rho_ntile != 64 && t->rho_ntile != 128)) {
+      set_error("kldi_plan_set_tuning: bad argument (v_seg >= 0, rho_ntile 0, 64 or 128)");
       return KLDI_EINVAL;
     }
-    if (t->v_seg == P->tune.v_seg) return KLDI_OK;
+    if (P->prec == KLDI_BF16X10 && t->rho_ntile == 128) {
+      set_error("kldi_plan_set_tuning: BF16X10 has only the 64-function density tile");
+      return KLDI_EUNSUPPORTED;
+    }
     KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
+    const bool rebuild = t->v_seg != P->tune.v_seg;
     P->tune = *t;
-    return build_work(P, P->tile_cap);
+    return rebuild ? build_work(P, P->tile_cap) : KLDI_OK;
   });
 }
 

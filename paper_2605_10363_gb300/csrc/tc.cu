@@ -766,18 +766,18 @@ __device__ __forceinline__ void issue_levels(uint32_t d0, uint32_t lstride, cons
 // products), 16 epilogue warps, two per (lane quarter, q block) draining half
 // the columns each and sharing the row-dot's shells, R and the row-dot in
 // double-float.
-template <int NS>
+template <int NS, int NQ = (NS == 4 ? 2 : 4)>
 struct RhoCfg {
-  static constexpr int kNQ = NS == 4 ? 2 : 4;                     // q blocks per N tile
-  static constexpr int kHalves = NS == 4 ? 2 : 1;                 // warps per (lane quarter, q block)
-  static constexpr int kEpi = 4 * kNQ * kHalves;                  // epilogue warps
+  static constexpr int kNQ = NQ;                                  // q blocks per N tile (2 or 4)
+  static constexpr int kHalves = NQ == 2 ? 2 : 1;                 // warps per (lane quarter, q block)
+  static constexpr int kEpi = 4 * kNQ * kHalves;                  // epilogue warps (16)
   static constexpr int kGroups = kNQ * kHalves;                   // epilogue groups of 4 warps (one per quarter)
   static constexpr int kColsPerWarp = 32 / kHalves;               // TMEM columns a warp drains
   static constexpr int kLevelCols = 32 * kNQ;                     // TMEM columns of one level accumulator
   static constexpr int kBufCols = NS * kLevelCols;                // NS level accumulators
   static constexpr int kBufs = 2 * kBufCols <= 512 ? 2 : 1;
   static constexpr int kStageBytes = NS * kPlaneBytes + NS * kNQ * kDPlane;
-  static constexpr int kStages = NS == 2 ? 3 : 2;
+  static constexpr int kStages = NS == 4 ? 2 : (NS == 2 || NQ == 2 ? 3 : 2);
   static constexpr int kRsElem = NS == 4 ? 8 : 4;                 // R staged as FP32, or hi / lo pairs
   static constexpr int kOffR = kStages * kStageBytes;             // [kNQ q blocks][32][128] R
   static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * kRsElem;   // [kGroups][4][128] double
@@ -791,6 +791,7 @@ struct RhoCfg {
   static constexpr int kThreads = 64 + 32 * kEpi;
   static_assert(kSmem <= 232448, "shared memory");
   static_assert(kBufs * kBufCols <= 512, "TMEM");
+  static_assert(NQ == 2 || NQ == 4, "N tile of 2 or 4 basis blocks");
 };
 
 // Row-dot of one basis block in double-float (BF16X10), over the shells
@@ -892,14 +893,14 @@ __device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad
 // kGradR takes the Phi~ tiles and contracts R with b . grad grad chi.
 enum { kRowDot = 0, kGradR = 1, kGradQ = 2 };
 
-template <int NS, bool GRAD, int MODE = kRowDot>
-__global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
+template <int NS, bool GRAD, int MODE = kRowDot, int NQ = (NS == 4 ? 2 : 4)>
+__global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
     k_rho_tc(BasisView B, GridView G, ListView L, int64_t g0, int64_t g1, int64_t t0,
              const uint8_t* __restrict__ phi, const uint8_t* __restrict__ dsplit, const uint8_t* __restrict__ zero,
              const double* __restrict__ dmax, const float* __restrict__ dscale, const float* __restrict__ rowscale,
              double t_b, double t_d, double* rho, double* grad, const double* __restrict__ xcoef, double* gout,
              int* err, uint64_t wait_ns, const float4* __restrict__ rad, const int64_t* __restrict__ rad_ptr) {
-  using C = RhoCfg<NS>;
+  using C = RhoCfg<NS, NQ>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   int32_t* meta_base = reinterpret_cast<int32_t*>(sm + C::kOffMeta);
@@ -1229,12 +1230,13 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
               Rs2[col * kBlockPts + i] = make_float2(r.h * f, r.l * f);
             }
             named_bar_sync(1 + k4, 128 * C::kHalves);
-          } else if (staged) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * rec->ds[c];
           } else {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) Rs[c * kBlockPts + i] = R[c] * dscale[q * kBasisBlk + c];
+            for (int c = 0; c < C::kColsPerWarp; ++c) {
+              const int col = half * C::kColsPerWarp + c;
+              Rs[col * kBlockPts + i] = R[c] * (staged ? rec->ds[col] : dscale[q * kBasisBlk + col]);
+            }
+            if constexpr (C::kHalves > 1) named_bar_sync(1 + k4, 128 * C::kHalves);
           }
           if constexpr (MODE == kRowDot && NS == 4) {
             if (staged) {
@@ -1263,8 +1265,8 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
               }
             };
             if (staged)
-              for_rec_functions<GRAD>(rec, prl.x, prl.y, prl.z, acc);
-            else
+              for_rec_functions<GRAD>(rec, prl.x, prl.y, prl.z, acc, half, C::kHalves);
+            else if (half == 0)
               for_block_functions<float, GRAD>(B, q, prl.x, prl.y, prl.z, acc, anc);
             ar = df_add(ar, f2{pr, 0.f});
             if (GRAD) {
@@ -1360,9 +1362,9 @@ __global__ void __launch_bounds__(RhoCfg<NS>::kThreads, 1)
 
 kldi_status prepare_tc_kernels();   // defined after the kernels: shared-memory opt-in, register check
 
-template <int NS>
+template <int NS, int NQ = (NS == 4 ? 2 : 4)>
 static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, double* grad_out, cudaStream_t s) {
-  using C = RhoCfg<NS>;
+  using C = RhoCfg<NS, NQ>;
   const int64_t n = b.g1 - b.g0;
   if (n == 0) return KLDI_OK;
   KLDI_TRY(prepare_tc_kernels());
@@ -1371,12 +1373,12 @@ static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, d
   const uint8_t* ds = reinterpret_cast<const uint8_t*>(P->d_dsplit);
   const uint8_t* z = reinterpret_cast<const uint8_t*>(P->d_zero);
   if (P->gga)
-    k_rho_tc<NS, true><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+    k_rho_tc<NS, true, kRowDot, NQ><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                            b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                            P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
                                                            nullptr, nullptr, P->d_err, P->wait_ns, P->d_rad, P->d_rad_ptr);
   else
-    k_rho_tc<NS, false><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
+    k_rho_tc<NS, false, kRowDot, NQ><<<grid, C::kThreads, C::kSmem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                             b.g1, b.t0, phi, ds, z, P->d_dmax, P->d_dscale,
                                                             P->d_rowscale, P->opt.t_b, P->opt.t_d, rho_out, grad_out,
                                                             nullptr, nullptr, P->d_err, P->wait_ns, P->d_rad, P->d_rad_ptr);
@@ -1384,11 +1386,15 @@ static kldi_status rho_ns(const kldi_plan* P, const Batch& b, double* rho_out, d
   return KLDI_OK;
 }
 
+// The density product's N tile: 2 basis blocks (64 functions, two TMEM
+// buffers) or 4 (128 functions; one buffer for BF16X6): the plan's tuning,
+// else the mode's default (BF16X10 only has the 64-function tile).
 kldi_status launch_rho_tc(const kldi_plan* P, const Batch& b, double* rho_out, double* grad_out, cudaStream_t s) {
+  const bool narrow = P->tune.rho_ntile == 64;
   switch (slices_of(P->prec)) {
     case 4: return rho_ns<4>(P, b, rho_out, grad_out, s);
-    case 3: return rho_ns<3>(P, b, rho_out, grad_out, s);
-    default: return rho_ns<2>(P, b, rho_out, grad_out, s);
+    case 3: return narrow ? rho_ns<3, 2>(P, b, rho_out, grad_out, s) : rho_ns<3>(P, b, rho_out, grad_out, s);
+    default: return narrow ? rho_ns<2, 2>(P, b, rho_out, grad_out, s) : rho_ns<2>(P, b, rho_out, grad_out, s);
   }
 }
 
@@ -1784,9 +1790,20 @@ static kldi_status prepare_v_kernel() {
   return KLDI_OK;
 }
 
+template <int NS, int NQ>
+static kldi_status prepare_rho_rowdot() {
+  using C = RhoCfg<NS, NQ>;
+  KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, true, kRowDot, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     C::kSmem));
+  KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false, kRowDot, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     C::kSmem));
+  return KLDI_OK;
+}
+
 template <int NS>
 static kldi_status prepare_rho_kernel() {
   using C = RhoCfg<NS>;
+  if constexpr (NS < 4) KLDI_TRY((prepare_rho_rowdot<NS, 2>()));
   KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
   KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
   KLDI_TRY_CUDA(cudaFuncSetAttribute(k_rho_tc<NS, false, kGradQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,

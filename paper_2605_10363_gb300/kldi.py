@@ -57,6 +57,10 @@ class TrainOptions(C.Structure):
 MLP_NPARAMS = 4482
 
 
+class Tuning(C.Structure):
+    _fields_ = [("v_seg", C.c_int), ("rho_ntile", C.c_int)]
+
+
 class PlanStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("nbf", "nbasis_blocks", "npoints", "nblocks", "retained",
                                           "pair_slots", "vtile_work", "workspace_bytes")]
@@ -98,10 +102,10 @@ def _load():
         "kldi_workspace_create": (C.c_int, [C.c_int64, C.POINTER(vp)]),
         "kldi_workspace_free": (None, [vp]),
         "kldi_plan_set_workspace": (C.c_int, [vp, vp]),
-        "kldi_plan_set_tuning": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "kldi_plan_set_tuning": (C.c_int, [vp, C.POINTER(Tuning)]),
         "kldi_plan_set_block_range": (C.c_int, [vp, C.c_int64, C.c_int64]),
-        "kldi_plan_get_tuning": (C.c_int, [vp, C.POINTER(C.c_int)]),
-        "kldi_plan_autotune": (C.c_int, [vp, C.c_int, vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "kldi_plan_get_tuning": (C.c_int, [vp, C.POINTER(Tuning)]),
+        "kldi_plan_autotune": (C.c_int, [vp, C.c_int, vp, C.c_int, C.POINTER(Tuning), C.POINTER(C.c_double)]),
         "kldi_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp), C.POINTER(vp), vp, vp,
                                         C.POINTER(vp)]),
         "kldi_batch_launch": (C.c_int, [vp]),
@@ -231,22 +235,22 @@ class Plan:
         """Evaluate only grid blocks [g0, g1) (partial E_xc and V)."""
         _check(LIB.kldi_plan_set_block_range(self.h, int(g0), int(g1)))
 
-    def set_tuning(self, v_seg):
-        t = C.c_int(int(v_seg))
+    def set_tuning(self, v_seg=0, rho_ntile=0):
+        t = Tuning(int(v_seg), int(rho_ntile))
         _check(LIB.kldi_plan_set_tuning(self.h, C.byref(t)))
 
     def tuning(self):
-        t = C.c_int()
+        t = Tuning()
         _check(LIB.kldi_plan_get_tuning(self.h, C.byref(t)))
-        return {"v_seg": t.value}
+        return {"v_seg": t.v_seg, "rho_ntile": t.rho_ntile}
 
     def autotune(self, xc, D, reps=3):
         """Tune on a device density matrix; returns (tuning, ms per call)."""
-        t = C.c_int()
+        t = Tuning()
         ms = C.c_double()
         _check(LIB.kldi_plan_autotune(self.h, XC[xc] if isinstance(xc, str) else int(xc), _ptr(D), int(reps),
                                       C.byref(t), C.byref(ms)))
-        return {"v_seg": t.value}, ms.value
+        return {"v_seg": t.v_seg, "rho_ntile": t.rho_ntile}, ms.value
 
     def set_precision(self, prec):
         _check(LIB.kldi_plan_set_precision(self.h, PREC[prec] if isinstance(prec, str) else int(prec)))

@@ -104,15 +104,42 @@ def test_autotune_keeps_results(frames):
     E0 = torch.zeros(1, dtype=torch.float64, device="cuda")
     kldi.exc(plan, "pbe", D, V0, E0)
     best, ms = plan.autotune("pbe", D, reps=2)
-    assert best["v_seg"] in (0, 4, 8, 16, 32, 64, 128) and ms > 0
+    assert best["v_seg"] in (0, 4, 8, 32, 64, 128) and best["rho_ntile"] in (64, 128) and ms > 0
     assert plan.tuning() == best
     V1 = torch.zeros_like(V0)
     E1 = torch.zeros_like(E0)
     kldi.exc(plan, "pbe", D, V1, E1)
-    assert E1.item() == E0.item()
+    # the density tile changes the order of the row-dot's sums (exact products,
+    # FP32 / double-float sums): E within rounding, V within 1e-12 relative
+    assert abs(E1.item() - E0.item()) <= 1e-12 * abs(E0.item())
     assert (V1 - V0).abs().max().item() <= 1e-12 * V0.abs().max().item()
-    plan.set_tuning(8)
-    assert plan.tuning()["v_seg"] == 8
+    plan.set_tuning(8, 64)
+    assert plan.tuning() == {"v_seg": 8, "rho_ntile": 64}
+    with pytest.raises(kldi.KldiError):
+        plan.set_tuning(8, 96)
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
+def test_density_tile_widths_agree(frames, prec):
+    """The 64- and 128-function density tiles compute the same exact-level
+    products: E and V agree to rounding, and both match the oracle."""
+    kldi = _kldi()
+    s = frames[1]
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    ref = oe.evaluate(s, g, ob.build_shells(s.xyz, s.basis), screened=True)
+    plan = kldi.plan_for_system(s, prec=prec, xc="pbe")
+    out = {}
+    for nt in (128, 64):
+        plan.set_tuning(0, nt)
+        V = np.zeros((s.nbf, s.nbf))
+        E = np.zeros(1)
+        kldi.exc(plan, "pbe", s.D, V, E)
+        out[nt] = (E[0], V)
+    assert abs(out[64][0] - out[128][0]) <= 1e-12 * abs(ref.E)
+    assert np.abs(out[64][1] - out[128][1]).max() <= 1e-12 * np.abs(ref.V).max()
+    tol = (1e-6, 3e-7) if prec == "bf16x6" else (3e-5 * abs(ref.E), 2e-4)
+    assert abs(out[64][0] - ref.E) <= tol[0]
+    assert np.abs(out[64][1] - ref.V).max() <= tol[1]
 
 
 def test_workspace_too_small(frames):
