@@ -268,6 +268,7 @@ struct kldi_plan {
   int64_t* d_rad_ptr = nullptr;
   float4* d_rad = nullptr;          // [shells of the batch][128]: g hi, g lo, gd hi, gd lo
   int64_t rad_cap = 0;              // shell rows d_rad holds
+  int64_t rad_rows_cap = INT64_MAX; // shell rows a batch may use (bounded when the rows live in a workspace)
   float* d_dscale = nullptr;    // [nbf_pad] column scales of d_dsplit
   uint16_t* d_dsplit = nullptr; // sliced D block pairs [nbb*nbb][NS planes][32][32]
   uint16_t* d_zero = nullptr;   // zero block (bulk-copy source for masked / absent blocks)

@@ -88,9 +88,11 @@ void free_plan_buffers(kldi_plan* P) {
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_prel_lo, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
                   P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
-                  P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero, P->d_rad_ptr, P->d_rad};
+                  P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero, P->d_rad_ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (P->d_rad && !P->ws) cudaFree(P->d_rad);   // else a view into the workspace
+  P->d_rad = nullptr;
   for (auto& b : P->batches) {
     if (b.d_v64_g) cudaFree(b.d_v64_g);
     if (b.d_v64_work) cudaFree(b.d_v64_work);
@@ -153,7 +155,10 @@ kldi_status build_work(kldi_plan* P, int64_t cap) {
     int64_t g0 = P->range_g0;
     while (g0 < gend) {
       int64_t g1 = g0;
-      while (g1 < gend && P->blk_ptr[g1 + 1] - P->blk_ptr[g0] <= cap) ++g1;
+      while (g1 < gend && P->blk_ptr[g1 + 1] - P->blk_ptr[g0] <= cap &&
+             P->rad_ptr[P->blk_ptr[g1 + 1]] - P->rad_ptr[P->blk_ptr[g0]] <= P->rad_rows_cap)
+        ++g1;
+      if (g1 == g0) ++g1;   // one grid block always fits (checked when the workspace is set)
       Batch b;
       b.g0 = g0;
       b.g1 = g1;
@@ -259,7 +264,12 @@ kldi_status ensure_tile_buffers(kldi_plan* P, int prec) {
     set_error("KLDI_BF16X10: a basis block has more than 40 shells or 80 primitives");
     return KLDI_EUNSUPPORTED;
   }
-  if (prec == KLDI_BF16X10) {
+  if (prec == KLDI_BF16X10 && P->ws) {
+    // the radial rows follow the tile buffers in the workspace
+    uint8_t* base = static_cast<uint8_t*>(P->ws->base);
+    P->d_rad = reinterpret_cast<float4*>(base + P->tile_cap * tile_bytes_max());
+    P->rad_cap = P->rad_rows_cap;
+  } else if (prec == KLDI_BF16X10) {
     // radial factors of the largest batch (the batches change with the block range and tuning)
     int64_t need = 1;
     for (const Batch& b : P->batches) need = std::max(need, P->rad_ptr[b.t1] - P->rad_ptr[b.t0]);
@@ -708,21 +718,34 @@ extern "C" kldi_status kldi_plan_set_workspace(kldi_plan* P, const kldi_workspac
         set_error("kldi_plan_set_workspace: workspace and plan live on different devices");
         return KLDI_EINVAL;
       }
-      cap = ws->bytes / tile_bytes_max();
-      int64_t maxblk = 0;
-      for (int64_t g = 0; g < P->nblocks; ++g) maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
-      if (cap < maxblk) {
+      // tiles first, then the BF16X10 radial rows (2 KB each; 1.25 x the
+      // plan's mean shells per tile reserved per tile)
+      const double mean_rows = P->ntiles ? (double)P->rad_ptr[P->ntiles] / (double)P->ntiles : 1.0;
+      const int64_t per_tile = tile_bytes_max() + (int64_t)std::ceil(1.25 * mean_rows) * kBlockPts * 16;
+      cap = ws->bytes / per_tile;
+      const int64_t rows_cap = (ws->bytes - cap * tile_bytes_max()) / (kBlockPts * 16);
+      int64_t maxblk = 0, maxrows = 0;
+      for (int64_t g = 0; g < P->nblocks; ++g) {
+        maxblk = std::max<int64_t>(maxblk, P->blk_ptr[g + 1] - P->blk_ptr[g]);
+        maxrows = std::max<int64_t>(maxrows, P->rad_ptr[P->blk_ptr[g + 1]] - P->rad_ptr[P->blk_ptr[g]]);
+      }
+      if (cap < maxblk || rows_cap < maxrows) {
         set_error("kldi_plan_set_workspace: %lld bytes hold %lld tiles, a grid block needs %lld", (long long)ws->bytes,
                   (long long)cap, (long long)maxblk);
         return KLDI_EINVAL;
       }
+      P->rad_rows_cap = rows_cap;
     } else {
       size_t free_b = 0, total_b = 0;
       cudaMemGetInfo(&free_b, &total_b);
       cap = (int64_t)(0.35 * (double)free_b) / tile_bytes_max();
+      P->rad_rows_cap = INT64_MAX;
     }
     KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
     free_own_tile_buffers(P);
+    if (P->d_rad && !P->ws) cudaFree(P->d_rad);   // a plan-owned radial buffer
+    P->d_rad = nullptr;
+    P->rad_cap = 0;
     P->ws = ws;
     KLDI_TRY(build_work(P, cap));
     if (ws) KLDI_TRY(ensure_tile_buffers(P, P->prec));

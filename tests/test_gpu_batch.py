@@ -109,10 +109,12 @@ def test_autotune_keeps_results(frames):
     V1 = torch.zeros_like(V0)
     E1 = torch.zeros_like(E0)
     kldi.exc(plan, "pbe", D, V1, E1)
-    # the density tile changes the order of the row-dot's sums (exact products,
-    # FP32 / double-float sums): E within rounding, V within 1e-12 relative
-    assert abs(E1.item() - E0.item()) <= 1e-12 * abs(E0.item())
-    assert (V1 - V0).abs().max().item() <= 1e-12 * V0.abs().max().item()
+    # the density tile changes how the executed K chunks are grouped into
+    # exact segments, whose levels BF16X6 combines in FP32: E and V agree at
+    # the mode's tolerance (the V decomposition alone changes only the order
+    # of FP64 atomics)
+    assert abs(E1.item() - E0.item()) <= 1e-6
+    assert (V1 - V0).abs().max().item() <= 3e-7
     plan.set_tuning(8, 64)
     assert plan.tuning() == {"v_seg": 8, "rho_ntile": 64}
     with pytest.raises(kldi.KldiError):
@@ -121,8 +123,8 @@ def test_autotune_keeps_results(frames):
 
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
 def test_density_tile_widths_agree(frames, prec):
-    """The 64- and 128-function density tiles compute the same exact-level
-    products: E and V agree to rounding, and both match the oracle."""
+    """The 64- and 128-function density tiles: both match the oracle, and
+    each other at the mode's tolerance."""
     kldi = _kldi()
     s = frames[1]
     g = og.build_grid(s.Z, s.xyz, s.grid)
@@ -135,9 +137,12 @@ def test_density_tile_widths_agree(frames, prec):
         E = np.zeros(1)
         kldi.exc(plan, "pbe", s.D, V, E)
         out[nt] = (E[0], V)
-    assert abs(out[64][0] - out[128][0]) <= 1e-12 * abs(ref.E)
-    assert np.abs(out[64][1] - out[128][1]).max() <= 1e-12 * np.abs(ref.V).max()
+    # the same exact-level products; the levels of each exact segment are
+    # combined in FP32, and the tile width changes how the executed K chunks
+    # form segments, so the two agree at the mode's FP32 level
     tol = (1e-6, 3e-7) if prec == "bf16x6" else (3e-5 * abs(ref.E), 2e-4)
+    assert abs(out[64][0] - out[128][0]) <= tol[0]
+    assert np.abs(out[64][1] - out[128][1]).max() <= tol[1]
     assert abs(out[64][0] - ref.E) <= tol[0]
     assert np.abs(out[64][1] - ref.V).max() <= tol[1]
 
