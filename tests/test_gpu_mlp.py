@@ -160,16 +160,17 @@ def test_mlp_call_needs_network():
 
 
 def test_what_training_gains(trained):
-    """The trained network against the method without it (the same network
-    untrained, which starts at Slater exchange) on the four-water system:
-    its E_xc error against the analytic PBE-form quadrature falls by more than
-    20x, and its functional stage is timed against the analytic FP64 stage."""
+    """The learned functional against the method without it, the analytic
+    PBE-form path (the judge), on the four-water system: the E_xc difference
+    and the time of the whole evaluation and of the functional stage are
+    measured and stated; the trained network's difference is bounded (1e-3
+    relative) and more than 20x smaller than that of the untrained network
+    (Slater exchange), which shows what the training adds."""
     kldi = _kldi()
     net, box, _ = trained
     s = synth.make_system(2, nwaters=4)
-    errs = {}
-    times = {}
-    for name, netw in (("trained", net), ("untrained", kldi.Mlp(synth.mlp_init(42), box)), ("analytic", None)):
+    E_of, stage_ms, total_ms = {}, {}, {}
+    for name, netw in (("analytic", None), ("trained", net), ("untrained", kldi.Mlp(synth.mlp_init(42), box))):
         plan = kldi.plan_for_system(s, prec="bf16x6", xc="pbe")
         xc = "pbe"
         if netw is not None:
@@ -182,12 +183,16 @@ def test_what_training_gains(trained):
         for _ in range(5):
             kldi.exc(plan, xc, s.D, V, E)
         ms, _ = plan.stage_times()
-        times[name] = ms[3] / 5
-        errs[name] = E[0]
-    d_tr = abs(errs["trained"] - errs["analytic"])
-    d_un = abs(errs["untrained"] - errs["analytic"])
-    print(f"E_xc error vs analytic: trained {d_tr:.3e} Ha, untrained {d_un:.3e} Ha; "
-          f"functional stage ms: mlp {times['trained']:.4f}, analytic {times['analytic']:.4f}")
+        stage_ms[name] = ms[3] / 5
+        total_ms[name] = ms.sum() / 5
+        E_of[name] = E[0]
+    d_tr = abs(E_of["trained"] - E_of["analytic"])
+    d_un = abs(E_of["untrained"] - E_of["analytic"])
+    print(f"learned vs analytic: dE {d_tr:.3e} Ha ({d_tr / abs(E_of['analytic']):.1e} relative), "
+          f"evaluation {total_ms['trained']:.3f} ms vs {total_ms['analytic']:.3f} ms, "
+          f"functional stage {stage_ms['trained']:.4f} ms vs {stage_ms['analytic']:.4f} ms; "
+          f"untrained network dE {d_un:.3e} Ha")
+    assert d_tr <= 1e-3 * abs(E_of["analytic"])
     assert d_tr < d_un / 20.0
 
 
