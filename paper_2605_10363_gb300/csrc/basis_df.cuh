@@ -224,26 +224,26 @@ __device__ __forceinline__ void for_rec_functions_df(const BlockRec* rec, const 
 // few double-float products.
 // The radial factors come from the Phi kernel: rad[s * 128] = (g hi, g lo,
 // gd hi, gd lo) of shell s of the block at this point.
-// Shells s0, s0 + sstep, ... of the block.
+// Shells sb .. se - 1 of the block; the offsets are formed once per run of
+// shells on one atom.
 template <bool GRAD, typename F>
-__device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float4* rad, int s0, int sstep, f2 px,
+__device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float4* rad, int sb, int se, f2 px,
                                                 f2 py, f2 pz, f2 a, f2 bx, f2 by, f2 bz, F&& f) {
   const f2 s3{kS3h, kS3l};
-  const int ns = rec->nshell;
   // radial factors loaded two shells ahead (the loads come from HBM / L2)
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 qa = s0 < ns ? rad[s0 * kBlockPts] : z4;
-  float4 qb = s0 + sstep < ns ? rad[(s0 + sstep) * kBlockPts] : z4;
-  for (int s = s0; s < ns; s += sstep) {
+  float4 qa = sb < se ? rad[sb * kBlockPts] : z4;
+  float4 qb = sb + 1 < se ? rad[(sb + 1) * kBlockPts] : z4;
+  f2 dx, dy, dz;
+  for (int s = sb; s < se; ++s) {
     const float4 q = qa;
     qa = qb;
-    qb = s + 2 * sstep < ns ? rad[(s + 2 * sstep) * kBlockPts] : z4;
+    qb = s + 2 < se ? rad[(s + 2) * kBlockPts] : z4;
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
     const int hdr = __float_as_int(c1.z);
     const int l = hdr & 255, first = (hdr >> 16) - 64;
     const f2 g{q.x, q.y}, gd{q.z, q.w};
-    f2 dx, dy, dz;
-    offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
+    if (s == sb || rec->atom[s] != rec->atom[s - 1]) offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
     f2 w{0.f, 0.f}, gbx{0.f, 0.f}, gby{0.f, 0.f}, gbz{0.f, 0.f};
     if (GRAD) {
       w = df_mul_u(df_scale(gd, -2.f), df_add_u(df_add_u(df_mul_u(bx, dx), df_mul_u(by, dy)), df_mul_u(bz, dz)));

@@ -330,7 +330,14 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     std::vector<int32_t> p_atom, p_l, p_nprim, fnperm;
     std::vector<double> p_exps, p_coefs;
     kldi_basis permuted;
-    if (opt->shell_order) {
+    {
+      // The plan's shell order: the caller's (shell_order) or the given one,
+      // refined so that within each 32-function block the shells that lie
+      // wholly inside it are grouped by atom (stable).  A block keeps its set
+      // of functions, hence every screening decision; the kernels form the
+      // point offsets once per run of shells on one atom.  fnperm maps an
+      // internal function index to the caller's; without a caller's order and
+      // with nothing to regroup (an atom-ordered basis) no permutation is made.
       const int ns0 = basis->nshell;
       std::vector<char> seen(ns0, 0);
       std::vector<int64_t> poff(ns0 + 1, 0), foff(ns0 + 1, 0);
@@ -343,24 +350,60 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
         poff[s + 1] = poff[s] + basis->nprim[s];
         foff[s + 1] = foff[s] + (l + 1) * (l + 2) / 2;
       }
+      std::vector<int> order(ns0);
       for (int k = 0; k < ns0; ++k) {
-        const int s = opt->shell_order[k];
+        const int s = opt->shell_order ? opt->shell_order[k] : k;
         if (s < 0 || s >= ns0 || seen[s]) {
           set_error("kldi_screen: shell_order is not a permutation of 0 .. %d", ns0 - 1);
           return KLDI_EINVAL;
         }
         seen[s] = 1;
-        p_atom.push_back(basis->atom[s]);
-        p_l.push_back(basis->l[s]);
-        p_nprim.push_back(basis->nprim[s]);
-        for (int64_t i = poff[s]; i < poff[s + 1]; ++i) {
-          p_exps.push_back(basis->exps[i]);
-          p_coefs.push_back(basis->coefs[i]);
-        }
-        for (int64_t f = foff[s]; f < foff[s + 1]; ++f) fnperm.push_back((int32_t)f);
+        order[k] = s;
       }
-      permuted = kldi_basis{ns0, p_atom.data(), p_l.data(), p_nprim.data(), p_exps.data(), p_coefs.data()};
-      basis = &permuted;
+      {
+        int64_t f = 0;
+        int k = 0;
+        while (k < ns0) {
+          const int l0 = basis->l[order[k]];
+          const int64_t f1 = f + (l0 + 1) * (l0 + 2) / 2;
+          if (f / kBasisBlk != (f1 - 1) / kBasisBlk) {   // straddles a block boundary: stays
+            f = f1;
+            ++k;
+            continue;
+          }
+          const int64_t blk = f / kBasisBlk;
+          int e = k;
+          int64_t fe = f;
+          while (e < ns0) {
+            const int le = basis->l[order[e]];
+            const int64_t fn1 = fe + (le + 1) * (le + 2) / 2;
+            if (fe / kBasisBlk != blk || (fn1 - 1) / kBasisBlk != blk) break;
+            fe = fn1;
+            ++e;
+          }
+          std::stable_sort(order.begin() + k, order.begin() + e,
+                           [&](int a, int b) { return basis->atom[a] < basis->atom[b]; });
+          f = fe;
+          k = e;
+        }
+      }
+      bool identity = true;
+      for (int k = 0; k < ns0 && identity; ++k) identity = order[k] == k;
+      if (opt->shell_order || !identity) {
+        for (int k = 0; k < ns0; ++k) {
+          const int s = order[k];
+          p_atom.push_back(basis->atom[s]);
+          p_l.push_back(basis->l[s]);
+          p_nprim.push_back(basis->nprim[s]);
+          for (int64_t i = poff[s]; i < poff[s + 1]; ++i) {
+            p_exps.push_back(basis->exps[i]);
+            p_coefs.push_back(basis->coefs[i]);
+          }
+          for (int64_t f = foff[s]; f < foff[s + 1]; ++f) fnperm.push_back((int32_t)f);
+        }
+        permuted = kldi_basis{ns0, p_atom.data(), p_l.data(), p_nprim.data(), p_exps.data(), p_coefs.data()};
+        basis = &permuted;
+      }
     }
     kldi_plan* P = new (std::nothrow) kldi_plan;
     if (!P) { set_error("kldi_screen: out of host memory"); return KLDI_ENOMEM; }

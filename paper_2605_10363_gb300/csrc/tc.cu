@@ -387,12 +387,13 @@ __global__ void __launch_bounds__(128) k_phi_split4(BasisView B, GridView G, Lis
     // per shell: the radial factors g (and gd) go to the radial buffer for the
     // row-dot and the X kernel, the values P g to the staging array
     float4* rtile = rad + (rad_ptr[j] - rad_ptr[t0]) * kBlockPts;
+    f2 dx, dy, dz, r2;   // offsets of the point from the current shell's atom
     for (int s = 0; s < rc->nshell; ++s) {
       const float4 c0 = rc->c0[s], c1 = rc->c1[s];
       const int hdr = __float_as_int(c1.z), pi = __float_as_int(c1.w);
       const int l = hdr & 255, np = (hdr >> 8) & 255, first = (hdr >> 16) - 64;
-      f2 dx, dy, dz, r2, g, gd;
-      offsets_df(c0, c1, px, py, pz, dx, dy, dz, r2);
+      f2 g, gd;
+      if (s == 0 || rc->atom[s] != rc->atom[s - 1]) offsets_df(c0, c1, px, py, pz, dx, dy, dz, r2);
       radial_df<GRAD>(rc->pf + pi, rc->pac + pi, np, r2, tab, g, gd);
       rtile[s * kBlockPts + i] = make_float4(g.h, g.l, gd.h, gd.l);
       const int ncomp = (l + 1) * (l + 2) / 2;
@@ -638,7 +639,9 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
   const float4 pr = G.prel[pt], pl = G.prel_lo[pt];
   stage_block_rec(B, p, G.anchor[g], &rec, threadIdx.x, kX4Threads);
   __syncthreads();
-  for_rec_phix_df<GRAD>(&rec, rad + (rad_ptr[t] - rad_ptr[t0]) * kBlockPts + i, half, 2, f2{pr.x, pl.x},
+  const int mid = (rec.nshell + 1) >> 1;   // the two halves take consecutive shell ranges
+  for_rec_phix_df<GRAD>(&rec, rad + (rad_ptr[t] - rad_ptr[t0]) * kBlockPts + i, half == 0 ? 0 : mid,
+                        half == 0 ? mid : rec.nshell, f2{pr.x, pl.x},
                         f2{pr.y, pl.y}, f2{pr.z, pl.z}, a, bx, by, bz, [&](int nu, f2 v, f2 x) {
                           sph[nu][i] = v.h * c;
                           spl[nu][i] = v.l * c;
@@ -1076,15 +1079,37 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
               tc_fence_after();
               const uint32_t a = smem_u32(sm + s * C::kStageBytes);
               const uint32_t bsm = a + NS * kPlaneBytes;
+              if constexpr (NQ == 2) {
+                // The NS planes of B lie one after another (64 rows each), and
+                // so do the level accumulators (64 columns each): one product
+                // of slice a_i with [b_0 | ... | b_{NS-1-i}] (N = 64 (NS - i))
+                // adds a_i b_j to level i + j for every j at once, NS
+                // products per K = 16 step instead of NS (NS + 1) / 2.  The
+                // first one of a segment (i = 0) starts all NS levels.  A tile
+                // of one q block leaves the second 32 columns of each level
+                // undefined; the drain reads only the first 32.
 #pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                uint64_t ad[NS], bd[NS];
+                for (int kk = 0; kk < 2; ++kk) {
+                  const uint64_t bd = smem_desc(bsm + kk * 32, 16, 512, kSwz64);
 #pragma unroll
-                for (int l = 0; l < NS; ++l) {
-                  ad[l] = smem_desc(a + l * kPlaneBytes + kk * 32, 16, 512, kSwz64);
-                  bd[l] = smem_desc(bsm + l * (C::kNQ * kDPlane) + kk * 32, 16, 512, kSwz64);
+                  for (int i = 0; i < NS; ++i) {
+                    const uint64_t ad = smem_desc(a + i * kPlaneBytes + kk * 32, 16, 512, kSwz64);
+                    mma_f16(d0 + i * C::kLevelCols, ad, bd, instr_desc(128, 64 * (NS - i), 1, 0, 0),
+                            i == 0 ? started[0] : 1u);
+                  }
+                  started[0] = 1;
                 }
-                issue_levels<NS>(d0, C::kLevelCols, ad, bd, idesc, started);
+              } else {
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                  uint64_t ad[NS], bd[NS];
+#pragma unroll
+                  for (int l = 0; l < NS; ++l) {
+                    ad[l] = smem_desc(a + l * kPlaneBytes + kk * 32, 16, 512, kSwz64);
+                    bd[l] = smem_desc(bsm + l * (C::kNQ * kDPlane) + kk * 32, 16, 512, kSwz64);
+                  }
+                  issue_levels<NS>(d0, C::kLevelCols, ad, bd, idesc, started);
+                }
               }
               mma_commit(&empty[s]);
               ++it;
