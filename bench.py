@@ -127,7 +127,7 @@ SPLITS = {"bf16x3": 3, "bf16x6": 6, "bf16x10": 10, "fp64": 1}
 NTILE = {"bf16x10": 2}     # basis blocks per N tile of the density product (4 otherwise)
 
 
-def work_counts(plan, system, splits, counts=None, nq=4):
+def work_counts(plan, system, splits, counts=None, nq=4, v_align=4):
     """Tensor-pipe FLOPs of one evaluation per product (algorithmic: executed
     block pairs x 2 x 128 x d_p d_q x slice products), from the retained lists
     and the D block maxima; `counts` (a dict) also receives the executed tensor
@@ -162,11 +162,16 @@ def work_counts(plan, system, splits, counts=None, nq=4):
         f_v_pq += 2.0 * 128 * float(np.triu(dd).sum())
         # executed tensor work (tile padding included): density chunks of
         # 128 x (32 nq) x 32 per (N tile of nq retained blocks, p with any
-        # executed pair); V jobs of 128 x 128 x 256 per tile pair P < Q, x 128
-        # for P = Q
+        # executed pair); V jobs of 128 x 128 x 256 per window pair P < Q, x 128
+        # for P = Q, over the plan's 4-block windows that cover S (greedy,
+        # starts at multiples of v_align)
         for q0 in range(0, S.size, nq):
             x_rho += 2.0 * 128 * (32 * nq) * 32 * float(np.any(e1[:, q0:q0 + nq], axis=1).sum())
-        nvt = len(set((S // 4).tolist()))
+        nvt, cov = 0, -1
+        for p in S.tolist():
+            if p > cov:
+                w = p - p % v_align
+                nvt, cov = nvt + 1, w + 3
         x_v += 2.0 * 128 * 128 * (256 * nvt * (nvt - 1) / 2 + 128 * nvt)
     counts.update(executed_rho=splits * x_rho, executed_v=splits * x_v, v_pairs_pq=splits * f_v_pq)
     return splits * f_rho, splits * f_v
@@ -324,7 +329,7 @@ def run_frames(args, dev, stream):
     tuning, _ = plans[big].autotune("pbe", Ds[big], reps=2)
     t_tune = time.perf_counter() - t1
     for p in plans:
-        p.set_tuning(tuning["v_seg"], tuning["rho_ntile"])
+        p.set_tuning(tuning["v_seg"], tuning["rho_ntile"], tuning["v_align"])
     batch = kldi.Batch(plans, "pbe", Ds, Vs, E, stream=stream.cuda_stream)
     for _ in range(max(1, args.warmup)):
         batch.launch()
@@ -621,7 +626,8 @@ def main():
 
     splits = SPLITS[args.prec]
     executed = {}
-    f_rho, f_v = work_counts(plan, s_int, splits, executed, nq=NTILE.get(args.prec, 4))
+    f_rho, f_v = work_counts(plan, s_int, splits, executed, nq=NTILE.get(args.prec, 4),
+                             v_align=plan.tuning()["v_align"] or 2)
     names = kldi.STAGES
     per_stage = {names[k]: round(stage_ms[k] / args.steps, 4) for k in range(len(names))}
     dom = "rho" if stage_ms[2] >= stage_ms[5] else "v"

@@ -299,17 +299,23 @@ kldi_status kldi_plan_set_workspace(kldi_plan* plan, const kldi_workspace* ws);
 
 /* Tunable shapes of the tensor-core products.
  * v_seg: the V product's decomposition: the grid blocks are cut into ranges
- * of v_seg consecutive blocks, a work item is one 128 x 128 tile pair over
- * the blocks of one range in its list, and items run range by range (so
- * concurrent items share the range's tiles in L2); 0 chooses 16.
+ * of v_seg consecutive blocks, a work item is one pair of 128-function
+ * windows over the blocks of one range in its list, and items run range by
+ * range (so concurrent items share the range's tiles in L2); 0 chooses 64.
  * rho_ntile: the density product's N tile, 128 functions (four basis
  * blocks, one TMEM buffer of the level accumulators for BF16X6) or 64 (two
  * basis blocks, two buffers, so the drains overlap the next tile's products,
  * and less padding where few blocks of a tile have executed pairs); 0 chooses
- * the mode's default (128; BF16X10 has only 64). */
+ * the mode's default (128; BF16X10 has only 64).
+ * v_align: the V product's windows of 4 consecutive basis blocks start at
+ * multiples of v_align blocks (4: fixed 128-function tiles; 2; 1: the
+ * fewest windows that cover each grid block's retained blocks, hence the
+ * fewest zero blocks in the products, but more distinct window pairs and so
+ * shorter work items); 0 chooses 2. */
 typedef struct {
   int v_seg;
   int rho_ntile;
+  int v_align;
 } kldi_tuning;
 
 kldi_status kldi_plan_set_tuning(kldi_plan* plan, const kldi_tuning* tuning);
@@ -318,8 +324,9 @@ kldi_status kldi_plan_get_tuning(const kldi_plan* plan, kldi_tuning* tuning);
 /* Time kldi_exc(plan, xc, D) (D on the device) with CUDA events over the
  * candidate tunings, `reps` timed calls each after one warm-up, and keep the
  * fastest on the plan: first the density product's N tile (128 and 64
- * functions for BF16X3 / BF16X6) at the default V decomposition, then v_seg
- * in {4, 8, 32, 64, 128} with the chosen tile.  best (host, may be NULL) receives it, best_ms (host,
+ * functions for BF16X3 / BF16X6) at the default V decomposition, then the V
+ * window alignment in {2, 4, 1}, then v_seg in {16, 32, 64, 128, 256} with
+ * the chosen tile and alignment.  best (host, may be NULL) receives it, best_ms (host,
  * may be NULL) its mean time per call in milliseconds.  Overwrites the
  * plan's scratch outputs; synchronises. */
 kldi_status kldi_plan_autotune(kldi_plan* plan, int xc, const double* D, int reps, kldi_tuning* best,

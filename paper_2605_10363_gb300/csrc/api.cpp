@@ -395,22 +395,30 @@ extern "C" kldi_status kldi_plan_autotune(kldi_plan* P, int xc, const double* D,
     const int prof = P->prof;
     P->prof = 0;
     // coordinate search: the density product's N tile at the default V
-    // decomposition, then the V work-item span with the chosen tile
-    kldi_tuning bt{0, 0};
+    // decomposition, then the V window alignment, then the V work-item span
+    // with the chosen tile and alignment
+    kldi_tuning bt{0, 0, 0};
     double bms = 1e300;
     kldi_status st = KLDI_OK;
     std::vector<int> tiles = {0};
     if (P->prec == KLDI_BF16X3 || P->prec == KLDI_BF16X6) tiles = {128, 64};
     for (int nt : tiles) {
       double ms = 0.0;
-      const kldi_tuning t{0, nt};
+      const kldi_tuning t{0, nt, 0};
       if ((st = time_tuning(P, xc, D, reps, t, e0, e1, &ms)) != KLDI_OK) break;
       if (ms < bms) { bms = ms; bt = t; }
     }
-    const int segs[] = {4, 8, 32, 64, 128};
-    for (int k = 0; k < 5 && st == KLDI_OK && P->prec != KLDI_FP64; ++k) {
+    const int aligns[] = {4, 1};
+    for (int k = 0; k < 2 && st == KLDI_OK && P->prec != KLDI_FP64; ++k) {
       double ms = 0.0;
-      const kldi_tuning t{segs[k], bt.rho_ntile};
+      const kldi_tuning t{0, bt.rho_ntile, aligns[k]};
+      if ((st = time_tuning(P, xc, D, reps, t, e0, e1, &ms)) != KLDI_OK) break;
+      if (ms < bms) { bms = ms; bt = t; }
+    }
+    const int segs[] = {16, 32, 128, 256};
+    for (int k = 0; k < 4 && st == KLDI_OK && P->prec != KLDI_FP64; ++k) {
+      double ms = 0.0;
+      const kldi_tuning t{segs[k], bt.rho_ntile, bt.v_align};
       if ((st = time_tuning(P, xc, D, reps, t, e0, e1, &ms)) != KLDI_OK) break;
       if (ms < bms) { bms = ms; bt = t; }
     }

@@ -234,7 +234,7 @@ __device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 qa = sb < se ? rad[sb * kBlockPts] : z4;
   float4 qb = sb + 1 < se ? rad[(sb + 1) * kBlockPts] : z4;
-  f2 dx, dy, dz;
+  f2 dx, dy, dz, br{0.f, 0.f};   // br = b . r, once per run of shells on one atom
   for (int s = sb; s < se; ++s) {
     const float4 q = qa;
     qa = qb;
@@ -243,10 +243,13 @@ __device__ __forceinline__ void for_rec_phix_df(const BlockRec* rec, const float
     const int hdr = __float_as_int(c1.z);
     const int l = hdr & 255, first = (hdr >> 16) - 64;
     const f2 g{q.x, q.y}, gd{q.z, q.w};
-    if (s == sb || rec->atom[s] != rec->atom[s - 1]) offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
+    if (s == sb || rec->atom[s] != rec->atom[s - 1]) {
+      offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
+      if (GRAD) br = df_add_u(df_add_u(df_mul_u(bx, dx), df_mul_u(by, dy)), df_mul_u(bz, dz));
+    }
     f2 w{0.f, 0.f}, gbx{0.f, 0.f}, gby{0.f, 0.f}, gbz{0.f, 0.f};
     if (GRAD) {
-      w = df_mul_u(df_scale(gd, -2.f), df_add_u(df_add_u(df_mul_u(bx, dx), df_mul_u(by, dy)), df_mul_u(bz, dz)));
+      w = df_mul_u(df_scale(gd, -2.f), br);
       gbx = df_mul_u(g, bx);
       gby = df_mul_u(g, by);
       gbz = df_mul_u(g, bz);

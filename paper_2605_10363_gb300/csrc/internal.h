@@ -139,8 +139,9 @@ struct VWork64 {
   int32_t beg, end;
 };
 
-// Work item of the tensor-core V product: one 128 x 128 tile pair P <= Q
-// (units of 4 basis blocks) over grid blocks list_g[beg, end).
+// Work item of the tensor-core V product: one pair of 128-function windows
+// (P, Q = the first of 4 consecutive basis blocks; P == Q, or P + 4 <= Q) over
+// grid blocks list_g[beg, end).
 struct VWorkTC {
   int32_t P, Q;
   int32_t beg, end;
@@ -191,7 +192,7 @@ struct kldi_workspace {
 struct kldi_plan {
   kldi_options opt{};
   const kldi_workspace* ws = nullptr;   // shared per-tile buffers (not owned), or NULL
-  kldi_tuning tune{0, 0};
+  kldi_tuning tune{0, 0, 0};
   bool work_fp64 = false;               // which V work lists the batches hold
   int64_t range_g0 = 0, range_g1 = -1;  // grid blocks evaluated: [range_g0, range_g1), -1 = all
   int gga = 0;
@@ -201,7 +202,6 @@ struct kldi_plan {
   int device = 0;
   int num_sms = 148;
   int64_t nbf = 0, nbb = 0, nbf_pad = 0, npoints = 0, nblocks = 0, ntiles = 0, nshell = 0, nprim_total = 0;
-  int64_t nvt = 0;  // 128-function V tiles per edge (ceil(nbb / 4))
   int* d_err = nullptr;         // device error word (bounded-wait timeouts)
   uint64_t wait_ns = 2000000000ull;   // limit of the tensor-core kernels' bounded waits
   int64_t withhold_item = -1;   // test hook: V work item not handed out (-1: none)

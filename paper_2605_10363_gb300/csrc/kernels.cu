@@ -381,16 +381,15 @@ __global__ void k_mirror(double* V, int nbf) {
   if (r > c) V[idx] = V[(int64_t)c * nbf + r];
 }
 
-// Tensor-core V: off-diagonal tile pairs hold V in the upper triangle, the
-// diagonal 128 x 128 tiles hold S with V = S + S^T.  One thread per pair r < c.
+// Tensor-core V: the products accumulated in A (off-diagonal window pairs
+// above the block diagonal, diagonal windows S = Phi^T X with both triangles)
+// give V = A + A^T.  One thread per pair r <= c.
 __global__ void k_finish_tc(double* V, int nbf) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nbf * nbf) return;
   const int r = (int)(idx / nbf), c = (int)(idx % nbf);
   if (r > c) return;
-  if ((r >> 7) != (c >> 7)) {
-    V[(int64_t)c * nbf + r] = V[idx];
-  } else if (r == c) {
+  if (r == c) {
     V[idx] = 2.0 * V[idx];
   } else {
     const double v = V[idx] + V[(int64_t)c * nbf + r];

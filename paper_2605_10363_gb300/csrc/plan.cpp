@@ -191,13 +191,27 @@ kldi_status build_work(kldi_plan* P, int64_t cap) {
       b.n_v64_work = (int64_t)wk.size();
       continue;
     }
+    // Each grid block's retained basis blocks (ascending) are covered by
+    // windows of 4 consecutive blocks, greedily: a window starts at the first
+    // retained block not yet covered, rounded down to a multiple of the
+    // alignment A (4: the fixed 128-function tiles; 1: the fewest windows
+    // that cover the list, and so the fewest zero blocks the 128 x 128
+    // products run over).  The windows of one grid block are disjoint (a
+    // start lies past the previous window's last block for A <= 4); V = A + A^T
+    // of the accumulated products A.
     std::map<int64_t, std::vector<int32_t>> tl;
-    const int64_t nvt = P->nvt;
+    const int64_t nvt = nbb;   // window keys: first blocks P, Q
+    const int32_t align = P->tune.v_align > 0 ? P->tune.v_align : 2;
     for (int64_t g = b.g0; g < b.g1; ++g) {
       std::vector<int32_t> vt;
+      int32_t cov = -1;
       for (int32_t i = P->blk_ptr[g]; i < P->blk_ptr[g + 1]; ++i) {
-        const int32_t T = P->blk_idx[i] / 4;
-        if (vt.empty() || vt.back() != T) vt.push_back(T);
+        const int32_t p = P->blk_idx[i];
+        if (p > cov) {
+          const int32_t w = p - p % align;
+          vt.push_back(w);
+          cov = w + 3;
+        }
       }
       for (size_t i = 0; i < vt.size(); ++i)
         for (size_t j = i; j < vt.size(); ++j) tl[(int64_t)vt[i] * nvt + vt[j]].push_back((int32_t)g);
@@ -207,8 +221,8 @@ kldi_status build_work(kldi_plan* P, int64_t cap) {
     // Work items are cut at grid-block ranges of `span` blocks and ordered
     // range-major: CTAs running at the same time then work on the same few
     // ranges, whose Phi~ / X~ tiles stay in L2 across the tile pairs that
-    // reuse them.  span: the tuned value, else 16 grid blocks.
-    const int64_t span = P->tune.v_seg > 0 ? P->tune.v_seg : 16;
+    // reuse them.  span: the tuned value, else 64 grid blocks.
+    const int64_t span = P->tune.v_seg > 0 ? P->tune.v_seg : 64;
     struct PairList {
       int32_t Pt, Qt, base, n;
     };
@@ -455,7 +469,6 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     P->nshell = ns;
     P->nbb = (fn + kBasisBlk - 1) / kBasisBlk;
     P->nbf_pad = P->nbb * kBasisBlk;
-    P->nvt = (P->nbb + 3) / 4;
     P->npoints = grid->npoints;
     P->nblocks = grid->nblocks;
     const int64_t nbb = P->nbb, nblk = P->nblocks;
@@ -835,8 +848,9 @@ extern "C" kldi_status kldi_plan_set_withhold(kldi_plan* P, int64_t item) {
 
 extern "C" kldi_status kldi_plan_set_tuning(kldi_plan* P, const kldi_tuning* t) {
   return kldi::guarded("kldi_plan_set_tuning", [&]() -> kldi_status {
-    if (!P || !t || t->v_seg < 0 || (t->rho_ntile != 0 && t->rho_ntile != 64 && t->rho_ntile != 128)) {
-      set_error("kldi_plan_set_tuning: bad argument (v_seg >= 0, rho_ntile 0, 64 or 128)");
+    if (!P || !t || t->v_seg < 0 || (t->rho_ntile != 0 && t->rho_ntile != 64 && t->rho_ntile != 128) ||
+        (t->v_align != 0 && t->v_align != 1 && t->v_align != 2 && t->v_align != 4)) {
+      set_error("kldi_plan_set_tuning: bad argument (v_seg >= 0, rho_ntile 0, 64 or 128, v_align 0, 1, 2 or 4)");
       return KLDI_EINVAL;
     }
     if (P->prec == KLDI_BF16X10 && t->rho_ntile == 128) {
@@ -844,7 +858,7 @@ extern "C" kldi_status kldi_plan_set_tuning(kldi_plan* P, const kldi_tuning* t) 
       return KLDI_EUNSUPPORTED;
     }
     KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
-    const bool rebuild = t->v_seg != P->tune.v_seg;
+    const bool rebuild = t->v_seg != P->tune.v_seg || t->v_align != P->tune.v_align;
     P->tune = *t;
     return rebuild ? build_work(P, P->tile_cap) : KLDI_OK;
   });

@@ -35,13 +35,14 @@
 //  k_x_split    X tile = w (v_rho / 2 phi + 2 v_sigma grad rho . grad phi);
 //               Phi~ = c phi and X~ = X / c (per-point balance c), sliced per
 //               function with one shared column scale; x_gq = max |X|.
-//  k_v_tc       V = Phi^T X + X^T Phi, one 128 x 128 tile pair P <= Q over a
+//  k_v_tc       V = Phi^T X + X^T Phi, one pair P <= Q of 128-function
+//               windows (4 consecutive basis blocks; each grid block's
+//               retained blocks are covered by the fewest windows) over a
 //               segment of its grid-block list; one grid block per exact
 //               accumulation (K = 256: [Phi~ | X~] against [X~ ; Phi~]),
 //               drained into compensated FP32 sums with the 32 x 32 block
 //               pairs that are not executed for that grid block left out,
-//               FP64 scatter-add; the lower block triangle is mirrored
-//               afterwards.
+//               FP64 scatter-add; V = A + A^T afterwards.
 //  BF16X10 (four slices): k_phi_split4 and k_x_split4 evaluate the basis in
 //  double-float (basis_df.cuh) and cut hi + lo into four slices; k_rho_tc<4>
 //  keeps four exact levels in N = 64 tiles (two TMEM buffers) and forms R and
@@ -798,30 +799,42 @@ struct RhoCfg {
 };
 
 // Row-dot of one basis block in double-float (BF16X10), over the shells
-// s0, s0 + sstep, ...: with R_nu (hi / lo, staged [32][128]) and the shell
+// sb .. se - 1: with R_nu (hi / lo, staged [32][128]) and the shell
 // factorisation chi = P g,
 // grad chi = (grad P) g + P u (u = -2 r gd),
 //   sum_nu chi R = sum_s g S0,   sum_nu grad chi R = sum_s (g S1 + u S0),
 // S0 = sum_c P_c R_c and S1 = sum_c (grad P_c) R_c over the shell's components.
-// The radial factors g, gd of each shell at this point come from the Phi
-// kernel (rad[s * 128]).
+// The shells of one atom share r, so their u S0 terms are gathered as
+// -2 r T with T = sum_s gd S0 over the run of shells on that atom (the
+// shells of a block are grouped by atom), and the offsets are formed once
+// per run.  The radial factors g, gd of each shell at this point come from
+// the Phi kernel (rad[s * 128]).
 template <bool GRAD>
-__device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad, const float2* Rs, int i, int s0,
-                                          int sstep, f2 px, f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
+__device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad, const float2* Rs, int i, int sb,
+                                          int se, f2 px, f2 py, f2 pz, f2& pr, f2& gx, f2& gy, f2& gz) {
   const f2 s3{kS3h, kS3l};
-  const int ns = rec->nshell;
   // radial factors loaded one shell ahead (the loads come from HBM / L2)
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 qa = s0 < ns ? rad[s0 * kBlockPts] : z4;
-  for (int s = s0; s < ns; s += sstep) {
+  float4 qa = sb < se ? rad[sb * kBlockPts] : z4;
+  f2 dx{0.f, 0.f}, dy{0.f, 0.f}, dz{0.f, 0.f}, T{0.f, 0.f};
+  auto flush = [&]() {   // the run's u S0 terms: -2 r T
+    const f2 m2 = df_scale(T, -2.f);
+    gx = df_add_u(gx, df_mul_u(dx, m2));
+    gy = df_add_u(gy, df_mul_u(dy, m2));
+    gz = df_add_u(gz, df_mul_u(dz, m2));
+    T = f2{0.f, 0.f};
+  };
+  for (int s = sb; s < se; ++s) {
     const float4 q = qa;
-    qa = s + sstep < ns ? rad[(s + sstep) * kBlockPts] : z4;
+    qa = s + 1 < se ? rad[(s + 1) * kBlockPts] : z4;
     const float4 c0 = rec->c0[s], c1 = rec->c1[s];
     const int hdr = __float_as_int(c1.z);
     const int l = hdr & 255, first = (hdr >> 16) - 64;
     const f2 g{q.x, q.y}, gd{q.z, q.w};
-    f2 dx, dy, dz;
-    offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
+    if (s == sb || rec->atom[s] != rec->atom[s - 1]) {
+      if (GRAD && s != sb) flush();
+      offsets3_df(c0, c1, px, py, pz, dx, dy, dz);
+    }
     auto Rv = [&](int c) -> f2 {
       const int nu = first + c;
       if (nu < 0 || nu >= kBasisBlk) return f2{0.f, 0.f};
@@ -880,12 +893,15 @@ __device__ __forceinline__ void rowdot_df(const BlockRec* rec, const float4* rad
     }
     pr = df_add_u(pr, df_mul_u(g, S0));
     if (GRAD) {
-      const f2 m2 = df_scale(gd, -2.f);
-      gx = df_add_u(gx, df_add_u(df_mul_u(g, S1x), df_mul_u(df_mul_u(dx, m2), S0)));
-      gy = df_add_u(gy, df_add_u(df_mul_u(g, S1y), df_mul_u(df_mul_u(dy, m2), S0)));
-      gz = df_add_u(gz, df_add_u(df_mul_u(g, S1z), df_mul_u(df_mul_u(dz, m2), S0)));
+      T = df_add_u(T, df_mul_u(gd, S0));
+      if (l > 0) {
+        gx = df_add_u(gx, df_mul_u(g, S1x));
+        gy = df_add_u(gy, df_mul_u(g, S1y));
+        gz = df_add_u(gz, df_mul_u(g, S1z));
+      }
     }
   }
+  if (GRAD && se > sb) flush();
 }
 
 // Epilogue of the density-product kernel: the row-dot (rho, grad rho), or
@@ -1267,8 +1283,10 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
             if (staged) {
               f2 pr{0.f, 0.f}, px_{0.f, 0.f}, py_{0.f, 0.f}, pz_{0.f, 0.f};
               const int64_t tq = m[1] + q0 + k4;   // tile (g, q block)
-              rowdot_df<GRAD>(rec, rad + (rad_ptr[tq] - rad_ptr[t0]) * kBlockPts + i, Rs2, i, half, C::kHalves,
-                              f2{prl.x, prlo.x}, f2{prl.y, prlo.y}, f2{prl.z, prlo.z}, pr, px_, py_, pz_);
+              const int nsh = rec->nshell, mid = (nsh + 1) >> 1;   // the halves take consecutive shells
+              rowdot_df<GRAD>(rec, rad + (rad_ptr[tq] - rad_ptr[t0]) * kBlockPts + i, Rs2, i, half == 0 ? 0 : mid,
+                              half == 0 ? mid : nsh, f2{prl.x, prlo.x}, f2{prl.y, prlo.y}, f2{prl.z, prlo.z}, pr,
+                              px_, py_, pz_);
               ar = df_add(ar, pr);
               if (GRAD) {
                 agx = df_add(agx, px_);
@@ -1462,12 +1480,13 @@ kldi_status launch_grad_tc(const kldi_plan* P, const Batch& b, bool gga_xc, doub
 }
 
 // ---------------------------------------------------------------------------
-// V product, persistent over work items (tile pair P <= Q of 128 functions,
-// segment of its grid-block list).  Per grid block one exact chain of K = 256:
-// A = [Phi~_P | X~_P]^T, B = [X~_Q ; Phi~_Q] (MN-major operands), so the chain
-// yields Phi^T X + X^T Phi of the tile pair at once.  A diagonal pair (P = Q)
-// runs the first half only (K = 128, S = Phi~_P^T X~_P): V_PP = S + S^T is
-// formed by the finish kernel.  384 threads in three
+// V product, persistent over work items (pair P <= Q of 128-function windows
+// of 4 consecutive basis blocks, segment of its grid-block list).  Per grid
+// block one exact chain of K = 256: A = [Phi~_P | X~_P]^T, B = [X~_Q ; Phi~_Q]
+// (MN-major operands), so the chain yields Phi^T X + X^T Phi of the window
+// pair at once.  A diagonal pair (P = Q) runs the first half only (K = 128,
+// S = Phi~_P^T X~_P).  The finish kernel forms V = A + A^T of the accumulated
+// products A (off-diagonal pairs lie above the block diagonal).  384 threads in three
 // warpgroups: warpgroup 0 = warp 0 producer (one lane per bulk copy), warp 1
 // TMEM owner + MMA issue, warps 2-3 idle; warpgroups 1-2 = epilogue (lane
 // quarter = warp % 4, column half = warpgroup - 1) with compensated FP32 sums
@@ -1581,7 +1600,7 @@ __global__ void __launch_bounds__(384, 1)
         const VWorkTC wk = work[wi];
         for (int e = 0; e < wk.end - wk.beg && ok; ++e) {
           const int64_t gb = glist[wk.beg + e];
-          const int p = (side == 0 ? wk.P : wk.Q) * 4 + j;
+          const int p = (side == 0 ? wk.P : wk.Q) + j;
           const uint8_t* sp = zero;   // Phi~ tile (gb, p), or zeros
           const uint8_t* sx = zero;   // X~ tile, or zeros (tile absent); pair screening in the epilogue
           if (p < L.nbb) {
@@ -1698,7 +1717,7 @@ __global__ void __launch_bounds__(384, 1)
       }
       for (int e = 0; e < wk.end - wk.beg; ++e, ++job) {
         const int64_t gb = glist[wk.beg + e];
-        const int pr = wk.P * 4 + (m >> 5);
+        const int pr = wk.P + (m >> 5);
         float rsc = 0.f;
         double bp = 0.0, xp = 0.0;
         if (pr < L.nbb) {
@@ -1715,7 +1734,7 @@ __global__ void __launch_bounds__(384, 1)
         float csc[2];
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
-          const int qb = wk.Q * 4 + half * 2 + cc;
+          const int qb = wk.Q + half * 2 + cc;
           csc[cc] = 0.f;
           if (qb < L.nbb) {
             const int t = L.tile_of[gb * L.nbb + qb];
@@ -1762,7 +1781,7 @@ __global__ void __launch_bounds__(384, 1)
         if (lane == 0) mbar_arrive(&tempty[0]);
       }
       if (!ok) break;
-      const int r = wk.P * 128 + m;
+      const int r = wk.P * kBasisBlk + m;
 #pragma unroll
       for (int cq = 0; cq < 4; ++cq) {
         float cmp[16];
@@ -1770,7 +1789,7 @@ __global__ void __launch_bounds__(384, 1)
         if (r < nbf) {
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            const int col = wk.Q * 128 + half * 64 + cq * 16 + c;
+            const int col = wk.Q * kBasisBlk + half * 64 + cq * 16 + c;
             if (col < nbf) atomicAdd(&V[(int64_t)r * nbf + col], (double)S[cq * 16 + c] + (double)cmp[c]);
           }
         }

@@ -58,7 +58,7 @@ MLP_NPARAMS = 4482
 
 
 class Tuning(C.Structure):
-    _fields_ = [("v_seg", C.c_int), ("rho_ntile", C.c_int)]
+    _fields_ = [("v_seg", C.c_int), ("rho_ntile", C.c_int), ("v_align", C.c_int)]
 
 
 class PlanStats(C.Structure):
@@ -235,14 +235,14 @@ class Plan:
         """Evaluate only grid blocks [g0, g1) (partial E_xc and V)."""
         _check(LIB.kldi_plan_set_block_range(self.h, int(g0), int(g1)))
 
-    def set_tuning(self, v_seg=0, rho_ntile=0):
-        t = Tuning(int(v_seg), int(rho_ntile))
+    def set_tuning(self, v_seg=0, rho_ntile=0, v_align=0):
+        t = Tuning(int(v_seg), int(rho_ntile), int(v_align))
         _check(LIB.kldi_plan_set_tuning(self.h, C.byref(t)))
 
     def tuning(self):
         t = Tuning()
         _check(LIB.kldi_plan_get_tuning(self.h, C.byref(t)))
-        return {"v_seg": t.v_seg, "rho_ntile": t.rho_ntile}
+        return {"v_seg": t.v_seg, "rho_ntile": t.rho_ntile, "v_align": t.v_align}
 
     def autotune(self, xc, D, reps=3):
         """Tune on a device density matrix; returns (tuning, ms per call)."""
@@ -250,7 +250,7 @@ class Plan:
         ms = C.c_double()
         _check(LIB.kldi_plan_autotune(self.h, XC[xc] if isinstance(xc, str) else int(xc), _ptr(D), int(reps),
                                       C.byref(t), C.byref(ms)))
-        return {"v_seg": t.v_seg, "rho_ntile": t.rho_ntile}, ms.value
+        return {"v_seg": t.v_seg, "rho_ntile": t.rho_ntile, "v_align": t.v_align}, ms.value
 
     def set_precision(self, prec):
         _check(LIB.kldi_plan_set_precision(self.h, PREC[prec] if isinstance(prec, str) else int(prec)))

@@ -104,7 +104,8 @@ def test_autotune_keeps_results(frames):
     E0 = torch.zeros(1, dtype=torch.float64, device="cuda")
     kldi.exc(plan, "pbe", D, V0, E0)
     best, ms = plan.autotune("pbe", D, reps=2)
-    assert best["v_seg"] in (0, 4, 8, 32, 64, 128) and best["rho_ntile"] in (64, 128) and ms > 0
+    assert best["v_seg"] in (0, 16, 32, 128, 256) and best["rho_ntile"] in (64, 128) and ms > 0
+    assert best["v_align"] in (0, 1, 4)
     assert plan.tuning() == best
     V1 = torch.zeros_like(V0)
     E1 = torch.zeros_like(E0)
@@ -115,10 +116,38 @@ def test_autotune_keeps_results(frames):
     # of FP64 atomics)
     assert abs(E1.item() - E0.item()) <= 1e-6
     assert (V1 - V0).abs().max().item() <= 3e-7
-    plan.set_tuning(8, 64)
-    assert plan.tuning() == {"v_seg": 8, "rho_ntile": 64}
+    plan.set_tuning(8, 64, 2)
+    assert plan.tuning() == {"v_seg": 8, "rho_ntile": 64, "v_align": 2}
     with pytest.raises(kldi.KldiError):
         plan.set_tuning(8, 96)
+    with pytest.raises(kldi.KldiError):
+        plan.set_tuning(8, 64, 3)
+
+
+@pytest.mark.parametrize("prec,tV", [("bf16x10", 1e-7), ("bf16x6", 3e-7)])
+def test_v_window_alignments_agree(frames, prec, tV):
+    """The V product's 4-block windows at alignments 4 (fixed tiles), 2 and 1
+    (fewest windows): every one matches the oracle's V, and they agree with
+    each other far inside the tolerance (the windows change only which zero
+    blocks are multiplied and how grid blocks are grouped into work items)."""
+    kldi = _kldi()
+    s = frames[1]
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    ref = oe.evaluate(s, g, ob.build_shells(s.xyz, s.basis), screened=True)
+    order = kldi.order_shells(synth.overlap_matrix(s.xyz, s.basis), synth.shell_sizes(s.basis))
+    plan = kldi.plan_for_system(s, prec=prec, xc="pbe", shell_order=order)
+    out = {}
+    for align in (4, 2, 1):
+        plan.set_tuning(0, 0, align)
+        V = np.zeros((s.nbf, s.nbf))
+        E = np.zeros(1)
+        kldi.exc(plan, "pbe", s.D, V, E)
+        out[align] = (E[0], V)
+        assert np.abs(V - ref.V).max() <= tV, (align, np.abs(V - ref.V).max())
+        assert np.allclose(V, V.T, rtol=0, atol=1e-15)
+    for align in (2, 1):
+        assert out[align][0] == out[4][0]
+        assert np.abs(out[align][1] - out[4][1]).max() <= 1e-11
 
 
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
