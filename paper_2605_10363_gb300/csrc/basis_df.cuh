@@ -76,10 +76,6 @@ __device__ __forceinline__ f2 df_sub_u(f2 a, f2 b) {
 }
 __device__ __forceinline__ f2 df_neg(f2 a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ double df_to_double(f2 a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ f2 df_from_double(double v) {
-  const float h = (float)v;
-  return {h, (float)(v - (double)h)};
-}
 
 // ln 2 / 256 in three parts: kC1 has 9 significant bits and kC1 <= ln2/256,
 // kC2 and kC3 the next 24 bits each.
@@ -122,7 +118,9 @@ __device__ __forceinline__ f2 exp_df(f2 x, const float2* __restrict__ tab) {
 constexpr float kS3h = 0.5773502588272095f, kS3l = 1.0362416702491828e-08f;
 
 // Radial factors of one shell at offset (dx, dy, dz): r^2, g = sum c e^{-a r^2}
-// and (GRAD) gd = sum a c e^{-a r^2}, primitives from a staged record.
+// and (GRAD) gd = sum a c e^{-a r^2}, primitives from a staged record.  The
+// exponent argument and the sums of at most a few terms use the unnormalised
+// products and sums (their consumers take both parts into account).
 template <bool GRAD>
 __device__ __forceinline__ void radial_df(const float4* pf, const float2* pac, int np, f2 r2, const float2* tab,
                                           f2& g, f2& gd) {
@@ -130,22 +128,23 @@ __device__ __forceinline__ void radial_df(const float4* pf, const float2* pac, i
   gd = {0.f, 0.f};
   for (int k = 0; k < np; ++k) {
     const float4 pr = pf[k];
-    const f2 e = exp_df(df_neg(df_mul(f2{pr.x, pr.y}, r2)), tab);
-    g = df_add(g, df_mul(f2{pr.z, pr.w}, e));
+    const f2 e = exp_df(df_neg(df_mul_u(f2{pr.x, pr.y}, r2)), tab);
+    g = df_add_u(g, df_mul_u(f2{pr.z, pr.w}, e));
     if (GRAD) {
       const float2 ac = pac[k];
-      gd = df_add(gd, df_mul(f2{ac.x, ac.y}, e));
+      gd = df_add_u(gd, df_mul_u(f2{ac.x, ac.y}, e));
     }
   }
 }
 
-// Offsets of a point from a staged shell centre and r^2, hi / lo.
+// Offsets of a point from a staged shell centre and r^2, hi / lo (r^2
+// unnormalised, a sum of three error-free squares).
 __device__ __forceinline__ void offsets_df(const float4& c0, const float4& c1, f2 px, f2 py, f2 pz, f2& dx, f2& dy,
                                            f2& dz, f2& r2) {
   dx = df_sub(px, f2{c0.x, c0.w});
   dy = df_sub(py, f2{c0.y, c1.x});
   dz = df_sub(pz, f2{c0.z, c1.y});
-  r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+  r2 = df_add_u(df_add_u(df_mul_u(dx, dx), df_mul_u(dy, dy)), df_mul_u(dz, dz));
 }
 
 // Offsets of a point from a staged shell centre, hi / lo (no r^2).

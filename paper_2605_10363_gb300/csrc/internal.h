@@ -246,6 +246,7 @@ struct kldi_plan {
   double* d_rho = nullptr;      // [npoints]
   double* d_grad = nullptr;     // [npoints*3]
   double* d_xcoef = nullptr;    // [npoints*4]: w v_rho / 2, 2 w v_sigma grad rho
+  float4* d_xdf = nullptr;      // [npoints*2]: the same as FP32 hi, lo (the double-float X kernel)
   double* d_xmax = nullptr;     // [ntiles]
   double* d_eblk = nullptr;     // [nblocks]
   double* d_exc = nullptr;      // [1]

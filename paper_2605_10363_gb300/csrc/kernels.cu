@@ -207,7 +207,7 @@ kldi_status launch_rho64(const kldi_plan* P, const Batch& b, const double* D, do
 // Functional (FP64) per point, E_xc partial per grid block, and the X
 // coefficients c = (w v_rho / 2, 2 w v_sigma grad rho).
 __global__ void k_xc(GridView G, int64_t g0, int xc, double rho_min, const double* rho, const double* grad,
-                     double* xcoef, double* eblk, float* pscale) {
+                     double* xcoef, float4* xdf, double* eblk, float* pscale) {
   __shared__ double red[4];
   const int64_t g = g0 + blockIdx.x;
   const int64_t pt = g * kBlockPts + threadIdx.x;
@@ -231,7 +231,7 @@ __global__ void k_xc(GridView G, int64_t g0, int xc, double rho_min, const doubl
       bz = c * g0z;
     }
   }
-  xc_point_tail(g, pt, e, a, bx, by, bz, xcoef, eblk, pscale, red);
+  xc_point_tail(g, pt, e, a, bx, by, bz, xcoef, xdf, eblk, pscale, red);
 }
 
 kldi_status launch_xc(const kldi_plan* P, const Batch& b, int xc, const double* rho, const double* grad,
@@ -240,7 +240,8 @@ kldi_status launch_xc(const kldi_plan* P, const Batch& b, int xc, const double* 
   const int64_t n = b.g1 - b.g0;
   if (n == 0) return KLDI_OK;
   k_xc<<<(unsigned)n, kBlockPts, 0, s>>>(P->grid_view(), b.g0, xc, P->opt.rho_min, rho, grad, P->d_xcoef,
-                                         P->d_eblk, P->prec == KLDI_FP64 ? nullptr : P->d_pscale);
+                                         P->prec == KLDI_BF16X10 ? P->d_xdf : nullptr, P->d_eblk,
+                                         P->prec == KLDI_FP64 ? nullptr : P->d_pscale);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }

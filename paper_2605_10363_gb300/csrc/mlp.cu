@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(128) k_mlp_eval(const __half* __restrict__ hw,
 // 128 threads per grid block, the same outputs as the analytic stage.
 __global__ void __launch_bounds__(128) k_xc_mlp(GridView G, int64_t g0, double rho_min, MlpMap M,
                                                 const __half* __restrict__ hw, const double* rho,
-                                                const double* grad, double* xcoef, double* eblk, float* pscale) {
+                                                const double* grad, double* xcoef, float4* xdf, double* eblk,
+                                                float* pscale) {
   __shared__ __align__(16) float W[kWPad];
   __shared__ double red[4];
   load_weights(hw, W);
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(128) k_xc_mlp(GridView G, int64_t g0, double r
   int used;
   const XcOut o = mlp_point(W, M, r, gx * gx + gy * gy + gz * gz, rho_min, used);
   const double c = 2.0 * w * o.vs;
-  xc_point_tail(g, pt, w * o.f, 0.5 * w * o.vr, c * gx, c * gy, c * gz, xcoef, eblk, pscale, red);
+  xc_point_tail(g, pt, w * o.f, 0.5 * w * o.vr, c * gx, c * gy, c * gz, xcoef, xdf, eblk, pscale, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,7 +487,8 @@ kldi_status launch_xc_mlp(const kldi_plan* P, const Batch& b, const double* rho,
   const int64_t n = b.g1 - b.g0;
   if (n == 0) return KLDI_OK;
   k_xc_mlp<<<(unsigned)n, kBlockPts, 0, s>>>(P->grid_view(), b.g0, P->opt.rho_min, map_of(P->mlp->box),
-                                             P->mlp->d_half, rho, grad, P->d_xcoef, P->d_eblk,
+                                             P->mlp->d_half, rho, grad, P->d_xcoef,
+                                             P->prec == KLDI_BF16X10 ? P->d_xdf : nullptr, P->d_eblk,
                                              P->prec == KLDI_FP64 ? nullptr : P->d_pscale);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;

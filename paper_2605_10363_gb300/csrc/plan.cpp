@@ -87,7 +87,7 @@ void free_plan_buffers(kldi_plan* P) {
   free_own_tile_buffers(P);
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_prel_lo, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
                   P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
-                  P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xmax, P->d_eblk,
+                  P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xdf, P->d_xmax, P->d_eblk,
                   P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero, P->d_rad_ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -703,6 +703,7 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     if ((st = dalloc(P, &P->d_rho, (size_t)P->npoints)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_grad, (size_t)P->npoints * 3)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_xcoef, (size_t)P->npoints * 4)) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_xdf, (size_t)P->npoints * 2)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_xmax, (size_t)std::max<int64_t>(P->ntiles, 1))) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_eblk, (size_t)nblk)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_exc, 1)) != KLDI_OK) return fail(st);

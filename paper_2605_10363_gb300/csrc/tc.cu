@@ -382,8 +382,10 @@ __global__ void __launch_bounds__(128) k_phi_split4(BasisView B, GridView G, Lis
   for (int j = tb; j < te; ++j) {
     BlockRec* rc = rec + ((j - tb + te - tb) & 1);
     stage_block_rec(B, L.blk_idx[j], anc, rc, i, kBlockPts);
+    if ((L.blk_idx[j] + 1) * kBasisBlk > B.nbf) {   // a partial last block: its padding columns are zero
 #pragma unroll
-    for (int nu = 0; nu < kBasisBlk; ++nu) sth[nu][i] = stl[nu][i] = 0.f;
+      for (int nu = 0; nu < kBasisBlk; ++nu) sth[nu][i] = stl[nu][i] = 0.f;
+    }
     __syncthreads();
     // per shell: the radial factors g (and gd) go to the radial buffer for the
     // row-dot and the X kernel, the values P g to the staging array
@@ -612,11 +614,12 @@ constexpr int kX4Threads = 256;
 
 template <bool GRAD>
 __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridView G, ListView L, int64_t g0,
-                                                         int64_t t0, const double* __restrict__ xcoef,
+                                                         int64_t t0, const float4* __restrict__ xdf,
                                                          const float* __restrict__ pscale, uint8_t* out_phi,
                                                          float* phi_scale, uint8_t* out_x, float* x_scale,
                                                          double* xmax, const float4* __restrict__ rad,
-                                                         const int64_t* __restrict__ rad_ptr) {
+                                                         const int64_t* __restrict__ rad_ptr, int64_t t1,
+                                                         int64_t ahead) {
   extern __shared__ float xsm[];
   float(*sph)[kBlockPts + 1] = reinterpret_cast<float(*)[kBlockPts + 1]>(xsm);
   float(*spl)[kBlockPts + 1] = sph + kBasisBlk;
@@ -630,14 +633,22 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
   const int i = threadIdx.x & (kBlockPts - 1), half = threadIdx.x >> 7;
   const int64_t pt = g * kBlockPts + i;
   const float c = pscale[pt], cinv = c > 0.f ? 1.f / c : 0.f;   // c = 0: X = 0 at this point
-  const f2 a = df_from_double(xcoef[pt * 4]), bx = df_from_double(xcoef[pt * 4 + 1]),
-           by = df_from_double(xcoef[pt * 4 + 2]), bz = df_from_double(xcoef[pt * 4 + 3]);
+  const float4 xh = xdf[pt * 2], xl = xdf[pt * 2 + 1];   // (a, b) hi / lo
+  const f2 a{xh.x, xl.x}, bx{xh.y, xl.y}, by{xh.z, xl.z}, bz{xh.w, xl.w};
+  if ((p + 1) * kBasisBlk > B.nbf) {   // a partial last block: its padding columns are zero
 #pragma unroll
-  for (int k = 0; k < kBasisBlk / 2; ++k) {
-    const int nu = half * (kBasisBlk / 2) + k;
-    sph[nu][i] = spl[nu][i] = sxh[nu][i] = sxl[nu][i] = 0.f;
+    for (int k = 0; k < kBasisBlk / 2; ++k) {
+      const int nu = half * (kBasisBlk / 2) + k;
+      sph[nu][i] = spl[nu][i] = sxh[nu][i] = sxl[nu][i] = 0.f;
+    }
   }
   const float4 pr = G.prel[pt], pl = G.prel_lo[pt];
+  if (threadIdx.x == 0 && t + ahead < t1) {
+    // the radial factors of the tile that runs about `ahead` tiles later
+    // (the CTAs resident on the GPU take tiles in order), moved into L2 now
+    const int64_t ra = rad_ptr[t + ahead], rb = rad_ptr[t + ahead + 1];
+    if (rb > ra) prefetch_l2(rad + (ra - rad_ptr[t0]) * kBlockPts, (uint32_t)((rb - ra) * kBlockPts * 16));
+  }
   stage_block_rec(B, p, G.anchor[g], &rec, threadIdx.x, kX4Threads);
   __syncthreads();
   const int mid = (rec.nshell + 1) >> 1;   // the two halves take consecutive shell ranges
@@ -721,12 +732,14 @@ static kldi_status x_ns4(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   uint8_t* ox = reinterpret_cast<uint8_t*>(P->d_x_s);
   if (P->gga)
     k_x_split4<true><<<(unsigned)n, kX4Threads, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
-                                                             b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
-                                                             P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr);
+                                                             b.t0, P->d_xdf, P->d_pscale, op, P->d_phic_scale, ox,
+                                                             P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr, b.t1,
+                                                             (int64_t)3 * P->num_sms);
   else
     k_x_split4<false><<<(unsigned)n, kX4Threads, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
-                                                              b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
-                                                              P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr);
+                                                              b.t0, P->d_xdf, P->d_pscale, op, P->d_phic_scale, ox,
+                                                              P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr, b.t1,
+                                                              (int64_t)3 * P->num_sms);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
@@ -1031,6 +1044,14 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
         bool ok = true;
         for (int nt = 0; nt < ntile && ok; ++nt) {
           const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+          if constexpr (MODE == kRowDot && NS == 4) {
+            // the radial factors the row-dot of this N tile reads, moved into
+            // L2 while its products run
+            if (lane < nq) {
+              const int64_t tq = tb + q0 + lane, r0 = rad_ptr[tq], r1 = rad_ptr[tq + 1];
+              if (r1 > r0) prefetch_l2(rad + (r0 - rad_ptr[t0]) * kBlockPts, (uint32_t)((r1 - r0) * kBlockPts * 16));
+            }
+          }
           for (int jp = 0; jp < n; ++jp) {
             const uint32_t bits = tile_bits(m, jp, q0, nq);
             if (!bits) continue;
