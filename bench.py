@@ -288,14 +288,14 @@ def _frame_system(task):
     return k, s, order
 
 
-def run_frames(args, dev, stream):
+def frames_measure(nframes, prec, basis_order, steps, warmup, dev, stream):
     """Frames of the trajectory recipe (20-130 waters, jittered, own D each)
     through one CUDA-graph batch with a shared tile workspace and the tuned
     tile shapes.  The frames are generated in host worker processes and the
     plans built from host threads (preprocessing, timed separately); the
     timed step is one graph launch over all frames.  Beside it: the same
     frames as back-to-back kldi_exc calls on the stream (the launches the
-    graph replaces)."""
+    graph replaces).  Returns the measurement as a dict."""
     import concurrent.futures as cf
     import multiprocessing as mp
 
@@ -306,14 +306,14 @@ def run_frames(args, dev, stream):
     t0 = time.perf_counter()
     nproc = max(1, min(16, os.cpu_count() or 1))
     with cf.ProcessPoolExecutor(nproc, mp_context=mp.get_context("spawn")) as ex:
-        out = list(ex.map(_frame_system, [(k, args.basis_order) for k in range(args.frames)], chunksize=1))
+        out = list(ex.map(_frame_system, [(k, basis_order) for k in range(nframes)], chunksize=1))
     out.sort(key=lambda x: x[0])
     systems = [s for _, s, _ in out]
     orders = [o for _, _, o in out]
     t_gen = time.perf_counter() - t0
     t1 = time.perf_counter()
     with cf.ThreadPoolExecutor(8) as ex:
-        plans = list(ex.map(lambda so: kldi.plan_for_system(so[0], prec=args.prec, xc="pbe",
+        plans = list(ex.map(lambda so: kldi.plan_for_system(so[0], prec=prec, xc="pbe",
                                                             stream=stream.cuda_stream, shell_order=so[1]),
                             zip(systems, orders)))
     t_plan = time.perf_counter() - t1
@@ -331,17 +331,17 @@ def run_frames(args, dev, stream):
     for p in plans:
         p.set_tuning(tuning["v_seg"], tuning["rho_ntile"], tuning["v_align"])
     batch = kldi.Batch(plans, "pbe", Ds, Vs, E, stream=stream.cuda_stream)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         batch.launch()
     batch.sync()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         batch.launch()
     b.record(stream)
     batch.sync()
-    ms = a.elapsed_time(b) / args.steps
+    ms = a.elapsed_time(b) / steps
     E_graph = E.cpu().numpy().copy()
     # the same frames as separate calls, back to back on the stream
     E1 = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -352,19 +352,27 @@ def run_frames(args, dev, stream):
     torch.cuda.synchronize(dev)
     ms_calls = a.elapsed_time(b)
     npts = sum(p.grid.nreal for p in plans)
-    sizes = [int(x) for x in synth.frame_sizes(args.frames)]
+    sizes = [int(x) for x in synth.frame_sizes(nframes)]
+    del batch, plans
+    return {"workload": f"frames: the first {nframes} frames of the trajectory recipe ({min(sizes)}-{max(sizes)} "
+                        f"waters, {sum(sizes)} in all), PBE-form, one CUDA-graph launch per step",
+            "precision": prec, "points": int(npts), "ms_per_step": ms, "value": npts / (ms * 1e-3),
+            "tuning": tuning, "host_seconds": {"frames": round(t_gen, 1), "plans": round(t_plan, 1),
+                                               "tune": round(t_tune, 1)},
+            "basis_order": "overlap-signature clustering" if basis_order == "overlap" else "atom order",
+            "back_to_back_calls_ms": ms_calls, "graph_vs_calls": ms / ms_calls, "E_xc_first": E_graph[:8].tolist()}
+
+
+def run_frames(args, dev, stream):
+    """The --workload frames line: frames_measure over the first --frames frames."""
+    r = frames_measure(args.frames, args.prec, args.basis_order, args.steps, args.warmup, dev, stream)
+    config = {k: r[k] for k in ("workload", "precision", "points", "tuning", "host_seconds", "basis_order")}
     print(json.dumps({
-        "metric": METRIC, "value": npts / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": f"frames: the first {args.frames} frames of the trajectory recipe "
-                               f"({min(sizes)}-{max(sizes)} waters, {sum(sizes)} in all), PBE-form, one CUDA-graph "
-                               f"launch per step", "precision": args.prec, "points": int(npts),
-                   "tuning": tuning, "host_seconds": {"frames": round(t_gen, 1), "plans": round(t_plan, 1),
-                                                      "tune": round(t_tune, 1)},
-                   "basis_order": "overlap-signature clustering" if args.basis_order == "overlap" else "atom order"},
-        "back_to_back_calls_ms": ms_calls, "graph_vs_calls": ms / ms_calls,
-        "E_xc_first": E_graph[:8].tolist()}), flush=True)
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": config,
+        "back_to_back_calls_ms": r["back_to_back_calls_ms"], "graph_vs_calls": r["graph_vs_calls"],
+        "E_xc_first": r["E_xc_first"]}), flush=True)
 
 
 # ---------------------------------------------------------------------------- side modes
@@ -702,6 +710,12 @@ def main():
         if not args.no_large and not args.nwaters:
             modes["cnoh1000"] = large_mode(kldi, dev, stream, args)
             modes["learned_water167"] = learned_mode(kldi, s, plan, dev, stream, args)
+            # the trajectory workload (20-130-water frames, BF16x3 as it is
+            # specified), bounded to its first 8 frames so that the default run
+            # stays within minutes; --workload frames --frames 256 runs it whole
+            side = torch.cuda.Stream(dev)
+            with torch.cuda.stream(side):
+                modes["frames8_bf16x3"] = frames_measure(8, "bf16x3", args.basis_order, 3, 1, dev, side)
 
     cpu = None
     if rank == 0 and world == 1 and not args.nwaters:
@@ -715,7 +729,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.prec,
+            "config": {"workload": WORKLOAD if not args.nwaters else
+                       f"water{args.nwaters}_pbe: {args.nwaters} waters of the 33-water recipe, PBE-form, "
+                       "t_b = t_d = 1e-10", "precision": args.prec,
                        "l2": "inputs larger than L2 (split tile buffers of several GB per step)",
                        "parallelism": f"replicas x{world}", "plan_seconds": round(t_plan, 2),
                        "basis_order": "overlap-signature clustering (kldi_order_shells, Sec. III-B), "

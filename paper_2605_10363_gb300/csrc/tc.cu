@@ -357,13 +357,22 @@ __global__ void __launch_bounds__(128) k_phi_split4(BasisView B, GridView G, Lis
   const float4 pr = G.prel[pt], pl = G.prel_lo[pt];
   const f2 px{pr.x, pl.x}, py{pr.y, pl.y}, pz{pr.z, pl.z};
   const int anc = G.anchor[g];
-  const int tb = L.blk_ptr[g], te = L.blk_ptr[g + 1];
+  const int tb = L.blk_ptr[g], te = L.blk_ptr[g + 1], n = te - tb;
+  // The shell records are staged one block ahead: step q (blocks of pass 1,
+  // then of pass 2) reads buffer q & 1, staged during step q - 1, while it
+  // stages step q + 1 into the other buffer (read last at step q - 1, which
+  // every thread has left at the barrier of step q).
+  auto stage_step = [&](int q) {
+    if (q < 2 * n) stage_block_rec(B, L.blk_idx[tb + (q < n ? q : q - n)], anc, rec + (q & 1), i, kBlockPts);
+  };
+  stage_step(0);
   // pass 1: point scale from the shell bound r^l sum_k |c_k| exp(-a_k r^2) (FP32, 1.001 margin)
   float M = 0.f;
   for (int j = tb; j < te; ++j) {
-    BlockRec* rc = rec + ((j - tb) & 1);
-    stage_block_rec(B, L.blk_idx[j], anc, rc, i, kBlockPts);
+    const int q = j - tb;
+    const BlockRec* rc = rec + (q & 1);
     __syncthreads();
+    stage_step(q + 1);
     for (int s = 0; s < rc->nshell; ++s) {
       const float4 c0 = rc->c0[s], c1 = rc->c1[s];
       const int hdr = __float_as_int(c1.z), l = hdr & 255, np = (hdr >> 8) & 255;
@@ -380,13 +389,14 @@ __global__ void __launch_bounds__(128) k_phi_split4(BasisView B, GridView G, Lis
   const float rinv = 1.f / rs;
   // pass 2: double-float values of every retained tile, four slices per point
   for (int j = tb; j < te; ++j) {
-    BlockRec* rc = rec + ((j - tb + te - tb) & 1);
-    stage_block_rec(B, L.blk_idx[j], anc, rc, i, kBlockPts);
+    const int q = n + j - tb;
+    const BlockRec* rc = rec + (q & 1);
     if ((L.blk_idx[j] + 1) * kBasisBlk > B.nbf) {   // a partial last block: its padding columns are zero
 #pragma unroll
       for (int nu = 0; nu < kBasisBlk; ++nu) sth[nu][i] = stl[nu][i] = 0.f;
     }
     __syncthreads();
+    stage_step(q + 1);
     // per shell: the radial factors g (and gd) go to the radial buffer for the
     // row-dot and the X kernel, the values P g to the staging array
     float4* rtile = rad + (rad_ptr[j] - rad_ptr[t0]) * kBlockPts;
@@ -626,6 +636,7 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
   float(*sxh)[kBlockPts + 1] = spl + kBasisBlk;
   float(*sxl)[kBlockPts + 1] = sxh + kBasisBlk;
   __shared__ float cp[kBasisBlk], cx[kBasisBlk], rawx[kBasisBlk];
+  __shared__ unsigned colmax[kBasisBlk];   // per function: max |Phi~|, |X~| (hi parts) as FP32 bits
   __shared__ BlockRec rec;
   const int64_t t = t0 + blockIdx.x;
   const int64_t g = L.tile_g[t];
@@ -634,6 +645,7 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
   const int64_t pt = g * kBlockPts + i;
   const float c = pscale[pt], cinv = c > 0.f ? 1.f / c : 0.f;   // c = 0: X = 0 at this point
   const float4 xh = xdf[pt * 2], xl = xdf[pt * 2 + 1];   // (a, b) hi / lo
+  if (threadIdx.x < kBasisBlk) colmax[threadIdx.x] = 0u;
   const f2 a{xh.x, xl.x}, bx{xh.y, xl.y}, by{xh.z, xl.z}, bz{xh.w, xl.w};
   if ((p + 1) * kBasisBlk > B.nbf) {   // a partial last block: its padding columns are zero
 #pragma unroll
@@ -655,19 +667,24 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
   for_rec_phix_df<GRAD>(&rec, rad + (rad_ptr[t] - rad_ptr[t0]) * kBlockPts + i, half == 0 ? 0 : mid,
                         half == 0 ? mid : rec.nshell, f2{pr.x, pl.x},
                         f2{pr.y, pl.y}, f2{pr.z, pl.z}, a, bx, by, bz, [&](int nu, f2 v, f2 x) {
-                          sph[nu][i] = v.h * c;
+                          const float ph = v.h * c, xhh = x.h * cinv;
+                          sph[nu][i] = ph;
                           spl[nu][i] = v.l * c;
-                          sxh[nu][i] = x.h * cinv;
+                          sxh[nu][i] = xhh;
                           sxl[nu][i] = x.l * cinv;
+                          // the function's column maximum: a warp reduction
+                          // (every lane evaluates the same function), then
+                          // one shared-memory maximum per warp; non-negative
+                          // FP32 values order like their bit patterns
+                          const unsigned m = __reduce_max_sync(
+                              0xffffffffu, __float_as_uint(fmaxf(fabsf(ph), fabsf(xhh))));
+                          if ((threadIdx.x & 31) == 0) atomicMax(&colmax[nu], m);
                         });
   __syncthreads();
-  if (threadIdx.x < kBlockPts) {
-    column_scales(sph, cp, nullptr);
-    column_scales(sxh, cx, rawx);
-  }
-  __syncthreads();
+  // one scale per function for Phi~ and X~ (they meet in one exact chain):
+  // the power of two above the larger of their column maxima
   if (threadIdx.x < kBasisBlk) {
-    cp[threadIdx.x] = fmaxf(cp[threadIdx.x], cx[threadIdx.x]);
+    cp[threadIdx.x] = pow2_ceil(__uint_as_float(colmax[threadIdx.x]) * 1.000001f);
     cx[threadIdx.x] = 1.f / cp[threadIdx.x];   // exact: the scales are powers of two
   }
   __syncthreads();
