@@ -149,7 +149,8 @@ struct BlockRec {
   float ds[kBasisBlk];     // per-function factor, filled by the caller where needed
   int atom[kRecShells];    // atom of each shell
   int nshell;
-  int pad[3];
+  int split;               // first shell of the second half (about half of the functions each)
+  int pad[2];
 };
 
 // True when basis block p fits a BlockRec (the same answer on every thread).
@@ -166,7 +167,10 @@ __device__ __forceinline__ bool block_rec_fits(const BasisView& B, int p) {
 __device__ __forceinline__ void stage_block_rec(const BasisView& B, int p, int anchor, BlockRec* rec, int t,
                                                 int nthr) {
   const int sb = B.bb_shell_begin[p], se = B.bb_shell_end[p];
-  if (t == 0) rec->nshell = se - sb;
+  if (t == 0) {
+    rec->nshell = se - sb;
+    rec->split = B.bb_split[p];
+  }
   if (se == sb) return;
   const int pbase = B.shell_f[sb].y;
   const int4 z = B.shell_f[se - 1];

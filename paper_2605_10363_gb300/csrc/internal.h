@@ -99,6 +99,7 @@ struct BasisView {
   const float* ac_lo;
   const int32_t* bb_shell_begin;  // [nbb] first shell with a function in basis block p
   const int32_t* bb_shell_end;    // [nbb] one past the last such shell
+  const int32_t* bb_split;        // [nbb] first shell (block-local) of the block's second half
   // FP32 evaluation in coordinates relative to an anchor atom: relatom[(a * natm + b) * 8 + 0..5]
   // = A_b - A_a as hi (0..2) and lo (3..5) FP32 parts
   const float* relatom;
@@ -229,6 +230,7 @@ struct kldi_plan {
   float4* d_prim_f = nullptr;   // packed per primitive
   float2* d_prim_ac = nullptr;
   int32_t* d_bb_begin = nullptr;
+  int32_t* d_bb_split = nullptr;
   int32_t* d_bb_end = nullptr;
   int32_t* d_blk_ptr = nullptr;
   int32_t* d_blk_idx = nullptr;
@@ -248,6 +250,8 @@ struct kldi_plan {
   double* d_xcoef = nullptr;    // [npoints*4]: w v_rho / 2, 2 w v_sigma grad rho
   float4* d_xdf = nullptr;      // [npoints*2]: the same as FP32 hi, lo (the double-float X kernel)
   double* d_xmax = nullptr;     // [ntiles]
+  float* d_xmaxf = nullptr;     // [ntiles] the same in FP32 (tensor-core V product's pair rule)
+  float* d_bmaxf = nullptr;     // [ntiles] b_gp in FP32 (tensor-core V product's pair rule)
   double* d_eblk = nullptr;     // [nblocks]
   double* d_exc = nullptr;      // [1]
   // tiles of the current batch

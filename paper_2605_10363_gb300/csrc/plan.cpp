@@ -6,6 +6,8 @@
 #include <omp.h>
 
 #include <algorithm>
+#include <climits>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -30,6 +32,7 @@ BasisView kldi_plan::basis_view() const {
   v.prim_ac = d_prim_ac;
   v.bb_shell_begin = d_bb_begin;
   v.bb_shell_end = d_bb_end;
+  v.bb_split = d_bb_split;
   v.relatom = d_relatom;
   v.natm = natm;
   v.nbf = (int32_t)nbf;
@@ -86,8 +89,8 @@ kldi_status upload(kldi_plan* P, T** p, const T* h, size_t count) {
 void free_plan_buffers(kldi_plan* P) {
   free_own_tile_buffers(P);
   void* ptrs[] = {P->d_xyz, P->d_w, P->d_prel, P->d_prel_lo, P->d_anchor, P->d_relatom, P->d_shells, P->d_alpha, P->d_coef, P->d_alpha_f, P->d_coef_f, P->d_shell_f, P->d_prim_f, P->d_prim_ac,
-                  P->d_bb_begin, P->d_bb_end, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
-                  P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xdf, P->d_xmax, P->d_eblk,
+                  P->d_bb_begin, P->d_bb_end, P->d_bb_split, P->d_blk_ptr, P->d_blk_idx, P->d_bmax, P->d_tile_of, P->d_tile_g,
+                  P->d_D, P->d_V, P->d_fnperm, P->d_Dint, P->d_Vint, P->d_dmax, P->d_rho, P->d_grad, P->d_xcoef, P->d_xdf, P->d_xmax, P->d_xmaxf, P->d_bmaxf, P->d_eblk,
                   P->d_exc, P->d_err, P->d_vnext, P->d_G, P->d_rowscale, P->d_pscale, P->d_zscale, P->d_dscale, P->d_dsplit, P->d_zero, P->d_rad_ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -567,6 +570,33 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     if ((st = upload(P, &P->d_bb_end, bb_end.data(), bb_end.size())) != KLDI_OK) return fail(st);
     P->bb_nshell.resize(nbb);
     for (int64_t p = 0; p < nbb; ++p) P->bb_nshell[p] = std::max(0, bb_end[p] - bb_begin[p]);
+    {
+      // the kernels that give a block's shells to two groups of threads take
+      // shells [0, split) and [split, nshell): about half of the block's
+      // functions each (a shell's components inside the block counted)
+      std::vector<int32_t> bb_split(nbb, 0);
+      for (int64_t p = 0; p < nbb; ++p) {
+        const int64_t lo = p * kBasisBlk, hi = std::min<int64_t>(lo + kBasisBlk, fn);
+        int64_t tot = 0;
+        for (int s = bb_begin[p]; s < bb_end[p]; ++s) {
+          const int64_t f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
+          tot += std::min(f1, hi) - std::max(f0, lo);
+        }
+        int64_t acc = 0, best = INT64_MAX;
+        int split = 0;
+        for (int k = 0; k <= bb_end[p] - bb_begin[p]; ++k) {   // split before block-local shell k
+          const int64_t d = std::llabs(2 * acc - tot);
+          if (d < best) { best = d; split = k; }
+          if (k < bb_end[p] - bb_begin[p]) {
+            const int s = bb_begin[p] + k;
+            const int64_t f0 = shells[s].fn_off, f1 = f0 + (shells[s].l + 1) * (shells[s].l + 2) / 2;
+            acc += std::min(f1, hi) - std::max(f0, lo);
+          }
+        }
+        bb_split[p] = split;
+      }
+      if ((st = upload(P, &P->d_bb_split, bb_split.data(), bb_split.size())) != KLDI_OK) return fail(st);
+    }
 
     // ---- geometric candidates: shell extent R_s beyond which the value (and
     // gradient) bound r^l sum|c| e^{-a r^2} (+ l r^(l-1) .. + 2 a r^(l+1) ..) < t_b/2.
@@ -705,6 +735,11 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
     if ((st = dalloc(P, &P->d_xcoef, (size_t)P->npoints * 4)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_xdf, (size_t)P->npoints * 2)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_xmax, (size_t)std::max<int64_t>(P->ntiles, 1))) != KLDI_OK) return fail(st);
+    if ((st = dalloc(P, &P->d_xmaxf, (size_t)std::max<int64_t>(P->ntiles, 1))) != KLDI_OK) return fail(st);
+    {
+      std::vector<float> bf(P->bmax.begin(), P->bmax.end());
+      if ((st = upload(P, &P->d_bmaxf, bf.data(), bf.size())) != KLDI_OK) return fail(st);
+    }
     if ((st = dalloc(P, &P->d_eblk, (size_t)nblk)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_exc, 1)) != KLDI_OK) return fail(st);
     if ((st = dalloc(P, &P->d_err, 1)) != KLDI_OK) return fail(st);

@@ -71,6 +71,19 @@ constexpr int kMaxRet = 256;        // retained basis blocks per grid block the 
 __host__ __device__ constexpr int tile_bytes(int ns) { return ns * kPlaneBytes; }
 
 // ---------------------------------------------------------------------------
+// f 2^k in FP64, exactly, for an FP32 f and -128 < k < 128: a normal f is
+// widened by integer operations on its bits (the conversion instruction runs
+// on the FP64 pipe, which this GPU provides at a small fraction of the FP32
+// rate); zero and the rare FP32 subnormals take the FP64 unit.
+__device__ __forceinline__ double f32_to_f64(float f, int k = 0) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u) return (u << 1) == 0u ? 0.0 : ldexp((double)f, k);
+  const uint64_t d = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u + (uint32_t)k) << 52) |
+                     ((uint64_t)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 // slicing helpers
 __device__ __forceinline__ float pow2_ceil(float m) {
   // smallest power of two >= m (m > 0), 1 for m <= 0, at least 2^-100 so that
@@ -551,7 +564,7 @@ template <int NS, bool GRAD>
 __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListView L, int64_t g0, int64_t t0,
                                                  const double* __restrict__ xcoef, const float* __restrict__ pscale,
                                                  uint8_t* out_phi, float* phi_scale, uint8_t* out_x, float* x_scale,
-                                                 double* xmax) {
+                                                 double* xmax, float* xmaxf) {
   __shared__ float sp[kBasisBlk][kBlockPts + 1];
   __shared__ float sx[kBasisBlk][kBlockPts + 1];
   __shared__ float cp[kBasisBlk], cx[kBasisBlk], rawx[kBasisBlk];
@@ -610,7 +623,11 @@ __global__ void __launch_bounds__(128) k_x_split(BasisView B, GridView G, ListVi
   __syncthreads();
   if ((i & 31) == 0) rawx[i >> 5] = mx;
   __syncthreads();
-  if (i == 0) xmax[t] = (double)fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
+  if (i == 0) {
+    const float m = fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
+    xmax[t] = (double)m;
+    xmaxf[t] = m;
+  }
 }
 
 // BF16X10 V-product operands: as k_x_split, with Phi and X in double-float
@@ -627,7 +644,7 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
                                                          int64_t t0, const float4* __restrict__ xdf,
                                                          const float* __restrict__ pscale, uint8_t* out_phi,
                                                          float* phi_scale, uint8_t* out_x, float* x_scale,
-                                                         double* xmax, const float4* __restrict__ rad,
+                                                         double* xmax, float* xmaxf, const float4* __restrict__ rad,
                                                          const int64_t* __restrict__ rad_ptr, int64_t t1,
                                                          int64_t ahead) {
   extern __shared__ float xsm[];
@@ -663,7 +680,7 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
   }
   stage_block_rec(B, p, G.anchor[g], &rec, threadIdx.x, kX4Threads);
   __syncthreads();
-  const int mid = (rec.nshell + 1) >> 1;   // the two halves take consecutive shell ranges
+  const int mid = rec.split;   // the two halves take consecutive shell ranges of about equal functions
   for_rec_phix_df<GRAD>(&rec, rad + (rad_ptr[t] - rad_ptr[t0]) * kBlockPts + i, half == 0 ? 0 : mid,
                         half == 0 ? mid : rec.nshell, f2{pr.x, pl.x},
                         f2{pr.y, pl.y}, f2{pr.z, pl.z}, a, bx, by, bz, [&](int nu, f2 v, f2 x) {
@@ -720,7 +737,11 @@ __global__ void __launch_bounds__(kX4Threads, 3) k_x_split4(BasisView B, GridVie
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (half == 0 && (i & 31) == 0) rawx[i >> 5] = mx;
   __syncthreads();
-  if (threadIdx.x == 0) xmax[t] = (double)fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
+  if (threadIdx.x == 0) {
+    const float m = fmaxf(fmaxf(rawx[0], rawx[1]), fmaxf(rawx[2], rawx[3]));
+    xmax[t] = (double)m;
+    xmaxf[t] = m;
+  }
 }
 
 template <int NS>
@@ -732,11 +753,11 @@ static kldi_status x_ns(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   if (P->gga)
     k_x_split<NS, true><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                           b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
-                                                          P->d_x_scale, P->d_xmax);
+                                                          P->d_x_scale, P->d_xmax, P->d_xmaxf);
   else
     k_x_split<NS, false><<<(unsigned)n, kBlockPts, 0, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                            b.t0, P->d_xcoef, P->d_pscale, op, P->d_phic_scale, ox,
-                                                           P->d_x_scale, P->d_xmax);
+                                                           P->d_x_scale, P->d_xmax, P->d_xmaxf);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
 }
@@ -750,12 +771,12 @@ static kldi_status x_ns4(const kldi_plan* P, const Batch& b, cudaStream_t s) {
   if (P->gga)
     k_x_split4<true><<<(unsigned)n, kX4Threads, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                              b.t0, P->d_xdf, P->d_pscale, op, P->d_phic_scale, ox,
-                                                             P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr, b.t1,
+                                                             P->d_x_scale, P->d_xmax, P->d_xmaxf, P->d_rad, P->d_rad_ptr, b.t1,
                                                              (int64_t)3 * P->num_sms);
   else
     k_x_split4<false><<<(unsigned)n, kX4Threads, kX4Smem, s>>>(P->basis_view(), P->grid_view(), P->list_view(), b.g0,
                                                               b.t0, P->d_xdf, P->d_pscale, op, P->d_phic_scale, ox,
-                                                              P->d_x_scale, P->d_xmax, P->d_rad, P->d_rad_ptr, b.t1,
+                                                              P->d_x_scale, P->d_xmax, P->d_xmaxf, P->d_rad, P->d_rad_ptr, b.t1,
                                                               (int64_t)3 * P->num_sms);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
@@ -815,7 +836,10 @@ struct RhoCfg {
   static constexpr int kRsElem = NS == 4 ? 8 : 4;                 // R staged as FP32, or hi / lo pairs
   static constexpr int kOffR = kStages * kStageBytes;             // [kNQ q blocks][32][128] R
   static constexpr int kOffRed = kOffR + kNQ * kBasisBlk * kBlockPts * kRsElem;   // [kGroups][4][128] double
-  static constexpr int kMetaWords = 4 + kMaxRet + kMaxRet * (kMaxRet / 32);
+  // per-block record: n, tb, the retained list, the executed-pair bit matrix,
+  // and per N tile the number of p blocks with an executed pair
+  static constexpr int kOffNexec = 4 + kMaxRet + kMaxRet * (kMaxRet / 32);
+  static constexpr int kMetaWords = kOffNexec + kMaxRet / 2;
   static constexpr int kOffMeta = kOffRed + kGroups * 4 * kBlockPts * 8;
   static constexpr int kOffRec = kOffMeta + 2 * kMetaWords * 4;  // [kNQ q blocks][2] BlockRec
   static constexpr int kOffTab = kOffRec + 2 * kNQ * (int)sizeof(BlockRec);
@@ -999,9 +1023,9 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
     const uint32_t* mask = reinterpret_cast<const uint32_t*>(m + 4 + kMaxRet);
     return (mask[jp * nw + (q0 >> 5)] >> (q0 & 31)) & ((1u << nq) - 1u);
   };
-  auto nsegs = [&](const int32_t* m, int q0, int nq) -> int {
-    int c = 0;
-    for (int jp = 0; jp < m[0]; ++jp) c += tile_bits(m, jp, q0, nq) != 0;
+  // exact segments of N tile nt (one empty segment when nothing is executed)
+  auto nsegs = [&](const int32_t* m, int nt) -> int {
+    const int c = m[C::kOffNexec + nt];
     return c == 0 ? 1 : (c + C::kSegChunks - 1) / C::kSegChunks;
   };
 
@@ -1051,6 +1075,13 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
       if (lane == 0) {
         m[0] = n;
         m[1] = tb;
+      }
+      __syncwarp();
+      for (int nt = lane; nt < (n + C::kNQ - 1) / C::kNQ; nt += 32) {
+        const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
+        int c = 0;
+        for (int jp = 0; jp < n; ++jp) c += tile_bits(m, jp, q0, nq) != 0;
+        m[C::kOffNexec + nt] = c;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&mfull[b]);
@@ -1114,7 +1145,7 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
           const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
           const uint32_t idesc = instr_desc(128, 32 * nq, 1, 0, 0);
           int jp = 0;
-          const int ns = nsegs(m, q0, nq);
+          const int ns = nsegs(m, nt);
           for (int sg = 0; sg < ns && ok; ++sg, ++job) {
             const int buf = job % C::kBufs;
             const uint32_t use = job / C::kBufs;
@@ -1216,7 +1247,6 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
       if constexpr (NS == 4) prlo = G.prel_lo[pt];
       const int anc = G.anchor[g];
       const double rsc = (double)rowscale[pt];
-      double r_i = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
       // the point's sums over its tiles in double-float (FP64 arithmetic is
       // slow on this GPU), scaled and converted once per grid block
       f2 ar{0.f, 0.f}, agx{0.f, 0.f}, agy{0.f, 0.f}, agz{0.f, 0.f};
@@ -1229,9 +1259,8 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
       const int ntile = (n + C::kNQ - 1) / C::kNQ;
       for (int nt = 0; nt < ntile && ok; ++nt) {
         const int q0 = nt * C::kNQ, nq = min(C::kNQ, n - q0);
-        const int ns = nsegs(m, q0, nq);
-        bool work = false;
-        for (int jp = 0; jp < n && !work; ++jp) work = tile_bits(m, jp, q0, nq) != 0;
+        const int ns = nsegs(m, nt);
+        const bool work = m[C::kOffNexec + nt] > 0;
         const bool mine = work && k4 < nq;
         // the four warps of this q block stage its shells (double-buffered
         // record, one named barrier per use) while the products run
@@ -1321,7 +1350,7 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
             if (staged) {
               f2 pr{0.f, 0.f}, px_{0.f, 0.f}, py_{0.f, 0.f}, pz_{0.f, 0.f};
               const int64_t tq = m[1] + q0 + k4;   // tile (g, q block)
-              const int nsh = rec->nshell, mid = (nsh + 1) >> 1;   // the halves take consecutive shells
+              const int nsh = rec->nshell, mid = rec->split;   // the halves take consecutive shells
               rowdot_df<GRAD>(rec, rad + (rad_ptr[tq] - rad_ptr[t0]) * kBlockPts + i, Rs2, i, half == 0 ? 0 : mid,
                               half == 0 ? mid : nsh, f2{prl.x, prlo.x}, f2{prl.y, prlo.y}, f2{prl.z, prlo.z}, pr,
                               px_, py_, pz_);
@@ -1359,10 +1388,10 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
             // per atom of the block's shells: the warp's sum over its 32
             // points, one FP64 atomic per atom and component (BF16X10: the
             // first half of the warps)
-            const float rscf = (float)rsc;
             int cur = -1;
             float tx = 0.f, ty = 0.f, tz = 0.f;
             auto flush = [&]() {
+              const float rscf = (float)rsc;
               float v[3] = {tx * rscf, ty * rscf, tz * rscf};
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1)
@@ -1401,10 +1430,10 @@ __global__ void __launch_bounds__(RhoCfg<NS, NQ>::kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&mempty[b]);
       if constexpr (MODE != kRowDot) continue;
-      r_i = rsc * df_to_double(ar);                  // rsc: a power of two
-      gx = 2.0 * rsc * df_to_double(agx);
-      gy = 2.0 * rsc * df_to_double(agy);
-      gz = 2.0 * rsc * df_to_double(agz);
+      const double r_i = rsc * df_to_double(ar);    // rsc: a power of two
+      const double gx = 2.0 * rsc * df_to_double(agx);
+      const double gy = 2.0 * rsc * df_to_double(agy);
+      const double gz = 2.0 * rsc * df_to_double(agz);
       // combine the four q-block groups of each point in a fixed order
       if (!mbar_wait_warp(rempty, (uint32_t)(k & 1) ^ 1u, abort_flag, err, 117, wait_ns)) break;
       red[(grp * 4 + 0) * kBlockPts + i] = r_i;
@@ -1552,6 +1581,8 @@ struct VCfg {
   static constexpr int kLaunchRegs = 168;               // per thread at launch (checked on the host)
   static constexpr uint32_t kRegsLow = 64, kRegsHigh = 200;
   static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * kLaunchRegs, "register budgets exceed the pool");
+  // per SM sub-partition: one warp of warpgroup 0 and two epilogue warps
+  static_assert(32 * kRegsLow + 2 * 32 * kRegsHigh <= 16384, "register file of an SM sub-partition");
   static_assert(8 * NS <= 32, "one producer lane per copy of a stage");
 };
 
@@ -1567,8 +1598,9 @@ template <int NS>
 __global__ void __launch_bounds__(384, 1)
     k_v_tc(ListView L, const VWorkTC* __restrict__ work, int64_t nwork, const int32_t* __restrict__ glist,
            int64_t t0, const uint8_t* __restrict__ phic, const uint8_t* __restrict__ xs,
-           const float* __restrict__ scale, const double* __restrict__ xmax, const uint8_t* __restrict__ zero,
-           int nbf, double t_b, double t_d, double* V, int* next, int* err, uint64_t wait_ns, int withhold) {
+           const float* __restrict__ scale, const float* __restrict__ bmaxf, const float* __restrict__ xmaxf,
+           const uint8_t* __restrict__ zero, int nbf, float t_bf, float t_df, double* V, int* next, int* err,
+           uint64_t wait_ns, int withhold) {
   using C = VCfg<NS>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1756,14 +1788,13 @@ __global__ void __launch_bounds__(384, 1)
       for (int e = 0; e < wk.end - wk.beg; ++e, ++job) {
         const int64_t gb = glist[wk.beg + e];
         const int pr = wk.P + (m >> 5);
-        float rsc = 0.f;
-        double bp = 0.0, xp = 0.0;
+        float rsc = 0.f, bp = 0.f, xp = 0.f;
         if (pr < L.nbb) {
           const int t = L.tile_of[gb * L.nbb + pr];
           if (t >= 0) {
             rsc = scale[(int64_t)(t - t0) * kBasisBlk + (m & 31)];
-            bp = L.bmax[t];
-            xp = xmax[t];
+            bp = bmaxf[t];
+            xp = xmaxf[t];
           }
         }
         // column scales, zero where the block pair (p, q) of this grid block
@@ -1777,8 +1808,8 @@ __global__ void __launch_bounds__(384, 1)
           if (qb < L.nbb) {
             const int t = L.tile_of[gb * L.nbb + qb];
             if (t >= 0) {
-              const double bq = L.bmax[t], xq = xmax[t];
-              const bool on = (xq >= t_b && bp * xq >= t_d) || (xp >= t_b && bq * xp >= t_d);
+              const float bq = bmaxf[t], xq = xmaxf[t];
+              const bool on = (xq >= t_bf && bp * xq >= t_df) || (xp >= t_bf && bq * xp >= t_df);
               if (on) csc[cc] = scale[(int64_t)(t - t0) * kBasisBlk + lane];
             }
           }
@@ -1828,7 +1859,12 @@ __global__ void __launch_bounds__(384, 1)
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const int col = wk.Q * kBasisBlk + half * 64 + cq * 16 + c;
-            if (col < nbf) atomicAdd(&V[(int64_t)r * nbf + col], (double)S[cq * 16 + c] + (double)cmp[c]);
+            if (col < nbf) {
+              // the sum and its compensation term, each widened to FP64 by
+              // integer operations (no FP64 arithmetic), added by the atomics
+              atomicAdd(&V[(int64_t)r * nbf + col], f32_to_f64(S[cq * 16 + c]));
+              if (cmp[c] != 0.f) atomicAdd(&V[(int64_t)r * nbf + col], f32_to_f64(cmp[c]));
+            }
           }
         }
       }
@@ -1851,8 +1887,9 @@ static kldi_status v_ns(const kldi_plan* P, const Batch& b, double* V, cudaStrea
   KLDI_TRY_CUDA(cudaMemsetAsync(P->d_vnext, 0, sizeof(int), s));
   k_v_tc<NS><<<grid, C::kThreads, C::kSmem, s>>>(
       P->list_view(), b.d_vtc_work, b.n_vtc_work, b.d_vtc_g, b.t0, reinterpret_cast<const uint8_t*>(P->d_phic_s),
-      reinterpret_cast<const uint8_t*>(P->d_x_s), P->d_phic_scale, P->d_xmax,
-      reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, P->opt.t_b, P->opt.t_d, V, P->d_vnext, P->d_err, P->wait_ns,
+      reinterpret_cast<const uint8_t*>(P->d_x_s), P->d_phic_scale, P->d_bmaxf, P->d_xmaxf,
+      reinterpret_cast<const uint8_t*>(P->d_zero), (int)P->nbf, (float)P->opt.t_b, (float)P->opt.t_d, V, P->d_vnext,
+      P->d_err, P->wait_ns,
       (int)P->withhold_item);
   KLDI_TRY_CUDA(cudaGetLastError());
   return KLDI_OK;
