@@ -228,13 +228,14 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
-# DRAM bytes per tensor FLOP of the product kernels, from an ncu capture of
-# the same kernel on a smaller case of the same recipe
-# (dram__bytes_read.sum + dram__bytes_write.sum over the launch's tensor
-# FLOPs); the benchmark scales them by the launch's FLOPs.  An entry is
-# removed when its kernel changes, until it is captured again.
-DRAM_BYTES_PER_FLOP = {}
-DRAM_SOURCE = None
+# DRAM bytes of one launch of the dominant kernel on the default workload
+# (33 waters, overlap-signature order), dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of that launch (one pass; the
+# command is in profiles/ncu_full_water12_bf16x10.md).  An entry is removed
+# when its kernel changes, until it is captured again.
+DRAM_BYTES_PER_LAUNCH = {("k_v_tc", "bf16x10"): 28.25e9 + 0.4065e9}
+DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_v_tc<4> launch of this workload "
+               "(profiles/ncu_full_water12_bf16x10.md)")
 
 
 # ---------------------------------------------------------------------------- other shell order
@@ -652,10 +653,12 @@ def main():
     oth = 5 if dom == "rho" else 2
     oth_ms = stage_ms[oth] / max(1, stage_n[oth])
     dom_kernel = "k_rho_tc" if dom == "rho" else "k_v_tc"
-    bpf = DRAM_BYTES_PER_FLOP.get((dom_kernel, args.prec))
+    traffic = None
+    if not args.nwaters and args.basis_order == "overlap":
+        traffic = DRAM_BYTES_PER_LAUNCH.get((dom_kernel, args.prec))
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": bpf * dom_flops if bpf else None,
-            "traffic_source": DRAM_SOURCE if bpf else None,
+            "traffic": traffic,
+            "traffic_source": DRAM_SOURCE if traffic else None,
             "kernel": dom_kernel, "peak_source": peak_src,
             "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
             "flops_note": ("tensor-pipe FLOPs = slice products x 2 x 128 x sum d_p d_q over the density "
