@@ -393,6 +393,16 @@ kldi_status kldi_mlp_create(const float* params, const double* box, kldi_mlp** o
 /* Copy the FP32 master parameters to params[KLDI_MLP_NPARAMS] (host). */
 kldi_status kldi_mlp_get_params(const kldi_mlp* mlp, float* params);
 
+/* Training checkpoint (the learned part's state; the paper has no
+ * counterpart): state[3 * KLDI_MLP_NPARAMS] (host, FP32) holds the FP32
+ * master parameters, then Adam's first and second moments; *step the Adam
+ * steps taken.  kldi_mlp_set_state restores all of them (and the FP16 copy the
+ * evaluation kernels read), so that training resumes bit for bit; the box is
+ * the one the network was created with.  Both synchronise; KLDI_EINVAL for a
+ * null argument or a negative step. */
+kldi_status kldi_mlp_get_state(const kldi_mlp* mlp, float* state, int64_t* step);
+kldi_status kldi_mlp_set_state(kldi_mlp* mlp, const float* state, int64_t step);
+
 /* Mean loss over the valid points of (rho[n], sigma[n]) (host or device,
  * FP64) of (o1 - F*)^2 + (o2 - G*)^2 with F* = f / e0, G* = v_rho / v0 of the
  * analytic PBE-form functional, and its gradient grad[KLDI_MLP_NPARAMS]

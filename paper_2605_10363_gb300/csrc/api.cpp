@@ -1,5 +1,7 @@
 // Compute entry points: kldi_density, kldi_vxc, kldi_exc, kldi_exc_batched.
 // Every step runs in this library's CUDA kernels on the plan's stream.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -26,10 +28,18 @@ using kldi::is_device_ptr;
 
 namespace {
 
+// Stage names of the NVTX ranges that bracket each stage's launches (a
+// profiler can filter kernels by them, e.g. ncu --nvtx --nvtx-include).
+const char* const kStageNames[] = {"kldi:dprep", "kldi:phi", "kldi:rho", "kldi:xc", "kldi:x", "kldi:v", "kldi:finish"};
+
 // Stage timing: record an event pair around `fn` when profiling is on.
 template <typename F>
 kldi_status staged(kldi_plan* P, int stage, int launches, F&& fn) {
   P->launch_count += launches;
+  struct Range {
+    explicit Range(int s) { nvtxRangePushA(kStageNames[s]); }
+    ~Range() { nvtxRangePop(); }
+  } range(stage);
   if (!P->prof || P->prof_stage.size() * 2 + 2 > P->prof_ev.size()) return fn();
   const size_t k = P->prof_stage.size() * 2;
   KLDI_TRY_CUDA(cudaEventRecord(P->prof_ev[k], P->stream));

@@ -553,6 +553,39 @@ extern "C" kldi_status kldi_mlp_get_params(const kldi_mlp* M, float* params) {
   });
 }
 
+extern "C" kldi_status kldi_mlp_get_state(const kldi_mlp* M, float* state, int64_t* step) {
+  return kldi::guarded("kldi_mlp_get_state", [&]() -> kldi_status {
+    if (!M || !state || !step) {
+      set_error("kldi_mlp_get_state: null argument");
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY_CUDA(cudaDeviceSynchronize());
+    KLDI_TRY_CUDA(cudaMemcpy(state, M->d_param, sizeof(float) * kNP, cudaMemcpyDeviceToHost));
+    KLDI_TRY_CUDA(cudaMemcpy(state + kNP, M->d_m, sizeof(float) * kNP, cudaMemcpyDeviceToHost));
+    KLDI_TRY_CUDA(cudaMemcpy(state + 2 * kNP, M->d_v, sizeof(float) * kNP, cudaMemcpyDeviceToHost));
+    *step = M->step;
+    return KLDI_OK;
+  });
+}
+
+extern "C" kldi_status kldi_mlp_set_state(kldi_mlp* M, const float* state, int64_t step) {
+  return kldi::guarded("kldi_mlp_set_state", [&]() -> kldi_status {
+    if (!M || !state || step < 0) {
+      set_error("kldi_mlp_set_state: null argument or negative step");
+      return KLDI_EINVAL;
+    }
+    KLDI_TRY_CUDA(cudaDeviceSynchronize());
+    KLDI_TRY_CUDA(cudaMemcpy(M->d_param, state, sizeof(float) * kNP, cudaMemcpyHostToDevice));
+    KLDI_TRY_CUDA(cudaMemcpy(M->d_m, state + kNP, sizeof(float) * kNP, cudaMemcpyHostToDevice));
+    KLDI_TRY_CUDA(cudaMemcpy(M->d_v, state + 2 * kNP, sizeof(float) * kNP, cudaMemcpyHostToDevice));
+    k_to_half<<<(kNP + 255) / 256, 256>>>(M->d_param, M->d_half);
+    KLDI_TRY_CUDA(cudaGetLastError());
+    KLDI_TRY_CUDA(cudaDeviceSynchronize());
+    M->step = step;
+    return KLDI_OK;
+  });
+}
+
 extern "C" kldi_status kldi_mlp_loss_grad(kldi_mlp* M, const double* rho, const double* sigma, int64_t n,
                                           double rho_min, float* grad, float* loss) {
   return kldi::guarded("kldi_mlp_loss_grad", [&]() -> kldi_status {

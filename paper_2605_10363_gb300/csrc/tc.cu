@@ -71,16 +71,21 @@ constexpr int kMaxRet = 256;        // retained basis blocks per grid block the 
 __host__ __device__ constexpr int tile_bytes(int ns) { return ns * kPlaneBytes; }
 
 // ---------------------------------------------------------------------------
-// f 2^k in FP64, exactly, for an FP32 f and -128 < k < 128: a normal f is
-// widened by integer operations on its bits (the conversion instruction runs
-// on the FP64 pipe, which this GPU provides at a small fraction of the FP32
-// rate); zero and the rare FP32 subnormals take the FP64 unit.
-__device__ __forceinline__ double f32_to_f64(float f, int k = 0) {
+// FP32 -> FP64, exactly, by integer operations on the bits (the conversion
+// instruction runs on the FP64 pipe, which this GPU provides at a small
+// fraction of the FP32 rate); an FP32 subnormal m 2^-149 is normalised with a
+// leading-zero count.
+__device__ __forceinline__ double f32_to_f64(float f) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0u) return (u << 1) == 0u ? 0.0 : ldexp((double)f, k);
-  const uint64_t d = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u + (uint32_t)k) << 52) |
-                     ((uint64_t)(u & 0x7fffffu) << 29);
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  if (e == 0u) {
+    if (m == 0u) return __longlong_as_double((long long)sign);
+    const int sh = __clz((int)m) - 8;   // moves the leading one to bit 23
+    m = (m << sh) & 0x7fffffu;
+    e = 1u - (uint32_t)sh;               // may wrap below zero: the FP64 exponent below stays positive
+  }
+  const uint64_t d = sign | ((uint64_t)(uint32_t)(e + 896u) << 52) | ((uint64_t)m << 29);
   return __longlong_as_double((long long)d);
 }
 

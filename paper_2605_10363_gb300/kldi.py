@@ -93,6 +93,8 @@ def _load():
         "kldi_exc_energy_noalloc": (C.c_int, [C.c_int, C.c_int64, vp, vp, vp, C.c_double, vp, vp]),
         "kldi_mlp_create": (C.c_int, [vp, vp, C.POINTER(vp)]),
         "kldi_mlp_get_params": (C.c_int, [vp, vp]),
+        "kldi_mlp_get_state": (C.c_int, [vp, vp, i64p]),
+        "kldi_mlp_set_state": (C.c_int, [vp, vp, C.c_int64]),
         "kldi_mlp_loss_grad": (C.c_int, [vp, vp, vp, C.c_int64, C.c_double, vp, vp]),
         "kldi_mlp_adam_step": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_double, C.c_double]),
         "kldi_mlp_train": (C.c_int, [vp, vp, vp, C.c_int64, C.POINTER(TrainOptions), vp]),
@@ -374,6 +376,18 @@ class Mlp:
         out = np.empty(MLP_NPARAMS, np.float32)
         _check(LIB.kldi_mlp_get_params(self.h, _ptr(out)))
         return out
+
+    def state(self):
+        """Training checkpoint: (parameters, Adam moments m and v stacked, step)."""
+        out = np.empty(3 * MLP_NPARAMS, np.float32)
+        step = C.c_int64()
+        _check(LIB.kldi_mlp_get_state(self.h, _ptr(out), C.byref(step)))
+        return out, int(step.value)
+
+    def set_state(self, state, step):
+        s = np.ascontiguousarray(state, np.float32)
+        assert s.size == 3 * MLP_NPARAMS
+        _check(LIB.kldi_mlp_set_state(self.h, _ptr(s), int(step)))
 
     def loss_grad(self, rho, sigma, rho_min=1e-14):
         rho = np.ascontiguousarray(rho, np.float64) if isinstance(rho, np.ndarray) else rho

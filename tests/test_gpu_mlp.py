@@ -119,6 +119,31 @@ def trained():
     return net, box, hist
 
 
+def test_checkpoint_resumes_training_bit_for_bit():
+    """The training state (parameters, Adam moments, step counter) saved after
+    some epochs and restored into a fresh network gives exactly the same
+    parameters and losses after the same further training."""
+    kldi = _kldi()
+    rho, sigma = _density_points(synth.make_system(1))
+    box = synth.mlp_box(rho, sigma)
+    net = kldi.Mlp(synth.mlp_init(42), box)
+    net.train(rho, sigma, epochs=3, batch=2048)
+    state, step = net.state()
+    assert step > 0 and np.all(np.isfinite(state))
+    assert np.array_equal(state[:kldi.MLP_NPARAMS], net.params())
+    h1 = net.train(rho, sigma, epochs=2, batch=2048)
+    p1 = net.params()
+    other = kldi.Mlp(synth.mlp_init(7), box)
+    other.set_state(state, step)
+    s2, step2 = other.state()
+    assert step2 == step and np.array_equal(s2, state)
+    h2 = other.train(rho, sigma, epochs=2, batch=2048)
+    assert np.array_equal(h1, h2)
+    assert np.array_equal(p1, other.params())
+    with pytest.raises(kldi.KldiError):
+        other.set_state(state, -1)
+
+
 def test_training_reduces_loss(trained):
     net, box, hist = trained
     assert np.all(np.isfinite(hist))
