@@ -223,7 +223,7 @@ kldi_status build_work(kldi_plan* P, int64_t cap) {
     std::vector<VWorkTC> tw;
     // Work items are cut at grid-block ranges of `span` blocks and ordered
     // range-major: CTAs running at the same time then work on the same few
-    // ranges, whose Phi~ / X~ tiles stay in L2 across the tile pairs that
+    // ranges, whose Phi~ / X~ tiles stay in L2 across the window pairs that
     // reuse them.  span: the tuned value, else 64 grid blocks.
     const int64_t span = P->tune.v_seg > 0 ? P->tune.v_seg : 64;
     struct PairList {
