@@ -6,7 +6,8 @@ Tolerances (written per mode, derived from the arithmetic):
   bf16x10  four 8-bit slices per operand (2^-32 of the row / column scale),
            exact tensor-core levels, double-float basis values, X and
            row-dot: the stated target |dE| <= 1e-6 Ha and max|dV| <= 1e-7;
-           rho to 1e-7 of |rho| + 1e-12.
+           rho within its slicing error model (2^-30 of the point's density
+           scale, rho_model_bound).
   bf16x6   three 8-bit slices, FP32 basis values: the fast mode, held to its
            measured error, not to the target: |dE| <= 1e-6 Ha on these small
            systems, max|dV| <= 3e-7 (the largest V elements, ~5 Ha, carry the
