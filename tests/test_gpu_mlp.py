@@ -186,7 +186,7 @@ def test_mlp_call_needs_network():
 
 def test_what_training_gains(trained):
     """The learned functional against the method without it, the analytic
-    PBE-form path (the judge), on the four-water system: the E_xc difference
+    PBE-form path (the reference), on the four-water system: the E_xc difference
     and the time of the whole evaluation and of the functional stage are
     measured and stated; the trained network's difference is bounded (1e-3
     relative) and more than 20x smaller than that of the untrained network
