@@ -201,6 +201,18 @@ def oracle_sample(system, nblocks_sample, seed=5):
     return nblocks_sample * 128 / dt, dt, blocks
 
 
+def arm_config(args, world):
+    """The workload configuration both arms report (the same dict for the
+    library and the CPU oracle on the same arguments)."""
+    workload = WORKLOAD if not args.nwaters else (
+        f"water{args.nwaters}_pbe: {args.nwaters} waters of the 33-water recipe, PBE-form, t_b = t_d = 1e-10")
+    return {"workload": workload,
+            "l2": "inputs larger than L2 (split tile buffers of several GB per step)",
+            "parallelism": f"replicas x{world}",
+            "basis_order": ("overlap-signature clustering (kldi_order_shells, Sec. III-B)"
+                            if args.basis_order == "overlap" else "atom order")}
+
+
 def run_reference(args, world, rank):
     import synth
     if rank != 0:
@@ -222,7 +234,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "arm": "CPU oracle (the reference arm of this repository)"},
+        "config": arm_config(args, world), "arm": "CPU oracle (the reference arm of this repository)",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -732,13 +744,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD if not args.nwaters else
-                       f"water{args.nwaters}_pbe: {args.nwaters} waters of the 33-water recipe, PBE-form, "
-                       "t_b = t_d = 1e-10", "precision": args.prec,
-                       "l2": "inputs larger than L2 (split tile buffers of several GB per step)",
-                       "parallelism": f"replicas x{world}", "plan_seconds": round(t_plan, 2),
-                       "basis_order": "overlap-signature clustering (kldi_order_shells, Sec. III-B), "
-                                      f"{t_order:.2f} s on the host" if order is not None else "atom order"},
+            "config": arm_config(args, world), "precision": args.prec,
+            "host_seconds": {"plan": round(t_plan, 2), "shell_order": round(t_order, 2)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(stage_n.sum()), "clocks": clk, "stage_ms_per_step": per_stage,
             "E_xc": E_ours, "modes": modes, **out_extra,
