@@ -48,7 +48,8 @@ typedef enum {
   KLDI_ENOMEM = -2,       /* host or device allocation failed                */
   KLDI_ECUDA = -3,        /* a CUDA runtime/driver call failed               */
   KLDI_ETIMEOUT = -4,     /* a bounded device wait gave up                   */
-  KLDI_EUNSUPPORTED = -5  /* valid request this build or device cannot serve */
+  KLDI_EUNSUPPORTED = -5, /* valid request this build or device cannot serve */
+  KLDI_EIO = -6           /* a file could not be opened, written or read     */
 } kldi_status;
 
 /* Functionals (Sec. III-F scope: local and semilocal).  KLDI_XC_LDA_X: Slater
@@ -182,6 +183,21 @@ kldi_status kldi_grid_info(const kldi_grid* grid, int64_t* npoints, int64_t* nre
 /* Copy the grid into caller host buffers: xyz[npoints*3], w[npoints],
  * atom_of[npoints]; any of the three may be NULL. */
 kldi_status kldi_grid_export(const kldi_grid* grid, double* xyz, double* w, int32_t* atom_of);
+
+/* Save a grid to the file at path (created or replaced), and load one back,
+ * so that a geometry's grid is built once (the Becke weights of Sec. III-D's
+ * preprocessing are the costly part of building it).  File, host byte order:
+ * the 8 bytes "KLDIGRD1"; int64 npoints, nreal, nblocks, block; then
+ * xyz[npoints*3] and w[npoints] (double) and atom_of[npoints] (int32), as
+ * kldi_grid_export gives them.  kldi_grid_load checks the header, the sizes
+ * (block = 128, npoints = nblocks * block, npoints - block < nreal <= npoints),
+ * the file length, the owning atoms (>= 0), finite coordinates and weights,
+ * and zero weights on the padding; kldi_screen refuses a grid whose owning
+ * atoms do not exist in its molecule.  KLDI_EINVAL: null argument or
+ * malformed file; KLDI_EIO: the file cannot be opened, written or read in
+ * full.  *out is library-owned (kldi_grid_free). */
+kldi_status kldi_grid_save(const kldi_grid* grid, const char* path);
+kldi_status kldi_grid_load(const char* path, kldi_grid** out);
 
 /* Geometry-fixed preprocessing (Sec. III-B-3, III-D): upload grid and basis,
  * evaluate the block summaries b_gp = max |phi| (and |grad phi| for the GGA)

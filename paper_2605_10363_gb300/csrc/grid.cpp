@@ -19,7 +19,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <memory>
 #include <numeric>
 
 #include "internal.h"
@@ -287,6 +289,116 @@ extern "C" kldi_status kldi_grid_export(const kldi_grid* g, double* xyz, double*
     if (xyz) std::memcpy(xyz, g->xyz.data(), sizeof(double) * g->xyz.size());
     if (w) std::memcpy(w, g->w.data(), sizeof(double) * g->w.size());
     if (atom_of) std::memcpy(atom_of, g->atom.data(), sizeof(int32_t) * g->atom.size());
+    return KLDI_OK;
+  });
+}
+
+namespace {
+
+const char kGridMagic[8] = {'K', 'L', 'D', 'I', 'G', 'R', 'D', '1'};
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+
+}  // namespace
+
+extern "C" kldi_status kldi_grid_save(const kldi_grid* g, const char* path) {
+  return kldi::guarded("kldi_grid_save", [&]() -> kldi_status {
+    using namespace kldi;
+    if (!g || !path) {
+      set_error("kldi_grid_save: null argument");
+      return KLDI_EINVAL;
+    }
+    FILE* f = std::fopen(path, "wb");
+    if (!f) {
+      set_error("kldi_grid_save: cannot open %s for writing", path);
+      return KLDI_EIO;
+    }
+    const int64_t head[4] = {g->npoints, g->nreal, g->nblocks, (int64_t)g->block};
+    bool ok = std::fwrite(kGridMagic, 1, sizeof kGridMagic, f) == sizeof kGridMagic &&
+              std::fwrite(head, sizeof(int64_t), 4, f) == 4 &&
+              std::fwrite(g->xyz.data(), sizeof(double), g->xyz.size(), f) == g->xyz.size() &&
+              std::fwrite(g->w.data(), sizeof(double), g->w.size(), f) == g->w.size() &&
+              std::fwrite(g->atom.data(), sizeof(int32_t), g->atom.size(), f) == g->atom.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) {
+      std::remove(path);
+      set_error("kldi_grid_save: writing %s failed", path);
+      return KLDI_EIO;
+    }
+    return KLDI_OK;
+  });
+}
+
+extern "C" kldi_status kldi_grid_load(const char* path, kldi_grid** out) {
+  return kldi::guarded("kldi_grid_load", [&]() -> kldi_status {
+    using namespace kldi;
+    if (!path || !out) {
+      set_error("kldi_grid_load: null argument");
+      return KLDI_EINVAL;
+    }
+    FileCloser fc{std::fopen(path, "rb")};
+    FILE* f = fc.f;
+    if (!f) {
+      set_error("kldi_grid_load: cannot open %s", path);
+      return KLDI_EIO;
+    }
+    if (std::fseek(f, 0, SEEK_END) != 0) {
+      set_error("kldi_grid_load: cannot seek in %s", path);
+      return KLDI_EIO;
+    }
+    const long long flen = (long long)ftello(f);
+    std::rewind(f);
+    char magic[8];
+    int64_t head[4];
+    if (flen < 0 || std::fread(magic, 1, sizeof magic, f) != sizeof magic || std::fread(head, sizeof(int64_t), 4, f) != 4) {
+      set_error("kldi_grid_load: %s is shorter than the header", path);
+      return flen < 0 ? KLDI_EIO : KLDI_EINVAL;
+    }
+    if (std::memcmp(magic, kGridMagic, sizeof magic) != 0) {
+      set_error("kldi_grid_load: %s is not a saved grid", path);
+      return KLDI_EINVAL;
+    }
+    const int64_t npoints = head[0], nreal = head[1], nblocks = head[2], block = head[3];
+    if (block != kBlockPts || nblocks <= 0 || nblocks > (INT64_C(1) << 40) / kBlockPts ||
+        npoints != nblocks * kBlockPts || nreal <= npoints - kBlockPts || nreal > npoints) {
+      set_error("kldi_grid_load: %s: inconsistent sizes (npoints %lld, nreal %lld, nblocks %lld, block %lld)", path,
+                (long long)npoints, (long long)nreal, (long long)nblocks, (long long)block);
+      return KLDI_EINVAL;
+    }
+    const long long want = (long long)(sizeof magic + sizeof head) +
+                           npoints * (long long)(4 * sizeof(double) + sizeof(int32_t));
+    if (flen != want) {
+      set_error("kldi_grid_load: %s has %lld bytes, the header implies %lld", path, flen, want);
+      return KLDI_EINVAL;
+    }
+    kldi_grid* G = new kldi_grid;
+    std::unique_ptr<kldi_grid> hold(G);
+    G->npoints = npoints;
+    G->nreal = nreal;
+    G->nblocks = nblocks;
+    G->xyz.resize(npoints * 3);
+    G->w.resize(npoints);
+    G->atom.resize(npoints);
+    if (std::fread(G->xyz.data(), sizeof(double), G->xyz.size(), f) != G->xyz.size() ||
+        std::fread(G->w.data(), sizeof(double), G->w.size(), f) != G->w.size() ||
+        std::fread(G->atom.data(), sizeof(int32_t), G->atom.size(), f) != G->atom.size()) {
+      set_error("kldi_grid_load: reading %s failed", path);
+      return KLDI_EIO;
+    }
+    for (int64_t k = 0; k < npoints; ++k) {
+      const double* p = &G->xyz[k * 3];
+      if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2]) || !std::isfinite(G->w[k]) ||
+          G->atom[k] < 0 || (k >= nreal && G->w[k] != 0.0)) {
+        set_error("kldi_grid_load: %s: point %lld is malformed", path, (long long)k);
+        return KLDI_EINVAL;
+      }
+    }
+    *out = hold.release();
     return KLDI_OK;
   });
 }

@@ -342,6 +342,24 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
       set_error("KLDI_TF32X3 is not provided: 11-bit slices cannot keep the tensor-core sums exact");
       return KLDI_EUNSUPPORTED;
     }
+    if (mol->natm <= 0 || !mol->xyz) {
+      set_error("kldi_screen: molecule without atoms or coordinates");
+      return KLDI_EINVAL;
+    }
+    // the grid's owning atoms index the molecule's coordinates here and the
+    // per-atom-pair offsets on the device: a grid made for another molecule
+    // must not get that far
+    if (grid->nblocks <= 0 || grid->npoints != grid->nblocks * kBlockPts ||
+        (int64_t)grid->atom.size() != grid->npoints) {
+      set_error("kldi_screen: malformed grid");
+      return KLDI_EINVAL;
+    }
+    for (int64_t k = 0; k < grid->npoints; ++k)
+      if (grid->atom[k] < 0 || grid->atom[k] >= mol->natm) {
+        set_error("kldi_screen: grid point %lld belongs to atom %d, the molecule has %d atoms", (long long)k,
+                  grid->atom[k], mol->natm);
+        return KLDI_EINVAL;
+      }
     // optional shell order: the plan works on the permuted basis; fnperm maps an
     // internal function index to the caller's
     std::vector<int32_t> p_atom, p_l, p_nprim, fnperm;

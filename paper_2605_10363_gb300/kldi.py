@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkldi.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = 0, -1, -2, -3, -4, -5, -6
 XC = {"lda_x": 1, "pbe": 2, "mlp": 3}
 PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "bf16x6": 3, "bf16x10": 4}
 STAGES = ("dprep", "phi", "rho", "xc", "x", "v", "finish")
@@ -76,6 +76,8 @@ def _load():
         "kldi_order_shells": (C.c_int, [C.c_int, vp, vp, vp]),
         "kldi_grid_info": (C.c_int, [vp, i64p, i64p, i64p]),
         "kldi_grid_export": (C.c_int, [vp, vp, vp, vp]),
+        "kldi_grid_save": (C.c_int, [vp, C.c_char_p]),
+        "kldi_grid_load": (C.c_int, [C.c_char_p, C.POINTER(vp)]),
         "kldi_screen": (C.c_int, [vp, C.POINTER(Molecule), C.POINTER(Basis), C.POINTER(Options), C.POINTER(vp)]),
         "kldi_plan_info": (C.c_int, [vp, C.POINTER(PlanStats)]),
         "kldi_plan_export_lists": (C.c_int, [vp, vp, vp, vp]),
@@ -162,6 +164,10 @@ class Grid:
         _check(LIB.kldi_grid_export(self.h, _ptr(xyz), _ptr(w), _ptr(atom)))
         return xyz, w, atom
 
+    def save(self, path):
+        """Write the grid to a file (kldi_grid_save); load_grid reads it back."""
+        _check(LIB.kldi_grid_save(self.h, os.fsencode(path)))
+
     def __del__(self):
         if getattr(self, "h", None) is not None and self.h.value:
             LIB.kldi_grid_free(self.h)
@@ -194,6 +200,13 @@ def make_grid(Z, xyz, nrad, ntheta, block=128) -> Grid:
     spec = GridSpec(int(nrad), len(nt), nt.ctypes.data_as(C.POINTER(C.c_int32)), int(block))
     h = C.c_void_p()
     _check(LIB.kldi_make_grid(C.byref(m), C.byref(spec), C.byref(h)))
+    return Grid(h.value)
+
+
+def load_grid(path) -> Grid:
+    """A grid saved by Grid.save (kldi_grid_load)."""
+    h = C.c_void_p()
+    _check(LIB.kldi_grid_load(os.fsencode(path), C.byref(h)))
     return Grid(h.value)
 
 
@@ -447,8 +460,11 @@ def version() -> str:
 
 # ----------------------------------------------------------------------------
 # convenience: build grid + plan for a ``synth.System``
-def plan_for_system(system, prec="bf16x3", xc=None, stream=0, rho_min=1e-14, shell_order=None):
-    g = make_grid(system.Z, system.xyz, system.grid.nrad, system.grid.ntheta, system.grid.block)
+def plan_for_system(system, prec="bf16x3", xc=None, stream=0, rho_min=1e-14, shell_order=None, grid=None):
+    """Grid (built here unless a Grid, e.g. from load_grid, is given) and plan
+    of a synthetic system."""
+    g = grid if grid is not None else make_grid(system.Z, system.xyz, system.grid.nrad, system.grid.ntheta,
+                                                system.grid.block)
     b = system.basis
     return screen(g, system.Z, system.xyz, b.atom, b.l, b.nprim, b.exps, b.coefs, system.t_b, system.t_d,
                   rho_min=rho_min, prec=prec, xc=xc or system.xc, stream=stream, shell_order=shell_order)

@@ -1,6 +1,7 @@
 /* The C ABI used from C: one water molecule with a small s/p basis.
- * Without arguments: host-only calls (grid, its export, the basis order);
- * with --gpu: also kldi_screen and kldi_exc in FP64 and BF16x6, printing E_xc.
+ * abi_smoke GRIDFILE [--gpu].  Host-only calls: the grid, its export, the
+ * grid saved to GRIDFILE and loaded back, the basis order; with --gpu also
+ * kldi_screen and kldi_exc in FP64 and BF16x6, printing E_xc.
  * Built and run by tests/test_c_abi.py. */
 #include <math.h>
 #include <stdio.h>
@@ -18,7 +19,12 @@ static int check(kldi_status st, const char* what) {
 }
 
 int main(int argc, char** argv) {
-  const int gpu = argc > 1 && strcmp(argv[1], "--gpu") == 0;
+  if (argc < 2) {
+    printf("usage: abi_smoke GRIDFILE [--gpu]\n");
+    return 2;
+  }
+  const char* grid_file = argv[1];
+  const int gpu = argc > 2 && strcmp(argv[2], "--gpu") == 0;
   const int32_t Z[3] = {8, 1, 1};
   const double xyz[9] = {0.0, 0.0, 0.0, 1.43, 1.11, 0.0, -1.43, 1.11, 0.0};
   const kldi_molecule mol = {3, Z, xyz};
@@ -42,6 +48,29 @@ int main(int argc, char** argv) {
     }
   printf("grid %lld %lld %lld\n", (long long)np, (long long)nreal, (long long)nb);
   printf("gauss %.10f %.10f %.10f\n", gsum[0], gsum[1], gsum[2]);
+
+  /* the grid saved and loaded back: same sizes and the same bytes */
+  kldi_grid* loaded = NULL;
+  if (check(kldi_grid_save(grid, grid_file), "kldi_grid_save")) return 1;
+  if (check(kldi_grid_load(grid_file, &loaded), "kldi_grid_load")) return 1;
+  int64_t np2 = 0, nreal2 = 0, nb2 = 0;
+  if (check(kldi_grid_info(loaded, &np2, &nreal2, &nb2), "kldi_grid_info (loaded)")) return 1;
+  int same = np2 == np && nreal2 == nreal && nb2 == nb;
+  if (same) {
+    double* p2 = malloc(sizeof(double) * 3 * np);
+    double* w2 = malloc(sizeof(double) * np);
+    int32_t* at2 = malloc(sizeof(int32_t) * np);
+    if (check(kldi_grid_export(loaded, p2, w2, at2), "kldi_grid_export (loaded)")) return 1;
+    same = memcmp(p, p2, sizeof(double) * 3 * np) == 0 && memcmp(w, w2, sizeof(double) * np) == 0 &&
+           memcmp(at, at2, sizeof(int32_t) * np) == 0;
+    free(p2);
+    free(w2);
+    free(at2);
+  }
+  kldi_grid_free(loaded);
+  kldi_grid* none = NULL;
+  const kldi_status missing = kldi_grid_load("", &none);
+  printf("reload %s %d\n", same ? "same" : "differs", (int)missing);
 
   /* basis: O 1s 2s 2p, H 1s on each hydrogen (one primitive each) */
   const int32_t satom[5] = {0, 0, 0, 1, 2}, sl[5] = {0, 0, 1, 0, 0}, snp[5] = {1, 1, 1, 1, 1};

@@ -26,7 +26,7 @@ def _run(tmp_path, *args):
     subprocess.run([cc, "-std=c99", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                     os.path.join(HERE, "c_abi", "abi_smoke.c"), "-L", PKG, "-lkldi", f"-Wl,-rpath,{PKG}", "-lm",
                     "-o", exe], check=True)
-    r = subprocess.run([exe, *args], capture_output=True, text=True, timeout=600)
+    r = subprocess.run([exe, str(tmp_path / "water.grid"), *args], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     out = {}
     for line in r.stdout.splitlines():
@@ -42,6 +42,7 @@ def test_c_program_host_calls(tmp_path):
     out = _run(tmp_path)
     g = kldi.make_grid(Z, XYZ, 40, [6])
     assert [int(v) for v in out["grid"]] == [g.npoints, g.nreal, g.nblocks]
+    assert out["reload"] == ["same", str(kldi.EIO)]
     for v in out["gauss"]:            # a Gaussian of integral pi^(3/2) on each atom
         assert abs(float(v) - math.pi ** 1.5) <= 1e-2
     S = np.eye(7)
