@@ -107,3 +107,22 @@ def test_screen_refuses_a_grid_of_a_larger_molecule(saved):
     for grid in (g, kldi.load_grid(path)):
         e = _raises(kldi.EINVAL, kldi.plan_for_system, one, "fp64", None, 0, 1e-14, None, grid)
         assert "atom" in str(e) and "3 atoms" in str(e)
+
+
+@pytest.mark.gpu
+def test_plan_from_a_loaded_grid_matches_a_fresh_one(saved):
+    """kldi_exc on a plan built from the loaded grid gives the energy and V of
+    the plan built from the grid it was saved from (FP64 block form; the V
+    scatter's atomic order leaves differences at rounding level)."""
+    kldi = _kldi()
+    s, g, path = saved
+    out = []
+    for grid in (g, kldi.load_grid(path)):
+        plan = kldi.plan_for_system(s, prec="fp64", xc="pbe", grid=grid)
+        V = np.zeros((s.nbf, s.nbf))
+        E = np.zeros(1)
+        kldi.exc(plan, "pbe", s.D, V, E)
+        out.append((E[0], V))
+    (e0, v0), (e1, v1) = out
+    assert abs(e1 - e0) <= 1e-13 * abs(e0)
+    assert np.abs(v1 - v0).max() <= 1e-13 * np.abs(v0).max()
