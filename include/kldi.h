@@ -205,7 +205,12 @@ kldi_status kldi_grid_load(const char* path, kldi_grid** out);
  * S_g = {p : b_gp >= t_b} as a block-CSR list per grid block (the BCS(R)
  * analogue of App. C) and the per-V-tile lists of grid blocks (the BCS(C)
  * analogue), and allocate all work buffers.  The grid must stay alive while
- * the plan is used.  *out is library-owned. */
+ * the plan is used.  *out is library-owned.  Before any device work,
+ * KLDI_EINVAL for: a null argument, a shell with l > 2 (KLDI_EUNSUPPORTED) or
+ * nprim <= 0 or an atom outside the molecule, an exponent that is not positive
+ * and finite, a non-finite coefficient or coordinate, negative thresholds, a
+ * shell_order that is not a permutation, and a grid whose points belong to
+ * atoms the molecule does not have. */
 kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* mol, const kldi_basis* basis,
                         const kldi_options* opt, kldi_plan** out);
 

@@ -102,6 +102,11 @@ extern "C" kldi_status kldi_make_grid(const kldi_molecule* mol, const kldi_grid_
       set_error("kldi_make_grid: null argument or natm <= 0");
       return KLDI_EINVAL;
     }
+    for (int64_t k = 0; k < 3 * (int64_t)mol->natm; ++k)
+      if (!std::isfinite(mol->xyz[k])) {
+        set_error("kldi_make_grid: atom %lld has a non-finite coordinate", (long long)(k / 3));
+        return KLDI_EINVAL;
+      }
     if (spec->nrad <= 0 || spec->nregions <= 0 || !spec->ntheta) {
       set_error("kldi_make_grid: bad grid spec");
       return KLDI_EINVAL;

@@ -346,6 +346,11 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
       set_error("kldi_screen: molecule without atoms or coordinates");
       return KLDI_EINVAL;
     }
+    for (int64_t k = 0; k < 3 * (int64_t)mol->natm; ++k)
+      if (!std::isfinite(mol->xyz[k])) {
+        set_error("kldi_screen: atom %lld has a non-finite coordinate", (long long)(k / 3));
+        return KLDI_EINVAL;
+      }
     // the grid's owning atoms index the molecule's coordinates here and the
     // per-atom-pair offsets on the device: a grid made for another molecule
     // must not get that far
@@ -378,13 +383,20 @@ extern "C" kldi_status kldi_screen(const kldi_grid* grid, const kldi_molecule* m
       std::vector<int64_t> poff(ns0 + 1, 0), foff(ns0 + 1, 0);
       for (int s = 0; s < ns0; ++s) {
         const int l = basis->l[s];
-        if (l < 0 || l > 2 || basis->nprim[s] <= 0) {
-          set_error("kldi_screen: shell %d has l=%d nprim=%d (supported: l <= 2)", s, l, basis->nprim[s]);
+        if (l < 0 || l > 2 || basis->nprim[s] <= 0 || basis->atom[s] < 0 || basis->atom[s] >= mol->natm) {
+          set_error("kldi_screen: shell %d has l=%d nprim=%d atom=%d (supported: l <= 2; %d atoms)", s, l,
+                    basis->nprim[s], basis->atom[s], mol->natm);
           return l > 2 ? KLDI_EUNSUPPORTED : KLDI_EINVAL;
         }
         poff[s + 1] = poff[s] + basis->nprim[s];
         foff[s + 1] = foff[s] + (l + 1) * (l + 2) / 2;
       }
+      for (int64_t k = 0; k < poff[ns0]; ++k)
+        if (!(basis->exps[k] > 0.0) || !std::isfinite(basis->exps[k]) || !std::isfinite(basis->coefs[k])) {
+          set_error("kldi_screen: primitive %lld has exponent %g, coefficient %g (exponents must be positive, "
+                    "both finite)", (long long)k, basis->exps[k], basis->coefs[k]);
+          return KLDI_EINVAL;
+        }
       std::vector<int> order(ns0);
       for (int k = 0; k < ns0; ++k) {
         const int s = opt->shell_order ? opt->shell_order[k] : k;
