@@ -69,6 +69,48 @@ def test_becke_partition_of_unity():
     assert np.allclose(tot, 1.0, atol=1e-14)
 
 
+def test_becke_cell_function_closed_forms():
+    """Becke's cell function (J. Chem. Phys. 88, 2547 (1988)): s = (1 - f_3) / 2,
+    f_k the k-th iterate of p(mu) = 3 mu / 2 - mu^3 / 2.  Fixed values s(-1) = 1,
+    s(0) = 1/2, s(1) = 0 and s(mu) + s(-mu) = 1.  Near mu = 1, p(1 - e) =
+    1 - (3/2) e^2 (1 - e/3), so each iterate squares the distance from 1 and
+    scales it by 3/2: 1 - f_3(1 - e) = (3/2)^7 e^8 (1 - 4e/3 + O(e^2)).  The e^8
+    fixes three iterations (two give e^4, four e^16), the constant the
+    polynomial's coefficients."""
+    s = og.becke_s
+    assert s(np.array(-1.0)) == 1.0 and s(np.array(0.0)) == 0.5 and s(np.array(1.0)) == 0.0
+    mu = np.linspace(-1.0, 1.0, 41)
+    assert np.abs(s(mu) + s(-mu) - 1.0).max() < 1e-15
+    assert np.all(np.diff(s(mu)) < 0)
+    for e in (0.05, 0.02):        # smaller e loses 1 - f_3 to cancellation in FP64
+        r = s(np.array(1.0 - e)) / (0.5 * 1.5 ** 7 * e ** 8)
+        assert abs(r - (1.0 - 4.0 * e / 3.0)) < 3.0 * e * e, (e, r)
+    assert 200.0 < s(np.array(0.95)) / s(np.array(0.975)) < 300.0       # 2^8 (1 - 2e/3)
+
+
+def test_becke_weights_at_nuclei_and_on_bisecting_planes():
+    """At a nucleus the cell function of its own atom is 1 (mu = -1 against every
+    other atom) and every other cell vanishes (its factor for this atom has
+    mu = 1), so the own weight is exactly 1; on the plane bisecting two atoms of
+    a diatomic both weights are exactly 1/2.  A sign error in mu puts the
+    weight of a nucleus on the other atoms."""
+    rng = np.random.default_rng(7)
+    xyz = rng.normal(scale=2.0, size=(5, 3))
+    for a in range(5):
+        own = og.becke_weights(xyz[a:a + 1], np.array([a]), xyz)
+        assert own[0] == 1.0
+        for b in range(5):
+            if b != a:
+                assert og.becke_weights(xyz[a:a + 1], np.array([b]), xyz)[0] == 0.0
+    two = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 2.0]])
+    plane = np.array([[0.3, -0.7, 1.0], [1.5, 2.0, 1.0], [-4.0, 0.25, 1.0]])
+    assert np.all(og.becke_weights(plane, np.zeros(3, int), two) == 0.5)
+    near = np.array([[0.0, 0.0, 0.5], [0.2, 0.1, 0.3]])
+    wa = og.becke_weights(near, np.zeros(2, int), two)
+    wb = og.becke_weights(near, np.ones(2, int), two)
+    assert np.all(wa > 0.9) and np.allclose(wa + wb, 1.0, atol=1e-15)
+
+
 def test_morton_bits_brute_force():
     rng = np.random.default_rng(7)
     q = rng.integers(0, 1 << 20, size=(200, 3))
