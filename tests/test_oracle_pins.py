@@ -34,6 +34,24 @@ def test_slater_exchange_single_s_gaussian(a, expected):
     assert abs(np.sum(g.weights * r.rho) - 2.0) < 1e-12
 
 
+def test_density_and_gradient_of_single_s_gaussian():
+    """A doubly occupied normalised s-Gaussian on the origin has
+    rho = 2 (2a/pi)^(3/2) exp(-2 a r^2) and grad rho = -4 a r rho: the oracle's
+    rho = Phi . (Phi D) and grad rho = 2 grad Phi . (Phi D) at the grid points."""
+    a = 0.8
+    s = single_gaussian_system(a, kind="pbe")
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    r = oe.evaluate(s, g, screened=False, want_v=False)
+    p = g.points[:g.nreal]
+    arg = 2.0 * a * np.sum(p * p, axis=1)
+    rho = 2.0 * (2.0 * a / math.pi) ** 1.5 * np.exp(-arg)
+    tol = 1e-14 + 1e-15 * arg               # exp's relative error grows with its argument
+    assert np.all(np.abs(r.rho[:g.nreal] - rho) <= tol * rho)
+    grad = -4.0 * a * p * rho[:, None]
+    bound = 2.0 * (tol * rho)[:, None] * (4.0 * a * np.abs(p) + 1e-300)
+    assert np.all(np.abs(r.grad[:g.nreal] - grad) <= bound)
+
+
 # ---------------------------------------------------------------- grid
 def test_radial_rule_gaussian_moments():
     r, w = og.treutler_radial(100)
@@ -354,6 +372,40 @@ def test_pw92_low_density_expansion():
     c = np.polynomial.polynomial.polyfit(u, ox.eps_pw92(u ** -2) * u ** -2, 5)
     assert abs(-c[0] - PW92_D0) < 1e-4
     assert abs(c[1] - PW92_D1) < 5e-4
+
+
+# PBE's published constants: the exchange enhancement is bounded by the local
+# Lieb-Oxford bound, F_x <= 1.804 (kappa = 0.804), and beta = 0.066725.
+PBE_FX_MAX = 1.804
+PBE_BETA = 0.066725
+
+
+def test_pbe_exchange_lieb_oxford_limit():
+    """F_x(s) rises monotonically to the Lieb-Oxford value 1.804 as s grows."""
+    s2 = np.geomspace(1e-6, 1e14, 60)
+    F = ox.pbe_exchange_factor(s2)
+    assert np.all(np.diff(F) > 0) and np.all(F < PBE_FX_MAX)
+    assert abs(F[-1] - PBE_FX_MAX) < 1e-12
+
+
+@pytest.mark.parametrize("s2", [0.25, 1.0, 4.0])
+def test_pbe_correlation_high_density_scaling(s2):
+    """Under uniform scaling to high density (r_s -> 0 at fixed s) PBE
+    correlation per particle stays finite: H cancels the c0 ln r_s of eps_PW92
+    because gamma = c0 = (1 - ln 2) / pi^2.  With t^2 = C s^2 / r_s,
+    C = (pi / 4)(9 pi / 4)^(1/3), and B t^2 -> y = (beta / gamma) e^(-c1 / gamma) C s^2,
+    the limit is -c1 + gamma ln((beta / gamma) C s^2 (1 + y) / (1 + y + y^2)),
+    c1 = 0.046644 (PW92).  A wrong gamma makes the energy drift as ln r_s or
+    vanish."""
+    g = (1.0 - math.log(2.0)) / math.pi ** 2
+    C = (math.pi / 4.0) * (9.0 * math.pi / 4.0) ** (1.0 / 3.0)
+    y = (PBE_BETA / g) * math.exp(-PW92_C1 / g) * C * s2
+    limit = -PW92_C1 + g * math.log((PBE_BETA / g) * C * s2 * (1.0 + y) / (1.0 + y + y * y))
+    for rs in (1e-6, 1e-8):
+        rho = 3.0 / (4.0 * math.pi * rs ** 3)
+        sigma = s2 * 4.0 * (3.0 * math.pi ** 2) ** (2.0 / 3.0) * rho ** (8.0 / 3.0)      # s^2 -> sigma
+        eps = ox.f_pbe_c(np.array([rho]), np.array([sigma]))[0] / rho
+        assert abs(eps - limit) < 2e-5, (rs, eps, limit)
 
 
 @pytest.mark.parametrize("rho", [1e-4, 1e-2, 1.0, 1e2, 1e4])
