@@ -171,6 +171,23 @@ def test_basis_unit_norm_and_gradient():
         assert np.allclose(fd, dphi[ax, :200], atol=2e-6, rtol=1e-6)
 
 
+def test_cartesian_component_order_and_norms():
+    """Functions of a shell in the documented order s | x y z | xx xy xz yy yz
+    zz: at a point r - A = (x, y, z) each d function is N_c x^i y^j z^k g(r), and
+    for one primitive N_xx / N_xy = 1 / sqrt(3) ((2i-1)!! ratio), so
+    chi_xy / chi_xx = sqrt(3) y / x and chi_xx / chi_yy = x^2 / y^2."""
+    bas = synth.Basis(np.array([0, 0, 0]), np.array([0, 1, 2]), np.array([1, 1, 1]), np.array([0.7, 0.7, 0.7]),
+                      np.array([1.0, 1.0, 1.0]))
+    sh = ob.build_shells(np.zeros((1, 3)), bas)
+    x, y, z = 0.3, -0.5, 0.8
+    phi, _ = ob.eval_basis(np.array([[x, y, z]]), sh)
+    s_, px, py, pz, dxx, dxy, dxz, dyy, dyz, dzz = phi[0]
+    assert np.allclose([px / s_, py / s_, pz / s_], np.array([x, y, z]) * math.sqrt(4 * 0.7), rtol=1e-13)
+    r3 = math.sqrt(3.0)
+    assert np.allclose([dxy / dxx, dxz / dxx, dyz / dxx], [r3 * y / x, r3 * z / x, r3 * y * z / (x * x)], rtol=1e-13)
+    assert np.allclose([dyy / dxx, dzz / dxx], [y * y / (x * x), z * z / (x * x)], rtol=1e-13)
+
+
 def test_overlap_two_independent_implementations_and_quadrature():
     s = synth.make_system(1)
     shells = ob.build_shells(s.xyz, s.basis)
@@ -303,6 +320,14 @@ def test_screened_limits(w1):
     # dropped pairs are bounded by t_d per element pair; the gap stays far below the bound
     assert abs(loose.E - dense.E) < 1e-4
     assert abs(loose.E - dense.E) > 0.0
+    # V is a symmetric matrix by definition; screening drops whole block pairs
+    # {p, q}, never one of the two mirror blocks (on these 20 grid blocks the
+    # V rule's ordered pairs (p, q) and (q, p) differ)
+    many = list(range(0, 180, 9))
+    d20 = oe.evaluate(s, g, sh, screened=False, blocks=many, xc_kind="pbe")
+    s20 = oe.evaluate(s, g, sh, screened=True, blocks=many, xc_kind="pbe", t_b=1e-6, t_d=1e-6)
+    assert not np.array_equal(s20.V, d20.V)
+    assert np.array_equal(s20.V, s20.V.T)
 
 
 # ---------------------------------------------------------------- screening
@@ -314,6 +339,30 @@ def test_parallel_addressing_against_nonzero():
         assert S == m.sum() and np.array_equal(I, np.nonzero(m)[0])
     S, I = osc.parallel_addressing(np.zeros(64, bool))
     assert S == 0 and I.size == 0
+
+
+def test_block_summaries_and_threshold_boundaries():
+    """Block summaries are maxima of absolute values (Eq. block_summary_A), and
+    the filters keep a block or pair whose value equals the threshold
+    (Eq. block_filter_A: b_p >= t_b; Eq. block_pair_filter: a b >= t_d)."""
+    D = np.zeros((64, 64))
+    D[:32, :32] = -0.5
+    D[3, 4] = 0.25
+    D[40, 7] = -3.0
+    dm = osc.d_block_max(D)
+    assert np.array_equal(dm, [[0.5, 0.0], [3.0, 0.0]])
+    M = np.zeros((128, 64))
+    M[17, 40] = -2.0
+    assert np.array_equal(osc.block_max_cols(M), [0.0, 2.0])
+    t = 0.125
+    assert np.array_equal(osc.retained(np.array([t, t / 2, 2 * t, 0.0]), t), [0, 2])
+    b = np.array([0.5, 0.25])
+    dmax = np.array([[0.5, 0.5], [0.5, 0.25]])
+    E1 = osc.executed_rho(np.array([0, 1]), b, dmax, 0.25, 0.0625)      # b_p d b_q: 0.125, 0.0625, 0.015625
+    assert E1.tolist() == [[True, True], [True, False]]
+    x = np.array([0.5, 0.25])
+    E2 = osc.executed_v(np.array([0, 1]), b, x, 0.25, 0.0625)           # b_p x_q: 0.25, 0.125, 0.125, 0.0625
+    assert E2.all()
 
 
 def test_executed_pairs_brute_force():
