@@ -40,6 +40,16 @@ def _d_block_max_signed(D, d=osc.D_BASIS):
     return np.array([[D[p * d:(p + 1) * d, q * d:(q + 1) * d].max() for q in range(nb)] for p in range(nb)])
 
 
+_evaluate = ox.evaluate
+
+
+def _evaluate_cutting_rho_min(kind, rho, sigma, rho_min=ox.RHO_MIN):
+    f, vr, vs = _evaluate(kind, rho, sigma, rho_min)
+    cut = np.asarray(rho) <= rho_min
+    f[cut] = vr[cut] = vs[cut] = 0.0
+    return f, vr, vs
+
+
 CART_SWAPPED = dict(ob.CART)
 CART_SWAPPED[2] = [(2, 0, 0), (1, 0, 1), (1, 1, 0), (0, 2, 0), (0, 1, 1), (0, 0, 2)]
 
@@ -62,6 +72,7 @@ CASES = [
      lambda: pins.test_block_summaries_and_threshold_boundaries()),
     ("retained with b > t_b", osc, "retained", lambda b, t: np.nonzero(b > t)[0],
      lambda: pins.test_block_summaries_and_threshold_boundaries()),
+    ("rho_min itself cut", ox, "evaluate", _evaluate_cutting_rho_min, lambda: pins.test_rho_min_cut_is_strict()),
 ]
 
 

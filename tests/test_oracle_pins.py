@@ -240,6 +240,15 @@ def test_xc_derivatives_central_difference():
     assert np.allclose(vr, -(3 / math.pi) ** (1 / 3) * rho ** (1 / 3), rtol=1e-14)
 
 
+def test_rho_min_cut_is_strict():
+    """Points with rho < rho_min contribute nothing; rho = rho_min itself counts."""
+    rho = np.array([ox.RHO_MIN, ox.RHO_MIN * (1.0 - 1e-15), 0.0])
+    for kind, sigma in (("lda_x", None), ("pbe", np.full(3, 1e-40))):
+        f, vr, vs = ox.evaluate(kind, rho, sigma)
+        assert f[0] < 0.0 and vr[0] < 0.0
+        assert f[1] == 0.0 and vr[1] == 0.0 and vs[1] == 0.0 and f[2] == 0.0
+
+
 # ---------------------------------------------------------------- quadrature invariants
 @pytest.fixture(scope="module")
 def w1():
