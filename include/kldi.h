@@ -223,7 +223,8 @@ kldi_status kldi_plan_export_lists(const kldi_plan* plan, int32_t* blk_ptr, int3
 
 /* Density (Eq. r_equals_dphi then the row-dot of App. A): rho[npoints] and,
  * for a GGA plan, grad[npoints*3] (may be NULL for LDA).  D is nbf x nbf,
- * symmetric (only its values are used as given; no symmetrisation). */
+ * symmetric (only its values are used as given; no symmetrisation).  rho and
+ * grad are both device or both host memory, else KLDI_EINVAL before any work. */
 kldi_status kldi_density(kldi_plan* plan, const double* D, double* rho, double* grad);
 
 /* Potential from a given density: E_xc (one double) and V[nbf*nbf]

@@ -162,13 +162,18 @@ extern "C" kldi_status kldi_density(kldi_plan* P, const double* D, double* rho, 
   return kldi::guarded("kldi_density", [&]() -> kldi_status {
     if (!P || !D || !rho) { set_error("kldi_density: null argument"); return KLDI_EINVAL; }
     if (P->gga && !grad) { set_error("kldi_density: a GGA plan needs grad"); return KLDI_EINVAL; }
+    const bool host_out = !is_device_ptr(rho);
+    if (P->gga && is_device_ptr(grad) == host_out) {
+      // checked before any work: the kernels write rho and grad where they point
+      set_error("kldi_density: rho and grad must both be device or both host memory");
+      return KLDI_EINVAL;
+    }
     const size_t nbf2 = (size_t)P->nbf * P->nbf;
     const double* dD = D;
     if (!is_device_ptr(D)) {
       KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
       dD = P->d_D;
     }
-    const bool host_out = !is_device_ptr(rho);
     double* drho = host_out ? P->d_rho : rho;
     double* dgrad = P->gga ? (host_out ? P->d_grad : grad) : P->d_grad;
     KLDI_TRY(ensure_tile_buffers(P, P->prec));
@@ -180,9 +185,6 @@ extern "C" kldi_status kldi_density(kldi_plan* P, const double* D, double* rho, 
       if (P->gga) KLDI_TRY_CUDA(cudaMemcpyAsync(grad, dgrad, P->npoints * 24, cudaMemcpyDeviceToHost, P->stream));
       KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
       KLDI_TRY(check_device_error(P));
-    } else if (P->gga && !is_device_ptr(grad)) {
-      set_error("kldi_density: rho and grad must both be device or both host memory");
-      return KLDI_EINVAL;
     }
     KLDI_TRY_CUDA(cudaGetLastError());
     return KLDI_OK;
