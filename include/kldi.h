@@ -247,9 +247,9 @@ kldi_status kldi_exc_batched(kldi_plan* const* plans, int nframes, int xc, const
  *   dE/dR_A = -2 sum_{mu on A} sum_i [grad chi_mu Q_mu,i + (b_i . grad grad chi_mu) R_mu,i],
  *   R = Phi D, Q = Z D over the executed pairs E1_g,
  *   Z = w v_rho chi + 2 w v_sigma grad rho . grad chi, b = 2 w v_sigma grad rho.
- * G[natm*3] (row-major per atom, bohr, Hartree/bohr) and Exc[1]: host or device
- * (both the same kind).  D as in kldi_exc.  FP64 plans use the FP64 block form;
- * BF16X3 / BF16X6 plans run R and Q through the tensor-core density product
+ * G[natm*3] (row-major per atom, bohr, Hartree/bohr) and Exc[1]: each host or
+ * device memory.  D as in kldi_exc.  FP64 plans use the FP64 block form;
+ * BF16X3 / BF16X6 / BF16X10 plans run R and Q through the tensor-core density product
  * (Z sliced per point like Phi) and contract them with FP32 first and second
  * basis derivatives, one FP64 atomic per atom, component and warp (summation
  * order, hence the last bits, vary between calls).  KLDI_EUNSUPPORTED for a

@@ -271,12 +271,13 @@ extern "C" kldi_status kldi_exc_grad(kldi_plan* P, int xc, const double* D, doub
       KLDI_TRY_CUDA(cudaMemcpyAsync(P->d_D, D, nbf2 * 8, cudaMemcpyHostToDevice, P->stream));
       dD = P->d_D;
     }
-    const bool host_out = !is_device_ptr(G);
+    // G and Exc may be host or device memory independently of each other
+    const bool hostG = !is_device_ptr(G), hostE = !is_device_ptr(Exc);
     if (!P->d_G) {
       KLDI_TRY_CUDA(cudaMalloc(&P->d_G, sizeof(double) * 3 * std::max(P->natm, 1)));
     }
-    double* dG = host_out ? P->d_G : G;
-    double* dE = host_out ? P->d_exc : Exc;
+    double* dG = hostG ? P->d_G : G;
+    double* dE = hostE ? P->d_exc : Exc;
     KLDI_TRY(ensure_tile_buffers(P, P->prec));
     if (P->prec != KLDI_FP64 && !P->d_zscale) {
       KLDI_TRY_CUDA(cudaMalloc(&P->d_zscale, sizeof(float) * std::max<int64_t>(P->npoints, 1)));
@@ -298,9 +299,9 @@ extern "C" kldi_status kldi_exc_grad(kldi_plan* P, int xc, const double* D, doub
       }
     }
     KLDI_TRY(staged(P, KLDI_STAGE_FINISH, 1, [&] { return launch_finish(P, nullptr, dE, P->stream); }));
-    if (host_out) {
-      KLDI_TRY_CUDA(cudaMemcpyAsync(G, dG, sizeof(double) * 3 * P->natm, cudaMemcpyDeviceToHost, P->stream));
-      KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
+    if (hostG) KLDI_TRY_CUDA(cudaMemcpyAsync(G, dG, sizeof(double) * 3 * P->natm, cudaMemcpyDeviceToHost, P->stream));
+    if (hostE) KLDI_TRY_CUDA(cudaMemcpyAsync(Exc, dE, 8, cudaMemcpyDeviceToHost, P->stream));
+    if (hostG || hostE) {
       KLDI_TRY_CUDA(cudaStreamSynchronize(P->stream));
       KLDI_TRY(check_device_error(P));
     }
