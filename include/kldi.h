@@ -447,7 +447,8 @@ kldi_status kldi_mlp_train(kldi_mlp* mlp, const double* rho, const double* sigma
 
 /* Evaluate the surrogate (with its fallback) at n points: f, vrho, vsigma
  * (FP64) and used[n] (1 where the network was used, int32), all host or all
- * device (used may be NULL).  Synchronises for host outputs. */
+ * device (used may be NULL; a mix is KLDI_EINVAL before any work).
+ * Synchronises for host outputs. */
 kldi_status kldi_mlp_eval(const kldi_mlp* mlp, const double* rho, const double* sigma, int64_t n,
                           double rho_min, double* f, double* vrho, double* vsigma, int32_t* used);
 

@@ -693,11 +693,16 @@ extern "C" kldi_status kldi_mlp_eval(const kldi_mlp* M, const double* rho, const
       set_error("kldi_mlp_eval: null argument or n <= 0");
       return KLDI_EINVAL;
     }
+    const bool host_out = !is_device_ptr(f);
+    if (is_device_ptr(vrho) == host_out || is_device_ptr(vsigma) == host_out ||
+        (used && is_device_ptr(used) == host_out)) {
+      set_error("kldi_mlp_eval: f, vrho, vsigma and used must be all host or all device memory");
+      return KLDI_EINVAL;
+    }
     cudaStream_t s = nullptr;
     DevBuf<double> tmp;
     const double *drho, *dsig;
     KLDI_TRY(device_inputs(rho, sigma, n, tmp, drho, dsig, s));
-    const bool host_out = !is_device_ptr(f);
     DevBuf<double> out;
     DevBuf<int32_t> dused;
     double *df = f, *dvr = vrho, *dvs = vsigma;
