@@ -93,6 +93,11 @@ int main(int argc, char** argv) {
     printf("FAIL kldi_order_shells accepted a shell without functions\n");
     return 1;
   }
+  /* the three-atom grid with a one-atom molecule: refused before any device work */
+  const kldi_molecule one = {1, Z, xyz};
+  const kldi_options opt0 = {1e-12, 1e-12, 1e-14, KLDI_FP64, KLDI_XC_LDA_X, NULL, NULL};
+  kldi_plan* none_plan = NULL;
+  printf("mismatch %d\n", (int)kldi_screen(grid, &one, &basis, &opt0, &none_plan));
 
   if (gpu) {
     double D[49];

@@ -43,6 +43,7 @@ def test_c_program_host_calls(tmp_path):
     g = kldi.make_grid(Z, XYZ, 40, [6])
     assert [int(v) for v in out["grid"]] == [g.npoints, g.nreal, g.nblocks]
     assert out["reload"] == ["same", str(kldi.EIO)]
+    assert out["mismatch"] == [str(kldi.EINVAL)]
     for v in out["gauss"]:            # a Gaussian of integral pi^(3/2) on each atom
         assert abs(float(v) - math.pi ** 1.5) <= 1e-2
     S = np.eye(7)
