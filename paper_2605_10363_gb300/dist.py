@@ -49,16 +49,34 @@ def partition_blocks(weights, world: int):
     return [(int(bounds[r]), int(bounds[r + 1])) for r in range(world)]
 
 
-def reduce_exc(V, E, group=None):
-    """Sum the ranks' partial V and E in place (torch tensors; gloo for CPU
-    tensors, NCCL for CUDA tensors)."""
+def _sum_in_rank_order(t, group=None):
+    """Every rank's t gathered and added in rank order, ((t_0 + t_1) + t_2) + ...,
+    into t on every rank: the same bits on every rank and in every run, and the
+    bits of one process that adds the same partials in that order."""
     import torch.distributed as dist
+    parts = [t.new_empty(t.shape) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, t.contiguous(), group=group)
+    acc = parts[0].clone()
+    for p in parts[1:]:
+        acc += p
+    t.copy_(acc)
+    return t
+
+
+def reduce_exc(V, E, group=None, ordered=False):
+    """Sum the ranks' partial V and E in place (torch tensors; gloo for CPU
+    tensors, NCCL for CUDA tensors).  ordered: add the partials in rank order
+    (all-gather, world x the memory of V) so the result does not depend on the
+    collective's internal summation order."""
+    import torch.distributed as dist
+    if ordered:
+        return _sum_in_rank_order(V, group), _sum_in_rank_order(E, group)
     dist.all_reduce(V, op=dist.ReduceOp.SUM, group=group)
     dist.all_reduce(E, op=dist.ReduceOp.SUM, group=group)
     return V, E
 
 
-def exc_sharded(plan, xc, D, V, E, rank: int, world: int, group=None):
+def exc_sharded(plan, xc, D, V, E, rank: int, world: int, group=None, ordered=False):
     """This rank's share of kldi_exc followed by the reduction: the plan is
     restricted to the rank's block range (balanced by block_weights), V and E
     (device tensors) receive the full result on every rank."""
@@ -67,18 +85,21 @@ def exc_sharded(plan, xc, D, V, E, rank: int, world: int, group=None):
     g0, g1 = partition_blocks(block_weights(ptr), world)[rank]
     plan.set_block_range(g0, g1)
     kldi.exc(plan, xc, D, V, E)
-    return reduce_exc(V, E, group)
+    return reduce_exc(V, E, group, ordered)
 
 
-def reduce_grad(G, E, group=None):
-    """Sum the ranks' partial nuclear gradients (natm x 3) and E_xc in place."""
+def reduce_grad(G, E, group=None, ordered=False):
+    """Sum the ranks' partial nuclear gradients (natm x 3) and E_xc in place
+    (ordered: in rank order, as in reduce_exc)."""
     import torch.distributed as dist
+    if ordered:
+        return _sum_in_rank_order(G, group), _sum_in_rank_order(E, group)
     dist.all_reduce(G, op=dist.ReduceOp.SUM, group=group)
     dist.all_reduce(E, op=dist.ReduceOp.SUM, group=group)
     return G, E
 
 
-def exc_grad_sharded(plan, xc, D, G, E, rank: int, world: int, group=None):
+def exc_grad_sharded(plan, xc, D, G, E, rank: int, world: int, group=None, ordered=False):
     """This rank's share of kldi_exc_grad (its balanced block range) followed by
     the reduction: G and E (device tensors) receive the full result on every
     rank.  The gradient is a sum over grid blocks like E_xc, so the partials add."""
@@ -87,7 +108,7 @@ def exc_grad_sharded(plan, xc, D, G, E, rank: int, world: int, group=None):
     g0, g1 = partition_blocks(block_weights(ptr), world)[rank]
     plan.set_block_range(g0, g1)
     kldi.exc_grad(plan, xc, D, G, E)
-    return reduce_grad(G, E, group)
+    return reduce_grad(G, E, group, ordered)
 
 
 class BlockQueue:

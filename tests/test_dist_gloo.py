@@ -80,6 +80,50 @@ def test_two_ranks_reduce_to_the_single_process_result(tmp_path):
         assert np.abs(V - ref.V).max() <= 1e-13 * np.abs(ref.V).max()
 
 
+def _rank_ordered(rank, world, port, ranges, out_dir):
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        s = synth.make_system(1)
+        g = og.build_grid(s.Z, s.xyz, s.grid)
+        sh = ob.build_shells(s.xyz, s.basis)
+        g0, g1 = ranges[rank]
+        part = oe.evaluate(s, g, sh, screened=True, blocks=range(g0, g1), xc_kind="pbe")
+        V = torch.from_numpy(part.V.copy())
+        E = torch.tensor([part.E], dtype=torch.float64)
+        kdist.reduce_exc(V, E, ordered=True)
+        np.save(os.path.join(out_dir, f"V{rank}.npy"), V.numpy())
+        np.save(os.path.join(out_dir, f"E{rank}.npy"), E.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_ordered_reduction_is_bitwise_that_of_one_process(tmp_path):
+    """Three ranks with the ordered reduction: every rank holds the same bits,
+    and they are the bits of one process adding the same block-range partials
+    in rank order (the reduction order is fixed, not the collective's)."""
+    import torch.multiprocessing as mp
+    s = synth.make_system(1)
+    g = og.build_grid(s.Z, s.xyz, s.grid)
+    sh = ob.build_shells(s.xyz, s.basis)
+    n = g.nblocks
+    ranges = [(0, n // 4), (n // 4, (2 * n) // 3), ((2 * n) // 3, n)]
+    mp.start_processes(_rank_ordered, args=(3, _free_port(), ranges, str(tmp_path)), nprocs=3, join=True,
+                       start_method="spawn")
+    parts = [oe.evaluate(s, g, sh, screened=True, blocks=range(g0, g1), xc_kind="pbe") for g0, g1 in ranges]
+    V = parts[0].V.copy()
+    E = np.array([parts[0].E])
+    for p in parts[1:]:
+        V += p.V
+        E += p.E
+    for r in range(3):
+        assert np.array_equal(np.load(tmp_path / f"V{r}.npy"), V)
+        assert np.array_equal(np.load(tmp_path / f"E{r}.npy"), E)
+    ref = oe.evaluate(s, g, sh, screened=True, xc_kind="pbe")
+    assert np.abs(V - ref.V).max() <= 1e-13 * np.abs(ref.V).max()
+
+
 def _rank_grad(rank, world, port, ranges, out_dir):
     import torch
     import torch.distributed as dist
