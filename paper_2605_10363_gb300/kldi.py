@@ -203,6 +203,21 @@ def make_grid(Z, xyz, nrad, ntheta, block=128) -> Grid:
     return Grid(h.value)
 
 
+def load_mlp(path) -> "Mlp":
+    """A learned functional from a checkpoint written by Mlp.save."""
+    with np.load(path) as z:
+        if set(z.files) != {"state", "step", "box"}:
+            raise ValueError(f"{path}: not a learned-functional checkpoint")
+        state = np.asarray(z["state"], np.float32)
+        step = int(z["step"])
+        box = np.asarray(z["box"], np.float64)
+    if state.shape != (3 * MLP_NPARAMS,) or box.shape != (4,) or step < 0:
+        raise ValueError(f"{path}: not a learned-functional checkpoint")
+    net = Mlp(state[:MLP_NPARAMS], box)
+    net.set_state(state, step)
+    return net
+
+
 def load_grid(path) -> Grid:
     """A grid saved by Grid.save (kldi_grid_load)."""
     h = C.c_void_p()
@@ -401,6 +416,13 @@ class Mlp:
         s = np.ascontiguousarray(state, np.float32)
         assert s.size == 3 * MLP_NPARAMS
         _check(LIB.kldi_mlp_set_state(self.h, _ptr(s), int(step)))
+
+    def save(self, path):
+        """Training checkpoint file (.npz): parameters, Adam moments, step
+        counter and training box; load_mlp restores a network whose training
+        continues bit for bit."""
+        state, step = self.state()
+        np.savez(path, state=state, step=np.int64(step), box=self.box)
 
     def loss_grad(self, rho, sigma, rho_min=1e-14):
         rho = np.ascontiguousarray(rho, np.float64) if isinstance(rho, np.ndarray) else rho
